@@ -1,0 +1,429 @@
+"""Pins of the FP64 CPU oracle to facts fixed by the paper and by mathematics.
+
+Each test ties an oracle function to something other than itself: a value the
+paper prints, a closed form, an invariant, brute force over all states, or an
+independent composition from PyTorch library routines.  None of these needs a
+GPU and none reads the CUDA path.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.special
+import torch
+
+import oracle
+from paper_2606_22984_gb300 import inputs
+
+import _torch_ref
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def ocfg(m: inputs.ModelShape) -> oracle.ModelCfg:
+    return oracle.ModelCfg(**vars(m))
+
+
+def all_states(N):
+    """Every configuration of N spins, +-1, as int8 [2^N, N]."""
+    idx = np.arange(2 ** N)[:, None]
+    bits = (idx >> np.arange(N)[None, :]) & 1
+    return np.where(bits == 1, 1, -1).astype(np.int8)
+
+
+# --------------------------------------------------------------------------
+# Philox4x32-10 (parity unpinned: statistical pins only)
+# --------------------------------------------------------------------------
+
+def test_philox_uniform_definition_and_statistics():
+    seed = 12345
+    us = np.array([oracle.uniform(seed, b, t, 0) for b in range(64) for t in range(256)])
+    # u = ((x0 >> 8) + 0.5) 2^-24: a half-integer multiple of 2^-24 inside (0, 1)
+    k = us * 2 ** 24 - 0.5
+    assert np.all(k == np.round(k)) and k.min() >= 0 and k.max() < 2 ** 24
+    x0 = oracle.philox([3, 7, 0, 0], [seed & 0xFFFFFFFF, seed >> 32])[0]
+    assert oracle.uniform(seed, 3, 7, 0) == ((int(x0) >> 8) + 0.5) / 2 ** 24
+    # uniformity: chi^2 over 64 bins, mean, lag-1 correlation
+    counts, _ = np.histogram(us, bins=64, range=(0, 1))
+    chi2 = ((counts - len(us) / 64) ** 2 / (len(us) / 64)).sum()
+    assert scipy_chi2_sf(chi2, 63) > 1e-4
+    assert abs(us.mean() - 0.5) < 4 * math.sqrt(1 / 12 / len(us))
+    assert abs(np.corrcoef(us[:-1], us[1:])[0, 1]) < 4 / math.sqrt(len(us))
+
+
+def scipy_chi2_sf(x, dof):
+    import scipy.stats
+    return scipy.stats.chi2.sf(x, dof)
+
+
+def test_philox_avalanche():
+    """Flipping any single counter or key bit changes about half the 128 output bits."""
+    base_c, base_k = np.array([1, 2, 3, 4], np.uint32), np.array([5, 6], np.uint32)
+    ref = oracle.philox(base_c, base_k)
+    dists = []
+    for word in range(6):
+        for bit in range(32):
+            c, k = base_c.copy(), base_k.copy()
+            if word < 4:
+                c[word] ^= np.uint32(1 << bit)
+            else:
+                k[word - 4] ^= np.uint32(1 << bit)
+            out = oracle.philox(c, k)
+            dists.append(sum(bin(int(a) ^ int(b)).count("1") for a, b in zip(ref, out)))
+    dists = np.array(dists)
+    assert abs(dists.mean() - 64) < 2.0
+    assert dists.min() > 32
+
+
+# --------------------------------------------------------------------------
+# Model: special cases with closed forms
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("mask_kind", [0, 1])
+def test_zero_model_is_uniform(mask_kind):
+    m = inputs.ModelShape(17, 2, 16, 4, mask_kind=mask_kind, W=3, S=4)
+    w = np.zeros(inputs.param_count(m), np.float32)
+    spins, lq, pp, _ = oracle.sample(ocfg(m), w, 9, seed=77)
+    assert np.all(pp == 0.5)
+    assert np.allclose(lq, -m.N * math.log(2), atol=1e-12, rtol=0)
+    u = np.array([[oracle.uniform(77, b, t, 0) for t in range(m.N)] for b in range(9)])
+    assert np.array_equal(spins, np.where(u < 0.5, 1, -1))
+
+
+def test_head_bias_alone_sets_the_conditional():
+    """With every weight zero but the head bias, l_t = bh1 - bh0 for all t
+    (softmax over two logits, index 1 = spin +1)."""
+    m = inputs.ModelShape(11, 1, 8, 2)
+    w = np.zeros(inputs.param_count(m), np.float32)
+    o, _ = inputs.offsets(m)["bh"]
+    w[o], w[o + 1] = -0.3, 0.9
+    ell = 0.9 - (-0.3)
+    spins, lq, pp, _ = oracle.sample(ocfg(m), w.astype(np.float64), 40, seed=3)
+    p = 1 / (1 + math.exp(-ell))
+    assert np.allclose(pp, p, rtol=1e-7)
+    n_up = (spins == 1).sum(1)
+    expect = n_up * math.log(p) + (m.N - n_up) * math.log(1 - p)
+    assert np.allclose(lq, expect, rtol=1e-6)
+    u = np.array([[oracle.uniform(3, b, t, 0) for t in range(m.N)] for b in range(40)])
+    assert np.array_equal(spins, np.where(u < np.float32(p), 1, -1))
+
+
+# --------------------------------------------------------------------------
+# Model: independent composition from PyTorch library routines
+# --------------------------------------------------------------------------
+
+MODELS = [
+    inputs.ModelShape(12, 2, 16, 2),
+    inputs.ModelShape(13, 3, 16, 4, mask_kind=1, W=3, S=4),
+    inputs.ModelShape(16, 2, 24, 3, d_token=2, mask_kind=1, W=4, S=5),
+]
+
+
+@pytest.mark.parametrize("m", MODELS)
+def test_teacher_forced_logq_matches_torch_composition(m):
+    w = inputs.make_weights(m, 11, scale=1.5)
+    spins = inputs.random_spins(7, m.N, 5)
+    lq = oracle.logprob(ocfg(m), w, spins)
+    ref = _torch_ref.logq(m, torch.tensor(w, dtype=torch.float64), spins).numpy()
+    assert np.allclose(lq, ref, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("m", MODELS)
+def test_sampled_logq_equals_teacher_forced(m):
+    """Algorithm 2 (KV-cache decode) and Algorithm 1 (full sequence) give the
+    same log q and the same conditionals on the sampled configurations."""
+    w = inputs.make_weights(m, 12)
+    spins, lq, pp, _ = oracle.sample(ocfg(m), w, 16, seed=9)
+    lq_tf, pp_tf = oracle.logprob(ocfg(m), w, spins, with_pplus=True)
+    assert np.allclose(lq, lq_tf, rtol=1e-12, atol=1e-12)
+    assert np.allclose(pp, pp_tf, rtol=1e-12, atol=1e-13)
+    ref = _torch_ref.logq(m, torch.tensor(w, dtype=torch.float64), spins).numpy()
+    assert np.allclose(lq, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_band_at_least_N_is_dense():
+    dense = inputs.ModelShape(14, 2, 16, 2)
+    band = inputs.ModelShape(14, 2, 16, 2, mask_kind=1, W=13, S=0)
+    w = inputs.make_weights(dense, 3)
+    s = inputs.random_spins(5, 14, 1)
+    assert np.array_equal(oracle.logprob(ocfg(dense), w, s), oracle.logprob(ocfg(band), w, s))
+    narrow = inputs.ModelShape(14, 2, 16, 2, mask_kind=1, W=12, S=0)
+    assert not np.allclose(oracle.logprob(ocfg(dense), w, s), oracle.logprob(ocfg(narrow), w, s))
+
+
+def test_one_layer_receptive_field_is_band_plus_sink():
+    """SI Sec. I.A: A_tk = 0 for t - k > W.  With one layer, the conditional of
+    query t sees the token of spin j (key j+1) iff t-(j+1) <= W or j+1 < S."""
+    W, S, N, t = 3, 2, 12, 10
+    m = inputs.ModelShape(N, 1, 16, 2, mask_kind=1, W=W, S=S)
+    w = inputs.make_weights(m, 21, scale=2.0)
+    base = inputs.random_spins(1, N, 8)
+    _, p0 = oracle.logprob(ocfg(m), w, base, with_pplus=True)
+    for j in range(t):
+        s = base.copy()
+        s[0, j] *= -1
+        _, p1 = oracle.logprob(ocfg(m), w, s, with_pplus=True)
+        seen = (t - (j + 1) <= W) or (j + 1 < S)
+        if seen:
+            assert abs(p1[0, t] - p0[0, t]) > 1e-9, j
+        else:
+            assert p1[0, t] == p0[0, t], j
+
+
+# --------------------------------------------------------------------------
+# Enumeration: normalisation, exact Z, F <= F_q
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("m", [inputs.ModelShape(12, 2, 16, 2),
+                               inputs.ModelShape(12, 2, 16, 4, mask_kind=1, W=3, S=4)])
+def test_enumeration_normalisation_Z_and_variational_bound(m):
+    inst = inputs.make_sk(m.N, 4)
+    w = inputs.make_weights(m, 5)
+    beta = 1.3
+    ex = oracle.enumerate_exact(ocfg(m), w, inst, beta)
+    assert abs(ex["sum_q"] - 1.0) < 1e-12
+    states = all_states(m.N)
+    E = -0.5 * np.einsum("bi,ij,bj->b", states.astype(np.float64), inst.J.astype(np.float64),
+                         states.astype(np.float64))
+    lnZ = scipy.special.logsumexp(-beta * E)
+    assert abs(ex["lnZ"] - lnZ) < 1e-10 * abs(lnZ)
+    assert abs(ex["Emin"] - E.min()) < 1e-10
+    lq = oracle.logprob(ocfg(m), w, states)
+    q = np.exp(lq)
+    assert abs(q.sum() - 1.0) < 1e-12
+    Fq = (q * (beta * E + lq)).sum() / beta
+    assert abs(ex["Fq"] - Fq) < 1e-10 * abs(Fq)
+    # Eq. (KL_div): D_KL = beta (F_q - F) >= 0
+    assert ex["Fq"] >= ex["F"]
+    kl = (q * (lq - (-beta * E - lnZ))).sum()
+    assert abs(kl - beta * (ex["Fq"] - ex["F"])) < 1e-9
+
+
+def test_sk_annealed_partition_function_and_paper_value():
+    """E_J[Z] = 2^N exp(beta^2 (N-1)/4) for J_ij ~ N(0, 1/N), i<j, which pins the
+    coupling normalisation; its N -> inf free energy per spin,
+    -ln2/beta - beta/4, is the paper's printed F_inf at beta = 0.5."""
+    beta, F_printed, tol = np.loadtxt(os.path.join(HERE, "golden",
+                                                   "sk_paramagnetic_free_energy.txt"))
+    f_inf = -math.log(2) / beta - beta / 4
+    assert abs(f_inf - F_printed) < tol
+    N = 10
+    m = inputs.ModelShape(N, 1, 4, 1)
+    w = inputs.make_weights(m, 1)
+    Z = []
+    for seed in range(300):
+        ex = oracle.enumerate_exact(ocfg(m), w, inputs.make_sk(N, 1000 + seed), beta)
+        Z.append(math.exp(ex["lnZ"]))
+    Z = np.array(Z)
+    expect = 2 ** N * math.exp(beta ** 2 * (N - 1) / 4)
+    assert abs(Z.mean() - expect) < 4 * Z.std(ddof=1) / math.sqrt(len(Z))
+    # the wrong normalisation (J ~ N(0,1)) would give a far larger mean
+    wrong = 2 ** N * math.exp(beta ** 2 * N * (N - 1) / 4)
+    assert abs(Z.mean() - wrong) > 20 * Z.std(ddof=1) / math.sqrt(len(Z))
+
+
+# --------------------------------------------------------------------------
+# Energies
+# --------------------------------------------------------------------------
+
+def test_sk_energy_is_half_quadratic_form():
+    inst = inputs.make_sk(30, 2)
+    s = inputs.random_spins(50, 30, 3)
+    E = oracle.energy(inst, s)
+    ref = -0.5 * np.einsum("bi,ij,bj->b", s.astype(np.float64), inst.J.astype(np.float64),
+                           s.astype(np.float64))
+    assert np.allclose(E, ref, rtol=1e-12, atol=1e-12)
+    assert np.array_equal(E, oracle.energy(inst, -s))
+
+
+@pytest.mark.parametrize("D,L", [(2, 4), (2, 5), (3, 4)])
+def test_ea_ferromagnet_closed_forms(D, L):
+    inst = inputs.make_ferro(D, L)
+    N = L ** D
+    up = np.ones((1, N), np.int8)
+    assert oracle.energy(inst, up)[0] == -D * N
+    if L % 2 == 0:
+        coords = np.indices((L,) * D).reshape(D, -1)[::-1]  # x0 fastest
+        cb = np.where(coords.sum(0) % 2 == 0, 1, -1).astype(np.int8)[None]
+        assert oracle.energy(inst, cb)[0] == D * N
+    open_inst = inputs.make_ferro(D, L, periodic=False)
+    assert oracle.energy(open_inst, up)[0] == -D * L ** (D - 1) * (L - 1)
+
+
+def test_ea_pm_energies_are_integers_and_flip_invariant():
+    inst = inputs.make_ea(3, 5, 7, pm=True)
+    s = inputs.random_spins(40, inst.N, 2)
+    E = oracle.energy(inst, s)
+    assert np.all(E == np.round(E))
+    assert np.array_equal(E, oracle.energy(inst, -s))
+    # brute-force pair list: each nearest-neighbour pair once
+    L, D = inst.L, inst.D
+    coords = np.indices((L,) * D).reshape(D, -1)[::-1].T
+    ref = np.zeros(40)
+    for i, x in enumerate(coords):
+        for mu in range(D):
+            y = x.copy()
+            y[mu] = (y[mu] + 1) % L
+            j = int(sum(y[k] * L ** k for k in range(D)))
+            ref -= inst.J[i, mu] * s[:, i] * s[:, j]
+    assert np.array_equal(E, ref)
+
+
+# --------------------------------------------------------------------------
+# Free energies from a batch
+# --------------------------------------------------------------------------
+
+def test_importance_weighted_free_energy_is_exact_on_full_uniform_batch():
+    """With q uniform and every state in the batch once, F_IS = -ln Z / beta."""
+    N, beta = 12, 0.8
+    inst = inputs.make_sk(N, 9)
+    states = all_states(N)
+    E = oracle.energy(inst, states)
+    lq = np.full(len(states), -N * math.log(2))
+    Fq, Fis, ess = oracle.free_energy(E, lq, beta)
+    assert abs(Fis - (-scipy.special.logsumexp(-beta * E) / beta)) < 1e-12
+    assert abs(Fq - (beta * E + lq).mean() / beta) < 1e-12
+    # Kish ESS of equal weights is B
+    _, _, ess_eq = oracle.free_energy(np.zeros(100), np.zeros(100), beta)
+    assert abs(ess_eq - 100) < 1e-9
+
+
+def test_importance_weighted_free_energy_below_batch_fq():
+    m = inputs.ModelShape(10, 2, 16, 2)
+    w = inputs.make_weights(m, 2)
+    inst = inputs.make_sk(10, 2)
+    s, lq, _, _ = oracle.sample(ocfg(m), w, 500, seed=1)
+    E = oracle.energy(inst, s)
+    Fq, Fis, ess = oracle.free_energy(E, lq, 1.0)
+    assert Fis <= Fq  # Jensen
+    assert 1.0 <= ess <= 500
+
+
+# --------------------------------------------------------------------------
+# Backward: finite differences, autograd, exact enumerated gradient
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("m", [inputs.ModelShape(6, 2, 8, 2, d_ff=16),
+                               inputs.ModelShape(7, 2, 8, 2, d_ff=12, mask_kind=1, W=2, S=2)])
+def test_grad_matches_central_finite_differences(m):
+    w = inputs.make_weights(m, 4, scale=1.3).astype(np.float64)
+    s = inputs.random_spins(3, m.N, 6)
+    c = np.array([0.7, -1.1, 0.4])
+    g, _ = oracle.grad(ocfg(m), w, s, c)
+    h = 1e-6
+    fd = np.zeros_like(w)
+    for i in range(len(w)):
+        wp, wm = w.copy(), w.copy()
+        wp[i] += h
+        wm[i] -= h
+        fd[i] = (c @ oracle.logprob(ocfg(m), wp, s) - c @ oracle.logprob(ocfg(m), wm, s)) / (2 * h)
+    assert np.allclose(g, fd, rtol=1e-5, atol=1e-7)
+
+
+def test_grad_matches_torch_autograd():
+    m = inputs.ModelShape(10, 2, 16, 4, mask_kind=1, W=3, S=3)
+    w = inputs.make_weights(m, 8, scale=1.2)
+    s = inputs.random_spins(5, m.N, 2)
+    c = np.linspace(-1, 1, 5)
+    wt = torch.tensor(w, dtype=torch.float64, requires_grad=True)
+    (torch.tensor(c) * _torch_ref.logq(m, wt, s)).sum().backward()
+    g, _ = oracle.grad(ocfg(m), w, s, c)
+    assert np.allclose(g, wt.grad.numpy(), rtol=1e-10, atol=1e-12)
+
+
+def test_reinforce_estimate_matches_exact_enumerated_gradient():
+    """Eq. (loss1): (1/M) sum (L - Lbar) grad ln q estimates
+    beta grad F_q = sum_sigma q grad ln q (beta E + ln q)."""
+    N, beta = 8, 1.0
+    m = inputs.ModelShape(N, 1, 8, 2, d_ff=16)
+    w = inputs.make_weights(m, 3)
+    inst = inputs.make_sk(N, 3)
+    states = all_states(N)
+    lq = oracle.logprob(ocfg(m), w, states)
+    E = oracle.energy(inst, states)
+    exact, _ = oracle.grad(ocfg(m), w, states, np.exp(lq) * (beta * E + lq))
+    K, M = 16, 4000
+    ests = []
+    for k in range(K):
+        s, lqs, _, _ = oracle.sample(ocfg(m), w, M, seed=100 + k)
+        Lb = beta * oracle.energy(inst, s) + lqs
+        g, _ = oracle.grad(ocfg(m), w, s, (Lb - Lb.mean()) / M)
+        ests.append(g)
+    ests = np.array(ests)
+    mean, se = ests.mean(0), ests.std(0, ddof=1) / math.sqrt(K)
+    big = np.abs(exact) > 1e-8
+    z = np.abs(mean - exact)[big] / np.maximum(se[big], 1e-12)
+    assert np.mean(z < 4) > 0.98
+    assert np.linalg.norm(mean - exact) < 0.1 * np.linalg.norm(exact)
+
+
+# --------------------------------------------------------------------------
+# Markov chains: stationary distributions against exact Boltzmann weights
+# --------------------------------------------------------------------------
+
+def _level_tv(E_samples, E_states, beta):
+    """Total variation between the energy-level histogram of samples and the
+    Boltzmann law over all states (levels merged to 1e-9)."""
+    levels = np.unique(np.round(E_states, 9))
+    p = np.exp(-beta * E_states - scipy.special.logsumexp(-beta * E_states))
+    pl = np.array([p[np.round(E_states, 9) == v].sum() for v in levels])
+    el = np.array([(np.round(E_samples, 9) == v).mean() for v in levels])
+    return 0.5 * np.abs(pl - el).sum()
+
+
+def test_independence_mh_targets_boltzmann():
+    N, beta, C, per = 6, 1.0, 64, 1500
+    m = inputs.ModelShape(N, 1, 8, 2, d_ff=16)
+    w = inputs.make_weights(m, 6)
+    inst = inputs.make_sk(N, 6)
+    s, lq, _, _ = oracle.sample(ocfg(m), w, C * per, seed=5)
+    E = oracle.energy(inst, s)
+    s0, lq0, _, _ = oracle.sample(ocfg(m), w, C, seed=6)
+    cE, cL, ci, trace, acc, _ = oracle.mh(E, lq, C, beta, 99, oracle.energy(inst, s0), lq0)
+    E_states = oracle.energy(inst, all_states(N))
+    tv = _level_tv(trace[100:].ravel(), E_states, beta)
+    assert tv < 0.02
+    assert _level_tv(E, E_states, beta) > 2 * tv  # raw proposals are off target
+    # chain_idx points at the proposal whose energy the chain holds
+    moved = ci >= 0
+    assert np.array_equal(cE[moved], E[ci[moved]])
+
+
+@pytest.mark.parametrize("kind", ["sk", "ea"])
+def test_metropolis_targets_boltzmann(kind):
+    beta = 0.9
+    inst = inputs.make_sk(8, 2) if kind == "sk" else inputs.make_ea(2, 3, 5, pm=True)
+    s0 = inputs.random_spins(256, inst.N, 1)
+    _, _, trace, nflag = oracle.metropolis(inst, s0, 300, beta, 4)
+    assert nflag == 0
+    tv = _level_tv(trace[50:].ravel(), oracle.energy(inst, all_states(inst.N)), beta)
+    assert tv < 0.02
+
+
+@pytest.mark.parametrize("kind", ["sk", "ea"])
+def test_metropolis_tracked_energy_equals_recomputed(kind):
+    """dE = 2 s_i h_i must be the exact energy change of every single flip:
+    the energy tracked by summing dE equals the recomputed energy, and at
+    beta = 0 a sweep flips every spin (E(-s) = E(s))."""
+    inst = inputs.make_sk(12, 3) if kind == "sk" else inputs.make_ea(3, 3, 2, pm=True)
+    s0 = inputs.random_spins(20, inst.N, 4)
+    s1, E1, trace, _ = oracle.metropolis(inst, s0, 1, 0.0, 1)
+    assert np.array_equal(s1, -s0)
+    assert np.allclose(E1, oracle.energy(inst, s0), atol=1e-9)
+    s2, E2, _, _ = oracle.metropolis(inst, s0, 5, 0.7, 2)
+    assert np.allclose(E2, oracle.energy(inst, s2), atol=1e-9)
+
+
+def test_overlap_histogram():
+    s = inputs.random_spins(10, 16, 1)
+    same = np.repeat(s, 2, axis=0)
+    h = oracle.overlap_hist(same)
+    assert h[16] == 10 and h.sum() == 10
+    opp = np.stack([s, -s], 1).reshape(20, 16)
+    assert oracle.overlap_hist(opp)[0] == 10
+    pairs = inputs.random_spins(2000, 16, 2)
+    h = oracle.overlap_hist(pairs)
+    q = (np.arange(17) * 2 - 16) / 16
+    assert h.sum() == 1000 and abs((h * q).sum() / 1000) < 0.05
