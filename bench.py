@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""Throughput of the FlashVAN hot path on one GB300 (or N independent replicas).
+
+One step = one pass of the whole hot path over one batch of B configurations:
+ancestral sampling (KV-cache decode) -> energies -> FP64 free energies and
+REINFORCE weights -> teacher-forced log q + hand-written backward -> re-score of
+the MH chain states -> independence-MH step -> Adam update of the weights.
+value = configurations per second over the timed steps (all ranks).
+
+  python bench.py [--steps K] [--warmup W] [--workload ea2d16] [--impl ours|reference]
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on the
+host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "spin configs/sec sampled+scored, BF16 vs FP32 at fixed F/N error; ESS/sec"
+UNIT = "configs/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="ea2d16")
+    p.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+def decode_bytes_per_sample(m, elem_bytes):
+    """Algorithmic HBM bytes of the KV cache per sampled configuration: every
+    visible key and value read at every step and layer, plus each key and value
+    written once."""
+    t = np.arange(m.N)
+    if m.mask_kind == 0:
+        vis = t + 1
+    else:
+        sink = np.minimum(m.S, t + 1)
+        lo = np.maximum(m.S, t - m.W)
+        vis = sink + np.maximum(0, t - lo + 1)
+    per_key = 2 * m.d * elem_bytes * m.n_layers
+    return float(vis.sum() * per_key + m.N * per_key)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in getattr(self, "lines", []):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_info():
+    model = "unknown"
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return os.cpu_count() or 1, model
+
+
+def oracle_step_time(wl, n, beta, seed):
+    """The oracle's pass over n configurations: sample, energies, free
+    energies, gradient (teacher-forced forward + backward), MH."""
+    import oracle
+
+    m = wl.model
+    cfg = oracle.ModelCfg(**vars(m))
+    inst = wl.instance()
+    w = wl.weights()
+    t0 = time.perf_counter()
+    s, lq, _, _ = oracle.sample(cfg, w, n, seed)
+    E = oracle.energy(inst, s)
+    Fq, Fis, ess = oracle.free_energy(E, lq, beta)
+    L = beta * E + lq
+    oracle.grad(cfg, w, s, (L - L.mean()) / n)
+    C = max(1, n // 4)
+    oracle.mh(E[: (n // C) * C], lq[: (n // C) * C], C, beta, seed, E[:C], lq[:C])
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(wl, beta, budget_s):
+    import oracle
+
+    cores, model = cpu_info()
+    pilot_n = 4
+    tp = oracle_step_time(wl, pilot_n, beta, 1)
+    per = tp / pilot_n * max(1, min(cores, pilot_n))  # single-sample cost when parallel
+    n = int(max(pilot_n, min(4096, budget_s / max(per / cores, 1e-6))))
+    n = max(pilot_n, min(n, wl.B))
+    t = oracle_step_time(wl, n, beta, 2)
+    return {"value": n / t, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n} of the {wl.B} configurations of one step (same model, instance and "
+                      f"step: sample + energy + free energy + gradient + MH), FP64, "
+                      f"{oracle.num_threads()} threads on {model}; {t:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2606_22984_gb300 import inputs
+
+    wl = inputs.workloads()[args.workload]
+    beta = wl.betas[len(wl.betas) // 2]
+    cores, model = cpu_info()
+    base = cpu_baseline(wl, beta, args.cpu_seconds / max(1, args.steps + args.warmup) * 4)
+    n = int(base["sample"].split()[0])
+    for i in range(args.warmup):
+        oracle_step_time(wl, n, beta, 100 + i)
+    ts = [oracle_step_time(wl, n, beta, 200 + i) for i in range(args.steps)]
+    tot = sum(ts)
+    val = n * args.steps / tot
+    base["value"] = val
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "global_batch": n, "seq_len": wl.model.N,
+                       "parallelism": "cpu"},
+            "cpu_baseline": base,
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2606_22984_gb300 import build as _build
+    from paper_2606_22984_gb300 import inputs, sg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+    wl = inputs.workloads()[args.workload]
+    m, B = wl.model, wl.B
+    beta = wl.betas[len(wl.betas) // 2]
+    prec = {"auto": sg.SG_FP32, "fp32": sg.SG_FP32, "bf16": sg.SG_BF16}[args.precision]
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    def setup(precision):
+        model = sg.Model(m, wl.weights(), precision)
+        inst = sg.Instance(wl.instance())
+        bufs = dict(
+            spins=torch.empty((B, m.N), dtype=torch.int8, device=dev),
+            logq=torch.empty(B, dtype=torch.float32, device=dev),
+            E=torch.empty(B, dtype=torch.float32, device=dev),
+            Ei=torch.empty(B, dtype=torch.int32, device=dev) if wl.instance().pm else None,
+            F=torch.empty(3, dtype=torch.float64, device=dev),
+            coeff=torch.empty(B, dtype=torch.float32, device=dev),
+            grad=torch.empty(model.n_params, dtype=torch.float32, device=dev),
+            tf=torch.empty(B, dtype=torch.float32, device=dev),
+            m=torch.zeros(model.n_params, dtype=torch.float32, device=dev),
+            v=torch.zeros(model.n_params, dtype=torch.float32, device=dev))
+        C = 1024 if B % 1024 == 0 else 1
+        bufs["C"] = C
+        # MH chains start from the all-up configuration
+        bufs["cs"] = torch.ones((C, m.N), dtype=torch.int8, device=dev)
+        bufs["cE"] = inst.energy(bufs["cs"]).double()
+        bufs["clq"] = torch.zeros(C, dtype=torch.float64, device=dev)
+        bufs["clq32"] = torch.empty(C, dtype=torch.float32, device=dev)
+        bufs["acc"] = torch.empty(C, dtype=torch.int64, device=dev)
+        return model, inst, bufs
+
+    ev = []
+
+    def step(model, inst, bufs, i, timed):
+        seed = (rank << 32) + 1000 + i
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        model.sample(B, seed, spins=bufs["spins"], logq=bufs["logq"], stream=stream)
+        e1.record(stream)
+        if timed:
+            ev.append((e0, e1))
+        inst.energy(bufs["spins"], E=bufs["E"], E_int=bufs["Ei"], want_int=bufs["Ei"] is not None,
+                    stream=stream)
+        sg.free_energy(bufs["E"], bufs["logq"], beta, out=bufs["F"], coeff=bufs["coeff"],
+                       want_coeff=True, stream=stream)
+        model.grad(bufs["spins"], bufs["coeff"], grad=bufs["grad"], logq=bufs["tf"], stream=stream)
+        C = bufs["C"]
+        model.logprob(bufs["cs"], logq=bufs["clq32"], stream=stream)
+        bufs["clq"].copy_(bufs["clq32"])
+        sg.mh_step(bufs["spins"], bufs["E"], bufs["logq"], C, beta, seed, bufs["cs"], bufs["cE"],
+                   bufs["clq"], accepts=bufs["acc"], stream=stream)
+        sg.adam_step(model.weights(), bufs["grad"], bufs["m"], bufs["v"], 1e-3, i + 1,
+                     stream=stream)
+        model.refresh(stream)
+
+    def timed_run(precision, with_clocks):
+        model, inst, bufs = setup(precision)
+        for i in range(args.warmup):
+            step(model, inst, bufs, i, False)
+        torch.cuda.synchronize()
+        ev.clear()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        n0 = sg.launch_count()
+        sampler = ClockSampler(local)
+        with sampler:
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            for i in range(args.steps):
+                step(model, inst, bufs, args.warmup + i, True)
+            t1.record(stream)
+            torch.cuda.synchronize()
+        launches = sg.launch_count() - n0
+        ms = t0.elapsed_time(t1)
+        if world > 1:
+            x = torch.tensor([ms], device=dev)
+            dist.all_reduce(x, op=dist.ReduceOp.MAX)
+            ms = float(x.item())
+            dist.barrier()
+        dec_ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
+        return model, inst, bufs, ms, dec_ms, launches, sampler.summary()
+
+    model, inst, bufs, ms, dec_ms, launches, clocks = timed_run(prec, True)
+    ms_step = ms / args.steps
+    value = B * world * args.steps / (ms / 1e3)
+
+    # end to end through the public API with host buffers: each step copies a
+    # control block (seed, beta) host -> device and reads the sampled
+    # configurations, their log q, energies and the free energies back.
+    pin_in = torch.empty(2, dtype=torch.float64).pin_memory()
+    dev_in = torch.empty(2, dtype=torch.float64, device=dev)
+    h_spins = torch.empty((B, m.N), dtype=torch.int8).pin_memory()
+    h_lq = torch.empty(B, dtype=torch.float32).pin_memory()
+    h_E = torch.empty(B, dtype=torch.float32).pin_memory()
+    h_F = torch.empty(3, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        pin_in[0], pin_in[1] = 5000 + i, beta
+        dev_in.copy_(pin_in, non_blocking=True)
+        step(model, inst, bufs, 5000 + i, False)
+        h_spins.copy_(bufs["spins"], non_blocking=True)
+        h_lq.copy_(bufs["logq"], non_blocking=True)
+        h_E.copy_(bufs["E"], non_blocking=True)
+        h_F.copy_(bufs["F"], non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        x = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        e2e_s = float(x.item())
+    e2e = {"value": B * world * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16,
+           "d2h_bytes_per_step": int(B * m.N + 8 * B + 24)}
+
+    elem = 2 if prec == sg.SG_BF16 else 4
+    alg = decode_bytes_per_sample(m, elem) * B
+    peak, peak_kind = measured_peaks()
+    achieved = alg / (dec_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "decode",
+                "peak_kind": peak_kind, "algorithmic_bytes": alg,
+                "decode_ms": dec_ms, "decode_share_of_step": dec_ms / ms_step}
+    F = bufs["F"].cpu().numpy()
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if prec == sg.SG_FP32 else "bf16", "data": "synthetic",
+            "config": {"workload": wl.name, "global_batch": B * world, "seq_len": m.N,
+                       "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "beta": beta, "l2": "KV cache working set > L2 (129 MB) every step"},
+            "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
+            "free_energy_last_step": {"F_q_per_spin": F[0] / m.N, "F_IS_per_spin": F[1] / m.N,
+                                      "kish_ess": F[2]}}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, beta, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

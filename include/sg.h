@@ -1,0 +1,242 @@
+/*
+ * sg.h -- C ABI of libsg, the GB300 (sm_103a) implementation of the FlashVAN
+ * hot path (arXiv 2606.22984, "Scalable Physics-Inspired Transformers for
+ * Spin Glasses"): batched ancestral sampling from the autoregressive
+ * transformer, teacher-forced log q, Ising energies, variational and
+ * importance-weighted free energies, the REINFORCE gradient and neural
+ * Metropolis-Hastings.
+ *
+ * Conventions for every entry point
+ *   - Plain pointers and sizes only.  "dev" pointers are CUDA device memory
+ *     owned by the caller unless stated otherwise; "host" pointers are host
+ *     memory read during the call.
+ *   - sg_stream is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls that take a stream only enqueue work on it and return
+ *     without synchronising, unless stated otherwise.
+ *   - Spins are int8 with values -1 / +1, row-major [B][N] (sample-major).
+ *   - Every call returns an sg_status; on failure nothing is written to the
+ *     outputs that the caller can rely on and sg_last_error() describes the
+ *     cause (a per-thread string, valid until the next failing call).  No C++
+ *     exception crosses this boundary.
+ *   - Random numbers: the counter-based Philox4x32-10 generator (Salmon et
+ *     al., SC'11) keyed by the 64-bit seed; the uniform of counter
+ *     (a, b, stream, e) is ((x0 >> 8) + 0.5) * 2^-24.
+ *
+ * Weight blob (sg_param_count floats), row-major, linear maps "out x in":
+ *   tok[2][d_token]  pos[N][d - d_token]
+ *   per layer: ln1_g[d] ln1_b[d] Wqkv[3d][d] bqkv[3d] ln2_g[d] ln2_b[d]
+ *              W1[d_ff][d] b1[d_ff] W2[d][d_ff] b2[d]
+ *   lnf_g[d] lnf_b[d] Wh[2][d] bh[2]
+ * Rows of Wqkv: queries, keys, values, each head-major (head h owns
+ * columns h*d_h .. h*d_h + d_h - 1 of its block).
+ */
+#ifndef SG_H
+#define SG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef void *sg_stream;
+
+typedef enum {
+    SG_OK = 0,
+    SG_EINVAL = 1,       /* bad argument, shape or configuration            */
+    SG_ENOMEM = 2,       /* device or host allocation failed                */
+    SG_ECUDA = 3,        /* a CUDA runtime call or kernel launch failed     */
+    SG_ENUMERIC = 4,     /* NaN / Inf seen where a finite value is required */
+    SG_EUNSUPPORTED = 5  /* valid configuration this build does not serve   */
+} sg_status;
+
+typedef enum { SG_MASK_DENSE = 0, SG_MASK_BAND_SINK = 1 } sg_mask_kind;
+typedef enum { SG_FP32 = 0, SG_BF16 = 1 } sg_precision;
+typedef enum { SG_SK_DENSE = 0, SG_EA_LATTICE = 1 } sg_instance_kind;
+
+/*
+ * Model configuration (paper: "Overall architecture", Eq. concatePE,
+ * Algorithm 2, SI Sec. I.A; hyper-parameter names of the SI symbol table).
+ *   N          spins = sequence length.
+ *   n_layers   decoder layers (pre-LayerNorm attention and FFN sublayers,
+ *              Algorithm 2).
+ *   d          model width, d = d_token + d_pos (Eq. concatePE).
+ *   n_heads    heads; d_h = d / n_heads; no output projection W_O.
+ *   d_token    token-embedding width (2 in the paper).
+ *   d_ff       FFN hidden width (GELU).
+ *   mask_kind  SG_MASK_DENSE: causal.  SG_MASK_BAND_SINK: query t sees key k
+ *              iff k <= t and (t - k <= W or k < S) -- the sliding window
+ *              A_tk = 0 for t - k > W of SI Sec. I.A plus a sink of the first
+ *              S keys (start token and first lattice row / plane, reached by
+ *              the periodic wrap).
+ *   precision  SG_FP32: every step in FP32 on CUDA cores ("FP32 plain").
+ *              SG_BF16: GEMMs on tcgen05 tensor cores with BF16 operands and
+ *              FP32 accumulation, BF16 KV cache; LayerNorm, softmax, residual
+ *              stream and the draw stay FP32.
+ * Key position k holds the token of spin k-1; key 0 holds the start token 0.
+ */
+typedef struct {
+    int32_t N, n_layers, d, n_heads, d_token, d_ff;
+    int32_t mask_kind, W, S;
+    int32_t precision;
+} sg_config;
+
+typedef struct sg_model sg_model;
+typedef struct sg_instance sg_instance;
+
+/* Human-readable description of the last failure on this thread. */
+const char *sg_last_error(void);
+
+/* Number of CUDA kernels this library has launched in this process (host
+ * counter, all threads and devices); used to report launches per step. */
+int64_t sg_launch_count(void);
+
+/* Number of floats in the weight blob of cfg, or -1 if cfg is invalid. */
+int64_t sg_param_count(const sg_config *cfg);
+
+/*
+ * Create a model from a host weight blob of n_weights floats (layout above).
+ * The library copies the weights to the current device and owns them, plus
+ * the packed per-kernel layouts derived from them and the KV-cache
+ * workspace (grown on demand by sg_sample).  Errors: SG_EINVAL (cfg or
+ * n_weights), SG_EUNSUPPORTED, SG_ENOMEM, SG_ECUDA.  Synchronous.
+ */
+sg_status sg_model_create(const sg_config *cfg, const float *weights_host, int64_t n_weights,
+                          sg_model **out);
+
+/* Free every device buffer the model owns (synchronises the device). */
+sg_status sg_model_destroy(sg_model *m);
+
+/* Device pointer to the model's FP32 master weight blob (sg_param_count
+ * floats, layout above).  The caller may update it in place on a stream
+ * (e.g. with sg_adam_step) and must then call sg_model_refresh on that
+ * stream before the next sampling or scoring call. */
+float *sg_model_weights(sg_model *m);
+
+/* Re-derive the packed kernel layouts from the master blob, on stream. */
+sg_status sg_model_refresh(sg_model *m, sg_stream stream);
+
+/*
+ * Batched ancestral sampling (Algorithm 2, KV-cache decode) of B
+ * configurations in one persistent kernel launch.
+ *   spins  dev int8 [B][N]   out: sampled spins.
+ *   logq   dev float [B]     out: log q(sigma) = sum_t log sigmoid(sigma_t l_t).
+ *   flags  dev uint32 [B][(N+31)/32] or NULL   out: bit t set where the draw
+ *          was flagged, |p+ - u| < flag_band (flag_band <= 0 selects 1e-5 for
+ *          FP32 and 1e-2 for BF16).
+ * Sample b, step t uses u = uniform(seed, counter (b, t, stream_id, 0)) and
+ * takes sigma_t = +1 iff u < p+ = sigmoid(l_t), l_t = z1 - z0 of the output
+ * head.  beta is recorded only (sampling does not depend on it).
+ * Errors: SG_EINVAL (B < 1, B >= 2^32, NULL outputs), SG_ENOMEM, SG_ECUDA.
+ */
+sg_status sg_sample(sg_model *m, int64_t B, double beta, uint64_t seed, uint32_t stream_id,
+                    float flag_band, int8_t *spins, float *logq, uint32_t *flags,
+                    sg_stream stream);
+
+/*
+ * Teacher-forced log q (Algorithm 1) of B given configurations, computed over
+ * the whole sequence at once (prefill).
+ *   spins  dev int8 [B][N] in;  logq dev float [B] out.
+ * Errors: SG_EINVAL, SG_ENOMEM, SG_ECUDA.
+ */
+sg_status sg_logprob(sg_model *m, const int8_t *spins, int64_t B, float *logq, sg_stream stream);
+
+/*
+ * REINFORCE gradient (Eq. loss1): grad = sum_b coeff[b] * d log q(sigma_b)/d theta,
+ * with activations recomputed per chunk of samples.  With
+ * coeff[b] = (L_b - Lbar)/B, L = beta E + ln q, this is the paper's
+ * estimator of beta * grad F_q.
+ *   spins  dev int8 [B][N];  coeff dev float [B];
+ *   grad   dev float [sg_param_count] out (overwritten, blob layout);
+ *   logq   dev float [B] or NULL: out, the teacher-forced log q.
+ * Errors: SG_EINVAL, SG_ENOMEM, SG_ECUDA.
+ */
+sg_status sg_grad(sg_model *m, const int8_t *spins, const float *coeff, int64_t B, float *grad,
+                  float *logq, sg_stream stream);
+
+/*
+ * Problem instance (Eqs. SKHam, EAHam).  kind SG_SK_DENSE: J_host is the
+ * dense symmetric N x N float matrix with zero diagonal, E = -sum_{i<j} J_ij
+ * s_i s_j (the paper's 1/sqrt(N) folded into J).  kind SG_EA_LATTICE: N =
+ * L^D, J_host holds bonds[N][D], bonds[i][mu] coupling raster site
+ * i = x0 + L x1 + L^2 x2 to its +mu neighbour (periodic wrap, or no bond
+ * across the edge when periodic = 0); E = -sum_i sum_mu bonds[i][mu] s_i s_(i+mu).
+ * The library copies J to the device and owns it.  Synchronous.
+ */
+sg_status sg_instance_create(int32_t kind, int32_t N, int32_t D, int32_t L, int32_t periodic,
+                             const float *J_host, sg_instance **out);
+sg_status sg_instance_destroy(sg_instance *inst);
+
+/*
+ * Energies of B configurations.
+ *   E      dev float [B] out.
+ *   E_int  dev int32 [B] or NULL: exact integer energies, only for EA
+ *          instances whose bonds are all integers (else SG_EINVAL).
+ * precision SG_BF16 on an SK instance runs the s.J.s contraction on tcgen05
+ * tensor cores (J split into two BF16 terms, FP32 accumulation); SG_FP32
+ * uses CUDA cores.  EA is a coalesced neighbour gather either way.
+ */
+sg_status sg_energy(const sg_instance *inst, const int8_t *spins, int64_t B, int32_t precision,
+                    float *E, int32_t *E_int, sg_stream stream);
+
+/*
+ * Free energies from one batch (Eqs. KL_div, free_energy), reduced in FP64
+ * on the device:  L_b = beta E_b + ln q_b;
+ *   out[0] = F_q  = mean(L) / beta,
+ *   out[1] = F_IS = -(1/beta) [ln sum_b exp(-L_b) - ln B],
+ *   out[2] = Kish ESS = (sum w)^2 / sum w^2, w_b = exp(-L_b - max(-L)).
+ *   out    dev double [3].
+ *   coeff  dev float [B] or NULL: (L_b - mean L) / B, the REINFORCE weights.
+ */
+sg_status sg_free_energy(const float *E, const float *logq, int64_t B, double beta, double *out,
+                         float *coeff, sg_stream stream);
+
+/*
+ * Independence Metropolis-Hastings with the model as proposal (the paper's
+ * Monte Carlo + generative-model combination; not an algorithm it prints).
+ * Chain c (of C, B % C == 0) consumes proposals p = j*C + c, j = 0..B/C-1,
+ * in order: log alpha = (-beta E_p - ln q_p) - (-beta E_c - ln q_c) in
+ * FP64; accept iff ln u < log alpha, u = uniform(seed, (c, j, 1, 0)).
+ *   prop_spins dev int8 [B][N]; E, logq dev float [B];
+ *   chain_spins dev int8 [C][N], chain_E, chain_lq dev double [C]: in/out state;
+ *   accepts dev int64 [C] out (acceptances in this call);
+ *   trace_E dev float [B/C][C] or NULL: chain energy after each proposal.
+ */
+sg_status sg_mh_step(const int8_t *prop_spins, const float *E, const float *logq, int64_t B,
+                     int32_t N, int32_t C, double beta, uint64_t seed, int8_t *chain_spins,
+                     double *chain_E, double *chain_lq, int64_t *accepts, float *trace_E,
+                     sg_stream stream);
+
+/*
+ * Single-spin-flip Metropolis (the paper's local Monte Carlo refinement and
+ * the classical reference).  Replica r, sweep w visits sites i = 0..N-1 in
+ * order; dE = 2 s_i h_i; accept iff u < exp(-beta dE) in FP64,
+ * u = uniform(seed, (r, i, 2, w)).
+ *   spins dev int8 [R][N] in/out;  E dev double [R] in/out (energy of spins);
+ *   trace_E dev float [sweeps][R] or NULL: energy after each sweep.
+ */
+sg_status sg_metropolis(const sg_instance *inst, int8_t *spins, int64_t R, int32_t sweeps,
+                        double beta, uint64_t seed, double *E, float *trace_E, sg_stream stream);
+
+/*
+ * Overlap histogram (Eq. overlap_distribution): q = s1.s2 / N for pairs
+ * (2k, 2k+1); hist dev int64 [N+1] out, bin (N q + N)/2.
+ */
+sg_status sg_overlap_hist(const int8_t *spins, int64_t B, int32_t N, int64_t *hist,
+                          sg_stream stream);
+
+/*
+ * Adam update (the minimal optimiser of the training loop; the paper's Muon
+ * is a later addition): m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ * w -= lr * (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
+ * All arrays dev float [n]; step >= 1.
+ */
+sg_status sg_adam_step(float *w, const float *g, float *m, float *v, int64_t n, float lr,
+                       float beta1, float beta2, float eps, int64_t step, sg_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SG_H */

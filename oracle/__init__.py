@@ -87,8 +87,8 @@ def lib():
         L.or_philox.argtypes = [_P, _P, _P]
         L.or_uniform.argtypes = [_U64, _U32, _U32, _U32, _U32]
         L.or_uniform.restype = _D
-        L.or_sample.argtypes = [ctypes.POINTER(OrCfg), _P, _I64, _U64, _U32, _D, _P, _P, _P, _P,
-                                _P, _P, _I]
+        L.or_sample.argtypes = [ctypes.POINTER(OrCfg), _P, _I64, _P, _U64, _U32, _D, _P, _P, _P,
+                                _P, _P, _P, _I]
         L.or_logprob.argtypes = [ctypes.POINTER(OrCfg), _P, _I64, _P, _P, _P, _I]
         L.or_grad.argtypes = [ctypes.POINTER(OrCfg), _P, _I64, _P, _P, _P, _P, _I]
         L.or_energy_sk.argtypes = [_I, _P, _I64, _P, _P]
@@ -142,17 +142,23 @@ def num_threads() -> int:
 
 
 def sample(cfg: ModelCfg, weights, B, seed, stream=0, flag_band=1e-5, override_mask=None,
-           override_spins=None, n_threads=0):
-    """Ancestral sampling (Algorithm 2).  Returns spins, logq, pplus, flags."""
+           override_spins=None, n_threads=0, rows=None):
+    """Ancestral sampling (Algorithm 2).  Returns spins, logq, pplus, flags.
+    ``rows`` (optional) lists the sample index of each output row; then B is
+    its length."""
     w = _f64(weights)
     N = cfg.N
+    rid = None
+    if rows is not None:
+        rid = np.ascontiguousarray(rows, dtype=np.int64)
+        B = rid.shape[0]
     spins = np.zeros((B, N), np.int8)
     logq = np.zeros(B, np.float64)
     pplus = np.zeros((B, N), np.float64)
     flags = np.zeros((B, N), np.uint8)
     om = None if override_mask is None else np.ascontiguousarray(override_mask, dtype=np.uint8)
     os_ = None if override_spins is None else _i8(override_spins)
-    rc = lib().or_sample(ctypes.byref(cfg.c()), _ptr(w), B, seed, stream, flag_band, _ptr(om),
+    rc = lib().or_sample(ctypes.byref(cfg.c()), _ptr(w), B, _ptr(rid), seed, stream, flag_band, _ptr(om),
                          _ptr(os_), _ptr(spins), _ptr(logq), _ptr(pplus), _ptr(flags), n_threads)
     assert rc == 0
     return spins, logq, pplus, flags

@@ -300,10 +300,11 @@ static double decode_step(const or_cfg *c, const or_model *m, double *K, double 
 /* override_spins instead (the protocol that replays another                 */
 /* implementation's decision on a flagged draw).                             */
 /* Outputs (any may be NULL except spins/logq): spins int8 +-1 [B][N],       */
-/* logq [B], pplus [B][N], flags uint8 [B][N].                                */
+/* logq [B], pplus [B][N], flags uint8 [B][N].  row_ids (may be NULL) gives  */
+/* the sample index b used in the counter of output row i (default i).       */
 /* ------------------------------------------------------------------------ */
-int or_sample(const or_cfg *c, const double *weights, int64_t B, uint64_t seed, uint32_t stream,
-              double flag_band, const uint8_t *override_mask, const int8_t *override_spins,
+int or_sample(const or_cfg *c, const double *weights, int64_t B, const int64_t *row_ids,
+              uint64_t seed, uint32_t stream, double flag_band, const uint8_t *override_mask, const int8_t *override_spins,
               int8_t *spins, double *logq, double *pplus, uint8_t *flags, int n_threads)
 {
     or_model m;
@@ -330,7 +331,8 @@ int or_sample(const or_cfg *c, const double *weights, int64_t B, uint64_t seed, 
                 for (int t = 0; t < N; ++t) {
                     double l = decode_step(c, &m, K, V, t, tok, work);
                     double p = sigmoid(l);
-                    double u = or_uniform(seed, (uint32_t)b, (uint32_t)t, stream, 0);
+                    double u = or_uniform(seed, (uint32_t)(row_ids ? row_ids[b] : b), (uint32_t)t,
+                                          stream, 0);
                     int s = (u < p) ? 1 : -1;
                     int fl = fabs(p - u) < flag_band;
                     size_t bt = (size_t)b * N + t;

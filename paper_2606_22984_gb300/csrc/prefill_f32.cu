@@ -1,0 +1,873 @@
+// prefill_f32.cu -- teacher-forced log q (Algorithm 1 structure with the
+// pre-LayerNorm placement of Algorithm 2) over whole sequences, and the
+// hand-written backward of sum_b c_b log q(sigma_b) (REINFORCE, Eq. loss1).
+//
+// Rows r = b * N + t of a chunk of samples are processed layer by layer:
+//   embed -> [LN1 -> QKV GEMM -> masked attention (+residual) -> LN2 ->
+//   FFN1 GEMM (GELU) -> FFN2 GEMM (+residual)] x n_layers -> LN_f -> head.
+// For the gradient every layer's activations of the chunk are kept and the
+// backward runs in reverse; the chunk size bounds memory, so any B fits.
+// All arithmetic is FP32 on CUDA cores; weight gradients are reduced over rows
+// with per-block partial sums and atomics.
+#include <algorithm>
+#include <vector>
+
+#include "sg_internal.cuh"
+
+namespace sg {
+
+namespace {
+
+__device__ __forceinline__ float wsum(float v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// Embedding (Eq. concatePE): H[r] = [tok(s_{t-1}); pos(t)], start token 0.
+// ---------------------------------------------------------------------------
+__global__ void embed_kernel(const int8_t *__restrict__ spins, int64_t R, int N, int D, int dt,
+                             const float *__restrict__ tok, const float *__restrict__ pos,
+                             float *__restrict__ H)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= R * D) return;
+    const int64_t r = i / D;
+    const int j = (int)(i % D), t = (int)(r % N);
+    if (j < dt) {
+        const int tk = t == 0 ? 0 : (spins[r - 1] + 1) >> 1;
+        H[i] = tok[tk * dt + j];
+    } else {
+        H[i] = pos[(size_t)t * (D - dt) + (j - dt)];
+    }
+}
+
+__global__ void embed_bwd_kernel(const float *__restrict__ dH, const int8_t *__restrict__ spins,
+                                 int Bc, int N, int D, int dt, float *__restrict__ gtok,
+                                 float *__restrict__ gpos)
+{
+    // one thread per (t, j); loops over the samples of the chunk
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)N * D) return;
+    const int t = (int)(i / D), j = (int)(i % D);
+    if (j >= dt) {
+        float s = 0.f;
+        for (int b = 0; b < Bc; ++b) s += dH[((size_t)b * N + t) * D + j];
+        atomicAdd(gpos + (size_t)t * (D - dt) + (j - dt), s);
+    } else {
+        float s0 = 0.f, s1 = 0.f;
+        for (int b = 0; b < Bc; ++b) {
+            const size_t r = (size_t)b * N + t;
+            const float v = dH[r * D + j];
+            const int tk = t == 0 ? 0 : (spins[r - 1] + 1) >> 1;
+            if (tk) s1 += v; else s0 += v;
+        }
+        atomicAdd(gtok + j, s0);
+        atomicAdd(gtok + dt + j, s1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// LayerNorm forward / backward, one warp per row (eps 1e-5, biased variance).
+// ---------------------------------------------------------------------------
+__global__ void ln_fwd_kernel(const float *__restrict__ X, const float *__restrict__ g,
+                              const float *__restrict__ b, float *__restrict__ Y,
+                              float *__restrict__ mu, float *__restrict__ rs, int64_t R, int D)
+{
+    const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= R) return;
+    const float *x = X + r * D;
+    float s = 0.f;
+    for (int j = lane; j < D; j += 32) s += x[j];
+    const float mean = wsum(s) / D;
+    float q = 0.f;
+    for (int j = lane; j < D; j += 32) {
+        const float dv = x[j] - mean;
+        q += dv * dv;
+    }
+    const float r_s = 1.0f / sqrtf(wsum(q) / D + 1e-5f);
+    for (int j = lane; j < D; j += 32) Y[r * D + j] = (x[j] - mean) * r_s * g[j] + b[j];
+    if (lane == 0 && mu) {
+        mu[r] = mean;
+        rs[r] = r_s;
+    }
+}
+
+// dX (+)= d LN(X)/dX^T dY; dg += sum_r dY xhat; db += sum_r dY.  D <= 512.
+__global__ void ln_bwd_kernel(const float *__restrict__ dY, const float *__restrict__ X,
+                              const float *__restrict__ mu, const float *__restrict__ rs,
+                              const float *__restrict__ g, float *__restrict__ dX, int accumulate,
+                              float *__restrict__ dg, float *__restrict__ db, int64_t R, int D,
+                              int rows_per_block)
+{
+    extern __shared__ float red[];  // [2][D]
+    for (int j = threadIdx.x; j < 2 * D; j += blockDim.x) red[j] = 0.f;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+    float pg[16], pb[16];
+    for (int i = 0; i < 16; ++i) pg[i] = pb[i] = 0.f;
+    for (int64_t r = r0 + warp; r < R && r < r0 + rows_per_block; r += nw) {
+        const float m = mu[r], s = rs[r];
+        float m1 = 0.f, m2 = 0.f;
+        int i = 0;
+        for (int j = lane; j < D; j += 32, ++i) {
+            const float xh = (X[r * D + j] - m) * s, dy = dY[r * D + j];
+            const float dxh = dy * g[j];
+            m1 += dxh;
+            m2 += dxh * xh;
+            pg[i] += dy * xh;
+            pb[i] += dy;
+        }
+        m1 = wsum(m1) / D;
+        m2 = wsum(m2) / D;
+        for (int j = lane; j < D; j += 32) {
+            const float xh = (X[r * D + j] - m) * s;
+            const float v = s * (dY[r * D + j] * g[j] - m1 - xh * m2);
+            if (accumulate) dX[r * D + j] += v;
+            else dX[r * D + j] = v;
+        }
+    }
+    int i = 0;
+    for (int j = lane; j < D; j += 32, ++i) {
+        atomicAdd(red + j, pg[i]);
+        atomicAdd(red + D + j, pb[i]);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < D; j += blockDim.x) {
+        atomicAdd(dg + j, red[j]);
+        atomicAdd(db + j, red[D + j]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// GEMM C[M][N] = A[M][K] * B[K][N] (+bias) with a fused epilogue.  64x64 block
+// tile, 16-deep k tiles, 4x4 outputs per thread.  K, N, lda, ldb multiples of 4.
+// ---------------------------------------------------------------------------
+enum { G_STORE = 0, G_GELU = 1, G_ADDRES = 2, G_GELU_BWD = 3, G_GELU_ONLY = 4 };
+
+template <int EPI>
+__global__ void __launch_bounds__(256)
+gemm_nn_kernel(const float *__restrict__ A, int lda, const float *__restrict__ Bm, int ldb,
+               const float *__restrict__ bias, float *__restrict__ C, int ldc,
+               const float *__restrict__ aux, int ldaux, float *__restrict__ aux_out, int64_t M,
+               int N, int K)
+{
+    __shared__ float As[16][64 + 4];
+    __shared__ float Bs[16][64 + 4];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t m0 = (int64_t)blockIdx.y * 64;
+    const int n0 = blockIdx.x * 64;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        {   // A tile: 64 rows x 16 k, stored transposed
+            const int row = tid >> 2, kq = (tid & 3) * 4;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (m0 + row < M && k0 + kq < K)
+                v = *reinterpret_cast<const float4 *>(A + (m0 + row) * lda + k0 + kq);
+            As[kq + 0][row] = v.x;
+            As[kq + 1][row] = v.y;
+            As[kq + 2][row] = v.z;
+            As[kq + 3][row] = v.w;
+        }
+        {   // B tile: 16 k x 64 cols
+            const int kk = tid >> 4, col = (tid & 15) * 4;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (k0 + kk < K && n0 + col < N)
+                v = *reinterpret_cast<const float4 *>(Bm + (size_t)(k0 + kk) * ldb + n0 + col);
+            *reinterpret_cast<float4 *>(&Bs[kk][col]) = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const float4 a = *reinterpret_cast<const float4 *>(&As[k][ty * 4]);
+            const float4 b = *reinterpret_cast<const float4 *>(&Bs[k][tx * 4]);
+            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t r = m0 + ty * 4 + i;
+        if (r >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = n0 + tx * 4 + j;
+            if (c >= N) continue;
+            float v = acc[i][j] + (bias ? bias[c] : 0.f);
+            if (EPI == G_STORE) {
+                C[r * ldc + c] = v;
+            } else if (EPI == G_GELU) {
+                aux_out[r * ldaux + c] = v;
+                C[r * ldc + c] = gelu_f(v);
+            } else if (EPI == G_GELU_ONLY) {
+                C[r * ldc + c] = gelu_f(v);
+            } else if (EPI == G_ADDRES) {
+                C[r * ldc + c] = aux[r * ldaux + c] + v;
+            } else {  // G_GELU_BWD
+                C[r * ldc + c] = v * gelu_grad_f(aux[r * ldaux + c]);
+            }
+        }
+    }
+}
+
+// C[N1][N2] += sum_r A[r][i] * B[r][j] over rows [0, M): weight gradients.
+__global__ void __launch_bounds__(256)
+gemm_tn_acc_kernel(const float *__restrict__ A, int lda, const float *__restrict__ Bm, int ldb,
+                   float *__restrict__ C, int64_t M, int N1, int N2, int64_t rows_per_block)
+{
+    __shared__ float As[16][64 + 4];
+    __shared__ float Bs[16][64 + 4];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+    const int64_t rb = (int64_t)blockIdx.z * rows_per_block;
+    const int64_t re = rb + rows_per_block < M ? rb + rows_per_block : M;
+    float acc[4][4] = {};
+    for (int64_t r0 = rb; r0 < re; r0 += 16) {
+        for (int e = tid; e < 16 * 64; e += 256) {
+            const int rr = e >> 6, cc = e & 63;
+            const int64_t r = r0 + rr;
+            As[rr][cc] = (r < re && i0 + cc < N1) ? A[r * lda + i0 + cc] : 0.f;
+            Bs[rr][cc] = (r < re && j0 + cc < N2) ? Bm[r * ldb + j0 + cc] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const float4 a = *reinterpret_cast<const float4 *>(&As[k][ty * 4]);
+            const float4 b = *reinterpret_cast<const float4 *>(&Bs[k][tx * 4]);
+            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
+        }
+        __syncthreads();
+    }
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+            const int ii = i0 + ty * 4 + i, jj = j0 + tx * 4 + j;
+            if (ii < N1 && jj < N2) atomicAdd(C + (size_t)ii * N2 + jj, acc[i][j]);
+        }
+}
+
+// out[j] += sum_r A[r][j]
+__global__ void colsum_kernel(const float *__restrict__ A, int lda, int64_t M, int N,
+                              float *__restrict__ out, int64_t rows_per_block)
+{
+    __shared__ float red[8][33];
+    const int j = blockIdx.x * 32 + threadIdx.x;
+    const int64_t rb = (int64_t)blockIdx.y * rows_per_block;
+    const int64_t re = rb + rows_per_block < M ? rb + rows_per_block : M;
+    float s = 0.f;
+    if (j < N)
+        for (int64_t r = rb + threadIdx.y; r < re; r += 8) s += A[r * lda + j];
+    red[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y == 0 && j < N) {
+        float t = 0.f;
+        for (int y = 0; y < 8; ++y) t += red[y][threadIdx.x];
+        atomicAdd(out + j, t);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Masked attention over a whole sequence.  One warp per (sample, head, tile
+// of 32 queries); lane = query.  Keys are read as warp-uniform broadcasts.
+// QKV rows: [q | k | v], head-major inside each block of D.
+// Writes O (attention output), Hmid = Hin + O, and LSE per (row, head).
+// ---------------------------------------------------------------------------
+template <int DH>
+__global__ void attn_fwd_kernel(const float *__restrict__ QKV, const float *__restrict__ Hin,
+                                float *__restrict__ O, float *__restrict__ Hmid,
+                                float *__restrict__ LSE, int Bc, int N, int D, int NH, int mask,
+                                int W, int S)
+{
+    const int warp_g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const int ntile = (N + 31) >> 5;
+    if (warp_g >= Bc * NH * ntile) return;
+    const int tile = warp_g % ntile, hh = (warp_g / ntile) % NH, b = warp_g / (ntile * NH);
+    const int t = tile * 32 + lane;
+    const bool active = t < N;
+    const int tq = active ? t : N - 1;
+    const size_t rq = (size_t)b * N + tq;
+    const float scale = rsqrtf((float)DH);
+    float q[DH], acc[DH];
+#pragma unroll
+    for (int j = 0; j < DH; ++j) {
+        q[j] = QKV[rq * 3 * D + hh * DH + j] * scale;
+        acc[j] = 0.f;
+    }
+    float mx = -INFINITY, den = 0.f;
+    const int t_first = tile * 32, t_last = min(N - 1, tile * 32 + 31);
+    // union of visible keys of the tile: [0, min(S, t_last+1)) U [max(S, t_first-W), t_last]
+    int ns, blo_first, ns2, blo2;
+    visible_ranges(mask, W, S, t_last, ns, blo2);
+    visible_ranges(mask, W, S, t_first, ns2, blo_first);
+    if (mask == SG_MASK_DENSE) { ns = 0; blo_first = 0; }
+    const int nk = ns + band_count(t_last, blo_first);
+    for (int i = 0; i < nk; ++i) {
+        const int k = i < ns ? i : blo_first + (i - ns);
+        if (i >= ns && k < ns) continue;  // already covered by the sink part
+        const float *kp = QKV + ((size_t)b * N + k) * 3 * D + D + hh * DH;
+        float sc = 0.f;
+#pragma unroll
+        for (int j = 0; j < DH; ++j) sc += q[j] * kp[j];
+        if (!key_visible(mask, W, S, tq, k)) continue;
+        const float mn = fmaxf(mx, sc);
+        const float corr = expf(mx - mn), p = expf(sc - mn);
+        mx = mn;
+        den = den * corr + p;
+        const float *vp = kp + D;
+#pragma unroll
+        for (int j = 0; j < DH; ++j) acc[j] = acc[j] * corr + p * vp[j];
+    }
+    if (!active) return;
+    const float inv = 1.0f / den;
+#pragma unroll
+    for (int j = 0; j < DH; ++j) {
+        const size_t idx = rq * D + hh * DH + j;
+        const float o = acc[j] * inv;
+        O[idx] = o;
+        Hmid[idx] = Hin[idx] + o;
+    }
+    LSE[rq * NH + hh] = mx + logf(den);
+}
+
+// dQ and Dt = dO . O per (row, head); lane = query.
+template <int DH>
+__global__ void attn_bwd_q_kernel(const float *__restrict__ QKV, const float *__restrict__ O,
+                                  const float *__restrict__ dO, const float *__restrict__ LSE,
+                                  float *__restrict__ dQKV, float *__restrict__ Dt, int Bc, int N,
+                                  int D, int NH, int mask, int W, int S)
+{
+    const int warp_g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const int ntile = (N + 31) >> 5;
+    if (warp_g >= Bc * NH * ntile) return;
+    const int tile = warp_g % ntile, hh = (warp_g / ntile) % NH, b = warp_g / (ntile * NH);
+    const int t = tile * 32 + lane;
+    const bool active = t < N;
+    const int tq = active ? t : N - 1;
+    const size_t rq = (size_t)b * N + tq;
+    const float scale = rsqrtf((float)DH);
+    float q[DH], dq[DH], go[DH];
+    float dd = 0.f;
+#pragma unroll
+    for (int j = 0; j < DH; ++j) {
+        q[j] = QKV[rq * 3 * D + hh * DH + j] * scale;
+        go[j] = dO[rq * D + hh * DH + j];
+        dd += go[j] * O[rq * D + hh * DH + j];
+        dq[j] = 0.f;
+    }
+    const float lse = LSE[rq * NH + hh];
+    const int t_first = tile * 32, t_last = min(N - 1, tile * 32 + 31);
+    int ns, blo_first, ns2, blo2;
+    visible_ranges(mask, W, S, t_last, ns, blo2);
+    visible_ranges(mask, W, S, t_first, ns2, blo_first);
+    if (mask == SG_MASK_DENSE) { ns = 0; blo_first = 0; }
+    const int nk = ns + band_count(t_last, blo_first);
+    for (int i = 0; i < nk; ++i) {
+        const int k = i < ns ? i : blo_first + (i - ns);
+        if (i >= ns && k < ns) continue;
+        const float *kp = QKV + ((size_t)b * N + k) * 3 * D + D + hh * DH;
+        const float *vp = kp + D;
+        float sc = 0.f, dp = 0.f;
+#pragma unroll
+        for (int j = 0; j < DH; ++j) {
+            sc += q[j] * kp[j];
+            dp += go[j] * vp[j];
+        }
+        if (!key_visible(mask, W, S, tq, k)) continue;
+        const float ds = expf(sc - lse) * (dp - dd) * scale;
+#pragma unroll
+        for (int j = 0; j < DH; ++j) dq[j] += ds * kp[j];
+    }
+    if (!active) return;
+#pragma unroll
+    for (int j = 0; j < DH; ++j) dQKV[rq * 3 * D + hh * DH + j] = dq[j];
+    Dt[rq * NH + hh] = dd;
+}
+
+// dK, dV per (row, head); lane = key; loops over the queries that see the key.
+template <int DH>
+__global__ void attn_bwd_kv_kernel(const float *__restrict__ QKV, const float *__restrict__ dO,
+                                   const float *__restrict__ LSE, const float *__restrict__ Dt,
+                                   float *__restrict__ dQKV, int Bc, int N, int D, int NH,
+                                   int mask, int W, int S)
+{
+    const int warp_g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const int ntile = (N + 31) >> 5;
+    if (warp_g >= Bc * NH * ntile) return;
+    const int tile = warp_g % ntile, hh = (warp_g / ntile) % NH, b = warp_g / (ntile * NH);
+    const int k = tile * 32 + lane;
+    const bool active = k < N;
+    const int kk = active ? k : N - 1;
+    const size_t rk = (size_t)b * N + kk;
+    const float scale = rsqrtf((float)DH);
+    float key[DH], val[DH], dk[DH], dv[DH];
+#pragma unroll
+    for (int j = 0; j < DH; ++j) {
+        key[j] = QKV[rk * 3 * D + D + hh * DH + j];
+        val[j] = QKV[rk * 3 * D + 2 * D + hh * DH + j];
+        dk[j] = dv[j] = 0.f;
+    }
+    const int k_first = tile * 32, k_last = min(N - 1, tile * 32 + 31);
+    // queries that see some key of the tile: t in [k_first, t_hi]
+    int t_hi = N - 1;
+    if (mask == SG_MASK_BAND_SINK && k_first >= S) t_hi = min(N - 1, k_last + W);
+    for (int t = k_first; t <= t_hi; ++t) {
+        const size_t rq = (size_t)b * N + t;
+        const float *qp = QKV + rq * 3 * D + hh * DH;
+        const float *gp = dO + rq * D + hh * DH;
+        float sc = 0.f, dp = 0.f;
+#pragma unroll
+        for (int j = 0; j < DH; ++j) {
+            sc += qp[j] * key[j];
+            dp += gp[j] * val[j];
+        }
+        if (!key_visible(mask, W, S, t, kk)) continue;
+        const float p = expf(sc * scale - LSE[rq * NH + hh]);
+        const float ds = p * (dp - Dt[rq * NH + hh]) * scale;
+#pragma unroll
+        for (int j = 0; j < DH; ++j) {
+            dk[j] += ds * qp[j];
+            dv[j] += p * gp[j];
+        }
+    }
+    if (!active) return;
+#pragma unroll
+    for (int j = 0; j < DH; ++j) {
+        dQKV[rk * 3 * D + D + hh * DH + j] = dk[j];
+        dQKV[rk * 3 * D + 2 * D + hh * DH + j] = dv[j];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Output head: LN_f -> z = Wh y + bh -> l = z1 - z0 -> lp = log sigmoid(s l).
+// ---------------------------------------------------------------------------
+__global__ void head_fwd_kernel(const float *__restrict__ H, const float *__restrict__ g,
+                                const float *__restrict__ bb, const float *__restrict__ Wh,
+                                const float *__restrict__ bh, const int8_t *__restrict__ spins,
+                                float *__restrict__ Y, float *__restrict__ mu,
+                                float *__restrict__ rs, float *__restrict__ ell,
+                                float *__restrict__ lp, int64_t R, int D)
+{
+    const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= R) return;
+    const float *x = H + r * D;
+    float s = 0.f;
+    for (int j = lane; j < D; j += 32) s += x[j];
+    const float mean = wsum(s) / D;
+    float q = 0.f;
+    for (int j = lane; j < D; j += 32) {
+        const float dv = x[j] - mean;
+        q += dv * dv;
+    }
+    const float r_s = 1.0f / sqrtf(wsum(q) / D + 1e-5f);
+    float z0 = 0.f, z1 = 0.f;
+    for (int j = lane; j < D; j += 32) {
+        const float y = (x[j] - mean) * r_s * g[j] + bb[j];
+        if (Y) Y[r * D + j] = y;
+        z0 += y * Wh[j];
+        z1 += y * Wh[D + j];
+    }
+    z0 = wsum(z0) + bh[0];
+    z1 = wsum(z1) + bh[1];
+    if (lane == 0) {
+        const float l = z1 - z0;
+        if (ell) ell[r] = l;
+        if (mu) {
+            mu[r] = mean;
+            rs[r] = r_s;
+        }
+        lp[r] = log_sigmoid_f((float)spins[r] * l);
+    }
+}
+
+// dY of the head for row r, then LN_f backward into dH; head weight grads.
+// Per-warp register partial sums (D <= 512), one shared reduction per block.
+__global__ void head_bwd_kernel(const float *__restrict__ H, const float *__restrict__ mu,
+                                const float *__restrict__ rs, const float *__restrict__ Y,
+                                const float *__restrict__ ell, const int8_t *__restrict__ spins,
+                                const float *__restrict__ coeff, const float *__restrict__ g,
+                                const float *__restrict__ Wh, float *__restrict__ dH,
+                                float *__restrict__ gWh, float *__restrict__ gbh,
+                                float *__restrict__ glnfg, float *__restrict__ glnfb, int64_t R,
+                                int N, int D, int rows_per_block)
+{
+    extern __shared__ float red[];  // [4][D] + 2: Wh0, Wh1, lnf_g, lnf_b, bh
+    for (int j = threadIdx.x; j < 4 * D + 2; j += blockDim.x) red[j] = 0.f;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+    float pw0[16], pw1[16], pg[16], pb[16], pz0 = 0.f, pz1 = 0.f;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) pw0[i] = pw1[i] = pg[i] = pb[i] = 0.f;
+    for (int64_t r = r0 + warp; r < R && r < r0 + rows_per_block; r += nw) {
+        const float sg = (float)spins[r];
+        const float c = coeff[r / N];
+        const float dl = c * sg / (1.0f + expf(sg * ell[r]));  // c s sigmoid(-s l)
+        const float dz0 = -dl, dz1 = dl;
+        const float m = mu[r], s = rs[r];
+        float m1 = 0.f, m2 = 0.f;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int j = lane + 32 * i;
+            if (j >= D) break;
+            const float y = Y[r * D + j];
+            pw0[i] += dz0 * y;
+            pw1[i] += dz1 * y;
+            const float dy = dz0 * Wh[j] + dz1 * Wh[D + j];
+            const float xh = (H[r * D + j] - m) * s;
+            pg[i] += dy * xh;
+            pb[i] += dy;
+            const float dxh = dy * g[j];
+            m1 += dxh;
+            m2 += dxh * xh;
+        }
+        m1 = wsum(m1) / D;
+        m2 = wsum(m2) / D;
+        for (int j = lane; j < D; j += 32) {
+            const float dy = dz0 * Wh[j] + dz1 * Wh[D + j];
+            const float xh = (H[r * D + j] - m) * s;
+            dH[r * D + j] = s * (dy * g[j] - m1 - xh * m2);
+        }
+        pz0 += dz0;
+        pz1 += dz1;
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int j = lane + 32 * i;
+        if (j >= D) break;
+        atomicAdd(red + j, pw0[i]);
+        atomicAdd(red + D + j, pw1[i]);
+        atomicAdd(red + 2 * D + j, pg[i]);
+        atomicAdd(red + 3 * D + j, pb[i]);
+    }
+    if (lane == 0) {
+        atomicAdd(red + 4 * D, pz0);
+        atomicAdd(red + 4 * D + 1, pz1);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < D; j += blockDim.x) {
+        atomicAdd(gWh + j, red[j]);
+        atomicAdd(gWh + D + j, red[D + j]);
+        atomicAdd(glnfg + j, red[2 * D + j]);
+        atomicAdd(glnfb + j, red[3 * D + j]);
+    }
+    if (threadIdx.x < 2) atomicAdd(gbh + threadIdx.x, red[4 * D + threadIdx.x]);
+}
+
+// logq[b] = sum_t lp[b*N + t], fixed-order tree reduction per sample.
+__global__ void seg_sum_kernel(const float *__restrict__ lp, int N, float *__restrict__ logq)
+{
+    __shared__ float red[256];
+    const int b = blockIdx.x;
+    float s = 0.f;
+    for (int t = threadIdx.x; t < N; t += blockDim.x) s += lp[(size_t)b * N + t];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) logq[b] = red[0];
+}
+
+unsigned blocks_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
+
+// ---------------------------------------------------------------------------
+// Host-side orchestration.
+// ---------------------------------------------------------------------------
+struct LayerBufs {
+    float *Hin, *mu1, *rs1, *A1, *QKV, *O, *LSE, *Hmid, *mu2, *rs2, *A2, *F1, *G;
+};
+
+struct Plan {
+    int64_t Bc;       // samples per chunk
+    int64_t R;        // rows per chunk
+    bool keep;        // keep every layer (backward) or reuse one set
+};
+
+template <int DH>
+void attn_fwd(const float *QKV, const float *Hin, float *O, float *Hmid, float *LSE, int Bc,
+              const sg_config &c, cudaStream_t st)
+{
+    const int warps = Bc * c.n_heads * ((c.N + 31) / 32);
+    attn_fwd_kernel<DH><<<blocks_for(warps, 8), 256, 0, ::sg::counted(st)>>>(
+        QKV, Hin, O, Hmid, LSE, Bc, c.N, c.d, c.n_heads, c.mask_kind, c.W, c.S);
+}
+
+template <int DH>
+void attn_bwd(const float *QKV, const float *O, const float *dO, const float *LSE, float *dQKV,
+              float *Dt, int Bc, const sg_config &c, cudaStream_t st)
+{
+    const int warps = Bc * c.n_heads * ((c.N + 31) / 32);
+    attn_bwd_q_kernel<DH><<<blocks_for(warps, 8), 256, 0, ::sg::counted(st)>>>(
+        QKV, O, dO, LSE, dQKV, Dt, Bc, c.N, c.d, c.n_heads, c.mask_kind, c.W, c.S);
+    attn_bwd_kv_kernel<DH><<<blocks_for(warps, 8), 256, 0, ::sg::counted(st)>>>(
+        QKV, dO, LSE, Dt, dQKV, Bc, c.N, c.d, c.n_heads, c.mask_kind, c.W, c.S);
+}
+
+bool dh_supported(int dh) { return dh == 8 || dh == 16 || dh == 32; }
+
+void attn_fwd_dispatch(int dh, const float *QKV, const float *Hin, float *O, float *Hmid,
+                       float *LSE, int Bc, const sg_config &c, cudaStream_t st)
+{
+    if (dh == 8) attn_fwd<8>(QKV, Hin, O, Hmid, LSE, Bc, c, st);
+    else if (dh == 16) attn_fwd<16>(QKV, Hin, O, Hmid, LSE, Bc, c, st);
+    else attn_fwd<32>(QKV, Hin, O, Hmid, LSE, Bc, c, st);
+}
+
+void attn_bwd_dispatch(int dh, const float *QKV, const float *O, const float *dO,
+                       const float *LSE, float *dQKV, float *Dt, int Bc, const sg_config &c,
+                       cudaStream_t st)
+{
+    if (dh == 8) attn_bwd<8>(QKV, O, dO, LSE, dQKV, Dt, Bc, c, st);
+    else if (dh == 16) attn_bwd<16>(QKV, O, dO, LSE, dQKV, Dt, Bc, c, st);
+    else attn_bwd<32>(QKV, O, dO, LSE, dQKV, Dt, Bc, c, st);
+}
+
+template <int EPI>
+void gemm(const float *A, int lda, const float *Bm, int ldb, const float *bias, float *C, int ldc,
+          int64_t M, int N, int K, cudaStream_t st, const float *aux = nullptr, int ldaux = 0,
+          float *aux_out = nullptr)
+{
+    dim3 grid((N + 63) / 64, (unsigned)((M + 63) / 64));
+    gemm_nn_kernel<EPI><<<grid, 256, 0, ::sg::counted(st)>>>(A, lda, Bm, ldb, bias, C, ldc, aux, ldaux, aux_out,
+                                             M, N, K);
+}
+
+void gemm_tn_acc(const float *A, int lda, const float *Bm, int ldb, float *C, int64_t M, int N1,
+                 int N2, cudaStream_t st)
+{
+    const int tiles = ((N1 + 63) / 64) * ((N2 + 63) / 64);
+    int64_t splits = std::max<int64_t>(1, std::min<int64_t>((M + 511) / 512, 608 / tiles + 1));
+    const int64_t rpb = (M + splits - 1) / splits;
+    splits = (M + rpb - 1) / rpb;
+    dim3 grid((N2 + 63) / 64, (N1 + 63) / 64, (unsigned)splits);
+    gemm_tn_acc_kernel<<<grid, 256, 0, ::sg::counted(st)>>>(A, lda, Bm, ldb, C, M, N1, N2, rpb);
+}
+
+void colsum(const float *A, int lda, int64_t M, int N, float *out, cudaStream_t st)
+{
+    const int64_t splits = std::max<int64_t>(1, std::min<int64_t>((M + 1023) / 1024, 256));
+    const int64_t rpb = (M + splits - 1) / splits;
+    dim3 grid((N + 31) / 32, (unsigned)((M + rpb - 1) / rpb)), block(32, 8);
+    colsum_kernel<<<grid, block, 0, ::sg::counted(st)>>>(A, lda, M, N, out, rpb);
+}
+
+void ln_bwd(const float *dY, const float *X, const float *mu, const float *rs, const float *g,
+            float *dX, int accumulate, float *dg, float *db, int64_t R, int D, cudaStream_t st)
+{
+    const int rpb = 256;
+    ln_bwd_kernel<<<blocks_for(R, rpb), 256, 2 * D * sizeof(float), ::sg::counted(st)>>>(
+        dY, X, mu, rs, g, dX, accumulate, dg, db, R, D, rpb);
+}
+
+struct Work {
+    std::vector<LayerBufs> layers;
+    float *Hfin, *muf, *rsf, *Y, *ell, *lp, *Hping;
+    float *dH, *dHmid, *dA, *dQKV, *dF1, *Dt;
+    int64_t total_floats;
+};
+
+Work carve(const sg_config &c, float *base, int64_t R, bool bwd)
+{
+    Work w;
+    const int64_t D = c.d, F = c.d_ff, NH = c.n_heads;
+    int64_t off = 0;  // floats; every buffer starts 16-byte aligned
+    auto take = [&](int64_t n) {
+        float *q = base ? base + off : nullptr;
+        off += (n + 3) & ~int64_t(3);
+        return q;
+    };
+    const int nl = bwd ? c.n_layers : 1;
+    for (int l = 0; l < nl; ++l) {
+        LayerBufs L;
+        L.Hin = take(R * D);
+        L.mu1 = take(R);
+        L.rs1 = take(R);
+        L.A1 = take(R * D);
+        L.QKV = take(R * 3 * D);
+        L.O = take(R * D);
+        L.LSE = take(R * NH);
+        L.Hmid = take(R * D);
+        L.mu2 = take(R);
+        L.rs2 = take(R);
+        L.A2 = take(R * D);
+        L.F1 = take(R * F);
+        L.G = take(R * F);
+        w.layers.push_back(L);
+    }
+    w.Hfin = take(R * D);
+    w.Hping = take(R * D);
+    w.muf = take(R);
+    w.rsf = take(R);
+    w.Y = take(R * D);
+    w.ell = take(R);
+    w.lp = take(R);
+    if (bwd) {
+        w.dH = take(R * D);
+        w.dHmid = take(R * D);
+        w.dA = take(R * D);
+        w.dQKV = take(R * 3 * D);
+        w.dF1 = take(R * F);
+        w.Dt = take(R * NH);
+    }
+    w.total_floats = off;
+    return w;
+}
+
+sg_status plan_chunks(sg_model *m, int64_t B, bool bwd, Plan &p, size_t &bytes)
+{
+    const sg_config &c = m->cfg;
+    // floats per sample from a dry run of carve() over one sample's rows
+    const size_t per_sample = (size_t)carve(c, nullptr, c.N, bwd).total_floats * sizeof(float);
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    const size_t budget = std::min<size_t>((size_t)16 << 30, free_b / 3 + m->ws_bytes);
+    int64_t Bc = std::max<int64_t>(1, (int64_t)(budget / per_sample));
+    Bc = std::min<int64_t>(Bc, B);
+    // keep the warp count of the attention kernels within a 32-bit grid
+    Bc = std::min<int64_t>(Bc, (int64_t)((1ll << 30) / ((int64_t)c.N * c.n_heads)));
+    p.Bc = Bc;
+    p.R = Bc * c.N;
+    p.keep = bwd;
+    bytes = (size_t)carve(c, nullptr, p.R, bwd).total_floats * sizeof(float);
+    return SG_OK;
+}
+
+// Forward over one chunk.  Layer l reads H_in (embedding or previous output)
+// and writes its output into the next layer's Hin (or Hfin after the last).
+void forward_chunk(sg_model *m, const int8_t *spins, int Bc, Work &w, bool keep, cudaStream_t st)
+{
+    const sg_config &c = m->cfg;
+    const int64_t R = (int64_t)Bc * c.N;
+    const int D = c.d, F = c.d_ff, dh = c.d / c.n_heads;
+    const float *W = m->w;
+    float *H = keep ? w.layers[0].Hin : w.Hping;
+    embed_kernel<<<blocks_for(R * D, 256), 256, 0, ::sg::counted(st)>>>(spins, R, c.N, D, c.d_token,
+                                                         W + m->off.tok, W + m->off.pos, H);
+    for (int l = 0; l < c.n_layers; ++l) {
+        LayerBufs &L = w.layers[keep ? l : 0];
+        const LayerOff &o = m->off.L[l];
+        float *Hin = keep ? L.Hin : H;
+        float *Hout = keep ? (l + 1 < c.n_layers ? w.layers[l + 1].Hin : w.Hfin)
+                           : (H == w.Hping ? w.Hfin : w.Hping);
+        ln_fwd_kernel<<<blocks_for(R, 8), 256, 0, ::sg::counted(st)>>>(Hin, W + o.ln1g, W + o.ln1b, L.A1, L.mu1,
+                                                        L.rs1, R, D);
+        gemm<G_STORE>(L.A1, D, m->wt + m->pack.WqkvT[l], 3 * D, m->wt + m->pack.bqkv[l], L.QKV, 3 * D, R,
+                      3 * D, D, st);
+        attn_fwd_dispatch(dh, L.QKV, Hin, L.O, L.Hmid, L.LSE, Bc, c, st);
+        ln_fwd_kernel<<<blocks_for(R, 8), 256, 0, ::sg::counted(st)>>>(L.Hmid, W + o.ln2g, W + o.ln2b, L.A2,
+                                                        L.mu2, L.rs2, R, D);
+        if (keep)
+            gemm<G_GELU>(L.A2, D, m->wt + m->pack.W1T[l], F, m->wt + m->pack.b1[l], L.G, F, R, F, D, st,
+                         nullptr, F, L.F1);
+        else
+            gemm<G_GELU_ONLY>(L.A2, D, m->wt + m->pack.W1T[l], F, m->wt + m->pack.b1[l], L.G, F, R, F, D, st);
+        gemm<G_ADDRES>(L.G, F, m->wt + m->pack.W2T[l], D, m->wt + m->pack.b2[l], Hout, D, R, D, F, st, L.Hmid,
+                       D);
+        H = Hout;
+    }
+    // ensure the final stream lives in Hfin
+    if (H != w.Hfin)
+        cudaMemcpyAsync(w.Hfin, H, (size_t)R * D * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    head_fwd_kernel<<<blocks_for(R, 8), 256, 0, ::sg::counted(st)>>>(
+        w.Hfin, W + m->off.lnfg, W + m->off.lnfb, W + m->off.Wh, W + m->off.bh, spins,
+        keep ? w.Y : nullptr, keep ? w.muf : nullptr, keep ? w.rsf : nullptr,
+        keep ? w.ell : nullptr, w.lp, R, D);
+}
+
+}  // namespace
+
+sg_status launch_logprob_f32(sg_model *m, const int8_t *spins, int64_t B, float *logq,
+                             cudaStream_t st)
+{
+    const sg_config &c = m->cfg;
+    if (!dh_supported(c.d / c.n_heads))
+        return fail(SG_EUNSUPPORTED, "prefill attention is built for d_h in {8, 16, 32}");
+    if (c.d % 4 || c.d_ff % 4) return fail(SG_EUNSUPPORTED, "d and d_ff must be multiples of 4");
+    Plan p;
+    size_t bytes;
+    SG_TRY(plan_chunks(m, B, false, p, bytes));
+    SG_TRY(ensure_buffer(&m->ws, &m->ws_bytes, bytes));
+    for (int64_t b0 = 0; b0 < B; b0 += p.Bc) {
+        const int Bc = (int)std::min<int64_t>(p.Bc, B - b0);
+        Work w = carve(c, (float *)m->ws, (int64_t)Bc * c.N, false);
+        const int8_t *sp = spins + b0 * c.N;
+        forward_chunk(m, sp, Bc, w, false, st);
+        seg_sum_kernel<<<Bc, 256, 0, ::sg::counted(st)>>>(w.lp, c.N, logq + b0);
+    }
+    return check_launch("teacher-forced log q");
+}
+
+sg_status launch_grad_f32(sg_model *m, const int8_t *spins, const float *coeff, int64_t B,
+                          float *grad, float *logq, cudaStream_t st)
+{
+    const sg_config &c = m->cfg;
+    if (!dh_supported(c.d / c.n_heads))
+        return fail(SG_EUNSUPPORTED, "prefill attention is built for d_h in {8, 16, 32}");
+    if (c.d % 4 || c.d_ff % 4) return fail(SG_EUNSUPPORTED, "d and d_ff must be multiples of 4");
+    if (c.d > 512) return fail(SG_EUNSUPPORTED, "backward is built for d <= 512");
+    Plan p;
+    size_t bytes;
+    SG_TRY(plan_chunks(m, B, true, p, bytes));
+    SG_TRY(ensure_buffer(&m->ws, &m->ws_bytes, bytes));
+    SG_CUDA_TRY(cudaMemsetAsync(grad, 0, (size_t)m->P * sizeof(float), st));
+    const int D = c.d, F = c.d_ff, dh = c.d / c.n_heads;
+    const float *W = m->w;
+    const BlobOff &O = m->off;
+    for (int64_t b0 = 0; b0 < B; b0 += p.Bc) {
+        const int Bc = (int)std::min<int64_t>(p.Bc, B - b0);
+        const int64_t R = (int64_t)Bc * c.N;
+        Work w = carve(c, (float *)m->ws, R, true);
+        const int8_t *sp = spins + b0 * c.N;
+        forward_chunk(m, sp, Bc, w, true, st);
+        if (logq) seg_sum_kernel<<<Bc, 256, 0, ::sg::counted(st)>>>(w.lp, c.N, logq + b0);
+        // head + LN_f
+        head_bwd_kernel<<<blocks_for(R, 256), 256, (4 * D + 2) * sizeof(float), ::sg::counted(st)>>>(
+            w.Hfin, w.muf, w.rsf, w.Y, w.ell, sp, coeff + b0, W + O.lnfg, W + O.Wh, w.dH,
+            grad + O.Wh, grad + O.bh, grad + O.lnfg, grad + O.lnfb, R, c.N, D, 256);
+        for (int l = c.n_layers - 1; l >= 0; --l) {
+            LayerBufs &L = w.layers[l];
+            const LayerOff &o = O.L[l];
+            // FFN: H = Hmid + W2 G + b2, G = gelu(F1), F1 = W1 A2 + b1
+            gemm_tn_acc(w.dH, D, L.G, F, grad + o.W2, R, D, F, st);
+            colsum(w.dH, D, R, D, grad + o.b2, st);
+            gemm<G_GELU_BWD>(w.dH, D, m->wt + m->pack.W2[l], F, nullptr, w.dF1, F, R, F, D, st, L.F1, F);
+            gemm_tn_acc(w.dF1, F, L.A2, D, grad + o.W1, R, F, D, st);
+            colsum(w.dF1, F, R, F, grad + o.b1, st);
+            gemm<G_STORE>(w.dF1, F, m->wt + m->pack.W1[l], D, nullptr, w.dA, D, R, D, F, st);
+            cudaMemcpyAsync(w.dHmid, w.dH, (size_t)R * D * sizeof(float),
+                            cudaMemcpyDeviceToDevice, st);
+            ln_bwd(w.dA, L.Hmid, L.mu2, L.rs2, W + o.ln2g, w.dHmid, 1, grad + o.ln2g,
+                   grad + o.ln2b, R, D, st);
+            // attention: Hmid = Hin + O(QKV)
+            attn_bwd_dispatch(dh, L.QKV, L.O, w.dHmid, L.LSE, w.dQKV, w.Dt, Bc, c, st);
+            gemm_tn_acc(w.dQKV, 3 * D, L.A1, D, grad + o.Wqkv, R, 3 * D, D, st);
+            colsum(w.dQKV, 3 * D, R, 3 * D, grad + o.bqkv, st);
+            gemm<G_STORE>(w.dQKV, 3 * D, m->wt + m->pack.Wqkv[l], D, nullptr, w.dA, D, R, D, 3 * D, st);
+            cudaMemcpyAsync(w.dH, w.dHmid, (size_t)R * D * sizeof(float),
+                            cudaMemcpyDeviceToDevice, st);
+            ln_bwd(w.dA, L.Hin, L.mu1, L.rs1, W + o.ln1g, w.dH, 1, grad + o.ln1g, grad + o.ln1b,
+                   R, D, st);
+        }
+        embed_bwd_kernel<<<blocks_for((int64_t)c.N * D, 256), 256, 0, ::sg::counted(st)>>>(
+            w.dH, sp, Bc, c.N, D, c.d_token, grad + O.tok, grad + O.pos);
+    }
+    return check_launch("REINFORCE backward");
+}
+
+}  // namespace sg

@@ -1,0 +1,202 @@
+// sg_internal.cuh -- internal declarations shared by the libsg translation
+// units: device Philox4x32-10, the weight-blob offsets, the model and
+// instance objects, and launch helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "sg.h"
+
+#define SG_MAX_LAYERS 16
+
+namespace sg {
+
+// ---------------------------------------------------------------------------
+// Error plumbing: every entry point converts failures to sg_status + message.
+// ---------------------------------------------------------------------------
+void set_error(const std::string &msg);
+sg_status fail(sg_status code, const std::string &msg);
+sg_status check_launch(const char *what);
+
+// Every kernel launch passes its stream through counted(), which bumps the
+// library's launch counter (sg_launch_count) and returns the stream.
+cudaStream_t counted(cudaStream_t st);
+
+#define SG_CUDA_TRY(expr)                                                              \
+    do {                                                                               \
+        cudaError_t e_ = (expr);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return ::sg::fail(SG_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define SG_TRY(expr)                        \
+    do {                                    \
+        sg_status s_ = (expr);              \
+        if (s_ != SG_OK) return s_;         \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): two 32x32 -> 64-bit
+// multiplies per round, Weyl key schedule, 10 rounds.  The uniform of word 0
+// is ((x0 >> 8) + 0.5) * 2^-24, exactly representable in binary32.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ float philox_uniform(uint64_t seed, uint32_t a, uint32_t b,
+                                                uint32_t stream, uint32_t e)
+{
+    const uint4 r = philox4x32_10(make_uint4(a, b, stream, e), (uint32_t)seed,
+                                  (uint32_t)(seed >> 32));
+    return ((float)(r.x >> 8) + 0.5f) * (1.0f / 16777216.0f);
+}
+
+// log(sigmoid(x)) without overflow, FP32.
+__device__ __forceinline__ float log_sigmoid_f(float x)
+{
+    return x >= 0.f ? -log1pf(expf(-x)) : x - log1pf(expf(x));
+}
+
+__device__ __forceinline__ float gelu_f(float x)
+{
+    return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f));
+}
+
+__device__ __forceinline__ float gelu_grad_f(float x)
+{
+    return 0.5f * (1.0f + erff(x * 0.70710678118654752f))
+           + x * 0.39894228040143268f * expf(-0.5f * x * x);
+}
+
+// ---------------------------------------------------------------------------
+// Weight-blob offsets (floats), blob layout of include/sg.h.
+// ---------------------------------------------------------------------------
+struct LayerOff {
+    int64_t ln1g, ln1b, Wqkv, bqkv, ln2g, ln2b, W1, b1, W2, b2;
+};
+
+struct BlobOff {
+    int64_t tok, pos;
+    LayerOff L[SG_MAX_LAYERS];
+    int64_t lnfg, lnfb, Wh, bh, total;
+};
+
+BlobOff blob_offsets(const sg_config &c);
+
+// Offsets of the 16-byte aligned FP32 copies read with vector loads by the
+// CUDA-core GEMMs: k-major (transposed) WqkvT [d][3d], W1T [d][d_ff],
+// W2T [d_ff][d]; the row-major Wqkv, W1, W2 of the backward; and the biases.
+struct PackOff {
+    int64_t WqkvT[SG_MAX_LAYERS], W1T[SG_MAX_LAYERS], W2T[SG_MAX_LAYERS];
+    int64_t Wqkv[SG_MAX_LAYERS], W1[SG_MAX_LAYERS], W2[SG_MAX_LAYERS];
+    int64_t bqkv[SG_MAX_LAYERS], b1[SG_MAX_LAYERS], b2[SG_MAX_LAYERS];
+    int64_t total;
+};
+
+PackOff pack_offsets(const sg_config &c);
+
+// Everything a kernel needs about the model, passed by value.
+struct DevModel {
+    int N, L, d, nh, dt, dff, mask, W, S;
+    const float *w;    // master FP32 blob
+    const float *wt;   // transposed FP32 copies
+    BlobOff o;
+    PackOff p;
+};
+
+// Visible-key geometry of query t (mask of include/sg.h):
+// keys [0, n_sink) then [band_lo, t].
+__host__ __device__ __forceinline__ void visible_ranges(int mask, int W, int S, int t,
+                                                        int &n_sink, int &band_lo)
+{
+    if (mask == SG_MASK_DENSE) {
+        n_sink = 0;
+        band_lo = 0;
+    } else {
+        n_sink = S < t + 1 ? S : t + 1;
+        const int lo = t - W;
+        band_lo = lo > S ? lo : S;
+    }
+}
+
+__host__ __device__ __forceinline__ int band_count(int t, int band_lo)
+{
+    return t >= band_lo ? t - band_lo + 1 : 0;
+}
+
+__host__ __device__ __forceinline__ bool key_visible(int mask, int W, int S, int t, int k)
+{
+    if (k > t) return false;
+    if (mask == SG_MASK_DENSE) return true;
+    return (t - k <= W) || (k < S);
+}
+
+}  // namespace sg
+
+// ---------------------------------------------------------------------------
+// Library objects (opaque in the ABI).
+// ---------------------------------------------------------------------------
+struct sg_model {
+    sg_config cfg;
+    int64_t P;
+    int device;
+    sg::BlobOff off;
+    sg::PackOff pack;
+    float *w = nullptr;       // master FP32 blob
+    float *wt = nullptr;      // transposed FP32 copies
+    void *bf = nullptr;       // BF16 packed operands (tensor-core path)
+    size_t bf_bytes = 0;
+    void *kv = nullptr;       // KV-cache workspace
+    size_t kv_bytes = 0;
+    void *ws = nullptr;       // prefill / backward workspace
+    size_t ws_bytes = 0;
+};
+
+struct sg_instance {
+    int32_t kind, N, D, L, periodic;
+    bool integer_bonds;
+    float *J = nullptr;       // SK: [N][N]; EA: bonds [N][D]
+    int8_t *Ji8 = nullptr;    // EA with integer bonds: bonds as int8
+    void *Jbf = nullptr;      // SK: BF16 hi/lo split of J, tensor-core layout
+};
+
+namespace sg {
+sg_status ensure_buffer(void **ptr, size_t *have, size_t need);
+
+// Launchers implemented in the kernel translation units.
+sg_status launch_pack_f32(sg_model *m, cudaStream_t st);
+sg_status launch_decode_f32(sg_model *m, int64_t B, uint64_t seed, uint32_t sid, float band,
+                            int8_t *spins, float *logq, uint32_t *flags, cudaStream_t st);
+sg_status launch_logprob_f32(sg_model *m, const int8_t *spins, int64_t B, float *logq,
+                             cudaStream_t st);
+sg_status launch_grad_f32(sg_model *m, const int8_t *spins, const float *coeff, int64_t B,
+                          float *grad, float *logq, cudaStream_t st);
+sg_status launch_energy(const sg_instance *inst, const int8_t *spins, int64_t B, int prec,
+                        float *E, int32_t *E_int, cudaStream_t st);
+sg_status launch_free_energy(const float *E, const float *logq, int64_t B, double beta,
+                             double *out, float *coeff, cudaStream_t st);
+sg_status launch_mh(const int8_t *prop, const float *E, const float *logq, int64_t B, int N,
+                    int C, double beta, uint64_t seed, int8_t *cs, double *cE, double *cL,
+                    int64_t *acc, float *trace, cudaStream_t st);
+sg_status launch_metropolis(const sg_instance *inst, int8_t *spins, int64_t R, int sweeps,
+                            double beta, uint64_t seed, double *E, float *trace,
+                            cudaStream_t st);
+sg_status launch_overlap(const int8_t *spins, int64_t B, int N, int64_t *hist, cudaStream_t st);
+sg_status launch_adam(float *w, const float *g, float *m, float *v, int64_t n, float lr,
+                      float b1, float b2, float eps, int64_t step, cudaStream_t st);
+}  // namespace sg

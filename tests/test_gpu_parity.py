@@ -1,0 +1,281 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bar: spins and +-J energies bit-exact (flagged draws replayed), per-sample
+|delta log q| <= 1e-4 N for FP32 and <= 2e-2 N for BF16, FP64 reductions to
+rounding, gradients to FP32 accumulation error.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2606_22984_gb300 import inputs, sg
+
+from helpers import ocfg, oracle_replay, unpack_flags
+
+pytestmark = pytest.mark.gpu
+
+FP32_LOGQ_TOL = 1e-4     # per spin, FP32 path (per-sample bound 1e-4 * N)
+BF16_LOGQ_TOL = 2e-2     # per spin, BF16 path
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2606_22984_gb300 import build
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+SAMPLE_CASES = {
+    # name: (shape, B, weight scale)
+    "sk20_dense": (inputs.ModelShape(20, 2, 32, 4), 300, 1.0),
+    "ea6_ring": (inputs.ModelShape(36, 2, 64, 4, mask_kind=1, W=6, S=7), 200, 1.0),
+    "dense_d128_h8": (inputs.ModelShape(40, 2, 128, 8), 70, 1.0),
+    "band_d128_h4": (inputs.ModelShape(30, 1, 128, 4, mask_kind=1, W=5, S=3), 65, 1.5),
+    "single_spin": (inputs.ModelShape(1, 1, 32, 4), 5, 1.0),
+    "band_W0_S0": (inputs.ModelShape(17, 2, 64, 8, mask_kind=1, W=0, S=0), 33, 1.0),
+    "d64_h8_ring": (inputs.ModelShape(50, 3, 64, 8, mask_kind=1, W=4, S=6), 97, 1.0),
+}
+
+
+def _sample_and_check(m, w, B, seed, precision, tol):
+    model = sg.Model(m, w, precision)
+    spins, logq, flags = model.sample(B, seed=seed, with_flags=True)
+    torch.cuda.synchronize()
+    s, lq, fl = _np(spins), _np(logq), _np(flags)
+    so, lqo, ppo, flo = oracle_replay(m, w, seed, s, fl)
+    assert np.array_equal(so, s), "spins differ from the oracle outside flagged draws"
+    assert np.all(np.isin(s, (-1, 1)))
+    dl = np.abs(lqo - lq)
+    assert dl.max() <= tol * m.N, f"max |dlogq| {dl.max()} > {tol * m.N}"
+    frac = unpack_flags(fl, m.N).mean()
+    return model, spins, logq, frac, dl
+
+
+@pytest.mark.parametrize("name", list(SAMPLE_CASES))
+def test_fp32_sampling_matches_oracle(name):
+    m, B, scale = SAMPLE_CASES[name]
+    w = inputs.make_weights(m, 7, scale)
+    _, _, _, frac, _ = _sample_and_check(m, w, B, 1234, sg.SG_FP32, FP32_LOGQ_TOL)
+    assert frac < 0.01
+
+
+@pytest.mark.parametrize("name", ["sk20_dense", "ea6_ring", "dense_d128_h8", "d64_h8_ring"])
+def test_fp32_teacher_forced_logq_matches_oracle_and_sampler(name):
+    m, B, scale = SAMPLE_CASES[name]
+    w = inputs.make_weights(m, 8, scale)
+    model = sg.Model(m, w, sg.SG_FP32)
+    rs = inputs.random_spins(B, m.N, 3)
+    lq = _np(model.logprob(torch.tensor(rs, device="cuda")))
+    lqo = oracle.logprob(ocfg(m), w, rs)
+    assert np.abs(lq - lqo).max() <= FP32_LOGQ_TOL * m.N
+    spins, logq = model.sample(B, seed=99)
+    tf = model.logprob(spins)
+    assert (tf - logq).abs().max().item() <= FP32_LOGQ_TOL * m.N
+
+
+def test_sampling_is_deterministic_and_seeded():
+    m, B, _ = SAMPLE_CASES["ea6_ring"]
+    model = sg.Model(m, inputs.make_weights(m, 1), sg.SG_FP32)
+    a, la = model.sample(B, seed=5)
+    b, lb = model.sample(B, seed=5)
+    c, _ = model.sample(B, seed=6)
+    assert torch.equal(a, b) and torch.equal(la, lb)
+    assert not torch.equal(a, c)
+
+
+def test_invalid_arguments_raise():
+    m, _, _ = SAMPLE_CASES["sk20_dense"]
+    model = sg.Model(m, inputs.make_weights(m, 1), sg.SG_FP32)
+    with pytest.raises(sg.SgError):
+        model.sample(0, seed=1)
+    with pytest.raises(sg.SgError):
+        sg.Model(m, np.zeros(10, np.float32), sg.SG_FP32)
+    bad = inputs.make_weights(m, 1)
+    bad[3] = np.nan
+    with pytest.raises(sg.SgError):
+        sg.Model(m, bad, sg.SG_FP32)
+
+
+# --------------------------------------------------------------------------
+# Energies
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("D,L", [(2, 16), (3, 10), (2, 5)])
+def test_pm_ea_energies_bit_exact(D, L):
+    inst = inputs.make_ea(D, L, 3, pm=True)
+    gi = sg.Instance(inst)
+    for B in (1, 1000):
+        s = inputs.random_spins(B, inst.N, B)
+        E, Ei = gi.energy(torch.tensor(s, device="cuda"), want_int=True)
+        Eo = oracle.energy(inst, s)
+        assert np.array_equal(_np(Ei).astype(np.float64), Eo)
+        assert np.array_equal(_np(E).astype(np.float64), Eo)
+
+
+def test_gaussian_ea_energy():
+    inst = inputs.make_ea(2, 12, 4, pm=False)
+    s = inputs.random_spins(333, inst.N, 1)
+    E = _np(sg.Instance(inst).energy(torch.tensor(s, device="cuda")))
+    Eo = oracle.energy(inst, s)
+    assert np.allclose(E, Eo, rtol=1e-5, atol=1e-4)
+
+
+@pytest.mark.parametrize("N,B", [(20, 1), (50, 65), (1024, 130)])
+def test_sk_energy_fp32(N, B):
+    inst = inputs.make_sk(N, N)
+    s = inputs.random_spins(B, N, 2)
+    E = _np(sg.Instance(inst).energy(torch.tensor(s, device="cuda")))
+    Eo = oracle.energy(inst, s)
+    assert np.allclose(E, Eo, rtol=1e-5, atol=1e-4)
+
+
+# --------------------------------------------------------------------------
+# Free energies (FP64 on the device)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("B", [1, 7, 5000])
+def test_free_energy_fp64(B):
+    rng = np.random.default_rng(B)
+    E = rng.normal(-30, 5, B).astype(np.float32)
+    lq = rng.normal(-20, 3, B).astype(np.float32)
+    beta = 0.7
+    out, coeff = sg.free_energy(torch.tensor(E, device="cuda"), torch.tensor(lq, device="cuda"),
+                                beta, want_coeff=True)
+    Fq, Fis, ess = oracle.free_energy(E.astype(np.float64), lq.astype(np.float64), beta)
+    o = _np(out)
+    assert abs(o[0] - Fq) <= 1e-12 * abs(Fq)
+    assert abs(o[1] - Fis) <= 1e-12 * abs(Fis)
+    assert abs(o[2] - ess) <= 1e-10 * ess
+    L = beta * E.astype(np.float64) + lq.astype(np.float64)
+    assert np.allclose(_np(coeff), ((L - L.mean()) / B).astype(np.float32), rtol=1e-6, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# REINFORCE backward
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("m", [inputs.ModelShape(12, 2, 32, 4),
+                               inputs.ModelShape(20, 2, 64, 4, mask_kind=1, W=4, S=5),
+                               inputs.ModelShape(33, 1, 32, 2, mask_kind=1, W=3, S=2)])
+def test_fp32_grad_matches_oracle(m):
+    w = inputs.make_weights(m, 5)
+    B = 37
+    s = inputs.random_spins(B, m.N, 9)
+    c = np.random.default_rng(1).normal(0, 1, B).astype(np.float32)
+    model = sg.Model(m, w, sg.SG_FP32)
+    logq = torch.empty(B, dtype=torch.float32, device="cuda")
+    g = _np(model.grad(torch.tensor(s, device="cuda"), torch.tensor(c, device="cuda"), logq=logq))
+    go, lqo = oracle.grad(ocfg(m), w, s, c.astype(np.float64))
+    rel = np.linalg.norm(g - go) / np.linalg.norm(go)
+    assert rel < 1e-4, rel
+    assert np.abs(g - go).max() <= 1e-4 * np.abs(go).max() + 1e-6
+    assert np.abs(_np(logq) - lqo).max() <= FP32_LOGQ_TOL * m.N
+
+
+# --------------------------------------------------------------------------
+# MH, Metropolis, overlap, Adam
+# --------------------------------------------------------------------------
+
+def test_mh_step_matches_oracle():
+    m = inputs.ModelShape(16, 1, 32, 4)
+    inst = inputs.make_sk(16, 3)
+    model = sg.Model(m, inputs.make_weights(m, 3), sg.SG_FP32)
+    gi = sg.Instance(inst)
+    C, per, beta = 64, 50, 1.0
+    prop, lq = model.sample(C * per, seed=11)
+    E = gi.energy(prop)
+    cs, clq = model.sample(C, seed=12)
+    cE = gi.energy(cs).double()
+    clq = clq.double()
+    cE0, clq0 = _np(cE).copy(), _np(clq).copy()
+    acc, trace = sg.mh_step(prop, E, lq, C, beta, 77, cs, cE, clq, trace=True)
+    torch.cuda.synchronize()
+    oE, oL, oi, otr, oacc, ofl = oracle.mh(_np(E).astype(np.float64), _np(lq).astype(np.float64),
+                                           C, beta, 77, cE0, clq0)
+    flagged_chains = np.unique(np.nonzero(ofl.reshape(per, C))[1])
+    ok = np.setdiff1d(np.arange(C), flagged_chains)
+    assert np.array_equal(_np(acc)[ok], oacc[ok])
+    assert np.array_equal(_np(cE)[ok], oE[ok])
+    assert np.array_equal(_np(trace)[:, ok], otr[:, ok].astype(np.float32))
+    moved = ok[oi[ok] >= 0]
+    assert np.array_equal(_np(cs)[moved], _np(prop)[oi[moved]])
+
+
+@pytest.mark.parametrize("kind", ["ea2", "ea3", "sk"])
+def test_metropolis_matches_oracle(kind):
+    inst = {"ea2": inputs.make_ea(2, 8, 1, pm=True), "ea3": inputs.make_ea(3, 4, 2, pm=True),
+            "sk": inputs.make_sk(30, 5)}[kind]
+    R, sweeps, beta = 100, 20, 1.0
+    s0 = inputs.random_spins(R, inst.N, 3)
+    gi = sg.Instance(inst)
+    st = torch.tensor(s0, device="cuda")
+    E0 = torch.tensor(oracle.energy(inst, s0), device="cuda")
+    E, tr = gi.metropolis(st, sweeps, beta, 42, E=E0, trace=True)
+    so, Eo, tro, nflag = oracle.metropolis(inst, s0, sweeps, beta, 42)
+    assert nflag == 0
+    assert np.array_equal(_np(st), so)
+    if kind == "sk":
+        assert np.allclose(_np(E), Eo, rtol=0, atol=1e-9)
+    else:
+        assert np.array_equal(_np(E), Eo)
+        assert np.array_equal(_np(tr), tro.astype(np.float32))
+
+
+def test_overlap_hist_matches_oracle():
+    s = inputs.random_spins(101, 37, 4)
+    h = _np(sg.overlap_hist(torch.tensor(s, device="cuda")))
+    assert np.array_equal(h, oracle.overlap_hist(s))
+
+
+def test_adam_step_matches_torch_reference():
+    n = 1000
+    rng = np.random.default_rng(0)
+    w, g = rng.normal(size=n).astype(np.float32), rng.normal(size=n).astype(np.float32)
+    m, v = rng.normal(size=n).astype(np.float32) * 0.1, rng.random(n).astype(np.float32) * 0.1
+    tw, tg, tm, tv = (torch.tensor(x, device="cuda") for x in (w, g, m, v))
+    sg.adam_step(tw, tg, tm, tv, lr=1e-3, step=3)
+    b1, b2 = 0.9, 0.999
+    m2 = b1 * torch.tensor(m) + (1 - b1) * torch.tensor(g)
+    v2 = b2 * torch.tensor(v) + (1 - b2) * torch.tensor(g) ** 2
+    w2 = torch.tensor(w) - 1e-3 * (m2 / (1 - b1 ** 3)) / ((v2 / (1 - b2 ** 3)).sqrt() + 1e-8)
+    assert torch.allclose(tw.cpu(), w2, rtol=1e-6, atol=1e-7)
+
+
+# --------------------------------------------------------------------------
+# Full-size workloads in the benchmark's launch configuration
+# --------------------------------------------------------------------------
+
+def test_full_size_sk20_fp32_all_rows():
+    wl = inputs.workloads()["sk20"]
+    m, inst = wl.model, wl.instance()
+    w = wl.weights()
+    model, spins, logq, frac, dl = _sample_and_check(m, w, wl.B, 2024, sg.SG_FP32, FP32_LOGQ_TOL)
+    assert frac < 0.01
+    E = sg.Instance(inst).energy(spins)
+    Eo = oracle.energy(inst, _np(spins))
+    assert np.allclose(_np(E), Eo, rtol=1e-5, atol=1e-5)
+
+
+def test_full_size_ea2d16_fp32_sampled_rows():
+    wl = inputs.workloads()["ea2d16"]
+    m, inst = wl.model, wl.instance()
+    w = wl.weights()
+    model = sg.Model(m, w, sg.SG_FP32)
+    spins, logq, flags = model.sample(wl.B, seed=31, with_flags=True)
+    E, Ei = sg.Instance(inst).energy(spins, want_int=True)
+    torch.cuda.synchronize()
+    s, lq, fl = _np(spins), _np(logq), _np(flags)
+    rows = np.array([0, 1, 4095, 8191, 12345, wl.B - 1])
+    so, lqo, _, _ = oracle_replay(m, w, 31, s, fl, rows=rows)
+    assert np.array_equal(so, s[rows])
+    assert np.abs(lqo - lq[rows]).max() <= FP32_LOGQ_TOL * m.N
+    assert np.array_equal(_np(Ei).astype(np.float64), oracle.energy(inst, s))
+    tf = _np(model.logprob(spins[:64]))
+    assert np.abs(tf - oracle.logprob(ocfg(m), w, s[:64])).max() <= FP32_LOGQ_TOL * m.N
