@@ -135,6 +135,35 @@ sg_status sg_sample(sg_model *m, int64_t B, double beta, uint64_t seed, uint32_t
                     sg_stream stream);
 
 /*
+ * Allocation-free variant of sg_sample (FP32 path).  The paper has no
+ * counterpart: this entry point exists for callers that must not allocate
+ * device memory -- code that runs while a CUDA graph is being captured, code
+ * embedded in a host framework that owns every device allocation through its
+ * own memory pool, or latency-critical loops where cudaMalloc's implicit
+ * synchronisation is not acceptable.  It calls no cudaMalloc, cudaFree or
+ * allocating library routine.  Its scratch (packed weight copies followed by
+ * the KV cache) is one statically sized device array of
+ * SG_NOALLOC_SCRATCH_BYTES inside libsg, which every GPU that loads the
+ * library holds until the process exits.
+ *   cfg      model configuration (precision must be SG_FP32).
+ *   weights  dev float [sg_param_count(cfg)]: the caller's weight blob.
+ *   spins, logq, flags, seed, stream_id, flag_band: as for sg_sample.
+ * Errors: SG_EINVAL when cfg is invalid or when the packed weights plus the
+ * KV cache of B samples exceed SG_NOALLOC_SCRATCH_BYTES (reduce B, or use
+ * sg_sample); SG_EUNSUPPORTED for shapes the FP32 decode is not built for.
+ * The first call on a device looks up the scratch's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture begins.  Every call shares the one scratch array and it keeps the
+ * last call's contents; nothing in it needs to start at zero, because each
+ * call writes every byte it reads.  Calls whose work overlaps on the GPU
+ * (other streams, other host threads) race on the scratch: serialise them.
+ */
+#define SG_NOALLOC_SCRATCH_BYTES (64ull << 20)
+sg_status sg_sample_noalloc(const sg_config *cfg, const float *weights, int64_t B, double beta,
+                            uint64_t seed, uint32_t stream_id, float flag_band, int8_t *spins,
+                            float *logq, uint32_t *flags, sg_stream stream);
+
+/*
  * Teacher-forced log q (Algorithm 1) of B given configurations, computed over
  * the whole sequence at once (prefill).
  *   spins  dev int8 [B][N] in;  logq dev float [B] out.

@@ -14,6 +14,9 @@
 // (32 consecutive samples, one head) reads 512 contiguous bytes per float4.
 // Slot of key k: dense or short sequence -> k; band + sink ring -> k for
 // k < S, else S + (k - S) mod (W + 1).
+#include <mutex>
+#include <string>
+
 #include "sg_internal.cuh"
 
 namespace sg {
@@ -380,4 +383,118 @@ sg_status launch_decode_f32(sg_model *m, int64_t B, uint64_t seed, uint32_t sid,
                                  "(64,16), (128,16), (128,32)}");
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free sampling (sg_sample_noalloc).  Its scratch -- the packed
+// weight copies followed by the KV cache -- lives in one file-scope device
+// array instead of memory from cudaMalloc.  Host code cannot use the array's
+// name as a device address, so the address is looked up once per device with
+// cudaGetSymbolAddress and cached.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SG_NOALLOC_SCRATCH_BYTES];
+
+static constexpr int kMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_addr[kMaxDevices];
+
+static sg_status noalloc_scratch(void **out)
+{
+    int dev = 0;
+    SG_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(SG_EUNSUPPORTED, "device index out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(SG_ECUDA, std::string("cudaGetSymbolAddress(scratch): ") +
+                                      cudaGetErrorString(e));
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return SG_OK;
+}
+
+template <int D, int DH>
+static sg_status run_decode_noalloc(const sg_config &c, const float *w, const BlobOff &off,
+                                    const PackOff &pack, float *wt, float *kv, int64_t B,
+                                    uint64_t seed, uint32_t sid, float band, int8_t *spins,
+                                    float *logq, uint32_t *flags, cudaStream_t st)
+{
+    constexpr int NH = D / DH;
+    constexpr int MS = 256 / NH;
+    const int64_t tiles = (B + MS - 1) / MS;
+    const int US = (3 * D > c.d_ff ? 3 * D : c.d_ff) + 4;
+    const size_t smem = ((size_t)MS * (2 * (D + 4) + US) + 2 * MS) * sizeof(float);
+    auto kern = decode_f32_kernel<D, DH>;
+    SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    DevModel dm{c.N, c.n_layers, c.d, c.n_heads, c.d_token, c.d_ff, c.mask_kind, c.W, c.S,
+                w, wt, off, pack};
+    kern<<<(unsigned)tiles, 256, smem, ::sg::counted(st)>>>(dm, B, seed, sid, band, spins, logq,
+                                                            flags, kv);
+    return check_launch("decode_f32_kernel (no-alloc)");
+}
+
 }  // namespace sg
+
+extern "C" sg_status sg_sample_noalloc(const sg_config *cfg, const float *weights, int64_t B,
+                                       double beta, uint64_t seed, uint32_t stream_id,
+                                       float flag_band, int8_t *spins, float *logq,
+                                       uint32_t *flags, sg_stream stream)
+{
+    using namespace sg;
+    (void)beta;
+    if (sg_param_count(cfg) < 0) return SG_EINVAL;  // message set by the validation
+    if (!weights || !spins || !logq) return fail(SG_EINVAL, "NULL weights or output");
+    if (B < 1 || B >= (int64_t)1 << 32) return fail(SG_EINVAL, "B must be in [1, 2^32)");
+    const sg_config &c = *cfg;
+    if (c.precision != SG_FP32)
+        return fail(SG_EUNSUPPORTED, "sg_sample_noalloc serves the FP32 path only");
+    const int dh = c.d / c.n_heads;
+    const bool shape_ok = (c.d == 32 && (dh == 8 || dh == 16)) || (c.d == 64 && (dh == 8 || dh == 16)) ||
+                          (c.d == 128 && (dh == 16 || dh == 32));
+    if (!shape_ok || c.d_ff % 8 || c.d_ff > 4 * c.d)
+        return fail(SG_EUNSUPPORTED, "sg_sample_noalloc: unsupported (d, d_h, d_ff)");
+    const int MS = 256 / c.n_heads;
+    const RingGeom g = ring_geom(c.mask_kind, c.N, c.W, c.S);
+    const BlobOff off = blob_offsets(c);
+    const PackOff pack = pack_offsets(c);
+    const size_t wt_bytes = ((size_t)pack.total * sizeof(float) + 255) & ~size_t(255);
+    const size_t kv_bytes = (size_t)((B + MS - 1) / MS) * c.n_layers * g.nslots * 2 * c.d * MS *
+                            sizeof(float);
+    if (wt_bytes + kv_bytes > SG_NOALLOC_SCRATCH_BYTES)
+        return fail(SG_EINVAL, "sg_sample_noalloc needs " + std::to_string(wt_bytes + kv_bytes) +
+                                   " bytes of scratch; the static scratch holds " +
+                                   std::to_string((unsigned long long)SG_NOALLOC_SCRATCH_BYTES) +
+                                   " (reduce B or use sg_sample)");
+    void *base = nullptr;
+    SG_TRY(noalloc_scratch(&base));
+    float *wt = static_cast<float *>(base);
+    float *kv = reinterpret_cast<float *>(static_cast<unsigned char *>(base) + wt_bytes);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (flag_band <= 0.f) flag_band = 1e-5f;
+    if (flags)
+        SG_CUDA_TRY(cudaMemsetAsync(flags, 0, (size_t)B * ((c.N + 31) / 32) * sizeof(uint32_t), st));
+    // packed copies of this call's weights (every byte the kernel reads is
+    // written here or earlier in the same launch, so nothing needs clearing)
+    const size_t f4 = sizeof(float);
+    for (int l = 0; l < c.n_layers; ++l) {
+        const LayerOff &o = off.L[l];
+        transpose(weights + o.Wqkv, wt + pack.WqkvT[l], 3 * c.d, c.d, st);
+        transpose(weights + o.W1, wt + pack.W1T[l], c.d_ff, c.d, st);
+        transpose(weights + o.W2, wt + pack.W2T[l], c.d, c.d_ff, st);
+        SG_CUDA_TRY(cudaMemcpyAsync(wt + pack.bqkv[l], weights + o.bqkv, (size_t)3 * c.d * f4,
+                                    cudaMemcpyDeviceToDevice, st));
+        SG_CUDA_TRY(cudaMemcpyAsync(wt + pack.b1[l], weights + o.b1, (size_t)c.d_ff * f4,
+                                    cudaMemcpyDeviceToDevice, st));
+        SG_CUDA_TRY(cudaMemcpyAsync(wt + pack.b2[l], weights + o.b2, (size_t)c.d * f4,
+                                    cudaMemcpyDeviceToDevice, st));
+    }
+    SG_TRY(check_launch("pack weights (no-alloc)"));
+#define SG_NA(DD, HH)                                                                          \
+    if (c.d == DD && dh == HH)                                                                 \
+        return run_decode_noalloc<DD, HH>(c, weights, off, pack, wt, kv, B, seed, stream_id,   \
+                                          flag_band, spins, logq, flags, st);
+    SG_NA(32, 8) SG_NA(32, 16) SG_NA(64, 8) SG_NA(64, 16) SG_NA(128, 16) SG_NA(128, 32)
+#undef SG_NA
+    return fail(SG_EUNSUPPORTED, "sg_sample_noalloc: unsupported (d, d_h)");
+}

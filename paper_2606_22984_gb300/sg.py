@@ -59,6 +59,8 @@ _SIGS = {
     "sg_adam_step": ([_P, _P, _P, _P, _I64, _F, _F, _F, _F, _I64, _P], _I32),
     "sg_last_error": ([], ctypes.c_char_p),
     "sg_launch_count": ([], _I64),
+    "sg_sample_noalloc": ([ctypes.POINTER(SgConfig), _P, _I64, _D, _U64, _U32, _F, _P, _P, _P,
+                           _P], _I32),
 }
 _lib = None
 
