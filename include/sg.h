@@ -118,6 +118,14 @@ float *sg_model_weights(sg_model *m);
 sg_status sg_model_refresh(sg_model *m, sg_stream stream);
 
 /*
+ * Synchronise stream and report the model's device error word, which kernels
+ * set instead of hanging or trapping: SG_ECUDA when a bounded wait inside a
+ * kernel gave up (the kernel stopped early; its outputs are invalid),
+ * SG_ENUMERIC when a non-finite logit was produced.  The word is cleared.
+ */
+sg_status sg_model_check(sg_model *m, sg_stream stream);
+
+/*
  * Batched ancestral sampling (Algorithm 2, KV-cache decode) of B
  * configurations in one persistent kernel launch.
  *   spins  dev int8 [B][N]   out: sampled spins.

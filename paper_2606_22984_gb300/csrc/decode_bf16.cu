@@ -1,0 +1,537 @@
+// decode_bf16.cu -- BF16 ancestral sampler (Algorithm 2, KV-cache sampling)
+// with the per-step GEMMs on the 5th-generation tensor cores (tcgen05).
+//
+// One CTA owns up to 128 samples (one MMA tile of M = 128 rows) for the
+// whole sequence.  Thread (row r, half hf) of the 256 threads keeps the FP32
+// residual stream h[r][32 hf .. 32 hf + 31] in registers.  Per step and layer:
+//   LN1 (row statistics exchanged through shared memory) -> BF16 A tile in
+//   shared memory -> tcgen05.mma QKV = A Wqkv^T (TMEM accumulators) ->
+//   tcgen05.ld, bias, append (k_t, v_t) in BF16 to the tile's KV ring in HBM
+//   -> attention of the thread's two heads over the visible keys, reading the
+//   ring straight from HBM with one key prefetched -> residual -> LN2 ->
+//   tcgen05.mma FFN1 -> GELU -> BF16 A2 tile -> tcgen05.mma FFN2 -> residual.
+// The output head and the draw u < sigmoid(l_t) run in registers.  Weights
+// are pre-packed in the operand layout of tc.cuh and streamed per layer into
+// three shared-memory buffers by 1D bulk copies (TMA), each refilled as soon
+// as the MMA that read it completes.  Every wait is bounded: on a timeout the
+// kernel records an error word, stops issuing work, drains what it issued and
+// frees its TMEM.
+//
+// KV ring layout per tile: [layer][slot][K|V][D/8][128 rows][8 bf16]; a warp
+// (32 consecutive rows) moves 512 contiguous bytes per 16-byte access.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "sg_internal.cuh"
+#include "tc.cuh"
+
+namespace sg {
+
+namespace {
+
+constexpr int kRows = 128;     // MMA M: samples per CTA tile
+constexpr int kThreads = 256;  // two threads per row
+
+struct Bf16Geom {
+    int nslots;
+    bool ring;
+};
+
+__host__ __device__ __forceinline__ Bf16Geom bgeom(int mask, int N, int W, int S)
+{
+    Bf16Geom g;
+    g.ring = mask == SG_MASK_BAND_SINK && (int64_t)S + W + 1 < N;
+    g.nslots = g.ring ? S + W + 1 : N;
+    return g;
+}
+
+__device__ __forceinline__ int bslot(const Bf16Geom &g, int S, int W, int k)
+{
+    return (!g.ring || k < S) ? k : S + (k - S) % (W + 1);
+}
+
+__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+
+__device__ __forceinline__ uint32_t pack_bf2(float a, float b)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+__device__ __forceinline__ float round_bf(float x) { return __bfloat162float(__float2bfloat16(x)); }
+
+// Pack W[rows][K] (fp32, row-major) into the bf16 core-matrix operand layout.
+__global__ void pack_cm_kernel(const float *__restrict__ W, __nv_bfloat16 *__restrict__ dst,
+                               int rows, int K)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)rows * K) return;
+    const int r = (int)(i / K), k = (int)(i % K);
+    dst[tc::cm_offset(r, k, K / 8) >> 1] = __float2bfloat16(W[i]);
+}
+
+struct DecodeArgs {
+    int N, L, dt, mask, W, S, dff;
+    int rows_per_cta;           // active rows per CTA (<= 128)
+    const float *w;             // master FP32 blob
+    const float *wt;            // packed FP32 (biases)
+    const unsigned char *bf;    // packed bf16 operands
+    size_t bf_layer_bytes;      // per-layer stride of the packed operands
+    BlobOff o;
+    PackOff p;
+    int64_t B;
+    uint64_t seed;
+    uint32_t sid;
+    float band;
+    int8_t *spins;
+    float *logq;
+    uint32_t *flags;
+    unsigned char *kv;          // KV ring workspace
+    int *err;                   // device error word
+};
+
+// Element (r, k) of a core-matrix tile as a 16-byte group store of 8 bf16.
+__device__ __forceinline__ void store8(unsigned char *tile, int r, int k0, int KG,
+                                       const float *v)
+{
+    uint4 q;
+    q.x = pack_bf2(v[0], v[1]);
+    q.y = pack_bf2(v[2], v[3]);
+    q.z = pack_bf2(v[4], v[5]);
+    q.w = pack_bf2(v[6], v[7]);
+    *reinterpret_cast<uint4 *>(tile + tc::cm_offset(r, k0, KG)) = q;
+}
+
+template <int D, int DFF>
+__global__ void __launch_bounds__(kThreads, 1) decode_bf16_kernel(const __grid_constant__ DecodeArgs a)
+{
+    static_assert(D == 64, "this build of the BF16 decode serves d = 64");
+    constexpr int DH = 16, HALF = D / 2, KG = D / 8, KG2 = DFF / 8;
+    constexpr uint32_t QKV_COL = 0, FF2_COL = 3 * D, FF1_COL = 256;
+    constexpr uint32_t A_BYTES = kRows * D * 2, A2_BYTES = kRows * DFF * 2;
+    constexpr uint32_t WQKV_BYTES = 3 * D * D * 2, W1_BYTES = DFF * D * 2, W2_BYTES = D * DFF * 2;
+    static_assert(3 * D <= 256 && DFF <= 256, "TMEM column plan");
+
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *Abuf = smem;
+    unsigned char *A2buf = Abuf + A_BYTES;
+    unsigned char *Wq = A2buf + A2_BYTES;
+    unsigned char *W1s = Wq + WQKV_BYTES;
+    unsigned char *W2s = W1s + W1_BYTES;
+    float *xln = reinterpret_cast<float *>(W2s + W2_BYTES);  // [2][128][2]
+    float *xhd = xln + 2 * kRows * 2;                          // [2][128][2]
+    __shared__ uint64_t wbar[3], mbar;
+    __shared__ uint32_t tslot;
+    __shared__ int s_err;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int r = 32 * (warp & 3) + lane, hf = warp >> 2;
+    const int64_t b = (int64_t)blockIdx.x * a.rows_per_cta + r;
+    const bool active = r < a.rows_per_cta && b < a.B;
+    const Bf16Geom g = bgeom(a.mask, a.N, a.W, a.S);
+    const size_t slot_bytes = (size_t)2 * D * kRows * 2;
+    const size_t layer_bytes = slot_bytes * g.nslots;
+    unsigned char *kvt = a.kv + (size_t)blockIdx.x * layer_bytes * a.L;
+    const int nfw = (a.N + 31) >> 5;
+    const uint32_t tq = (uint32_t)(32 * (warp & 3)) << 16;  // TMEM lane base of this warp
+
+    if (tid == 0) {
+        tc::mbar_init(&wbar[0], 1);
+        tc::mbar_init(&wbar[1], 1);
+        tc::mbar_init(&wbar[2], 1);
+        tc::mbar_init(&mbar, 1);
+        tc::fence_mbar_init();
+        s_err = 0;
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(&tslot, 512);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = tslot;
+
+    // weight streaming state (thread 0 only)
+    uint32_t wphase[3] = {0, 0, 0}, mphase = 0;
+    bool wpending[3] = {false, false, false};
+    auto issue = [&](int which, int layer) {
+        const unsigned char *src = a.bf + (size_t)layer * a.bf_layer_bytes;
+        unsigned char *dst = which == 0 ? Wq : (which == 1 ? W1s : W2s);
+        const uint32_t bytes = which == 0 ? WQKV_BYTES : (which == 1 ? W1_BYTES : W2_BYTES);
+        const size_t off = which == 0 ? 0 : (which == 1 ? WQKV_BYTES : WQKV_BYTES + W1_BYTES);
+        tc::mbar_arrive_expect_tx(&wbar[which], bytes);
+        tc::bulk_g2s(dst, src + off, bytes, &wbar[which]);
+        wpending[which] = true;
+    };
+    if (tid == 0) {
+        issue(0, 0);
+        issue(1, 0);
+        issue(2, 0);
+    }
+
+    float h[HALF];
+    float lq = 0.f;
+    int tok = 0;
+    const float qscale = 0.25f;  // 1 / sqrt(16)
+
+    // MMA helper run by thread 0: waits for the weights, issues the K steps,
+    // commits to mbar.  Every thread then waits on mbar.
+    auto gemm = [&](int which, const unsigned char *A, uint32_t a_kg, const unsigned char *Bw,
+                    uint32_t n, uint32_t k_total, uint32_t col) {
+        if (tid == 0) {
+            bool ok = s_err == 0 && tc::mbar_wait(&wbar[which], wphase[which]);
+            if (ok) {
+                wphase[which] ^= 1u;
+                wpending[which] = false;
+                tc::tc_fence_after();
+                const uint32_t idesc = tc::idesc_bf16(kRows, (int)n);
+                const uint32_t sa = tc::smem_u32(A), sb = tc::smem_u32(Bw);
+                for (uint32_t s = 0; s < k_total / 16; ++s)
+                    tc::mma_bf16(tmem + col, tc::smem_desc(sa + 256 * s, 128, a_kg * 128),
+                                 tc::smem_desc(sb + 256 * s, 128, a_kg * 128), idesc, s > 0);
+            } else {
+                atomicExch(a.err, 1);
+                s_err = 1;
+            }
+            tc::mma_commit(&mbar);
+        }
+        __syncwarp();
+        if (!tc::mbar_wait(&mbar, mphase)) {
+            if (lane == 0) atomicExch(a.err, 2);
+            s_err = 1;
+        }
+        mphase ^= 1u;
+        __syncthreads();  // makes s_err uniform before anyone branches on it
+        tc::tc_fence_after();
+    };
+
+    for (int t = 0; t < a.N && !s_err; ++t) {
+        // concatenated positional embedding
+        {
+            const float *pos = a.w + a.o.pos + (size_t)t * (D - a.dt);
+#pragma unroll
+            for (int j = 0; j < HALF; ++j) {
+                const int d = HALF * hf + j;
+                h[j] = d < a.dt ? __ldg(a.w + a.o.tok + tok * a.dt + d) : __ldg(pos + d - a.dt);
+            }
+        }
+        int n_sink, band_lo;
+        visible_ranges(a.mask, a.W, a.S, t, n_sink, band_lo);
+        const int slot_t = bslot(g, a.S, a.W, t);
+
+        for (int l = 0; l < a.L; ++l) {
+            const LayerOff &o = a.o.L[l];
+            const bool last = (t == a.N - 1) && (l == a.L - 1);
+            const int nl = l + 1 < a.L ? l + 1 : 0;  // layer of the next use of each buffer
+            // ---- LN1 -> A tile
+            auto layernorm_to = [&](const float *gam, const float *bet) {
+                float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+                for (int j = 0; j < HALF; ++j) {
+                    s1 += h[j];
+                    s2 += h[j] * h[j];
+                }
+                xln[(hf * kRows + r) * 2] = s1;
+                xln[(hf * kRows + r) * 2 + 1] = s2;
+                __syncthreads();
+                const float t1 = xln[r * 2] + xln[(kRows + r) * 2];
+                const float t2 = xln[r * 2 + 1] + xln[(kRows + r) * 2 + 1];
+                const float mean = t1 * (1.0f / D);
+                const float var = fmaxf(t2 * (1.0f / D) - mean * mean, 0.f);
+                const float rs = 1.0f / sqrtf(var + 1e-5f);
+#pragma unroll
+                for (int c = 0; c < HALF / 8; ++c) {
+                    float v[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int d = HALF * hf + 8 * c + j;
+                        v[j] = (h[8 * c + j] - mean) * rs * __ldg(gam + d) + __ldg(bet + d);
+                    }
+                    store8(Abuf, r, HALF * hf + 8 * c, KG, v);
+                }
+                tc::fence_async_smem();
+                tc::tc_fence_before();
+                __syncthreads();
+            };
+            layernorm_to(a.w + o.ln1g, a.w + o.ln1b);
+            gemm(0, Abuf, KG, Wq, 3 * D, D, QKV_COL);
+            if (tid == 0 && !last && !s_err) issue(0, nl);
+            if (s_err) break;
+            // ---- QKV epilogue: bias, KV append, attention of heads 2hf, 2hf+1
+            {
+                float q[HALF], kk[HALF], vv[HALF];
+                tc::tmem_ld32(tmem + tq + QKV_COL + HALF * hf, q);
+                tc::tmem_ld32(tmem + tq + QKV_COL + D + HALF * hf, kk);
+                tc::tmem_ld32(tmem + tq + QKV_COL + 2 * D + HALF * hf, vv);
+                tc::tmem_wait_ld();
+                const float *bq = a.wt + a.p.bqkv[l];
+#pragma unroll
+                for (int j = 0; j < HALF; ++j) {
+                    q[j] = (q[j] + __ldg(bq + HALF * hf + j)) * qscale;
+                    kk[j] = round_bf(kk[j] + __ldg(bq + D + HALF * hf + j));
+                    vv[j] = round_bf(vv[j] + __ldg(bq + 2 * D + HALF * hf + j));
+                }
+                unsigned char *kvl = kvt + (size_t)l * layer_bytes;
+                if (active) {
+                    uint4 *dk = reinterpret_cast<uint4 *>(kvl + (size_t)slot_t * slot_bytes);
+                    uint4 *dv = dk + (D / 8) * kRows;
+#pragma unroll
+                    for (int c = 0; c < HALF / 8; ++c) {
+                        uint4 x, y;
+                        x.x = pack_bf2(kk[8 * c], kk[8 * c + 1]);
+                        x.y = pack_bf2(kk[8 * c + 2], kk[8 * c + 3]);
+                        x.z = pack_bf2(kk[8 * c + 4], kk[8 * c + 5]);
+                        x.w = pack_bf2(kk[8 * c + 6], kk[8 * c + 7]);
+                        y.x = pack_bf2(vv[8 * c], vv[8 * c + 1]);
+                        y.y = pack_bf2(vv[8 * c + 2], vv[8 * c + 3]);
+                        y.z = pack_bf2(vv[8 * c + 4], vv[8 * c + 5]);
+                        y.w = pack_bf2(vv[8 * c + 6], vv[8 * c + 7]);
+                        dk[(4 * hf + c) * kRows + r] = x;
+                        dv[(4 * hf + c) * kRows + r] = y;
+                    }
+                }
+                // the current key from registers
+                float m0, m1, l0 = 1.f, l1 = 1.f, acc[HALF];
+                {
+                    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+                    for (int j = 0; j < DH; ++j) {
+                        s0 += q[j] * kk[j];
+                        s1 += q[DH + j] * kk[DH + j];
+                    }
+                    m0 = s0;
+                    m1 = s1;
+#pragma unroll
+                    for (int j = 0; j < HALF; ++j) acc[j] = vv[j];
+                }
+                const int nk = active ? n_sink + band_count(t, band_lo) - 1 : 0;  // keys < t
+                const uint4 *kb = reinterpret_cast<const uint4 *>(kvl) + (4 * hf) * kRows + r;
+                auto key_of = [&](int i) { return i < n_sink ? i : band_lo + (i - n_sink); };
+                uint4 ck[4], cv[4];
+                if (nk > 0) {
+                    const uint4 *p = kb + (size_t)bslot(g, a.S, a.W, key_of(0)) * (slot_bytes / 16);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        ck[c] = __ldcg(p + c * kRows);
+                        cv[c] = __ldcg(p + (D / 8) * kRows + c * kRows);
+                    }
+                }
+                for (int i = 0; i < nk; ++i) {
+                    uint4 nk4[4], nv4[4];
+                    if (i + 1 < nk) {
+                        const uint4 *p =
+                            kb + (size_t)bslot(g, a.S, a.W, key_of(i + 1)) * (slot_bytes / 16);
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            nk4[c] = __ldcg(p + c * kRows);
+                            nv4[c] = __ldcg(p + (D / 8) * kRows + c * kRows);
+                        }
+                    }
+                    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        const uint32_t w0[4] = {ck[c].x, ck[c].y, ck[c].z, ck[c].w};
+                        const uint32_t w1[4] = {ck[c + 2].x, ck[c + 2].y, ck[c + 2].z, ck[c + 2].w};
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            s0 += q[8 * c + 2 * j] * bf_lo(w0[j]) + q[8 * c + 2 * j + 1] * bf_hi(w0[j]);
+                            s1 += q[DH + 8 * c + 2 * j] * bf_lo(w1[j]) +
+                                  q[DH + 8 * c + 2 * j + 1] * bf_hi(w1[j]);
+                        }
+                    }
+                    const float n0 = fmaxf(m0, s0), n1 = fmaxf(m1, s1);
+                    const float c0 = __expf(m0 - n0), p0 = __expf(s0 - n0);
+                    const float c1 = __expf(m1 - n1), p1 = __expf(s1 - n1);
+                    m0 = n0;
+                    m1 = n1;
+                    l0 = l0 * c0 + p0;
+                    l1 = l1 * c1 + p1;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const uint32_t wv[4] = {cv[c].x, cv[c].y, cv[c].z, cv[c].w};
+                        const float cc = c < 2 ? c0 : c1, pp = c < 2 ? p0 : p1;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            acc[8 * c + 2 * j] = acc[8 * c + 2 * j] * cc + pp * bf_lo(wv[j]);
+                            acc[8 * c + 2 * j + 1] = acc[8 * c + 2 * j + 1] * cc + pp * bf_hi(wv[j]);
+                        }
+                    }
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        ck[c] = nk4[c];
+                        cv[c] = nv4[c];
+                    }
+                }
+                const float i0 = 1.0f / l0, i1 = 1.0f / l1;
+#pragma unroll
+                for (int j = 0; j < DH; ++j) {
+                    h[j] += acc[j] * i0;
+                    h[DH + j] += acc[DH + j] * i1;
+                }
+            }
+            // ---- LN2 -> A tile -> FFN1 -> GELU -> A2 tile -> FFN2
+            layernorm_to(a.w + o.ln2g, a.w + o.ln2b);
+            gemm(1, Abuf, KG, W1s, DFF, D, FF1_COL);
+            if (tid == 0 && !last && !s_err) issue(1, nl);
+            if (s_err) break;
+            {
+                const float *b1 = a.wt + a.p.b1[l];
+#pragma unroll
+                for (int c = 0; c < DFF / 2 / 32; ++c) {
+                    float v[32];
+                    tc::tmem_ld32(tmem + tq + FF1_COL + (DFF / 2) * hf + 32 * c, v);
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int g8 = 0; g8 < 4; ++g8) {
+                        float x[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const int col = (DFF / 2) * hf + 32 * c + 8 * g8 + j;
+                            x[j] = gelu_f(v[8 * g8 + j] + __ldg(b1 + col));
+                        }
+                        store8(A2buf, r, (DFF / 2) * hf + 32 * c + 8 * g8, KG2, x);
+                    }
+                }
+                tc::fence_async_smem();
+                tc::tc_fence_before();
+                __syncthreads();
+            }
+            gemm(2, A2buf, KG2, W2s, D, DFF, FF2_COL);
+            if (tid == 0 && !last && !s_err) issue(2, nl);
+            if (s_err) break;
+            {
+                float v[32];
+                tc::tmem_ld32(tmem + tq + FF2_COL + HALF * hf, v);
+                tc::tmem_wait_ld();
+                const float *b2 = a.wt + a.p.b2[l];
+#pragma unroll
+                for (int j = 0; j < HALF; ++j) h[j] += v[j] + __ldg(b2 + HALF * hf + j);
+            }
+        }
+        if (s_err) break;
+        // ---- output head and the draw
+        {
+            float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+            for (int j = 0; j < HALF; ++j) {
+                s1 += h[j];
+                s2 += h[j] * h[j];
+            }
+            xln[(hf * kRows + r) * 2] = s1;
+            xln[(hf * kRows + r) * 2 + 1] = s2;
+            __syncthreads();
+            const float mean = (xln[r * 2] + xln[(kRows + r) * 2]) * (1.0f / D);
+            const float var = fmaxf((xln[r * 2 + 1] + xln[(kRows + r) * 2 + 1]) * (1.0f / D) -
+                                        mean * mean, 0.f);
+            const float rs = 1.0f / sqrtf(var + 1e-5f);
+            float z0 = 0.f, z1 = 0.f;
+#pragma unroll
+            for (int j = 0; j < HALF; ++j) {
+                const int d = HALF * hf + j;
+                const float y = (h[j] - mean) * rs * __ldg(a.w + a.o.lnfg + d) + __ldg(a.w + a.o.lnfb + d);
+                z0 += y * __ldg(a.w + a.o.Wh + d);
+                z1 += y * __ldg(a.w + a.o.Wh + D + d);
+            }
+            xhd[(hf * kRows + r) * 2] = z0;
+            xhd[(hf * kRows + r) * 2 + 1] = z1;
+            __syncthreads();
+            if (hf == 0) {
+                z0 = xhd[r * 2] + xhd[(kRows + r) * 2] + __ldg(a.w + a.o.bh);
+                z1 = xhd[r * 2 + 1] + xhd[(kRows + r) * 2 + 1] + __ldg(a.w + a.o.bh + 1);
+                const float ell = z1 - z0;
+                const float p = 1.0f / (1.0f + expf(-ell));
+                const float u = philox_uniform(a.seed, (uint32_t)b, (uint32_t)t, a.sid, 0u);
+                const int sp = u < p ? 1 : -1;
+                lq += log_sigmoid_f((float)sp * ell);
+                tok = (sp + 1) >> 1;
+                if (active) {
+                    a.spins[(size_t)b * a.N + t] = (int8_t)sp;
+                    if (a.flags && fabsf(p - u) < a.band)
+                        a.flags[(size_t)b * nfw + (t >> 5)] |= 1u << (t & 31);
+                    if (!isfinite(ell)) atomicOr(a.err, 4);
+                }
+            }
+        }
+    }
+    if (hf == 0 && active) a.logq[b] = lq;
+    // drain: no bulk copy or MMA may be in flight when the CTA exits
+    if (tid == 0)
+        for (int i = 0; i < 3; ++i)
+            if (wpending[i] && !tc::mbar_wait(&wbar[i], wphase[i])) atomicExch(a.err, 3);
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+}  // namespace
+
+sg_status launch_pack_bf16(sg_model *m, cudaStream_t st)
+{
+    const sg_config &c = m->cfg;
+    const size_t per_layer = ((size_t)3 * c.d * c.d + 2 * (size_t)c.d_ff * c.d) * 2;
+    SG_TRY(ensure_buffer(&m->bf, &m->bf_bytes, per_layer * c.n_layers));
+    for (int l = 0; l < c.n_layers; ++l) {
+        __nv_bfloat16 *dst = reinterpret_cast<__nv_bfloat16 *>((unsigned char *)m->bf + per_layer * l);
+        const LayerOff &o = m->off.L[l];
+        const int64_t n1 = (int64_t)3 * c.d * c.d, n2 = (int64_t)c.d_ff * c.d;
+        pack_cm_kernel<<<(unsigned)((n1 + 255) / 256), 256, 0, ::sg::counted(st)>>>(m->w + o.Wqkv, dst, 3 * c.d, c.d);
+        pack_cm_kernel<<<(unsigned)((n2 + 255) / 256), 256, 0, ::sg::counted(st)>>>(m->w + o.W1, dst + n1, c.d_ff, c.d);
+        pack_cm_kernel<<<(unsigned)((n2 + 255) / 256), 256, 0, ::sg::counted(st)>>>(m->w + o.W2, dst + n1 + n2, c.d, c.d_ff);
+    }
+    return check_launch("pack bf16 operands");
+}
+
+sg_status launch_decode_bf16(sg_model *m, int64_t B, uint64_t seed, uint32_t sid, float band,
+                             int8_t *spins, float *logq, uint32_t *flags, cudaStream_t st)
+{
+    const sg_config &c = m->cfg;
+    if (!(c.d == 64 && c.n_heads == 4 && c.d_ff == 256 && c.d_token <= 32))
+        return fail(SG_EUNSUPPORTED, "BF16 decode is built for d = 64, 4 heads, d_ff = 256");
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // spread the batch over every SM: rows per CTA = ceil(B / SMs), at most 128
+    int rows = (int)std::min<int64_t>(kRows, (B + sms - 1) / sms);
+    rows = std::max(rows, 1);
+    const int64_t tiles = (B + rows - 1) / rows;
+    const Bf16Geom g = bgeom(c.mask_kind, c.N, c.W, c.S);
+    const size_t kv_bytes = (size_t)tiles * c.n_layers * g.nslots * 2 * c.d * kRows * 2;
+    SG_TRY(ensure_buffer(&m->kv, &m->kv_bytes, kv_bytes));
+    SG_TRY(ensure_buffer(&m->err, &m->err_bytes, sizeof(int)));
+    const size_t smem = (size_t)kRows * c.d * 2 + (size_t)kRows * c.d_ff * 2 +
+                        (size_t)3 * c.d * c.d * 2 + 2 * (size_t)c.d_ff * c.d * 2 +
+                        4 * kRows * 2 * sizeof(float);
+    auto kern = decode_bf16_kernel<64, 256>;
+    SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    DecodeArgs a{};
+    a.N = c.N;
+    a.L = c.n_layers;
+    a.dt = c.d_token;
+    a.mask = c.mask_kind;
+    a.W = c.W;
+    a.S = c.S;
+    a.dff = c.d_ff;
+    a.rows_per_cta = rows;
+    a.w = m->w;
+    a.wt = m->wt;
+    a.bf = (const unsigned char *)m->bf;
+    a.bf_layer_bytes = ((size_t)3 * c.d * c.d + 2 * (size_t)c.d_ff * c.d) * 2;
+    a.o = m->off;
+    a.p = m->pack;
+    a.B = B;
+    a.seed = seed;
+    a.sid = sid;
+    a.band = band;
+    a.spins = spins;
+    a.logq = logq;
+    a.flags = flags;
+    a.kv = (unsigned char *)m->kv;
+    a.err = (int *)m->err;
+    kern<<<(unsigned)tiles, kThreads, smem, ::sg::counted(st)>>>(a);
+    return check_launch("decode_bf16_kernel");
+}
+
+}  // namespace sg

@@ -163,6 +163,9 @@ sg_status sg_model_create(const sg_config *cfg, const float *weights_host, int64
     if (s == SG_OK && cudaMemcpy(m->w, weights_host, (size_t)P * sizeof(float),
                                  cudaMemcpyHostToDevice) != cudaSuccess)
         s = fail(SG_ECUDA, "copying weights to the device failed");
+    if (s == SG_OK) s = ensure_buffer(&m->err, &m->err_bytes, sizeof(int));
+    if (s == SG_OK && cudaMemset(m->err, 0, sizeof(int)) != cudaSuccess)
+        s = fail(SG_ECUDA, "clearing the error word failed");
     if (s == SG_OK) s = sg_model_refresh(m, nullptr);
     if (s == SG_OK && cudaDeviceSynchronize() != cudaSuccess)
         s = fail(SG_ECUDA, "model set-up failed on the device");
@@ -183,6 +186,7 @@ sg_status sg_model_destroy(sg_model *m)
     cudaFree(m->bf);
     cudaFree(m->kv);
     cudaFree(m->ws);
+    cudaFree(m->err);
     delete m;
     return SG_OK;
 }
@@ -192,7 +196,22 @@ float *sg_model_weights(sg_model *m) { return m ? m->w : nullptr; }
 sg_status sg_model_refresh(sg_model *m, sg_stream stream)
 {
     if (!m) return fail(SG_EINVAL, "NULL model");
-    return launch_pack_f32(m, (cudaStream_t)stream);
+    SG_TRY(launch_pack_f32(m, (cudaStream_t)stream));
+    if (m->cfg.precision == SG_BF16) SG_TRY(launch_pack_bf16(m, (cudaStream_t)stream));
+    return SG_OK;
+}
+
+sg_status sg_model_check(sg_model *m, sg_stream stream)
+{
+    if (!m) return fail(SG_EINVAL, "NULL model");
+    SG_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    int e = 0;
+    SG_CUDA_TRY(cudaMemcpy(&e, m->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!e) return SG_OK;
+    SG_CUDA_TRY(cudaMemset(m->err, 0, sizeof(int)));
+    if (e & 4) return fail(SG_ENUMERIC, "a kernel produced a non-finite logit");
+    return fail(SG_ECUDA, "a kernel gave up a bounded wait (code " + std::to_string(e) +
+                              "); its outputs are not valid");
 }
 
 sg_status sg_sample(sg_model *m, int64_t B, double beta, uint64_t seed, uint32_t stream_id,
@@ -206,6 +225,8 @@ sg_status sg_sample(sg_model *m, int64_t B, double beta, uint64_t seed, uint32_t
     if (flags)
         SG_CUDA_TRY(cudaMemsetAsync(flags, 0,
                                     (size_t)B * ((m->cfg.N + 31) / 32) * sizeof(uint32_t), st));
+    if (m->cfg.precision == SG_BF16)
+        return launch_decode_bf16(m, B, seed, stream_id, flag_band, spins, logq, flags, st);
     return launch_decode_f32(m, B, seed, stream_id, flag_band, spins, logq, flags, st);
 }
 

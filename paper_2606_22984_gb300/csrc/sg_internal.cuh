@@ -165,6 +165,8 @@ struct sg_model {
     size_t kv_bytes = 0;
     void *ws = nullptr;       // prefill / backward workspace
     size_t ws_bytes = 0;
+    void *err = nullptr;      // device error word written by kernels (bounded waits, NaN)
+    size_t err_bytes = 0;
 };
 
 struct sg_instance {
@@ -180,6 +182,9 @@ sg_status ensure_buffer(void **ptr, size_t *have, size_t need);
 
 // Launchers implemented in the kernel translation units.
 sg_status launch_pack_f32(sg_model *m, cudaStream_t st);
+sg_status launch_pack_bf16(sg_model *m, cudaStream_t st);
+sg_status launch_decode_bf16(sg_model *m, int64_t B, uint64_t seed, uint32_t sid, float band,
+                             int8_t *spins, float *logq, uint32_t *flags, cudaStream_t st);
 sg_status launch_decode_f32(sg_model *m, int64_t B, uint64_t seed, uint32_t sid, float band,
                             int8_t *spins, float *logq, uint32_t *flags, cudaStream_t st);
 sg_status launch_logprob_f32(sg_model *m, const int8_t *spins, int64_t B, float *logq,

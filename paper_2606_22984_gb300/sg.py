@@ -46,6 +46,7 @@ _SIGS = {
     "sg_model_destroy": ([_P], _I32),
     "sg_model_weights": ([_P], _P),
     "sg_model_refresh": ([_P, _P], _I32),
+    "sg_model_check": ([_P, _P], _I32),
     "sg_sample": ([_P, _I64, _D, _U64, _U32, _F, _P, _P, _P, _P], _I32),
     "sg_logprob": ([_P, _P, _I64, _P, _P], _I32),
     "sg_grad": ([_P, _P, _P, _I64, _P, _P, _P], _I32),
@@ -153,6 +154,10 @@ class Model:
 
     def refresh(self, stream=None):
         _check("sg_model_refresh", lib().sg_model_refresh(self.handle, _stream(stream)))
+
+    def check(self, stream=None):
+        """Synchronise and raise if a kernel recorded a bounded-wait timeout or NaN."""
+        _check("sg_model_check", lib().sg_model_check(self.handle, _stream(stream)))
 
     def sample(self, B, seed, stream_id=0, beta=1.0, flag_band=0.0, with_flags=False,
                spins=None, logq=None, stream=None):

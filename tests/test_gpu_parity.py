@@ -66,6 +66,47 @@ def test_fp32_sampling_matches_oracle(name):
     assert frac < 0.01
 
 
+BF16_CASES = {
+    "ea6_ring": (inputs.ModelShape(36, 2, 64, 4, mask_kind=1, W=6, S=7), 200, 1.0),
+    "dense_n40": (inputs.ModelShape(40, 3, 64, 4), 300, 1.0),
+    "single_spin": (inputs.ModelShape(1, 1, 64, 4), 5, 1.0),
+    "band_W0_S0": (inputs.ModelShape(17, 2, 64, 4, mask_kind=1, W=0, S=0), 129, 1.0),
+    "short_sink": (inputs.ModelShape(20, 2, 64, 4, mask_kind=1, W=3, S=30), 64, 1.0),
+}
+
+
+@pytest.mark.parametrize("name", list(BF16_CASES))
+def test_bf16_sampling_matches_oracle(name):
+    """BF16 decode on tcgen05: spins equal to the oracle once the draws inside
+    the BF16 flag band (|p+ - u| < 1e-2) replay the GPU's decision; per-sample
+    |delta log q| <= 2e-2 N."""
+    m, B, scale = BF16_CASES[name]
+    w = inputs.make_weights(m, 7, scale)
+    model, _, _, frac, dl = _sample_and_check(m, w, B, 4321, sg.SG_BF16, BF16_LOGQ_TOL)
+    model.check()
+    assert frac < 0.05
+    print(f"{name}: flagged {frac:.4f} of draws, max |dlogq|/N {dl.max() / m.N:.2e}")
+
+
+def test_full_size_ea2d16_bf16_sampled_rows():
+    wl = inputs.workloads()["ea2d16"]
+    m = wl.model
+    w = wl.weights()
+    model = sg.Model(m, w, sg.SG_BF16)
+    spins, logq, flags = model.sample(wl.B, seed=77, with_flags=True)
+    model.check()
+    s, lq, fl = _np(spins), _np(logq), _np(flags)
+    rows = np.array([0, 107, 108, 5000, 9999, wl.B - 1])
+    so, lqo, _, _ = oracle_replay(m, w, 77, s, fl, rows=rows)
+    assert np.array_equal(so, s[rows])
+    assert np.abs(lqo - lq[rows]).max() <= BF16_LOGQ_TOL * m.N
+    assert unpack_flags(fl, m.N).mean() < 0.05
+    # BF16 sampled log q against the FP32 teacher-forced log q of the same spins
+    m32 = sg.Model(m, w, sg.SG_FP32)
+    tf = _np(m32.logprob(spins[:512]))
+    assert np.abs(tf - lq[:512]).max() <= BF16_LOGQ_TOL * m.N
+
+
 @pytest.mark.parametrize("name", ["sk20_dense", "ea6_ring", "dense_d128_h8", "d64_h8_ring"])
 def test_fp32_teacher_forced_logq_matches_oracle_and_sampler(name):
     m, B, scale = SAMPLE_CASES[name]
