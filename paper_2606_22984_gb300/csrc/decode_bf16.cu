@@ -466,11 +466,416 @@ __global__ void __launch_bounds__(kThreads, 1) decode_bf16_kernel(const __grid_c
     if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
+// ---------------------------------------------------------------------------
+// d = 128 variant (8 heads of 16, d_ff = 512).  512 threads: thread (row r,
+// quarter qr) keeps h[r][32 qr .. 32 qr + 31] and serves heads 2 qr, 2 qr + 1
+// one after the other.  Weights are too large to hold per layer, so every
+// layer is streamed as 11 chunks of 32 KB ([128 out rows x 128 K] operands):
+// Wq, Wk, Wv, then (W1 rows 128j..) and (W2 K-slice 128j..) for j = 0..3,
+// through a 3-stage ring of bulk copies.  TMEM: QKV at columns [0, 384), the
+// FFN1 slice at [0, 128), the FFN2 accumulator at [384, 512).
+// ---------------------------------------------------------------------------
+constexpr int kChunkBytes = 128 * 128 * 2;
+constexpr int kChunksPerLayer = 11;
+constexpr int kStages = 3;
+
+// chunk c of a layer, element (r, k) of the [128 x 128] operand
+__global__ void pack_chunks128_kernel(const float *__restrict__ Wqkv,
+                                      const float *__restrict__ W1,
+                                      const float *__restrict__ W2, __nv_bfloat16 *__restrict__ dst)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)kChunksPerLayer * 128 * 128) return;
+    const int c = (int)(i / (128 * 128)), r = (int)((i / 128) % 128), k = (int)(i % 128);
+    float v;
+    if (c < 3) v = Wqkv[(size_t)(128 * c + r) * 128 + k];
+    else if ((c - 3) % 2 == 0) v = W1[(size_t)(128 * ((c - 3) / 2) + r) * 128 + k];
+    else v = W2[(size_t)r * 512 + 128 * ((c - 4) / 2) + k];
+    dst[(size_t)c * (kChunkBytes / 2) + (tc::cm_offset(r, k, 16) >> 1)] = __float2bfloat16(v);
+}
+
+__global__ void __launch_bounds__(512, 1) decode_bf16_d128_kernel(const __grid_constant__ DecodeArgs a)
+{
+    constexpr int D = 128, DH = 16, Q32 = 32, KG = D / 8;
+    constexpr uint32_t QKV_COL = 0, FF1_COL = 0, FF2_COL = 384;
+    constexpr uint32_t A_BYTES = kRows * D * 2;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *Abuf = smem;
+    unsigned char *A2buf = Abuf + A_BYTES;
+    unsigned char *ring = A2buf + A_BYTES;
+    float *xln = reinterpret_cast<float *>(ring + kStages * kChunkBytes);  // [4][128][2]
+    float *xhd = xln + 4 * kRows * 2;                                     // [4][128][2]
+    __shared__ uint64_t full[kStages], mbar;
+    __shared__ uint32_t tslot;
+    __shared__ int s_err;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int r = 32 * (warp & 3) + lane, qr = warp >> 2;
+    const int64_t b = (int64_t)blockIdx.x * a.rows_per_cta + r;
+    const bool active = r < a.rows_per_cta && b < a.B;
+    const Bf16Geom g = bgeom(a.mask, a.N, a.W, a.S);
+    const size_t slot_bytes = (size_t)2 * D * kRows * 2;
+    const size_t layer_bytes = slot_bytes * g.nslots;
+    unsigned char *kvt = a.kv + (size_t)blockIdx.x * layer_bytes * a.L;
+    const int nfw = (a.N + 31) >> 5;
+    const uint32_t tq = (uint32_t)(32 * (warp & 3)) << 16;
+    const int64_t total_chunks = (int64_t)a.N * a.L * kChunksPerLayer;
+
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) tc::mbar_init(&full[s], 1);
+        tc::mbar_init(&mbar, 1);
+        tc::fence_mbar_init();
+        s_err = 0;
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(&tslot, 512);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = tslot;
+
+    // chunk stream state (thread 0): chunk gidx lives in stage gidx % kStages
+    int64_t next_load = 0, next_use = 0;
+    uint32_t fphase[kStages] = {0, 0, 0}, mphase = 0;
+    auto load_more = [&]() {
+        while (next_load < total_chunks && next_load < next_use + kStages) {
+            const int s = (int)(next_load % kStages);
+            const int64_t lc = next_load % ((int64_t)a.L * kChunksPerLayer);
+            tc::mbar_arrive_expect_tx(&full[s], kChunkBytes);
+            tc::bulk_g2s(ring + (size_t)s * kChunkBytes, a.bf + (size_t)lc * kChunkBytes,
+                         kChunkBytes, &full[s]);
+            ++next_load;
+        }
+    };
+    if (tid == 0) load_more();
+
+    // MMAs of `nchunks` consecutive chunks, chunk i into TMEM column col + i*col_step
+    // (accumulating over chunks when col_step == 0), then one commit; all wait.
+    auto run_chunks = [&](const unsigned char *A, int nchunks, uint32_t col, uint32_t col_step,
+                          bool accumulate_first) {
+        if (tid == 0) {
+            bool ok = s_err == 0;
+            for (int i = 0; i < nchunks && ok; ++i) {
+                const int s = (int)(next_use % kStages);
+                ok = tc::mbar_wait(&full[s], fphase[s]);
+                if (!ok) break;
+                fphase[s] ^= 1u;
+                tc::tc_fence_after();
+                const uint32_t sa = tc::smem_u32(A), sb = tc::smem_u32(ring + (size_t)s * kChunkBytes);
+                const uint32_t idesc = tc::idesc_bf16(kRows, 128);
+                for (int k = 0; k < 8; ++k)
+                    tc::mma_bf16(tmem + col + i * col_step, tc::smem_desc(sa + 256 * k, 128, KG * 128),
+                                 tc::smem_desc(sb + 256 * k, 128, KG * 128), idesc,
+                                 (k > 0 || (i > 0 && col_step == 0) || accumulate_first) ? 1u : 0u);
+                ++next_use;
+            }
+            if (!ok) {
+                atomicExch(a.err, 1);
+                s_err = 1;
+            }
+            tc::mma_commit(&mbar);
+        }
+        __syncwarp();
+        if (!tc::mbar_wait(&mbar, mphase)) {
+            if (lane == 0) atomicExch(a.err, 2);
+            s_err = 1;
+        }
+        mphase ^= 1u;
+        __syncthreads();
+        tc::tc_fence_after();
+        if (tid == 0 && !s_err) load_more();  // stages of completed MMAs are free
+    };
+
+    float h[Q32];
+    auto layernorm_to = [&](const float *gam, const float *bet) {
+        float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+        for (int j = 0; j < Q32; ++j) {
+            s1 += h[j];
+            s2 += h[j] * h[j];
+        }
+        xln[(qr * kRows + r) * 2] = s1;
+        xln[(qr * kRows + r) * 2 + 1] = s2;
+        __syncthreads();
+        float t1 = 0.f, t2 = 0.f;
+#pragma unroll
+        for (int q4 = 0; q4 < 4; ++q4) {
+            t1 += xln[(q4 * kRows + r) * 2];
+            t2 += xln[(q4 * kRows + r) * 2 + 1];
+        }
+        const float mean = t1 * (1.0f / D);
+        const float var = fmaxf(t2 * (1.0f / D) - mean * mean, 0.f);
+        const float rs = 1.0f / sqrtf(var + 1e-5f);
+#pragma unroll
+        for (int c = 0; c < Q32 / 8; ++c) {
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int d = Q32 * qr + 8 * c + j;
+                v[j] = (h[8 * c + j] - mean) * rs * __ldg(gam + d) + __ldg(bet + d);
+            }
+            store8(Abuf, r, Q32 * qr + 8 * c, KG, v);
+        }
+        tc::fence_async_smem();
+        tc::tc_fence_before();
+        __syncthreads();
+    };
+
+    float lq = 0.f;
+    int tok = 0;
+    const float qscale = 0.25f;
+
+    for (int t = 0; t < a.N && !s_err; ++t) {
+        {
+            const float *pos = a.w + a.o.pos + (size_t)t * (D - a.dt);
+#pragma unroll
+            for (int j = 0; j < Q32; ++j) {
+                const int d = Q32 * qr + j;
+                h[j] = d < a.dt ? __ldg(a.w + a.o.tok + tok * a.dt + d) : __ldg(pos + d - a.dt);
+            }
+        }
+        int n_sink, band_lo;
+        visible_ranges(a.mask, a.W, a.S, t, n_sink, band_lo);
+        const int slot_t = bslot(g, a.S, a.W, t);
+        const int nk = active ? n_sink + band_count(t, band_lo) - 1 : 0;  // keys < t
+        for (int l = 0; l < a.L; ++l) {
+            const LayerOff &o = a.o.L[l];
+            layernorm_to(a.w + o.ln1g, a.w + o.ln1b);
+            run_chunks(Abuf, 3, QKV_COL, 128, false);
+            if (s_err) break;
+            unsigned char *kvl = kvt + (size_t)l * layer_bytes;
+            {
+                const float *bq = a.wt + a.p.bqkv[l];
+                // append k_t, v_t (this thread's 32 dims) to the ring
+                float kk[Q32];
+                tc::tmem_ld32(tmem + tq + QKV_COL + D + Q32 * qr, kk);
+                tc::tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < Q32; ++j) kk[j] = round_bf(kk[j] + __ldg(bq + D + Q32 * qr + j));
+                uint4 *dk = reinterpret_cast<uint4 *>(kvl + (size_t)slot_t * slot_bytes);
+                if (active)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        uint4 x;
+                        x.x = pack_bf2(kk[8 * c], kk[8 * c + 1]);
+                        x.y = pack_bf2(kk[8 * c + 2], kk[8 * c + 3]);
+                        x.z = pack_bf2(kk[8 * c + 4], kk[8 * c + 5]);
+                        x.w = pack_bf2(kk[8 * c + 6], kk[8 * c + 7]);
+                        dk[(4 * qr + c) * kRows + r] = x;
+                    }
+                tc::tmem_ld32(tmem + tq + QKV_COL + 2 * D + Q32 * qr, kk);  // now v_t
+                tc::tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < Q32; ++j) kk[j] = round_bf(kk[j] + __ldg(bq + 2 * D + Q32 * qr + j));
+                uint4 *dv = dk + (D / 8) * kRows;
+                if (active)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        uint4 x;
+                        x.x = pack_bf2(kk[8 * c], kk[8 * c + 1]);
+                        x.y = pack_bf2(kk[8 * c + 2], kk[8 * c + 3]);
+                        x.z = pack_bf2(kk[8 * c + 4], kk[8 * c + 5]);
+                        x.w = pack_bf2(kk[8 * c + 6], kk[8 * c + 7]);
+                        dv[(4 * qr + c) * kRows + r] = x;
+                    }
+                // attention, one head at a time; the current key comes from registers
+#pragma unroll 1
+                for (int p = 0; p < 2; ++p) {
+                    const int hh = 2 * qr + p;
+                    float q[DH], acc[DH];
+                    __syncwarp();
+                    tc::tmem_ld32(tmem + tq + QKV_COL + Q32 * qr, kk);  // q of both heads
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < DH; ++j)
+                        q[j] = (kk[DH * p + j] + __ldg(bq + DH * hh + j)) * qscale;
+                    // the current key and value, rounded to BF16 as stored
+                    tc::tmem_ld32(tmem + tq + QKV_COL + D + Q32 * qr, kk);
+                    tc::tmem_wait_ld();
+                    float m0 = 0.f, l0 = 1.f;
+#pragma unroll
+                    for (int j = 0; j < DH; ++j)
+                        m0 += q[j] * round_bf(kk[DH * p + j] + __ldg(bq + D + DH * hh + j));
+                    tc::tmem_ld32(tmem + tq + QKV_COL + 2 * D + Q32 * qr, kk);
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < DH; ++j)
+                        acc[j] = round_bf(kk[DH * p + j] + __ldg(bq + 2 * D + DH * hh + j));
+                    const uint4 *kb = reinterpret_cast<const uint4 *>(kvl) + (2 * hh) * kRows + r;
+                    auto key_of = [&](int i) { return i < n_sink ? i : band_lo + (i - n_sink); };
+                    uint4 ck[2], cv[2];
+                    if (nk > 0) {
+                        const uint4 *pp = kb + (size_t)bslot(g, a.S, a.W, key_of(0)) * (slot_bytes / 16);
+                        ck[0] = __ldcg(pp);
+                        ck[1] = __ldcg(pp + kRows);
+                        cv[0] = __ldcg(pp + (D / 8) * kRows);
+                        cv[1] = __ldcg(pp + (D / 8) * kRows + kRows);
+                    }
+                    for (int i = 0; i < nk; ++i) {
+                        uint4 nk2[2], nv2[2];
+                        if (i + 1 < nk) {
+                            const uint4 *pp =
+                                kb + (size_t)bslot(g, a.S, a.W, key_of(i + 1)) * (slot_bytes / 16);
+                            nk2[0] = __ldcg(pp);
+                            nk2[1] = __ldcg(pp + kRows);
+                            nv2[0] = __ldcg(pp + (D / 8) * kRows);
+                            nv2[1] = __ldcg(pp + (D / 8) * kRows + kRows);
+                        }
+                        float s = 0.f;
+#pragma unroll
+                        for (int c = 0; c < 2; ++c) {
+                            const uint32_t wk[4] = {ck[c].x, ck[c].y, ck[c].z, ck[c].w};
+#pragma unroll
+                            for (int j = 0; j < 4; ++j)
+                                s += q[8 * c + 2 * j] * bf_lo(wk[j]) + q[8 * c + 2 * j + 1] * bf_hi(wk[j]);
+                        }
+                        const float n0 = fmaxf(m0, s);
+                        const float c0 = __expf(m0 - n0), p0 = __expf(s - n0);
+                        m0 = n0;
+                        l0 = l0 * c0 + p0;
+#pragma unroll
+                        for (int c = 0; c < 2; ++c) {
+                            const uint32_t wv[4] = {cv[c].x, cv[c].y, cv[c].z, cv[c].w};
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                acc[8 * c + 2 * j] = acc[8 * c + 2 * j] * c0 + p0 * bf_lo(wv[j]);
+                                acc[8 * c + 2 * j + 1] = acc[8 * c + 2 * j + 1] * c0 + p0 * bf_hi(wv[j]);
+                            }
+                        }
+                        ck[0] = nk2[0];
+                        ck[1] = nk2[1];
+                        cv[0] = nv2[0];
+                        cv[1] = nv2[1];
+                    }
+                    const float inv = 1.0f / l0;
+#pragma unroll
+                    for (int j = 0; j < DH; ++j) h[DH * p + j] += acc[j] * inv;
+                }
+            }
+            layernorm_to(a.w + o.ln2g, a.w + o.ln2b);
+            const float *b1 = a.wt + a.p.b1[l];
+            for (int j = 0; j < 4 && !s_err; ++j) {
+                run_chunks(Abuf, 1, FF1_COL, 0, false);
+                if (s_err) break;
+                {
+                    float v[32];
+                    tc::tmem_ld32(tmem + tq + FF1_COL + Q32 * qr, v);
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int g8 = 0; g8 < 4; ++g8) {
+                        float x[8];
+#pragma unroll
+                        for (int jj = 0; jj < 8; ++jj)
+                            x[jj] = gelu_f(v[8 * g8 + jj] + __ldg(b1 + 128 * j + Q32 * qr + 8 * g8 + jj));
+                        store8(A2buf, r, Q32 * qr + 8 * g8, KG, x);
+                    }
+                    tc::fence_async_smem();
+                    tc::tc_fence_before();
+                    __syncthreads();
+                }
+                run_chunks(A2buf, 1, FF2_COL, 0, j > 0);
+            }
+            if (s_err) break;
+            {
+                float v[32];
+                tc::tmem_ld32(tmem + tq + FF2_COL + Q32 * qr, v);
+                tc::tmem_wait_ld();
+                const float *b2 = a.wt + a.p.b2[l];
+#pragma unroll
+                for (int j = 0; j < Q32; ++j) h[j] += v[j] + __ldg(b2 + Q32 * qr + j);
+            }
+        }
+        if (s_err) break;
+        {
+            float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+            for (int j = 0; j < Q32; ++j) {
+                s1 += h[j];
+                s2 += h[j] * h[j];
+            }
+            xln[(qr * kRows + r) * 2] = s1;
+            xln[(qr * kRows + r) * 2 + 1] = s2;
+            __syncthreads();
+            float t1 = 0.f, t2 = 0.f;
+#pragma unroll
+            for (int q4 = 0; q4 < 4; ++q4) {
+                t1 += xln[(q4 * kRows + r) * 2];
+                t2 += xln[(q4 * kRows + r) * 2 + 1];
+            }
+            const float mean = t1 * (1.0f / D);
+            const float var = fmaxf(t2 * (1.0f / D) - mean * mean, 0.f);
+            const float rs = 1.0f / sqrtf(var + 1e-5f);
+            float z0 = 0.f, z1 = 0.f;
+#pragma unroll
+            for (int j = 0; j < Q32; ++j) {
+                const int d = Q32 * qr + j;
+                const float y = (h[j] - mean) * rs * __ldg(a.w + a.o.lnfg + d) + __ldg(a.w + a.o.lnfb + d);
+                z0 += y * __ldg(a.w + a.o.Wh + d);
+                z1 += y * __ldg(a.w + a.o.Wh + D + d);
+            }
+            xhd[(qr * kRows + r) * 2] = z0;
+            xhd[(qr * kRows + r) * 2 + 1] = z1;
+            __syncthreads();
+            if (qr == 0) {
+                z0 = __ldg(a.w + a.o.bh);
+                z1 = __ldg(a.w + a.o.bh + 1);
+#pragma unroll
+                for (int q4 = 0; q4 < 4; ++q4) {
+                    z0 += xhd[(q4 * kRows + r) * 2];
+                    z1 += xhd[(q4 * kRows + r) * 2 + 1];
+                }
+                const float ell = z1 - z0;
+                const float p = 1.0f / (1.0f + expf(-ell));
+                const float u = philox_uniform(a.seed, (uint32_t)b, (uint32_t)t, a.sid, 0u);
+                const int sp = u < p ? 1 : -1;
+                lq += log_sigmoid_f((float)sp * ell);
+                tok = (sp + 1) >> 1;
+                if (active) {
+                    a.spins[(size_t)b * a.N + t] = (int8_t)sp;
+                    if (a.flags && fabsf(p - u) < a.band)
+                        a.flags[(size_t)b * nfw + (t >> 5)] |= 1u << (t & 31);
+                    if (!isfinite(ell)) atomicOr(a.err, 4);
+                }
+            }
+        }
+    }
+    if (qr == 0 && active) a.logq[b] = lq;
+    // drain the bulk copies still in flight before the CTA exits
+    if (tid == 0)
+        while (next_use < next_load) {
+            const int s = (int)(next_use % kStages);
+            if (!tc::mbar_wait(&full[s], fphase[s])) {
+                atomicExch(a.err, 3);
+                break;
+            }
+            fphase[s] ^= 1u;
+            ++next_use;
+        }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
 }  // namespace
 
 sg_status launch_pack_bf16(sg_model *m, cudaStream_t st)
 {
     const sg_config &c = m->cfg;
+    if (c.d == 128) {
+        const size_t per_layer = (size_t)kChunksPerLayer * kChunkBytes;
+        SG_TRY(ensure_buffer(&m->bf, &m->bf_bytes, per_layer * c.n_layers));
+        if (c.d_ff != 512) return SG_OK;  // the d = 128 decode needs d_ff = 512
+        const int64_t n = (int64_t)kChunksPerLayer * 128 * 128;
+        for (int l = 0; l < c.n_layers; ++l) {
+            const LayerOff &o = m->off.L[l];
+            pack_chunks128_kernel<<<(unsigned)((n + 255) / 256), 256, 0, ::sg::counted(st)>>>(
+                m->w + o.Wqkv, m->w + o.W1, m->w + o.W2,
+                reinterpret_cast<__nv_bfloat16 *>((unsigned char *)m->bf + per_layer * l));
+        }
+        return check_launch("pack bf16 chunks (d = 128)");
+    }
     const size_t per_layer = ((size_t)3 * c.d * c.d + 2 * (size_t)c.d_ff * c.d) * 2;
     SG_TRY(ensure_buffer(&m->bf, &m->bf_bytes, per_layer * c.n_layers));
     for (int l = 0; l < c.n_layers; ++l) {
@@ -488,8 +893,11 @@ sg_status launch_decode_bf16(sg_model *m, int64_t B, uint64_t seed, uint32_t sid
                              int8_t *spins, float *logq, uint32_t *flags, cudaStream_t st)
 {
     const sg_config &c = m->cfg;
-    if (!(c.d == 64 && c.n_heads == 4 && c.d_ff == 256 && c.d_token <= 32))
-        return fail(SG_EUNSUPPORTED, "BF16 decode is built for d = 64, 4 heads, d_ff = 256");
+    const bool d64 = c.d == 64 && c.n_heads == 4 && c.d_ff == 256 && c.d_token <= 32;
+    const bool d128 = c.d == 128 && c.n_heads == 8 && c.d_ff == 512 && c.d_token <= 32;
+    if (!d64 && !d128)
+        return fail(SG_EUNSUPPORTED, "BF16 decode is built for (d, heads, d_ff) = (64, 4, 256) "
+                                     "and (128, 8, 512)");
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -505,7 +913,6 @@ sg_status launch_decode_bf16(sg_model *m, int64_t B, uint64_t seed, uint32_t sid
                         (size_t)3 * c.d * c.d * 2 + 2 * (size_t)c.d_ff * c.d * 2 +
                         4 * kRows * 2 * sizeof(float);
     auto kern = decode_bf16_kernel<64, 256>;
-    SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     DecodeArgs a{};
     a.N = c.N;
     a.L = c.n_layers;
@@ -530,6 +937,15 @@ sg_status launch_decode_bf16(sg_model *m, int64_t B, uint64_t seed, uint32_t sid
     a.flags = flags;
     a.kv = (unsigned char *)m->kv;
     a.err = (int *)m->err;
+    if (d128) {
+        const size_t smem128 = 2 * (size_t)kRows * 128 * 2 + (size_t)kStages * kChunkBytes +
+                               8 * kRows * 2 * sizeof(float);
+        SG_CUDA_TRY(cudaFuncSetAttribute(decode_bf16_d128_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem128));
+        decode_bf16_d128_kernel<<<(unsigned)tiles, 512, smem128, ::sg::counted(st)>>>(a);
+        return check_launch("decode_bf16_d128_kernel");
+    }
+    SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<(unsigned)tiles, kThreads, smem, ::sg::counted(st)>>>(a);
     return check_launch("decode_bf16_kernel");
 }

@@ -599,10 +599,230 @@ struct Plan {
     bool keep;        // keep every layer (backward) or reuse one set
 };
 
+// ---------------------------------------------------------------------------
+// Shared-memory attention: one CTA per (sample, head) stages the head's rows
+// of the sequence in padded shared memory (row stride DH + 4 floats, an odd
+// number of 16-byte units, so 16-byte row reads by 32 different rows are
+// conflict-free) and walks the visible keys there.
+// ---------------------------------------------------------------------------
+template <int DH>
+__device__ __forceinline__ void stage_rows(float *dst, const float *__restrict__ src, int N,
+                                           int stride_src)
+{
+    constexpr int DP = DH + 4;
+    for (int e = threadIdx.x; e < N * (DH / 4); e += blockDim.x) {
+        const int t = e / (DH / 4), c = e % (DH / 4);
+        *reinterpret_cast<float4 *>(dst + t * DP + 4 * c) =
+            *reinterpret_cast<const float4 *>(src + (size_t)t * stride_src + 4 * c);
+    }
+}
+
+template <int DH>
+__device__ __forceinline__ float dot_row(const float *q, const float *row)
+{
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < DH / 4; ++c) {
+        const float4 k = *reinterpret_cast<const float4 *>(row + 4 * c);
+        s += q[4 * c] * k.x + q[4 * c + 1] * k.y + q[4 * c + 2] * k.z + q[4 * c + 3] * k.w;
+    }
+    return s;
+}
+
+template <int DH>
+__global__ void __launch_bounds__(256)
+attn_fwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ Hin,
+                     float *__restrict__ O, float *__restrict__ Hmid, float *__restrict__ LSE,
+                     int N, int D, int NH, int mask, int W, int S)
+{
+    constexpr int DP = DH + 4;
+    extern __shared__ float4 sm4[];
+    float *Ks = reinterpret_cast<float *>(sm4);
+    float *Vs = Ks + N * DP;
+    const int b = blockIdx.x / NH, hh = blockIdx.x % NH;
+    const float *base = QKV + (size_t)b * N * 3 * D;
+    stage_rows<DH>(Ks, base + D + hh * DH, N, 3 * D);
+    stage_rows<DH>(Vs, base + 2 * D + hh * DH, N, 3 * D);
+    __syncthreads();
+    const float scale = rsqrtf((float)DH);
+    for (int t = threadIdx.x; t < N; t += blockDim.x) {
+        const size_t r = (size_t)b * N + t;
+        float q[DH], acc[DH];
+#pragma unroll
+        for (int j = 0; j < DH; ++j) {
+            q[j] = QKV[r * 3 * D + hh * DH + j] * scale;
+            acc[j] = 0.f;
+        }
+        int n_sink, band_lo;
+        visible_ranges(mask, W, S, t, n_sink, band_lo);
+        const int nk = n_sink + band_count(t, band_lo);
+        float mx = -INFINITY, den = 0.f;
+        for (int i = 0; i < nk; ++i) {
+            const int k = i < n_sink ? i : band_lo + (i - n_sink);
+            const float sc = dot_row<DH>(q, Ks + k * DP);
+            const float mn = fmaxf(mx, sc);
+            const float corr = __expf(mx - mn), p = __expf(sc - mn);
+            mx = mn;
+            den = den * corr + p;
+            const float *vr = Vs + k * DP;
+#pragma unroll
+            for (int c = 0; c < DH / 4; ++c) {
+                const float4 v = *reinterpret_cast<const float4 *>(vr + 4 * c);
+                acc[4 * c] = acc[4 * c] * corr + p * v.x;
+                acc[4 * c + 1] = acc[4 * c + 1] * corr + p * v.y;
+                acc[4 * c + 2] = acc[4 * c + 2] * corr + p * v.z;
+                acc[4 * c + 3] = acc[4 * c + 3] * corr + p * v.w;
+            }
+        }
+        const float inv = 1.0f / den;
+#pragma unroll
+        for (int j = 0; j < DH; ++j) {
+            const size_t idx = r * D + hh * DH + j;
+            const float o = acc[j] * inv;
+            O[idx] = o;
+            Hmid[idx] = Hin[idx] + o;
+        }
+        LSE[r * NH + hh] = mx + logf(den);
+    }
+}
+
+// Backward of one (sample, head): dQ by query threads; dK, dV of band keys by
+// key threads (each sees at most W + 1 queries); sink keys (and every key of
+// a dense mask) by warps, lanes striding over the queries with a shuffle
+// reduction.
+template <int DH>
+__global__ void __launch_bounds__(256)
+attn_bwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ O,
+                     const float *__restrict__ dO, const float *__restrict__ LSE,
+                     float *__restrict__ dQKV, int N, int D, int NH, int mask, int W, int S)
+{
+    constexpr int DP = DH + 4;
+    extern __shared__ float4 sm4[];
+    float *Qs = reinterpret_cast<float *>(sm4);
+    float *Ks = Qs + N * DP;
+    float *Vs = Ks + N * DP;
+    float *Gs = Vs + N * DP;  // dO
+    float *Ls = Gs + N * DP;  // LSE
+    float *Ds = Ls + N;       // D_t = dO_t . O_t
+    const int b = blockIdx.x / NH, hh = blockIdx.x % NH;
+    const float *base = QKV + (size_t)b * N * 3 * D;
+    stage_rows<DH>(Qs, base + hh * DH, N, 3 * D);
+    stage_rows<DH>(Ks, base + D + hh * DH, N, 3 * D);
+    stage_rows<DH>(Vs, base + 2 * D + hh * DH, N, 3 * D);
+    stage_rows<DH>(Gs, dO + (size_t)b * N * D + hh * DH, N, D);
+    const float scale = rsqrtf((float)DH);
+    for (int t = threadIdx.x; t < N; t += blockDim.x) {
+        const size_t r = (size_t)b * N + t;
+        Ls[t] = LSE[r * NH + hh];
+        float dd = 0.f;
+#pragma unroll
+        for (int j = 0; j < DH; ++j) dd += dO[r * D + hh * DH + j] * O[r * D + hh * DH + j];
+        Ds[t] = dd;
+    }
+    __syncthreads();
+    // dQ_t = scale * sum_k P_tk (dP_tk - D_t) k_k
+    for (int t = threadIdx.x; t < N; t += blockDim.x) {
+        float q[DH], g[DH], dq[DH];
+#pragma unroll
+        for (int j = 0; j < DH; ++j) {
+            q[j] = Qs[t * DP + j] * scale;
+            g[j] = Gs[t * DP + j];
+            dq[j] = 0.f;
+        }
+        const float lse = Ls[t], dd = Ds[t];
+        int n_sink, band_lo;
+        visible_ranges(mask, W, S, t, n_sink, band_lo);
+        const int nk = n_sink + band_count(t, band_lo);
+        for (int i = 0; i < nk; ++i) {
+            const int k = i < n_sink ? i : band_lo + (i - n_sink);
+            const float p = __expf(dot_row<DH>(q, Ks + k * DP) - lse);
+            const float ds = p * (dot_row<DH>(g, Vs + k * DP) - dd) * scale;
+#pragma unroll
+            for (int j = 0; j < DH; ++j) dq[j] += ds * Ks[k * DP + j];
+        }
+        float *out = dQKV + ((size_t)b * N + t) * 3 * D + hh * DH;
+#pragma unroll
+        for (int j = 0; j < DH; ++j) out[j] = dq[j];
+    }
+    // keys seen only through the band: one thread per key
+    const int k_band0 = mask == SG_MASK_DENSE ? N : (S < N ? S : N);
+    for (int k = k_band0 + threadIdx.x; k < N; k += blockDim.x) {
+        float key[DH], val[DH], dk[DH], dv[DH];
+#pragma unroll
+        for (int j = 0; j < DH; ++j) {
+            key[j] = Ks[k * DP + j] * scale;
+            val[j] = Vs[k * DP + j];
+            dk[j] = dv[j] = 0.f;
+        }
+        const int t_hi = min(N - 1, k + W);
+        for (int t = k; t <= t_hi; ++t) {
+            const float p = __expf(dot_row<DH>(key, Qs + t * DP) - Ls[t]);
+            const float ds = p * (dot_row<DH>(val, Gs + t * DP) - Ds[t]) * scale;
+#pragma unroll
+            for (int j = 0; j < DH; ++j) {
+                dk[j] += ds * Qs[t * DP + j];
+                dv[j] += p * Gs[t * DP + j];
+            }
+        }
+        float *out = dQKV + ((size_t)b * N + k) * 3 * D + hh * DH;
+#pragma unroll
+        for (int j = 0; j < DH; ++j) {
+            out[D + j] = dk[j];
+            out[2 * D + j] = dv[j];
+        }
+    }
+    // keys visible to every later query (sink, or all keys when dense): warps
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int k = warp; k < k_band0; k += nw) {
+        float key[DH], val[DH], dk[DH], dv[DH];
+#pragma unroll
+        for (int j = 0; j < DH; ++j) {
+            key[j] = Ks[k * DP + j] * scale;
+            val[j] = Vs[k * DP + j];
+            dk[j] = dv[j] = 0.f;
+        }
+        for (int t = k + lane; t < N; t += 32) {
+            const float p = __expf(dot_row<DH>(key, Qs + t * DP) - Ls[t]);
+            const float ds = p * (dot_row<DH>(val, Gs + t * DP) - Ds[t]) * scale;
+#pragma unroll
+            for (int j = 0; j < DH; ++j) {
+                dk[j] += ds * Qs[t * DP + j];
+                dv[j] += p * Gs[t * DP + j];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < DH; ++j) {
+            dk[j] = wsum(dk[j]);
+            dv[j] = wsum(dv[j]);
+        }
+        if (lane == 0) {
+            float *out = dQKV + ((size_t)b * N + k) * 3 * D + hh * DH;
+#pragma unroll
+            for (int j = 0; j < DH; ++j) {
+                out[D + j] = dk[j];
+                out[2 * D + j] = dv[j];
+            }
+        }
+    }
+}
+
+constexpr size_t kAttnSmemMax = 200 * 1024;
+
+template <int DH>
+size_t attn_bwd_smem_bytes(int N) { return ((size_t)4 * N * (DH + 4) + 2 * N) * sizeof(float); }
+
 template <int DH>
 void attn_fwd(const float *QKV, const float *Hin, float *O, float *Hmid, float *LSE, int Bc,
               const sg_config &c, cudaStream_t st)
 {
+    const size_t fwd_smem = (size_t)2 * c.N * (DH + 4) * sizeof(float);
+    if (attn_bwd_smem_bytes<DH>(c.N) <= kAttnSmemMax) {
+        cudaFuncSetAttribute(attn_fwd_smem_kernel<DH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)fwd_smem);
+        attn_fwd_smem_kernel<DH><<<(unsigned)(Bc * c.n_heads), 256, fwd_smem, ::sg::counted(st)>>>(
+            QKV, Hin, O, Hmid, LSE, c.N, c.d, c.n_heads, c.mask_kind, c.W, c.S);
+        return;
+    }
     const int warps = Bc * c.n_heads * ((c.N + 31) / 32);
     attn_fwd_kernel<DH><<<blocks_for(warps, 8), 256, 0, ::sg::counted(st)>>>(
         QKV, Hin, O, Hmid, LSE, Bc, c.N, c.d, c.n_heads, c.mask_kind, c.W, c.S);
@@ -612,6 +832,14 @@ template <int DH>
 void attn_bwd(const float *QKV, const float *O, const float *dO, const float *LSE, float *dQKV,
               float *Dt, int Bc, const sg_config &c, cudaStream_t st)
 {
+    const size_t smem = attn_bwd_smem_bytes<DH>(c.N);
+    if (smem <= kAttnSmemMax) {
+        cudaFuncSetAttribute(attn_bwd_smem_kernel<DH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        attn_bwd_smem_kernel<DH><<<(unsigned)(Bc * c.n_heads), 256, smem, ::sg::counted(st)>>>(
+            QKV, O, dO, LSE, dQKV, c.N, c.d, c.n_heads, c.mask_kind, c.W, c.S);
+        return;
+    }
     const int warps = Bc * c.n_heads * ((c.N + 31) / 32);
     attn_bwd_q_kernel<DH><<<blocks_for(warps, 8), 256, 0, ::sg::counted(st)>>>(
         QKV, O, dO, LSE, dQKV, Dt, Bc, c.N, c.d, c.n_heads, c.mask_kind, c.W, c.S);

@@ -28,8 +28,10 @@ cudaStream_t counted(cudaStream_t st);
 #define SG_CUDA_TRY(expr)                                                              \
     do {                                                                               \
         cudaError_t e_ = (expr);                                                       \
-        if (e_ != cudaSuccess)                                                         \
+        if (e_ != cudaSuccess) {                                                       \
+            cudaGetLastError(); /* clear a non-sticky error so it cannot leak */       \
             return ::sg::fail(SG_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+        }                                                                              \
     } while (0)
 
 #define SG_TRY(expr)                        \

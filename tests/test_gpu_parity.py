@@ -72,7 +72,41 @@ BF16_CASES = {
     "single_spin": (inputs.ModelShape(1, 1, 64, 4), 5, 1.0),
     "band_W0_S0": (inputs.ModelShape(17, 2, 64, 4, mask_kind=1, W=0, S=0), 129, 1.0),
     "short_sink": (inputs.ModelShape(20, 2, 64, 4, mask_kind=1, W=3, S=30), 64, 1.0),
+    "dense_d128": (inputs.ModelShape(40, 2, 128, 8), 200, 1.0),
+    "ring_d128": (inputs.ModelShape(64, 3, 128, 8, mask_kind=1, W=6, S=9), 300, 1.0),
+    "tiny_d128": (inputs.ModelShape(3, 1, 128, 8), 7, 1.0),
 }
+
+
+@pytest.mark.parametrize("name,precision,rows", [("sk1024", "bf16", [0, 4321, 8191]),
+                                                 ("ea3d10", "bf16", [0, 127, 128, 32767]),
+                                                 ("sk1024", "fp32", [1, 8190])])
+def test_full_size_d128_sampled_rows(name, precision, rows):
+    """Full-size SK N=1024 (dense) and 3D EA L=10 (band + sink) workloads in
+    the benchmark's launch configuration: sampled rows against the oracle,
+    every energy against the oracle (bit-exact for +-J)."""
+    wl = inputs.workloads()[name]
+    m, inst = wl.model, wl.instance()
+    w = wl.weights()
+    prec = sg.SG_BF16 if precision == "bf16" else sg.SG_FP32
+    tol = BF16_LOGQ_TOL if precision == "bf16" else FP32_LOGQ_TOL
+    model = sg.Model(m, w, prec)
+    spins, logq, flags = model.sample(wl.B, seed=2025, with_flags=True)
+    model.check()
+    gi = sg.Instance(inst)
+    s, lq, fl = _np(spins), _np(logq), _np(flags)
+    rows = np.array(rows)
+    so, lqo, _, _ = oracle_replay(m, w, 2025, s, fl, rows=rows)
+    assert np.array_equal(so, s[rows])
+    assert np.abs(lqo - lq[rows]).max() <= tol * m.N
+    assert unpack_flags(fl, m.N).mean() < (0.05 if precision == "bf16" else 0.01)
+    if inst.pm:
+        _, Ei = gi.energy(spins, want_int=True)
+        assert np.array_equal(_np(Ei).astype(np.float64), oracle.energy(inst, s))
+    else:
+        E = _np(gi.energy(spins[:256]))
+        assert np.allclose(E, oracle.energy(inst, s[:256]), rtol=1e-5, atol=1e-3)
+    del model
 
 
 @pytest.mark.parametrize("name", list(BF16_CASES))
