@@ -1,0 +1,406 @@
+// gemm_tc.cu -- tcgen05 GEMMs for the BF16 teacher-forced pass and backward.
+//
+// row_gemm_kernel: C[R][N] = A[R][K] B[N][K]^T with a fused epilogue.  A
+// persistent CTA walks row blocks of 128; warp 0 streams A tiles by bulk copy
+// into two shared-memory stages, warp 1 issues the MMAs into one of two TMEM
+// accumulators, warps 2-5 drain the other accumulator through the epilogue.
+// B (the weights, <= 256 x 256) stays resident in shared memory.
+//
+// wgrad_kernel: C[M][N] += A[M][Kr] B[N][Kr]^T, a split-K reduction over the
+// batch rows for weight gradients: each CTA owns one 128-row block of C and a
+// range of K chunks, pipelines them through four stages, and adds its TMEM
+// accumulator to C with atomics.
+//
+// Every wait is bounded; on a timeout the kernel sets the error word and the
+// roles stop issuing work.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "gemm_tc.cuh"
+
+namespace sg {
+
+namespace {
+
+__device__ __forceinline__ uint32_t pk2(float a, float b)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+__device__ __forceinline__ void st8(unsigned char *base, size_t off, const float *v)
+{
+    uint4 q;
+    q.x = pk2(v[0], v[1]);
+    q.y = pk2(v[2], v[3]);
+    q.z = pk2(v[4], v[5]);
+    q.w = pk2(v[6], v[7]);
+    *reinterpret_cast<uint4 *>(base + off) = q;
+}
+
+__device__ __forceinline__ void ld8(const unsigned char *base, size_t off, float *v)
+{
+    const uint4 q = *reinterpret_cast<const uint4 *>(base + off);
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        v[2 * i] = __uint_as_float(w[i] << 16);
+        v[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+    }
+}
+
+template <int EPI>
+__device__ __forceinline__ void row_epilogue(const RowGemm &g, const float (&v)[32], int64_t r,
+                                             int col0, bool valid)
+{
+    if (EPI == TE_STORE_F32 || EPI == TE_RESID_F32 || EPI == TE_STORE_F32_T) {
+        if (!valid && EPI != TE_STORE_F32_T) return;
+        float o[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            o[j] = v[j] + (g.bias ? __ldg(g.bias + col0 + j) : 0.f);
+            if (EPI == TE_RESID_F32) o[j] += g.resid[r * g.ld_resid + col0 + j];
+        }
+        if (valid) {
+            float4 *dst = reinterpret_cast<float4 *>(g.out_f32 + r * g.ld_out + col0);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) dst[j] = make_float4(o[4 * j], o[4 * j + 1], o[4 * j + 2], o[4 * j + 3]);
+        }
+        if (EPI == TE_STORE_F32_T) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) o[j] = valid ? o[j] : 0.f;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) st8(g.out_t, tl_offset(r, col0 + 8 * c, g.RB), o + 8 * c);
+        }
+    } else if (EPI == TE_GELU_T) {
+        float x[32], y[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            x[j] = valid ? v[j] + __ldg(g.bias + col0 + j) : 0.f;
+            y[j] = valid ? gelu_f(x[j]) : 0.f;
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            st8(g.out_t, tl_offset(r, col0 + 8 * c, g.RB), y + 8 * c);
+            st8(g.out_t2, tl_offset(r, col0 + 8 * c, g.RB), x + 8 * c);
+        }
+    } else {  // TE_GELU_BWD_T
+        float y[32];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            float f1[8];
+            ld8(g.aux_t, tl_offset(r, col0 + 8 * c, g.RB), f1);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) y[8 * c + j] = valid ? v[8 * c + j] * gelu_grad_f(f1[j]) : 0.f;
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) st8(g.out_t, tl_offset(r, col0 + 8 * c, g.RB), y + 8 * c);
+    }
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(192, 1) row_gemm_kernel(const __grid_constant__ RowGemm g)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const uint32_t stage_bytes = (uint32_t)g.KC * kTileBytes;
+    unsigned char *Bs = smem;
+    unsigned char *As = smem + (size_t)g.NBw * g.KC * kTileBytes;
+    __shared__ uint64_t full[2], empty[2], tfull[2], tempty[2], wfull;
+    __shared__ uint32_t tslot;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < 2; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+            tc::mbar_init(&tfull[s], 1);
+            tc::mbar_init(&tempty[s], 4);
+        }
+        tc::mbar_init(&wfull, 1);
+        tc::fence_mbar_init();
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(&tslot, 512);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = tslot;
+    const int64_t nblk = g.RB;
+    const int64_t my_n = (int64_t)blockIdx.x < nblk ? (nblk - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+    if (warp == 0 && lane == 0) {
+        const uint32_t wbytes = (uint32_t)(g.NBw * g.KC) * kTileBytes;
+        tc::mbar_arrive_expect_tx(&wfull, wbytes);
+        for (int t = 0; t < g.NBw * g.KC; ++t)
+            tc::bulk_g2s(Bs + (size_t)t * kTileBytes, g.Bw + (size_t)t * kTileBytes, kTileBytes, &wfull);
+        for (int64_t i = 0; i < my_n; ++i) {
+            const int s = (int)(i & 1);
+            const int64_t rb = blockIdx.x + i * gridDim.x;
+            if (i >= 2 && !tc::mbar_wait(&empty[s], (uint32_t)(((i >> 1) - 1) & 1))) {
+                atomicExch(g.err, 11);
+                break;
+            }
+            tc::mbar_arrive_expect_tx(&full[s], stage_bytes);
+            for (int kc = 0; kc < g.KC; ++kc)
+                tc::bulk_g2s(As + (size_t)s * stage_bytes + (size_t)kc * kTileBytes,
+                             g.A + ((size_t)(kc * g.RB + rb) << 14), kTileBytes, &full[s]);
+        }
+    } else if (warp == 1 && lane == 0) {
+        bool ok = tc::mbar_wait(&wfull, 0);
+        const uint32_t idesc = tc::idesc_bf16(128, g.N);
+        for (int64_t i = 0; i < my_n && ok; ++i) {
+            const int s = (int)(i & 1), acc = (int)(i & 1);
+            ok = tc::mbar_wait(&full[s], (uint32_t)((i >> 1) & 1));
+            if (ok && i >= 2) ok = tc::mbar_wait(&tempty[acc], (uint32_t)(((i >> 1) - 1) & 1));
+            if (!ok) break;
+            tc::tc_fence_after();
+            for (int kc = 0; kc < g.KC; ++kc) {
+                const uint32_t sa = tc::smem_u32(As + (size_t)s * stage_bytes + (size_t)kc * kTileBytes);
+                const uint32_t sb = tc::smem_u32(Bs + (size_t)kc * g.NBw * kTileBytes);
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks)
+                    tc::mma_bf16(tmem + acc * 256, tc::smem_desc(sa + 256 * ks, 128, 1024),
+                                 tc::smem_desc(sb + 256 * ks, 128, 1024), idesc,
+                                 (kc | ks) != 0 ? 1u : 0u);
+            }
+            tc::mma_commit(&empty[s]);
+            tc::mma_commit(&tfull[acc]);
+        }
+        if (!ok) atomicExch(g.err, 12);
+    } else if (warp >= 2) {
+        const int q = warp & 3;
+        const int row = 32 * q + lane;
+        for (int64_t i = 0; i < my_n; ++i) {
+            const int acc = (int)(i & 1);
+            const int64_t rb = blockIdx.x + i * gridDim.x;
+            if (!tc::mbar_wait(&tfull[acc], (uint32_t)((i >> 1) & 1))) {
+                if (lane == 0) atomicExch(g.err, 13);
+                break;
+            }
+            tc::tc_fence_after();
+            const int64_t r = rb * 128 + row;
+            const bool valid = r < g.R;
+            for (int c = 0; c < g.N / 32; ++c) {
+                float v[32];
+                tc::tmem_ld32(tmem + acc * 256 + ((uint32_t)(32 * q) << 16) + 32 * c, v);
+                tc::tmem_wait_ld();
+                row_epilogue<EPI>(g, v, r, 32 * c, valid);
+            }
+            tc::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&tempty[acc]);
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) tc::tmem_dealloc(tmem, 512);
+}
+
+constexpr int kWStages = 4;
+
+__global__ void __launch_bounds__(192, 1) wgrad_kernel(const __grid_constant__ WgradGemm g)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const uint32_t stage_bytes = (uint32_t)(1 + g.NB) * kTileBytes;
+    __shared__ uint64_t full[kWStages], empty[kWStages], tfull;
+    __shared__ uint32_t tslot;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t mb = blockIdx.x % g.MB, split = blockIdx.x / g.MB;
+    const int64_t kc0 = split * g.kc_per_cta;
+    const int64_t kc1 = kc0 + g.kc_per_cta < g.KCtot ? kc0 + g.kc_per_cta : g.KCtot;
+    const int64_t n = kc1 > kc0 ? kc1 - kc0 : 0;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kWStages; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        tc::mbar_init(&tfull, 1);
+        tc::fence_mbar_init();
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(&tslot, 256);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = tslot;
+    if (warp == 0 && lane == 0) {
+        for (int64_t j = 0; j < n; ++j) {
+            const int s = (int)(j % kWStages);
+            const int64_t kc = kc0 + j;
+            if (j >= kWStages && !tc::mbar_wait(&empty[s], (uint32_t)((j / kWStages - 1) & 1))) {
+                atomicExch(g.err, 21);
+                break;
+            }
+            unsigned char *dst = smem + (size_t)s * stage_bytes;
+            tc::mbar_arrive_expect_tx(&full[s], stage_bytes);
+            tc::bulk_g2s(dst, g.A + ((size_t)(kc * g.MB + mb) << 14), kTileBytes, &full[s]);
+            for (int nb = 0; nb < g.NB; ++nb)
+                tc::bulk_g2s(dst + (size_t)(1 + nb) * kTileBytes,
+                             g.Bm + ((size_t)(kc * g.NB + nb) << 14), kTileBytes, &full[s]);
+        }
+    } else if (warp == 1 && lane == 0) {
+        const uint32_t idesc = tc::idesc_bf16(128, g.N);
+        bool ok = true;
+        for (int64_t j = 0; j < n; ++j) {
+            const int s = (int)(j % kWStages);
+            if (!tc::mbar_wait(&full[s], (uint32_t)((j / kWStages) & 1))) {
+                ok = false;
+                break;
+            }
+            tc::tc_fence_after();
+            const uint32_t sa = tc::smem_u32(smem + (size_t)s * stage_bytes);
+            const uint32_t sb = sa + kTileBytes;
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)
+                tc::mma_bf16(tmem, tc::smem_desc(sa + 256 * ks, 128, 1024),
+                             tc::smem_desc(sb + 256 * ks, 128, 1024), idesc,
+                             (j | ks) != 0 ? 1u : 0u);
+            tc::mma_commit(&empty[s]);
+        }
+        if (!ok) atomicExch(g.err, 22);
+        tc::mma_commit(&tfull);
+    } else if (warp >= 2 && n > 0) {
+        const int q = warp & 3;
+        const int64_t m = mb * 128 + 32 * q + lane;
+        if (tc::mbar_wait(&tfull, 0)) {
+            tc::tc_fence_after();
+            for (int c = 0; c < g.N / 32; ++c) {
+                float v[32];
+                tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + 32 * c, v);
+                tc::tmem_wait_ld();
+                if (m < g.M)
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) atomicAdd(g.C + m * g.N + 32 * c + j, v[j]);
+            }
+        } else if (lane == 0) {
+            atomicExch(g.err, 23);
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) tc::tmem_dealloc(tmem, 256);
+}
+
+// FP32 row-major -> tiled BF16.  Thread = (8-element group along the tiled
+// K axis, tiled row); padding is written as zeros.
+__global__ void to_tiled_kernel(const float *__restrict__ X, int64_t R, int F, int ldx,
+                                unsigned char *__restrict__ dst, int transpose)
+{
+    // tiled matrix: rows_t x K_t
+    const int64_t rows_t = transpose ? F : R;
+    const int64_t K_t = transpose ? R : F;
+    const int64_t RBt = tl_blocks(rows_t);
+    const int64_t groups = ((K_t + 63) >> 6) * 8;  // 8-wide groups along K (padded)
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= RBt * 128 * groups) return;
+    int64_t rt, kg;
+    if (transpose) {  // consecutive threads take consecutive tiled rows (features)
+        rt = i % (RBt * 128);
+        kg = i / (RBt * 128);
+    } else {
+        kg = i % groups;
+        rt = i / groups;
+    }
+    float v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int64_t kt = kg * 8 + j;
+        float x = 0.f;
+        if (rt < rows_t && kt < K_t)
+            x = transpose ? X[kt * ldx + rt] : X[rt * ldx + kt];
+        v[j] = x;
+    }
+    st8(dst, tl_offset(rt, (int)(kg * 8), RBt), v);
+}
+
+// T(R, F) -> T(F, R).  Thread = (tiled output row f, 8-group of R).
+__global__ void tiled_transpose_kernel(const unsigned char *__restrict__ src, int64_t R, int F,
+                                       unsigned char *__restrict__ dst)
+{
+    const int64_t RBs = tl_blocks(R), RBd = tl_blocks(F);
+    const int64_t groups = ((R + 63) >> 6) * 8;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= RBd * 128 * groups) return;
+    const int64_t f = i % (RBd * 128), rg = i / (RBd * 128);
+    float v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int64_t r = rg * 8 + j;
+        float x = 0.f;
+        if (f < F && r < R) {
+            const uint16_t b = *reinterpret_cast<const uint16_t *>(src + tl_offset(r, (int)f, RBs));
+            x = __uint_as_float((uint32_t)b << 16);
+        }
+        v[j] = x;
+    }
+    st8(dst, tl_offset(f, (int)(rg * 8), RBd), v);
+}
+
+unsigned grid_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
+
+}  // namespace
+
+sg_status launch_to_tiled(const float *X, int64_t R, int F, int ldx, unsigned char *dst,
+                          bool transpose, cudaStream_t st)
+{
+    const int64_t rows_t = transpose ? F : R, K_t = transpose ? R : F;
+    const int64_t n = tl_blocks(rows_t) * 128 * (((K_t + 63) >> 6) * 8);
+    to_tiled_kernel<<<grid_for(n, 256), 256, 0, ::sg::counted(st)>>>(X, R, F, ldx, dst,
+                                                                     transpose ? 1 : 0);
+    return check_launch("to_tiled_kernel");
+}
+
+sg_status launch_tiled_transpose(const unsigned char *src, int64_t R, int F, unsigned char *dst,
+                                 cudaStream_t st)
+{
+    const int64_t n = tl_blocks(F) * 128 * (((R + 63) >> 6) * 8);
+    tiled_transpose_kernel<<<grid_for(n, 256), 256, 0, ::sg::counted(st)>>>(src, R, F, dst);
+    return check_launch("tiled_transpose_kernel");
+}
+
+sg_status launch_pack_tiled(const float *W, int rows, int K, unsigned char *dst, bool transpose,
+                            cudaStream_t st)
+{
+    // W[rows][K] row-major; transpose packs W^T (K x rows)
+    return launch_to_tiled(W, rows, K, K, dst, transpose, st);
+}
+
+sg_status launch_row_gemm(const RowGemm &g, int epi, cudaStream_t st)
+{
+    if (g.N % 32 || g.N > 256 || g.N > g.NBw * 128 || g.KC < 1 || g.KC > 4)
+        return fail(SG_EUNSUPPORTED, "row GEMM needs N a multiple of 32, N <= 256, K <= 256");
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = (size_t)(g.NBw * g.KC + 2 * g.KC) * kTileBytes;
+    const unsigned grid = (unsigned)std::min<int64_t>(g.RB, sms);
+    auto go = [&](auto kern) -> sg_status {
+        SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<grid, 192, smem, ::sg::counted(st)>>>(g);
+        return check_launch("row_gemm_kernel");
+    };
+    switch (epi) {
+    case TE_STORE_F32: return go(row_gemm_kernel<TE_STORE_F32>);
+    case TE_RESID_F32: return go(row_gemm_kernel<TE_RESID_F32>);
+    case TE_GELU_T: return go(row_gemm_kernel<TE_GELU_T>);
+    case TE_GELU_BWD_T: return go(row_gemm_kernel<TE_GELU_BWD_T>);
+    default: return go(row_gemm_kernel<TE_STORE_F32_T>);
+    }
+}
+
+sg_status launch_wgrad_gemm(const WgradGemm &g, cudaStream_t st)
+{
+    if (g.N % 32 || g.N > 256 || g.N > g.NB * 128)
+        return fail(SG_EUNSUPPORTED, "weight-gradient GEMM needs N a multiple of 32, <= 256");
+    const size_t smem = (size_t)kWStages * (1 + g.NB) * kTileBytes;
+    const int64_t splits = (g.KCtot + g.kc_per_cta - 1) / g.kc_per_cta;
+    SG_CUDA_TRY(cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    wgrad_kernel<<<(unsigned)(g.MB * splits), 192, smem, ::sg::counted(st)>>>(g);
+    return check_launch("wgrad_kernel");
+}
+
+}  // namespace sg

@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "gemm_tc.cuh"
 #include "sg_internal.cuh"
 
 namespace sg {
@@ -591,7 +592,41 @@ unsigned blocks_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per)
 // ---------------------------------------------------------------------------
 struct LayerBufs {
     float *Hin, *mu1, *rs1, *A1, *QKV, *O, *LSE, *Hmid, *mu2, *rs2, *A2, *F1, *G;
+    // tensor-core path: tiled BF16 operands kept for the backward
+    unsigned char *A1t, *A2t, *Gt, *F1t;
 };
+
+// The BF16 model runs its teacher-forced GEMMs on tcgen05 when every GEMM
+// fits the row-GEMM kernel (N <= 256 columns, K <= 256).
+bool use_tc(const sg_config &c)
+{
+    return c.precision == SG_BF16 && c.d % 32 == 0 && 3 * c.d <= 256 && c.d_ff % 32 == 0 &&
+           c.d_ff <= 256;
+}
+
+// out[j] += sum_r T[r][j] over a tiled BF16 matrix T(R, F)
+__global__ void colsum_tiled_kernel(const unsigned char *__restrict__ T, int64_t R, int F,
+                                    float *__restrict__ out, int64_t rows_per_block)
+{
+    __shared__ float red[8][33];
+    const int j = blockIdx.x * 32 + threadIdx.x;
+    const int64_t RB = tl_blocks(R);
+    const int64_t rb0 = (int64_t)blockIdx.y * rows_per_block;
+    const int64_t re = rb0 + rows_per_block < R ? rb0 + rows_per_block : R;
+    float s = 0.f;
+    if (j < F)
+        for (int64_t r = rb0 + threadIdx.y; r < re; r += 8) {
+            const uint16_t b = *reinterpret_cast<const uint16_t *>(T + tl_offset(r, j, RB));
+            s += __uint_as_float((uint32_t)b << 16);
+        }
+    red[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y == 0 && j < F) {
+        float t = 0.f;
+        for (int y = 0; y < 8; ++y) t += red[y][threadIdx.x];
+        atomicAdd(out + j, t);
+    }
+}
 
 struct Plan {
     int64_t Bc;       // samples per chunk
@@ -907,22 +942,28 @@ struct Work {
     std::vector<LayerBufs> layers;
     float *Hfin, *muf, *rsf, *Y, *ell, *lp, *Hping;
     float *dH, *dHmid, *dA, *dQKV, *dF1, *Dt;
+    // tensor-core backward scratch (tiled BF16; T* = transposed operands)
+    unsigned char *dHt, *dF1t, *dQKVt, *TdH, *TG, *TdF1, *TA2, *TdQKV, *TA1;
     int64_t total_floats;
 };
 
 Work carve(const sg_config &c, float *base, int64_t R, bool bwd)
 {
-    Work w;
+    Work w{};
     const int64_t D = c.d, F = c.d_ff, NH = c.n_heads;
+    const bool tc = use_tc(c);
     int64_t off = 0;  // floats; every buffer starts 16-byte aligned
     auto take = [&](int64_t n) {
         float *q = base ? base + off : nullptr;
         off += (n + 3) & ~int64_t(3);
         return q;
     };
+    auto take_t = [&](int64_t rows, int64_t K) {  // tiled BF16 T(rows, K)
+        return reinterpret_cast<unsigned char *>(take((int64_t)(tl_bytes(rows, (int)K) / 4)));
+    };
     const int nl = bwd ? c.n_layers : 1;
     for (int l = 0; l < nl; ++l) {
-        LayerBufs L;
+        LayerBufs L{};
         L.Hin = take(R * D);
         L.mu1 = take(R);
         L.rs1 = take(R);
@@ -934,9 +975,27 @@ Work carve(const sg_config &c, float *base, int64_t R, bool bwd)
         L.mu2 = take(R);
         L.rs2 = take(R);
         L.A2 = take(R * D);
-        L.F1 = take(R * F);
-        L.G = take(R * F);
+        if (tc) {
+            L.A1t = take_t(R, D);
+            L.A2t = take_t(R, D);
+            L.Gt = take_t(R, F);
+            L.F1t = take_t(R, F);
+        } else {
+            L.F1 = take(R * F);
+            L.G = take(R * F);
+        }
         w.layers.push_back(L);
+    }
+    if (tc && bwd) {
+        w.dHt = take_t(R, D);
+        w.dF1t = take_t(R, F);
+        w.dQKVt = take_t(R, 3 * D);
+        w.TdH = take_t(D, R);
+        w.TG = take_t(F, R);
+        w.TdF1 = take_t(F, R);
+        w.TA2 = take_t(D, R);
+        w.TdQKV = take_t(3 * D, R);
+        w.TA1 = take_t(D, R);
     }
     w.Hfin = take(R * D);
     w.Hping = take(R * D);
@@ -995,6 +1054,29 @@ void forward_chunk(sg_model *m, const int8_t *spins, int Bc, Work &w, bool keep,
                            : (H == w.Hping ? w.Hfin : w.Hping);
         ln_fwd_kernel<<<blocks_for(R, 8), 256, 0, ::sg::counted(st)>>>(Hin, W + o.ln1g, W + o.ln1b, L.A1, L.mu1,
                                                         L.rs1, R, D);
+        if (use_tc(c)) {
+            // tensor-core GEMMs over tiled BF16 operands
+            const unsigned char *bt = (const unsigned char *)m->bt;
+            launch_to_tiled(L.A1, R, D, D, L.A1t, false, st);
+            RowGemm g{};
+            g.A = L.A1t; g.RB = tl_blocks(R); g.KC = (D + 63) / 64; g.R = R; g.err = (int *)m->err;
+            g.Bw = bt + m->bt_off[l][0]; g.NBw = (int)tl_blocks(3 * D); g.N = 3 * D;
+            g.bias = m->wt + m->pack.bqkv[l]; g.out_f32 = L.QKV; g.ld_out = 3 * D;
+            launch_row_gemm(g, TE_STORE_F32, st);
+            attn_fwd_dispatch(dh, L.QKV, Hin, L.O, L.Hmid, L.LSE, Bc, c, st);
+            ln_fwd_kernel<<<blocks_for(R, 8), 256, 0, ::sg::counted(st)>>>(L.Hmid, W + o.ln2g, W + o.ln2b, L.A2,
+                                                                L.mu2, L.rs2, R, D);
+            launch_to_tiled(L.A2, R, D, D, L.A2t, false, st);
+            g.A = L.A2t; g.Bw = bt + m->bt_off[l][1]; g.NBw = (int)tl_blocks(F); g.N = F;
+            g.bias = m->wt + m->pack.b1[l]; g.out_t = L.Gt; g.out_t2 = L.F1t;
+            launch_row_gemm(g, TE_GELU_T, st);
+            g.A = L.Gt; g.KC = (F + 63) / 64; g.Bw = bt + m->bt_off[l][2]; g.NBw = (int)tl_blocks(D);
+            g.N = D; g.bias = m->wt + m->pack.b2[l]; g.out_f32 = Hout; g.ld_out = D;
+            g.resid = L.Hmid; g.ld_resid = D;
+            launch_row_gemm(g, TE_RESID_F32, st);
+            H = Hout;
+            continue;
+        }
         gemm<G_STORE>(L.A1, D, m->wt + m->pack.WqkvT[l], 3 * D, m->wt + m->pack.bqkv[l], L.QKV, 3 * D, R,
                       3 * D, D, st);
         attn_fwd_dispatch(dh, L.QKV, Hin, L.O, L.Hmid, L.LSE, Bc, c, st);
@@ -1019,6 +1101,37 @@ void forward_chunk(sg_model *m, const int8_t *spins, int Bc, Work &w, bool keep,
 }
 
 }  // namespace
+
+// Tiled BF16 copies of the weights for the tensor-core teacher-forced pass:
+// Wqkv, W1, W2 (forward B operands) and W2^T, W1^T, Wqkv^T (backward).
+sg_status launch_pack_tiled_weights(sg_model *m, cudaStream_t st)
+{
+    const sg_config &c = m->cfg;
+    if (!use_tc(c)) return SG_OK;
+    const int D = c.d, F = c.d_ff;
+    const size_t sizes[6] = {tl_bytes(3 * D, D), tl_bytes(F, D), tl_bytes(D, F),
+                             tl_bytes(F, D), tl_bytes(D, F), tl_bytes(D, 3 * D)};
+    size_t per_layer = 0;
+    for (size_t s : sizes) per_layer += s;
+    SG_TRY(ensure_buffer(&m->bt, &m->bt_bytes, per_layer * c.n_layers));
+    unsigned char *bt = (unsigned char *)m->bt;
+    for (int l = 0; l < c.n_layers; ++l) {
+        size_t off = per_layer * l;
+        for (int i = 0; i < 6; ++i) {
+            m->bt_off[l][i] = off;
+            off += sizes[i];
+        }
+        const LayerOff &o = m->off.L[l];
+        const float *W = m->w;
+        SG_TRY(launch_pack_tiled(W + o.Wqkv, 3 * D, D, bt + m->bt_off[l][0], false, st));
+        SG_TRY(launch_pack_tiled(W + o.W1, F, D, bt + m->bt_off[l][1], false, st));
+        SG_TRY(launch_pack_tiled(W + o.W2, D, F, bt + m->bt_off[l][2], false, st));
+        SG_TRY(launch_pack_tiled(W + o.W2, D, F, bt + m->bt_off[l][3], true, st));
+        SG_TRY(launch_pack_tiled(W + o.W1, F, D, bt + m->bt_off[l][4], true, st));
+        SG_TRY(launch_pack_tiled(W + o.Wqkv, 3 * D, D, bt + m->bt_off[l][5], true, st));
+    }
+    return SG_OK;
+}
 
 sg_status launch_logprob_f32(sg_model *m, const int8_t *spins, int64_t B, float *logq,
                              cudaStream_t st)
@@ -1068,7 +1181,62 @@ sg_status launch_grad_f32(sg_model *m, const int8_t *spins, const float *coeff, 
         head_bwd_kernel<<<blocks_for(R, 256), 256, (4 * D + 2) * sizeof(float), ::sg::counted(st)>>>(
             w.Hfin, w.muf, w.rsf, w.Y, w.ell, sp, coeff + b0, W + O.lnfg, W + O.Wh, w.dH,
             grad + O.Wh, grad + O.bh, grad + O.lnfg, grad + O.lnfb, R, c.N, D, 256);
-        for (int l = c.n_layers - 1; l >= 0; --l) {
+        for (int l = c.n_layers - 1; l >= 0 && use_tc(c); --l) {
+            // tensor-core backward: dX GEMMs by row_gemm, weight gradients by
+            // split-K wgrad over tiled (transposed) BF16 operands
+            LayerBufs &L = w.layers[l];
+            const LayerOff &o = O.L[l];
+            const unsigned char *bt = (const unsigned char *)m->bt;
+            const int64_t RB = tl_blocks(R), KCr = (R + 63) / 64;
+            auto wgrad = [&](const unsigned char *A, int M, const unsigned char *Bm, int N, float *C) {
+                WgradGemm g{};
+                g.A = A; g.MB = tl_blocks(M); g.Bm = Bm; g.NB = (int)tl_blocks(N); g.N = N; g.M = M;
+                g.KCtot = KCr;
+                const int64_t splits = std::max<int64_t>(1, 304 / g.MB);
+                g.kc_per_cta = (KCr + splits - 1) / splits;
+                g.C = C; g.err = (int *)m->err;
+                launch_wgrad_gemm(g, st);
+            };
+            RowGemm g{};
+            g.RB = RB; g.R = R; g.err = (int *)m->err;
+            // FFN: H = Hmid + W2 G + b2, G = gelu(F1), F1 = W1 A2 + b1
+            launch_to_tiled(w.dH, R, D, D, w.dHt, false, st);
+            launch_to_tiled(w.dH, R, D, D, w.TdH, true, st);
+            g.A = w.dHt; g.KC = (D + 63) / 64; g.Bw = bt + m->bt_off[l][3]; g.NBw = (int)tl_blocks(F);
+            g.N = F; g.aux_t = L.F1t; g.out_t = w.dF1t;
+            launch_row_gemm(g, TE_GELU_BWD_T, st);
+            launch_tiled_transpose(L.Gt, R, F, w.TG, st);
+            wgrad(w.TdH, D, w.TG, F, grad + o.W2);
+            colsum(w.dH, D, R, D, grad + o.b2, st);
+            launch_tiled_transpose(w.dF1t, R, F, w.TdF1, st);
+            launch_to_tiled(L.A2, R, D, D, w.TA2, true, st);
+            wgrad(w.TdF1, F, w.TA2, D, grad + o.W1);
+            {
+                const int64_t rpb = 4096;
+                dim3 grid((F + 31) / 32, (unsigned)((R + rpb - 1) / rpb)), block(32, 8);
+                colsum_tiled_kernel<<<grid, block, 0, ::sg::counted(st)>>>(w.dF1t, R, F, grad + o.b1, rpb);
+            }
+            g.A = w.dF1t; g.KC = (F + 63) / 64; g.Bw = bt + m->bt_off[l][4]; g.NBw = (int)tl_blocks(D);
+            g.N = D; g.out_f32 = w.dA; g.ld_out = D;
+            launch_row_gemm(g, TE_STORE_F32, st);
+            cudaMemcpyAsync(w.dHmid, w.dH, (size_t)R * D * sizeof(float), cudaMemcpyDeviceToDevice, st);
+            ln_bwd(w.dA, L.Hmid, L.mu2, L.rs2, W + o.ln2g, w.dHmid, 1, grad + o.ln2g, grad + o.ln2b,
+                   R, D, st);
+            // attention: Hmid = Hin + O(QKV)
+            attn_bwd_dispatch(dh, L.QKV, L.O, w.dHmid, L.LSE, w.dQKV, w.Dt, Bc, c, st);
+            launch_to_tiled(w.dQKV, R, 3 * D, 3 * D, w.dQKVt, false, st);
+            launch_to_tiled(w.dQKV, R, 3 * D, 3 * D, w.TdQKV, true, st);
+            launch_to_tiled(L.A1, R, D, D, w.TA1, true, st);
+            wgrad(w.TdQKV, 3 * D, w.TA1, D, grad + o.Wqkv);
+            colsum(w.dQKV, 3 * D, R, 3 * D, grad + o.bqkv, st);
+            g.A = w.dQKVt; g.KC = (3 * D + 63) / 64; g.Bw = bt + m->bt_off[l][5];
+            g.NBw = (int)tl_blocks(D); g.N = D; g.out_f32 = w.dA; g.ld_out = D;
+            launch_row_gemm(g, TE_STORE_F32, st);
+            cudaMemcpyAsync(w.dH, w.dHmid, (size_t)R * D * sizeof(float), cudaMemcpyDeviceToDevice, st);
+            ln_bwd(w.dA, L.Hin, L.mu1, L.rs1, W + o.ln1g, w.dH, 1, grad + o.ln1g, grad + o.ln1b,
+                   R, D, st);
+        }
+        for (int l = c.n_layers - 1; l >= 0 && !use_tc(c); --l) {
             LayerBufs &L = w.layers[l];
             const LayerOff &o = O.L[l];
             // FFN: H = Hmid + W2 G + b2, G = gelu(F1), F1 = W1 A2 + b1

@@ -197,7 +197,10 @@ sg_status sg_model_refresh(sg_model *m, sg_stream stream)
 {
     if (!m) return fail(SG_EINVAL, "NULL model");
     SG_TRY(launch_pack_f32(m, (cudaStream_t)stream));
-    if (m->cfg.precision == SG_BF16) SG_TRY(launch_pack_bf16(m, (cudaStream_t)stream));
+    if (m->cfg.precision == SG_BF16) {
+        SG_TRY(launch_pack_bf16(m, (cudaStream_t)stream));
+        SG_TRY(launch_pack_tiled_weights(m, (cudaStream_t)stream));
+    }
     return SG_OK;
 }
 

@@ -169,6 +169,12 @@ struct sg_model {
     size_t ws_bytes = 0;
     void *err = nullptr;      // device error word written by kernels (bounded waits, NaN)
     size_t err_bytes = 0;
+    // tiled BF16 weights for the tensor-core teacher-forced pass and backward
+    // (byte offsets per layer: Wqkv, W1, W2 as forward B operands; W2^T, W1^T,
+    // Wqkv^T as backward B operands)
+    void *bt = nullptr;
+    size_t bt_bytes = 0;
+    size_t bt_off[SG_MAX_LAYERS][6] = {};
 };
 
 struct sg_instance {
@@ -185,6 +191,7 @@ sg_status ensure_buffer(void **ptr, size_t *have, size_t need);
 // Launchers implemented in the kernel translation units.
 sg_status launch_pack_f32(sg_model *m, cudaStream_t st);
 sg_status launch_pack_bf16(sg_model *m, cudaStream_t st);
+sg_status launch_pack_tiled_weights(sg_model *m, cudaStream_t st);
 sg_status launch_decode_bf16(sg_model *m, int64_t B, uint64_t seed, uint32_t sid, float band,
                              int8_t *spins, float *logq, uint32_t *flags, cudaStream_t st);
 sg_status launch_decode_f32(sg_model *m, int64_t B, uint64_t seed, uint32_t sid, float band,

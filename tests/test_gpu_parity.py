@@ -254,6 +254,35 @@ def test_fp32_grad_matches_oracle(m):
     assert np.abs(_np(logq) - lqo).max() <= FP32_LOGQ_TOL * m.N
 
 
+BF16_TF_MODELS = [inputs.ModelShape(20, 2, 32, 4), inputs.ModelShape(40, 2, 64, 4),
+                  inputs.ModelShape(70, 3, 64, 4, mask_kind=1, W=8, S=9),
+                  inputs.ModelShape(33, 1, 64, 4, mask_kind=1, W=3, S=2)]
+
+
+@pytest.mark.parametrize("m", BF16_TF_MODELS)
+def test_bf16_teacher_forced_logq_and_grad(m):
+    """BF16 teacher-forced pass and REINFORCE backward with the GEMMs on
+    tcgen05 (tiled BF16 operands, FP32 accumulation): log q within the BF16
+    bound of the oracle, gradient within BF16 rounding of the oracle's."""
+    w = inputs.make_weights(m, 5)
+    B = 300  # several row blocks of 128 and a ragged tail
+    s = inputs.random_spins(B, m.N, 9)
+    c = np.random.default_rng(2).normal(0, 1, B).astype(np.float32)
+    model = sg.Model(m, w, sg.SG_BF16)
+    ts = torch.tensor(s, device="cuda")
+    lq = _np(model.logprob(ts))
+    lqo = oracle.logprob(ocfg(m), w, s)
+    assert np.abs(lq - lqo).max() <= BF16_LOGQ_TOL * m.N
+    logq = torch.empty(B, dtype=torch.float32, device="cuda")
+    g = _np(model.grad(ts, torch.tensor(c, device="cuda"), logq=logq))
+    model.check()
+    go, _ = oracle.grad(ocfg(m), w, s, c.astype(np.float64))
+    rel = np.linalg.norm(g - go) / np.linalg.norm(go)
+    print(f"N={m.N} d={m.d}: max|dlogq|/N {np.abs(lq - lqo).max() / m.N:.2e}, grad rel err {rel:.2e}")
+    assert rel < 2e-2
+    assert np.abs(_np(logq) - lqo).max() <= BF16_LOGQ_TOL * m.N
+
+
 # --------------------------------------------------------------------------
 # MH, Metropolis, overlap, Adam
 # --------------------------------------------------------------------------
