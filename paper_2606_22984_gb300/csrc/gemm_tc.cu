@@ -99,8 +99,10 @@ __device__ __forceinline__ void row_epilogue(const RowGemm &g, const float (&v)[
     }
 }
 
+constexpr int kEpiWarps = 8;  // two epilogue warps per TMEM lane quadrant
+
 template <int EPI>
-__global__ void __launch_bounds__(192, 1) row_gemm_kernel(const __grid_constant__ RowGemm g)
+__global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) row_gemm_kernel(const __grid_constant__ RowGemm g)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     const uint32_t stage_bytes = (uint32_t)g.KC * kTileBytes;
@@ -114,7 +116,7 @@ __global__ void __launch_bounds__(192, 1) row_gemm_kernel(const __grid_constant_
             tc::mbar_init(&full[s], 1);
             tc::mbar_init(&empty[s], 1);
             tc::mbar_init(&tfull[s], 1);
-            tc::mbar_init(&tempty[s], 4);
+            tc::mbar_init(&tempty[s], kEpiWarps);
         }
         tc::mbar_init(&wfull, 1);
         tc::fence_mbar_init();
@@ -170,7 +172,8 @@ __global__ void __launch_bounds__(192, 1) row_gemm_kernel(const __grid_constant_
         }
         if (!ok) atomicExch(g.err, 12);
     } else if (warp >= 2) {
-        const int q = warp & 3;
+        const int q = warp & 3;             // TMEM lane quadrant of this warp
+        const int half = (warp - 2) >> 2;   // which alternate 32-column chunks
         const int row = 32 * q + lane;
         for (int64_t i = 0; i < my_n; ++i) {
             const int acc = (int)(i & 1);
@@ -182,7 +185,7 @@ __global__ void __launch_bounds__(192, 1) row_gemm_kernel(const __grid_constant_
             tc::tc_fence_after();
             const int64_t r = rb * 128 + row;
             const bool valid = r < g.R;
-            for (int c = 0; c < g.N / 32; ++c) {
+            for (int c = half; c < g.N / 32; c += 2) {
                 float v[32];
                 tc::tmem_ld32(tmem + acc * 256 + ((uint32_t)(32 * q) << 16) + 32 * c, v);
                 tc::tmem_wait_ld();
@@ -380,7 +383,7 @@ sg_status launch_row_gemm(const RowGemm &g, int epi, cudaStream_t st)
     const unsigned grid = (unsigned)std::min<int64_t>(g.RB, sms);
     auto go = [&](auto kern) -> sg_status {
         SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<grid, 192, smem, ::sg::counted(st)>>>(g);
+        kern<<<grid, 64 + 32 * kEpiWarps, smem, ::sg::counted(st)>>>(g);
         return check_launch("row_gemm_kernel");
     };
     switch (epi) {

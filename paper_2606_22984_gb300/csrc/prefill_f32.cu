@@ -9,6 +9,8 @@
 // backward runs in reverse; the chunk size bounds memory, so any B fits.
 // All arithmetic is FP32 on CUDA cores; weight gradients are reduced over rows
 // with per-block partial sums and atomics.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <vector>
 
@@ -75,7 +77,8 @@ __global__ void embed_bwd_kernel(const float *__restrict__ dH, const int8_t *__r
 // ---------------------------------------------------------------------------
 __global__ void ln_fwd_kernel(const float *__restrict__ X, const float *__restrict__ g,
                               const float *__restrict__ b, float *__restrict__ Y,
-                              float *__restrict__ mu, float *__restrict__ rs, int64_t R, int D)
+                              float *__restrict__ mu, float *__restrict__ rs, int64_t R, int D,
+                              unsigned char *__restrict__ At = nullptr)
 {
     const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -90,7 +93,16 @@ __global__ void ln_fwd_kernel(const float *__restrict__ X, const float *__restri
         q += dv * dv;
     }
     const float r_s = 1.0f / sqrtf(wsum(q) / D + 1e-5f);
-    for (int j = lane; j < D; j += 32) Y[r * D + j] = (x[j] - mean) * r_s * g[j] + b[j];
+    if (Y)
+        for (int j = lane; j < D; j += 32) Y[r * D + j] = (x[j] - mean) * r_s * g[j] + b[j];
+    if (At) {  // tiled BF16 copy, two columns per lane (D even)
+        const int64_t RB = tl_blocks(R);
+        for (int j = 2 * lane; j < D; j += 64) {
+            const __nv_bfloat162 v = __floats2bfloat162_rn((x[j] - mean) * r_s * g[j] + b[j],
+                                                           (x[j + 1] - mean) * r_s * g[j + 1] + b[j + 1]);
+            *reinterpret_cast<__nv_bfloat162 *>(At + tl_offset(r, j, RB)) = v;
+        }
+    }
     if (lane == 0 && mu) {
         mu[r] = mean;
         rs[r] = r_s;
@@ -672,10 +684,12 @@ attn_fwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ Hi
 {
     constexpr int DP = DH + 4;
     extern __shared__ float4 sm4[];
-    float *Ks = reinterpret_cast<float *>(sm4);
+    float *Qs = reinterpret_cast<float *>(sm4);  // Q in, attention output out
+    float *Ks = Qs + N * DP;
     float *Vs = Ks + N * DP;
     const int b = blockIdx.x / NH, hh = blockIdx.x % NH;
     const float *base = QKV + (size_t)b * N * 3 * D;
+    stage_rows<DH>(Qs, base + hh * DH, N, 3 * D);
     stage_rows<DH>(Ks, base + D + hh * DH, N, 3 * D);
     stage_rows<DH>(Vs, base + 2 * D + hh * DH, N, 3 * D);
     __syncthreads();
@@ -685,7 +699,7 @@ attn_fwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ Hi
         float q[DH], acc[DH];
 #pragma unroll
         for (int j = 0; j < DH; ++j) {
-            q[j] = QKV[r * 3 * D + hh * DH + j] * scale;
+            q[j] = Qs[t * DP + j] * scale;
             acc[j] = 0.f;
         }
         int n_sink, band_lo;
@@ -711,13 +725,19 @@ attn_fwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ Hi
         }
         const float inv = 1.0f / den;
 #pragma unroll
-        for (int j = 0; j < DH; ++j) {
-            const size_t idx = r * D + hh * DH + j;
-            const float o = acc[j] * inv;
-            O[idx] = o;
-            Hmid[idx] = Hin[idx] + o;
-        }
+        for (int j = 0; j < DH; ++j) Qs[t * DP + j] = acc[j] * inv;  // own row only
         LSE[r * NH + hh] = mx + logf(den);
+    }
+    __syncthreads();
+    // coalesced float4 writes of O and Hmid = Hin + O for this head's columns
+    for (int e = threadIdx.x; e < N * (DH / 4); e += blockDim.x) {
+        const int t = e / (DH / 4), c = e % (DH / 4);
+        const size_t idx = ((size_t)b * N + t) * D + hh * DH + 4 * c;
+        const float4 o = *reinterpret_cast<const float4 *>(Qs + t * DP + 4 * c);
+        const float4 hin = *reinterpret_cast<const float4 *>(Hin + idx);
+        *reinterpret_cast<float4 *>(O + idx) = o;
+        *reinterpret_cast<float4 *>(Hmid + idx) =
+            make_float4(hin.x + o.x, hin.y + o.y, hin.z + o.z, hin.w + o.w);
     }
 }
 
@@ -737,7 +757,8 @@ attn_bwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ O,
     float *Ks = Qs + N * DP;
     float *Vs = Ks + N * DP;
     float *Gs = Vs + N * DP;  // dO
-    float *Ls = Gs + N * DP;  // LSE
+    float *Os = Gs + N * DP;  // O in; then the dQ, dK, dV rows out
+    float *Ls = Os + N * DP;  // LSE
     float *Ds = Ls + N;       // D_t = dO_t . O_t
     const int b = blockIdx.x / NH, hh = blockIdx.x % NH;
     const float *base = QKV + (size_t)b * N * 3 * D;
@@ -745,16 +766,27 @@ attn_bwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ O,
     stage_rows<DH>(Ks, base + D + hh * DH, N, 3 * D);
     stage_rows<DH>(Vs, base + 2 * D + hh * DH, N, 3 * D);
     stage_rows<DH>(Gs, dO + (size_t)b * N * D + hh * DH, N, D);
+    stage_rows<DH>(Os, O + (size_t)b * N * D + hh * DH, N, D);
+    for (int t = threadIdx.x; t < N; t += blockDim.x) Ls[t] = LSE[((size_t)b * N + t) * NH + hh];
+    __syncthreads();
     const float scale = rsqrtf((float)DH);
     for (int t = threadIdx.x; t < N; t += blockDim.x) {
-        const size_t r = (size_t)b * N + t;
-        Ls[t] = LSE[r * NH + hh];
         float dd = 0.f;
 #pragma unroll
-        for (int j = 0; j < DH; ++j) dd += dO[r * D + hh * DH + j] * O[r * D + hh * DH + j];
+        for (int j = 0; j < DH; ++j) dd += Gs[t * DP + j] * Os[t * DP + j];
         Ds[t] = dd;
     }
     __syncthreads();
+    // out_part 0/1/2 = q/k/v columns of dQKV: coalesced float4 rows from Os
+    auto flush = [&](int part) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < N * (DH / 4); e += blockDim.x) {
+            const int t = e / (DH / 4), c = e % (DH / 4);
+            *reinterpret_cast<float4 *>(dQKV + ((size_t)b * N + t) * 3 * D + part * D + hh * DH + 4 * c) =
+                *reinterpret_cast<const float4 *>(Os + t * DP + 4 * c);
+        }
+        __syncthreads();
+    };
     // dQ_t = scale * sum_k P_tk (dP_tk - D_t) k_k
     for (int t = threadIdx.x; t < N; t += blockDim.x) {
         float q[DH], g[DH], dq[DH];
@@ -775,13 +807,20 @@ attn_bwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ O,
 #pragma unroll
             for (int j = 0; j < DH; ++j) dq[j] += ds * Ks[k * DP + j];
         }
-        float *out = dQKV + ((size_t)b * N + t) * 3 * D + hh * DH;
 #pragma unroll
-        for (int j = 0; j < DH; ++j) out[j] = dq[j];
+        for (int j = 0; j < DH; ++j) Os[t * DP + j] = dq[j];  // own row
     }
-    // keys seen only through the band: one thread per key
+    flush(0);
+    // dK and dV.  Keys seen only through the band: one thread per key, up to
+    // W + 1 queries each; keys visible to every later query (sink, or all keys
+    // when dense): one warp per key, lanes over queries, shuffle reduction.
+    // Each key's dV is parked in registers while dK goes out first.
     const int k_band0 = mask == SG_MASK_DENSE ? N : (S < N ? S : N);
-    for (int k = k_band0 + threadIdx.x; k < N; k += blockDim.x) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    constexpr int KPT = 2;  // band keys per thread kept in registers (N <= 512)
+    float dv_keep[KPT][DH];
+    int kk_i = 0;
+    for (int k = k_band0 + threadIdx.x; k < N; k += blockDim.x, ++kk_i) {
         float key[DH], val[DH], dk[DH], dv[DH];
 #pragma unroll
         for (int j = 0; j < DH; ++j) {
@@ -799,15 +838,12 @@ attn_bwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ O,
                 dv[j] += p * Gs[t * DP + j];
             }
         }
-        float *out = dQKV + ((size_t)b * N + k) * 3 * D + hh * DH;
 #pragma unroll
         for (int j = 0; j < DH; ++j) {
-            out[D + j] = dk[j];
-            out[2 * D + j] = dv[j];
+            Os[k * DP + j] = dk[j];
+            if (kk_i < KPT) dv_keep[kk_i][j] = dv[j];
         }
     }
-    // keys visible to every later query (sink, or all keys when dense): warps
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int k = warp; k < k_band0; k += nw) {
         float key[DH], val[DH], dk[DH], dv[DH];
 #pragma unroll
@@ -830,27 +866,44 @@ attn_bwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ O,
             dk[j] = wsum(dk[j]);
             dv[j] = wsum(dv[j]);
         }
-        if (lane == 0) {
-            float *out = dQKV + ((size_t)b * N + k) * 3 * D + hh * DH;
+        // dK to the output buffer; dV parked in row k of Vs, which nothing
+        // reads again (the dQ phase is over and key k is owned by this warp)
+        if (lane == 0)
 #pragma unroll
             for (int j = 0; j < DH; ++j) {
-                out[D + j] = dk[j];
-                out[2 * D + j] = dv[j];
+                Os[k * DP + j] = dk[j];
+                Vs[k * DP + j] = dv[j];
             }
-        }
     }
+    flush(1);
+    // dV: band keys from registers, sink keys from their parked rows in Vs
+    kk_i = 0;
+    for (int k = k_band0 + threadIdx.x; k < N; k += blockDim.x, ++kk_i)
+#pragma unroll
+        for (int j = 0; j < DH; ++j) Os[k * DP + j] = dv_keep[kk_i < KPT ? kk_i : 0][j];
+    for (int k = warp; k < k_band0; k += nw)
+        if (lane == 0)
+#pragma unroll
+            for (int j = 0; j < DH; ++j) Os[k * DP + j] = Vs[k * DP + j];
+    flush(2);
 }
 
 constexpr size_t kAttnSmemMax = 200 * 1024;
 
 template <int DH>
-size_t attn_bwd_smem_bytes(int N) { return ((size_t)4 * N * (DH + 4) + 2 * N) * sizeof(float); }
+size_t attn_bwd_smem_bytes(int N)
+{
+    // Q, K, V, dO, O/out rows + LSE, D.  The backward keeps at most two band
+    // keys' dV per thread in registers, so it serves N <= 512 (256 threads).
+    if (N > 512) return (size_t)1 << 40;
+    return ((size_t)5 * N * (DH + 4) + 2 * N) * sizeof(float);
+}
 
 template <int DH>
 void attn_fwd(const float *QKV, const float *Hin, float *O, float *Hmid, float *LSE, int Bc,
               const sg_config &c, cudaStream_t st)
 {
-    const size_t fwd_smem = (size_t)2 * c.N * (DH + 4) * sizeof(float);
+    const size_t fwd_smem = (size_t)3 * c.N * (DH + 4) * sizeof(float);
     if (attn_bwd_smem_bytes<DH>(c.N) <= kAttnSmemMax) {
         cudaFuncSetAttribute(attn_fwd_smem_kernel<DH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)fwd_smem);
@@ -1052,21 +1105,22 @@ void forward_chunk(sg_model *m, const int8_t *spins, int Bc, Work &w, bool keep,
         float *Hin = keep ? L.Hin : H;
         float *Hout = keep ? (l + 1 < c.n_layers ? w.layers[l + 1].Hin : w.Hfin)
                            : (H == w.Hping ? w.Hfin : w.Hping);
-        ln_fwd_kernel<<<blocks_for(R, 8), 256, 0, ::sg::counted(st)>>>(Hin, W + o.ln1g, W + o.ln1b, L.A1, L.mu1,
-                                                        L.rs1, R, D);
-        if (use_tc(c)) {
-            // tensor-core GEMMs over tiled BF16 operands
+        const bool tcp = use_tc(c);
+        ln_fwd_kernel<<<blocks_for(R, 8), 256, 0, ::sg::counted(st)>>>(
+            Hin, W + o.ln1g, W + o.ln1b, tcp ? nullptr : L.A1, L.mu1, L.rs1, R, D,
+            tcp ? L.A1t : nullptr);
+        if (tcp) {
+            // tensor-core GEMMs over tiled BF16 operands; the LayerNorms write
+            // the tiled A operands directly
             const unsigned char *bt = (const unsigned char *)m->bt;
-            launch_to_tiled(L.A1, R, D, D, L.A1t, false, st);
             RowGemm g{};
             g.A = L.A1t; g.RB = tl_blocks(R); g.KC = (D + 63) / 64; g.R = R; g.err = (int *)m->err;
             g.Bw = bt + m->bt_off[l][0]; g.NBw = (int)tl_blocks(3 * D); g.N = 3 * D;
             g.bias = m->wt + m->pack.bqkv[l]; g.out_f32 = L.QKV; g.ld_out = 3 * D;
             launch_row_gemm(g, TE_STORE_F32, st);
             attn_fwd_dispatch(dh, L.QKV, Hin, L.O, L.Hmid, L.LSE, Bc, c, st);
-            ln_fwd_kernel<<<blocks_for(R, 8), 256, 0, ::sg::counted(st)>>>(L.Hmid, W + o.ln2g, W + o.ln2b, L.A2,
-                                                                L.mu2, L.rs2, R, D);
-            launch_to_tiled(L.A2, R, D, D, L.A2t, false, st);
+            ln_fwd_kernel<<<blocks_for(R, 8), 256, 0, ::sg::counted(st)>>>(
+                L.Hmid, W + o.ln2g, W + o.ln2b, nullptr, L.mu2, L.rs2, R, D, L.A2t);
             g.A = L.A2t; g.Bw = bt + m->bt_off[l][1]; g.NBw = (int)tl_blocks(F); g.N = F;
             g.bias = m->wt + m->pack.b1[l]; g.out_t = L.Gt; g.out_t2 = L.F1t;
             launch_row_gemm(g, TE_GELU_T, st);
@@ -1209,7 +1263,7 @@ sg_status launch_grad_f32(sg_model *m, const int8_t *spins, const float *coeff, 
             wgrad(w.TdH, D, w.TG, F, grad + o.W2);
             colsum(w.dH, D, R, D, grad + o.b2, st);
             launch_tiled_transpose(w.dF1t, R, F, w.TdF1, st);
-            launch_to_tiled(L.A2, R, D, D, w.TA2, true, st);
+            launch_tiled_transpose(L.A2t, R, D, w.TA2, st);
             wgrad(w.TdF1, F, w.TA2, D, grad + o.W1);
             {
                 const int64_t rpb = 4096;
@@ -1226,7 +1280,7 @@ sg_status launch_grad_f32(sg_model *m, const int8_t *spins, const float *coeff, 
             attn_bwd_dispatch(dh, L.QKV, L.O, w.dHmid, L.LSE, w.dQKV, w.Dt, Bc, c, st);
             launch_to_tiled(w.dQKV, R, 3 * D, 3 * D, w.dQKVt, false, st);
             launch_to_tiled(w.dQKV, R, 3 * D, 3 * D, w.TdQKV, true, st);
-            launch_to_tiled(L.A1, R, D, D, w.TA1, true, st);
+            launch_tiled_transpose(L.A1t, R, D, w.TA1, st);
             wgrad(w.TdQKV, 3 * D, w.TA1, D, grad + o.Wqkv);
             colsum(w.dQKV, 3 * D, R, 3 * D, grad + o.bqkv, st);
             g.A = w.dQKVt; g.KC = (3 * D + 63) / 64; g.Bw = bt + m->bt_off[l][5];
