@@ -220,7 +220,8 @@ def run_ours(args):
     wl = inputs.workloads()[args.workload]
     m, B = wl.model, wl.B
     beta = wl.betas[len(wl.betas) // 2]
-    prec = {"auto": sg.SG_FP32, "fp32": sg.SG_FP32, "bf16": sg.SG_BF16}[args.precision]
+    # BF16 (tensor cores) is the headline; "auto" also times the FP32 plain path
+    prec = {"auto": sg.SG_BF16, "fp32": sg.SG_FP32, "bf16": sg.SG_BF16}[args.precision]
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
 
@@ -356,6 +357,19 @@ def run_ours(args):
             "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
             "free_energy_last_step": {"F_q_per_spin": F[0] / m.N, "F_IS_per_spin": F[1] / m.N,
                                       "kish_ess": F[2]}}
+    if args.precision == "auto":
+        # the FP32 plain path on the same workload and step, for the BF16/FP32 ratio
+        del model, inst, bufs
+        torch.cuda.empty_cache()
+        _, _, bufs32, ms32, dec32, _, _ = timed_run(sg.SG_FP32, False)
+        F32 = bufs32["F"].cpu().numpy()
+        alg32 = decode_bytes_per_sample(m, 4) * B
+        line["fp32_plain"] = {
+            "value": B * world * args.steps / (ms32 / 1e3), "unit": UNIT,
+            "ms_per_step": ms32 / args.steps, "decode_ms": dec32,
+            "decode_roofline_frac": alg32 / (dec32 / 1e3) / 1e9 / peak,
+            "F_IS_per_spin_last_step": F32[1] / m.N}
+        line["bf16_over_fp32"] = value / line["fp32_plain"]["value"]
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, beta, args.cpu_seconds)
     if rank == 0:

@@ -467,6 +467,360 @@ __global__ void __launch_bounds__(kThreads, 1) decode_bf16_kernel(const __grid_c
 }
 
 // ---------------------------------------------------------------------------
+// d = 64 (4 heads of 16, d_ff = 256) with four threads per sample: thread
+// (row r, quarter qr) keeps h[r][16 qr .. 16 qr + 15] and serves head qr.
+// The 512 threads (16 warps) keep twice as many KV loads in flight as two
+// threads per row do, and split the LayerNorm and GELU epilogues four ways.
+// Weights stream per layer into three buffers exactly as in the kernel above.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512, 1) decode_bf16_d64_kernel(const __grid_constant__ DecodeArgs a)
+{
+    constexpr int D = 64, DFF = 256, DH = 16, KG = D / 8, KG2 = DFF / 8;
+    constexpr uint32_t QKV_COL = 0, FF2_COL = 3 * D, FF1_COL = 256;
+    constexpr uint32_t A_BYTES = kRows * D * 2, A2_BYTES = kRows * DFF * 2;
+    constexpr uint32_t WQKV_BYTES = 3 * D * D * 2, W1_BYTES = DFF * D * 2, W2_BYTES = D * DFF * 2;
+
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *Abuf = smem;
+    unsigned char *A2buf = Abuf + A_BYTES;
+    unsigned char *Wq = A2buf + A2_BYTES;
+    unsigned char *W1s = Wq + WQKV_BYTES;
+    unsigned char *W2s = W1s + W1_BYTES;
+    float *xln = reinterpret_cast<float *>(W2s + W2_BYTES);  // [4][128][2]
+    float *xhd = xln + 4 * kRows * 2;                          // [4][128][2]
+    uint32_t *koff = reinterpret_cast<uint32_t *>(xhd + 4 * kRows * 2);  // [N]
+    __shared__ uint64_t wbar[3], mbar;
+    __shared__ uint32_t tslot;
+    __shared__ int s_err;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int r = 32 * (warp & 3) + lane, qr = warp >> 2;
+    const int64_t b = (int64_t)blockIdx.x * a.rows_per_cta + r;
+    const bool active = r < a.rows_per_cta && b < a.B;
+    const Bf16Geom g = bgeom(a.mask, a.N, a.W, a.S);
+    const size_t slot_bytes = (size_t)2 * D * kRows * 2;
+    const size_t layer_bytes = slot_bytes * g.nslots;
+    unsigned char *kvt = a.kv + (size_t)blockIdx.x * layer_bytes * a.L;
+    const int nfw = (a.N + 31) >> 5;
+    const uint32_t tq = (uint32_t)(32 * (warp & 3)) << 16;
+
+    if (tid == 0) {
+        tc::mbar_init(&wbar[0], 1);
+        tc::mbar_init(&wbar[1], 1);
+        tc::mbar_init(&wbar[2], 1);
+        tc::mbar_init(&mbar, 1);
+        tc::fence_mbar_init();
+        s_err = 0;
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(&tslot, 512);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = tslot;
+
+    uint32_t wphase[3] = {0, 0, 0}, mphase = 0;
+    bool wpending[3] = {false, false, false};
+    auto issue = [&](int which, int layer) {
+        const unsigned char *src = a.bf + (size_t)layer * a.bf_layer_bytes;
+        unsigned char *dst = which == 0 ? Wq : (which == 1 ? W1s : W2s);
+        const uint32_t bytes = which == 0 ? WQKV_BYTES : (which == 1 ? W1_BYTES : W2_BYTES);
+        const size_t off = which == 0 ? 0 : (which == 1 ? WQKV_BYTES : WQKV_BYTES + W1_BYTES);
+        tc::mbar_arrive_expect_tx(&wbar[which], bytes);
+        tc::bulk_g2s(dst, src + off, bytes, &wbar[which]);
+        wpending[which] = true;
+    };
+    if (tid == 0) {
+        issue(0, 0);
+        issue(1, 0);
+        issue(2, 0);
+    }
+
+    float h[DH];
+    float lq = 0.f;
+    int tok = 0;
+    const float qscale = 0.25f;  // 1 / sqrt(16)
+
+    auto gemm = [&](int which, const unsigned char *A, uint32_t a_kg, const unsigned char *Bw,
+                    uint32_t n, uint32_t k_total, uint32_t col) {
+        if (tid == 0) {
+            bool ok = s_err == 0 && tc::mbar_wait(&wbar[which], wphase[which]);
+            if (ok) {
+                wphase[which] ^= 1u;
+                wpending[which] = false;
+                tc::tc_fence_after();
+                const uint32_t idesc = tc::idesc_bf16(kRows, (int)n);
+                const uint32_t sa = tc::smem_u32(A), sb = tc::smem_u32(Bw);
+                for (uint32_t s = 0; s < k_total / 16; ++s)
+                    tc::mma_bf16(tmem + col, tc::smem_desc(sa + 256 * s, 128, a_kg * 128),
+                                 tc::smem_desc(sb + 256 * s, 128, a_kg * 128), idesc, s > 0);
+            } else {
+                atomicExch(a.err, 1);
+                s_err = 1;
+            }
+            tc::mma_commit(&mbar);
+        }
+        __syncwarp();
+        if (!tc::mbar_wait(&mbar, mphase)) {
+            if (lane == 0) atomicExch(a.err, 2);
+            s_err = 1;
+        }
+        mphase ^= 1u;
+        __syncthreads();
+        tc::tc_fence_after();
+    };
+
+    // LayerNorm of the row (statistics from the four quarters) into the A tile
+    auto layernorm_to = [&](const float *gam, const float *bet) {
+        float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+        for (int j = 0; j < DH; ++j) {
+            s1 += h[j];
+            s2 += h[j] * h[j];
+        }
+        xln[(qr * kRows + r) * 2] = s1;
+        xln[(qr * kRows + r) * 2 + 1] = s2;
+        __syncthreads();
+        float t1 = 0.f, t2 = 0.f;
+#pragma unroll
+        for (int q4 = 0; q4 < 4; ++q4) {
+            t1 += xln[(q4 * kRows + r) * 2];
+            t2 += xln[(q4 * kRows + r) * 2 + 1];
+        }
+        const float mean = t1 * (1.0f / D);
+        const float var = fmaxf(t2 * (1.0f / D) - mean * mean, 0.f);
+        const float rs = 1.0f / sqrtf(var + 1e-5f);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int d = DH * qr + 8 * c + j;
+                v[j] = (h[8 * c + j] - mean) * rs * __ldg(gam + d) + __ldg(bet + d);
+            }
+            store8(Abuf, r, DH * qr + 8 * c, KG, v);
+        }
+        tc::fence_async_smem();
+        tc::tc_fence_before();
+        __syncthreads();
+    };
+
+    for (int t = 0; t < a.N && !s_err; ++t) {
+        {
+            const float *pos = a.w + a.o.pos + (size_t)t * (D - a.dt);
+#pragma unroll
+            for (int j = 0; j < DH; ++j) {
+                const int d = DH * qr + j;
+                h[j] = d < a.dt ? __ldg(a.w + a.o.tok + tok * a.dt + d) : __ldg(pos + d - a.dt);
+            }
+        }
+        int n_sink, band_lo;
+        visible_ranges(a.mask, a.W, a.S, t, n_sink, band_lo);
+        const int slot_t = bslot(g, a.S, a.W, t);
+        const int nk_all = n_sink + band_count(t, band_lo) - 1;  // keys < t
+        const int nk = active ? nk_all : 0;
+        // ring offsets (in 16-byte units) of this step's visible keys, the same
+        // for every row and layer: computed once, read as broadcasts
+        for (int i = tid; i < nk_all; i += blockDim.x)
+            koff[i] = (uint32_t)bslot(g, a.S, a.W, i < n_sink ? i : band_lo + (i - n_sink)) *
+                      (uint32_t)(slot_bytes / 16);
+        // (the first LayerNorm's barrier orders these writes before any read)
+
+        for (int l = 0; l < a.L; ++l) {
+            const LayerOff &o = a.o.L[l];
+            const bool last = (t == a.N - 1) && (l == a.L - 1);
+            const int nl = l + 1 < a.L ? l + 1 : 0;
+            layernorm_to(a.w + o.ln1g, a.w + o.ln1b);
+            gemm(0, Abuf, KG, Wq, 3 * D, D, QKV_COL);
+            if (tid == 0 && !last && !s_err) issue(0, nl);
+            if (s_err) break;
+            {
+                float q[DH], acc[DH], tmp[DH];
+                const float *bq = a.wt + a.p.bqkv[l];
+                tc::tmem_ld16(tmem + tq + QKV_COL + DH * qr, q);
+                tc::tmem_ld16(tmem + tq + QKV_COL + D + DH * qr, tmp);
+                tc::tmem_ld16(tmem + tq + QKV_COL + 2 * D + DH * qr, acc);
+                tc::tmem_wait_ld();
+                float m0 = 0.f, l0 = 1.f;
+#pragma unroll
+                for (int j = 0; j < DH; ++j) {
+                    q[j] = (q[j] + __ldg(bq + DH * qr + j)) * qscale;
+                    tmp[j] = round_bf(tmp[j] + __ldg(bq + D + DH * qr + j));      // k_t
+                    acc[j] = round_bf(acc[j] + __ldg(bq + 2 * D + DH * qr + j));  // v_t
+                    m0 += q[j] * tmp[j];
+                }
+                unsigned char *kvl = kvt + (size_t)l * layer_bytes;
+                if (active) {
+                    uint4 *dk = reinterpret_cast<uint4 *>(kvl + (size_t)slot_t * slot_bytes);
+                    uint4 *dv = dk + (D / 8) * kRows;
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        uint4 x, y;
+                        x.x = pack_bf2(tmp[8 * c], tmp[8 * c + 1]);
+                        x.y = pack_bf2(tmp[8 * c + 2], tmp[8 * c + 3]);
+                        x.z = pack_bf2(tmp[8 * c + 4], tmp[8 * c + 5]);
+                        x.w = pack_bf2(tmp[8 * c + 6], tmp[8 * c + 7]);
+                        y.x = pack_bf2(acc[8 * c], acc[8 * c + 1]);
+                        y.y = pack_bf2(acc[8 * c + 2], acc[8 * c + 3]);
+                        y.z = pack_bf2(acc[8 * c + 4], acc[8 * c + 5]);
+                        y.w = pack_bf2(acc[8 * c + 6], acc[8 * c + 7]);
+                        dk[(2 * qr + c) * kRows + r] = x;
+                        dv[(2 * qr + c) * kRows + r] = y;
+                    }
+                }
+                // keys < t of head qr straight from the ring, one key prefetched
+                const uint4 *kb = reinterpret_cast<const uint4 *>(kvl) + (2 * qr) * kRows + r;
+                uint4 ck[2], cv[2];
+                if (nk > 0) {
+                    const uint4 *p = kb + koff[0];
+                    ck[0] = __ldcg(p);
+                    ck[1] = __ldcg(p + kRows);
+                    cv[0] = __ldcg(p + (D / 8) * kRows);
+                    cv[1] = __ldcg(p + (D / 8) * kRows + kRows);
+                }
+                for (int i = 0; i < nk; ++i) {
+                    uint4 nk2[2], nv2[2];
+                    if (i + 1 < nk) {
+                        const uint4 *p = kb + koff[i + 1];
+                        nk2[0] = __ldcg(p);
+                        nk2[1] = __ldcg(p + kRows);
+                        nv2[0] = __ldcg(p + (D / 8) * kRows);
+                        nv2[1] = __ldcg(p + (D / 8) * kRows + kRows);
+                    }
+                    float s = 0.f;
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        const uint32_t wk[4] = {ck[c].x, ck[c].y, ck[c].z, ck[c].w};
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            s += q[8 * c + 2 * j] * bf_lo(wk[j]) + q[8 * c + 2 * j + 1] * bf_hi(wk[j]);
+                    }
+                    const float n0 = fmaxf(m0, s);
+                    const float c0 = __expf(m0 - n0), p0 = __expf(s - n0);
+                    m0 = n0;
+                    l0 = l0 * c0 + p0;
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        const uint32_t wv[4] = {cv[c].x, cv[c].y, cv[c].z, cv[c].w};
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            acc[8 * c + 2 * j] = acc[8 * c + 2 * j] * c0 + p0 * bf_lo(wv[j]);
+                            acc[8 * c + 2 * j + 1] = acc[8 * c + 2 * j + 1] * c0 + p0 * bf_hi(wv[j]);
+                        }
+                    }
+                    ck[0] = nk2[0];
+                    ck[1] = nk2[1];
+                    cv[0] = nv2[0];
+                    cv[1] = nv2[1];
+                }
+                const float inv = 1.0f / l0;
+#pragma unroll
+                for (int j = 0; j < DH; ++j) h[j] += acc[j] * inv;
+            }
+            layernorm_to(a.w + o.ln2g, a.w + o.ln2b);
+            gemm(1, Abuf, KG, W1s, DFF, D, FF1_COL);
+            if (tid == 0 && !last && !s_err) issue(1, nl);
+            if (s_err) break;
+            {
+                const float *b1 = a.wt + a.p.b1[l];
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    float v[32];
+                    tc::tmem_ld32(tmem + tq + FF1_COL + 64 * qr + 32 * c, v);
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int g8 = 0; g8 < 4; ++g8) {
+                        float x[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            x[j] = gelu_f(v[8 * g8 + j] + __ldg(b1 + 64 * qr + 32 * c + 8 * g8 + j));
+                        store8(A2buf, r, 64 * qr + 32 * c + 8 * g8, KG2, x);
+                    }
+                }
+                tc::fence_async_smem();
+                tc::tc_fence_before();
+                __syncthreads();
+            }
+            gemm(2, A2buf, KG2, W2s, D, DFF, FF2_COL);
+            if (tid == 0 && !last && !s_err) issue(2, nl);
+            if (s_err) break;
+            {
+                float v[16];
+                tc::tmem_ld16(tmem + tq + FF2_COL + DH * qr, v);
+                tc::tmem_wait_ld();
+                const float *b2 = a.wt + a.p.b2[l];
+#pragma unroll
+                for (int j = 0; j < DH; ++j) h[j] += v[j] + __ldg(b2 + DH * qr + j);
+            }
+        }
+        if (s_err) break;
+        {
+            float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+            for (int j = 0; j < DH; ++j) {
+                s1 += h[j];
+                s2 += h[j] * h[j];
+            }
+            xln[(qr * kRows + r) * 2] = s1;
+            xln[(qr * kRows + r) * 2 + 1] = s2;
+            __syncthreads();
+            float t1 = 0.f, t2 = 0.f;
+#pragma unroll
+            for (int q4 = 0; q4 < 4; ++q4) {
+                t1 += xln[(q4 * kRows + r) * 2];
+                t2 += xln[(q4 * kRows + r) * 2 + 1];
+            }
+            const float mean = t1 * (1.0f / D);
+            const float var = fmaxf(t2 * (1.0f / D) - mean * mean, 0.f);
+            const float rs = 1.0f / sqrtf(var + 1e-5f);
+            float z0 = 0.f, z1 = 0.f;
+#pragma unroll
+            for (int j = 0; j < DH; ++j) {
+                const int d = DH * qr + j;
+                const float y = (h[j] - mean) * rs * __ldg(a.w + a.o.lnfg + d) + __ldg(a.w + a.o.lnfb + d);
+                z0 += y * __ldg(a.w + a.o.Wh + d);
+                z1 += y * __ldg(a.w + a.o.Wh + D + d);
+            }
+            xhd[(qr * kRows + r) * 2] = z0;
+            xhd[(qr * kRows + r) * 2 + 1] = z1;
+            __syncthreads();
+            if (qr == 0) {
+                z0 = __ldg(a.w + a.o.bh);
+                z1 = __ldg(a.w + a.o.bh + 1);
+#pragma unroll
+                for (int q4 = 0; q4 < 4; ++q4) {
+                    z0 += xhd[(q4 * kRows + r) * 2];
+                    z1 += xhd[(q4 * kRows + r) * 2 + 1];
+                }
+                const float ell = z1 - z0;
+                const float p = 1.0f / (1.0f + expf(-ell));
+                const float u = philox_uniform(a.seed, (uint32_t)b, (uint32_t)t, a.sid, 0u);
+                const int sp = u < p ? 1 : -1;
+                lq += log_sigmoid_f((float)sp * ell);
+                tok = (sp + 1) >> 1;
+                if (active) {
+                    a.spins[(size_t)b * a.N + t] = (int8_t)sp;
+                    if (a.flags && fabsf(p - u) < a.band)
+                        a.flags[(size_t)b * nfw + (t >> 5)] |= 1u << (t & 31);
+                    if (!isfinite(ell)) atomicOr(a.err, 4);
+                }
+            }
+            // tok lives in the qr == 0 thread, which is the only one that
+            // reads it (the token columns are in quarter 0)
+        }
+    }
+    if (qr == 0 && active) a.logq[b] = lq;
+    if (tid == 0)
+        for (int i = 0; i < 3; ++i)
+            if (wpending[i] && !tc::mbar_wait(&wbar[i], wphase[i])) atomicExch(a.err, 3);
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+// ---------------------------------------------------------------------------
 // d = 128 variant (8 heads of 16, d_ff = 512).  512 threads: thread (row r,
 // quarter qr) keeps h[r][32 qr .. 32 qr + 31] and serves heads 2 qr, 2 qr + 1
 // one after the other.  Weights are too large to hold per layer, so every
@@ -944,6 +1298,16 @@ sg_status launch_decode_bf16(sg_model *m, int64_t B, uint64_t seed, uint32_t sid
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem128));
         decode_bf16_d128_kernel<<<(unsigned)tiles, 512, smem128, ::sg::counted(st)>>>(a);
         return check_launch("decode_bf16_d128_kernel");
+    }
+    if (c.d_token <= 16) {
+        // four threads per sample (16 warps): the default for d = 64
+        const size_t smem4 = smem + 4 * kRows * 2 * sizeof(float) + (size_t)c.N * sizeof(uint32_t);
+        if (smem4 > 227 * 1024)
+            return fail(SG_EUNSUPPORTED, "BF16 decode (d = 64) needs N <= 11000");
+        SG_CUDA_TRY(cudaFuncSetAttribute(decode_bf16_d64_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem4));
+        decode_bf16_d64_kernel<<<(unsigned)tiles, 512, smem4, ::sg::counted(st)>>>(a);
+        return check_launch("decode_bf16_d64_kernel");
     }
     SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<(unsigned)tiles, kThreads, smem, ::sg::counted(st)>>>(a);
