@@ -61,6 +61,32 @@ def decode_bytes_per_sample(m, elem_bytes):
     return float(vis.sum() * per_key + m.N * per_key)
 
 
+def captured_traffic(precision_bf16):
+    """DRAM bytes per decode launch from the committed ncu summary, or None if
+    the decode sources changed since that capture."""
+    import hashlib
+
+    if not precision_bf16:
+        return None
+    csrc = os.path.join(ROOT, "paper_2606_22984_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in ("decode_bf16.cu", "tc.cuh", "sg_internal.cuh"):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    summary = os.path.join(ROOT, "profiles", "decode_bf16_ea2d16_b16384.md")
+    if not os.path.exists(summary):
+        return None
+    fields = {}
+    with open(summary) as fh:
+        for line in fh:
+            if ":" in line and line.split(":")[0] in ("traffic_bytes_per_launch", "source_sha256"):
+                k, v = line.split(":", 1)
+                fields[k] = v.strip()
+    if fields.get("source_sha256") != h.hexdigest()[:16]:
+        return None
+    return float(fields["traffic_bytes_per_launch"])
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -133,6 +159,15 @@ def cpu_info():
                     break
     except OSError:
         pass
+    if model == "unknown":  # Arm hosts: lscpu names the core
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
     return os.cpu_count() or 1, model
 
 
@@ -341,8 +376,9 @@ def run_ours(args):
     alg = decode_bytes_per_sample(m, elem) * B
     peak, peak_kind = measured_peaks()
     achieved = alg / (dec_ms / 1e3) / 1e9
+    traffic = captured_traffic(prec == sg.SG_BF16) if args.workload == "ea2d16" else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "decode",
+                "frac": achieved / peak, "traffic": traffic, "kernel": "decode",
                 "peak_kind": peak_kind, "algorithmic_bytes": alg,
                 "decode_ms": dec_ms, "decode_share_of_step": dec_ms / ms_step}
     F = bufs["F"].cpu().numpy()

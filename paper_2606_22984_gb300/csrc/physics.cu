@@ -338,6 +338,10 @@ sg_status launch_energy(const sg_instance *inst, const int8_t *spins, int64_t B,
                                                             nullptr);
         return check_launch("ea_energy_kernel");
     }
+    if (prec == SG_BF16 && sk_tc_supported(inst->N)) {
+        sg_instance *mi = const_cast<sg_instance *>(inst);  // workspace only
+        return launch_energy_sk_tc(inst, spins, B, E, &mi->ws, &mi->ws_bytes, (int *)mi->err, st);
+    }
     const size_t smem = (size_t)64 * inst->N;
     if (smem > 200 * 1024) return fail(SG_EUNSUPPORTED, "SK energy on CUDA cores needs N <= 3200");
     SG_CUDA_TRY(cudaFuncSetAttribute(sk_energy_f32_kernel,

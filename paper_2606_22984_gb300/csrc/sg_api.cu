@@ -302,6 +302,11 @@ sg_status sg_instance_create(int32_t kind, int32_t N, int32_t D, int32_t L, int3
             inst->integer_bonds = s == SG_OK;
         }
     }
+    have = 0;
+    if (s == SG_OK) s = ensure_buffer(&inst->err, &have, sizeof(int));
+    if (s == SG_OK && cudaMemset(inst->err, 0, sizeof(int)) != cudaSuccess)
+        s = fail(SG_ECUDA, "clearing the error word failed");
+    if (s == SG_OK && kind == SG_SK_DENSE) s = prepare_sk_tc(inst);
     if (s != SG_OK) {
         sg_instance_destroy(inst);
         return s;
@@ -317,6 +322,8 @@ sg_status sg_instance_destroy(sg_instance *inst)
     cudaFree(inst->J);
     cudaFree(inst->Ji8);
     cudaFree(inst->Jbf);
+    cudaFree(inst->ws);
+    cudaFree(inst->err);
     delete inst;
     return SG_OK;
 }

@@ -183,6 +183,10 @@ struct sg_instance {
     float *J = nullptr;       // SK: [N][N]; EA: bonds [N][D]
     int8_t *Ji8 = nullptr;    // EA with integer bonds: bonds as int8
     void *Jbf = nullptr;      // SK: BF16 hi/lo split of J, tensor-core layout
+    void *ws = nullptr;       // SK tensor-core path: tiled spins
+    size_t ws_bytes = 0;
+    void *err = nullptr;      // device error word
+    size_t err_bytes = 0;
 };
 
 namespace sg {
@@ -192,6 +196,10 @@ sg_status ensure_buffer(void **ptr, size_t *have, size_t need);
 sg_status launch_pack_f32(sg_model *m, cudaStream_t st);
 sg_status launch_pack_bf16(sg_model *m, cudaStream_t st);
 sg_status launch_pack_tiled_weights(sg_model *m, cudaStream_t st);
+bool sk_tc_supported(int N);
+sg_status prepare_sk_tc(sg_instance *inst);
+sg_status launch_energy_sk_tc(const sg_instance *inst, const int8_t *spins, int64_t B, float *E,
+                              void **ws, size_t *ws_bytes, int *err, cudaStream_t st);
 sg_status launch_decode_bf16(sg_model *m, int64_t B, uint64_t seed, uint32_t sid, float band,
                              int8_t *spins, float *logq, uint32_t *flags, cudaStream_t st);
 sg_status launch_decode_f32(sg_model *m, int64_t B, uint64_t seed, uint32_t sid, float band,

@@ -211,6 +211,21 @@ def test_sk_energy_fp32(N, B):
     assert np.allclose(E, Eo, rtol=1e-5, atol=1e-4)
 
 
+@pytest.mark.parametrize("N,B", [(256, 1), (256, 130), (1024, 8192)])
+def test_sk_energy_bf16_tensor_cores(N, B):
+    """s.J.s on tcgen05 with J split into two BF16 terms: FP32-level accuracy."""
+    inst = inputs.make_sk(N, N + 1)
+    s = inputs.random_spins(B, N, 5)
+    gi = sg.Instance(inst)
+    ts = torch.tensor(s, device="cuda")
+    E = _np(gi.energy(ts, precision=sg.SG_BF16))
+    E32 = _np(gi.energy(ts, precision=sg.SG_FP32))
+    rows = np.arange(B) if B <= 256 else np.linspace(0, B - 1, 256).astype(int)
+    Eo = oracle.energy(inst, s[rows])
+    assert np.allclose(E[rows], Eo, rtol=1e-5, atol=1e-3)
+    assert np.allclose(E, E32, rtol=1e-5, atol=1e-3)
+
+
 # --------------------------------------------------------------------------
 # Free energies (FP64 on the device)
 # --------------------------------------------------------------------------
