@@ -74,12 +74,18 @@ typedef enum { SG_SK_DENSE = 0, SG_EA_LATTICE = 1 } sg_instance_kind;
  *              SG_BF16: GEMMs on tcgen05 tensor cores with BF16 operands and
  *              FP32 accumulation, BF16 KV cache; LayerNorm, softmax, residual
  *              stream and the draw stay FP32.
+ *   n_models   0 or 1: one model.  n > 1: a group of n models of this shape
+ *              (e.g. one per temperature), weight blobs concatenated; in
+ *              sg_sample, sample b of B uses model b / (B / n).  Grouped
+ *              models are served by the BF16 decode for d = 256; other calls
+ *              return SG_EUNSUPPORTED for n > 1.
  * Key position k holds the token of spin k-1; key 0 holds the start token 0.
  */
 typedef struct {
     int32_t N, n_layers, d, n_heads, d_token, d_ff;
     int32_t mask_kind, W, S;
     int32_t precision;
+    int32_t n_models;
 } sg_config;
 
 typedef struct sg_model sg_model;
@@ -92,7 +98,8 @@ const char *sg_last_error(void);
  * counter, all threads and devices); used to report launches per step. */
 int64_t sg_launch_count(void);
 
-/* Number of floats in the weight blob of cfg, or -1 if cfg is invalid. */
+/* Number of floats in the weight blob of cfg (all n_models blobs), or -1 if
+ * cfg is invalid. */
 int64_t sg_param_count(const sg_config *cfg);
 
 /*

@@ -90,6 +90,11 @@ struct DecodeArgs {
     uint32_t *flags;
     unsigned char *kv;          // KV ring workspace
     int *err;                   // device error word
+    // grouped models (d = 256 kernel): sample b uses model b / rows_per_model
+    int64_t rows_per_model;
+    int64_t stride_w, stride_wt;  // floats between consecutive models' blobs
+    size_t stride_bf;             // bytes between consecutive models' packed chunks
+    int max_keys;                 // capacity of the per-step key-offset table
 };
 
 // Element (r, k) of a core-matrix tile as a 16-byte group store of 8 bf16.
@@ -1212,11 +1217,460 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d128_kernel(const __grid_c
     if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
+// ---------------------------------------------------------------------------
+// d = 256 variant (8 heads of 32, d_ff = 1024).  A row's 256-dim FP32 residual
+// stream does not fit in registers, so it lives in TMEM columns [256, 512);
+// the accumulators use columns [0, 256).  Per layer:
+//   LN1 (h read from TMEM) -> A tile -> MMA k (N = 256) -> ring; MMA v -> ring;
+//   MMA q -> TMEM -> attention of the thread's two heads (keys, including
+//   t itself, read back from the ring) -> h += o (TMEM ld/st) -> LN2 ->
+//   4 x [MMA FFN1 slice -> GELU -> A2 -> MMA FFN2 K-slice accumulated straight
+//   into the residual columns] -> h += b2.
+// Weights stream as 44 chunks of 32 KB per layer ([256 out rows x 64 K]) through
+// a two-stage ring.  Grouped models: CTA c serves rows of model
+// (c * rows_per_cta) / rows_per_model and reads that model's weights.
+// ---------------------------------------------------------------------------
+constexpr int kChunk256 = 256 * 64 * 2;
+constexpr int kChunks256 = 44;
+constexpr int kStages256 = 2;
+
+// chunk c of a layer, element (r, k) of the [256 x 64] operand
+__global__ void pack_chunks256_kernel(const float *__restrict__ Wqkv,
+                                      const float *__restrict__ W1,
+                                      const float *__restrict__ W2, __nv_bfloat16 *__restrict__ dst)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)kChunks256 * 256 * 64) return;
+    const int c = (int)(i / (256 * 64)), r = (int)((i / 64) % 256), k = (int)(i % 64);
+    float v;
+    if (c < 4) v = Wqkv[(size_t)(256 + r) * 256 + 64 * c + k];            // k rows
+    else if (c < 8) v = Wqkv[(size_t)(512 + r) * 256 + 64 * (c - 4) + k];  // v rows
+    else if (c < 12) v = Wqkv[(size_t)r * 256 + 64 * (c - 8) + k];         // q rows
+    else {
+        const int f = c - 12, j = f / 8, w = f % 8;
+        if (w < 4) v = W1[(size_t)(256 * j + r) * 256 + 64 * w + k];
+        else v = W2[(size_t)r * 1024 + 256 * j + 64 * (w - 4) + k];
+    }
+    dst[(size_t)c * (kChunk256 / 2) + (tc::cm_offset(r, k, 8) >> 1)] = __float2bfloat16(v);
+}
+
+__global__ void __launch_bounds__(512, 1) decode_bf16_d256_kernel(const __grid_constant__ DecodeArgs a)
+{
+    constexpr int D = 256, DH = 32, KG = D / 8;
+    constexpr uint32_t ACC = 0, HCOL = 256;
+    constexpr uint32_t A_BYTES = kRows * D * 2;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *Abuf = smem;
+    unsigned char *A2buf = Abuf + A_BYTES;
+    unsigned char *ring = A2buf + A_BYTES;
+    float *xln = reinterpret_cast<float *>(ring + kStages256 * kChunk256);  // [4][128][2]
+    float *xhd = xln + 4 * kRows * 2;                                        // [4][128][2]
+    uint32_t *koff = reinterpret_cast<uint32_t *>(xhd + 4 * kRows * 2);     // [max_keys]
+    __shared__ uint64_t full[kStages256], empty[kStages256], mbar;
+    __shared__ uint32_t tslot;
+    __shared__ int s_err;
+    __shared__ int stok[kRows];  // token of each row drawn at the previous step
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int r = 32 * (warp & 3) + lane, qr = warp >> 2;
+    const int64_t b = (int64_t)blockIdx.x * a.rows_per_cta + r;
+    const bool active = r < a.rows_per_cta && b < a.B;
+    const int64_t mdl = ((int64_t)blockIdx.x * a.rows_per_cta) / a.rows_per_model;
+    const float *w = a.w + mdl * a.stride_w;
+    const float *wt = a.wt + mdl * a.stride_wt;
+    const unsigned char *bf = a.bf + mdl * a.stride_bf;
+    const Bf16Geom g = bgeom(a.mask, a.N, a.W, a.S);
+    const size_t slot_bytes = (size_t)2 * D * kRows * 2;
+    const size_t layer_bytes = slot_bytes * g.nslots;
+    unsigned char *kvt = a.kv + (size_t)blockIdx.x * layer_bytes * a.L;
+    const int nfw = (a.N + 31) >> 5;
+    const uint32_t tq = (uint32_t)(32 * (warp & 3)) << 16;
+    const int64_t total_chunks = (int64_t)a.N * a.L * kChunks256;
+
+    if (tid == 0) {
+        for (int s = 0; s < kStages256; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        tc::mbar_init(&mbar, 1);
+        tc::fence_mbar_init();
+        s_err = 0;
+    }
+    if (tid < kRows) stok[tid] = 0;
+    if (warp == 0) {
+        tc::tmem_alloc(&tslot, 512);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = tslot;
+
+    // chunk stream (thread 0): chunk c sits in stage c % 2; chunk c >= 2 is
+    // loaded once the MMAs of chunk c - 2 have completed (commit on empty[]).
+    int64_t next_load = 0, next_use = 0;
+    uint32_t fphase[kStages256] = {0, 0}, ephase[kStages256] = {0, 0}, mphase = 0;
+    auto load_chunk = [&]() {
+        const int s = (int)(next_load % kStages256);
+        const int64_t lc = next_load % ((int64_t)a.L * kChunks256);
+        tc::mbar_arrive_expect_tx(&full[s], kChunk256);
+        tc::bulk_g2s(ring + (size_t)s * kChunk256, bf + (size_t)lc * kChunk256, kChunk256, &full[s]);
+        ++next_load;
+    };
+    if (tid == 0)
+        while (next_load < total_chunks && next_load < kStages256) load_chunk();
+
+    // MMAs of `nchunks` consecutive K chunks (64 wide) of A x chunk^T into TMEM
+    // column col; accumulate onto existing contents when `onto` is set.
+    auto run = [&](const unsigned char *A, int nchunks, uint32_t col, bool onto) {
+        if (tid == 0) {
+            bool ok = s_err == 0;
+            const uint32_t idesc = tc::idesc_bf16(kRows, 256);
+            for (int i = 0; i < nchunks && ok; ++i) {
+                const int s = (int)(next_use % kStages256);
+                ok = tc::mbar_wait(&full[s], fphase[s]);
+                if (!ok) break;
+                fphase[s] ^= 1u;
+                tc::tc_fence_after();
+                const uint32_t sa = tc::smem_u32(A) + (uint32_t)(8 * i) * 128;
+                const uint32_t sb = tc::smem_u32(ring + (size_t)s * kChunk256);
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    tc::mma_bf16(tmem + col, tc::smem_desc(sa + 256 * k, 128, KG * 128),
+                                 tc::smem_desc(sb + 256 * k, 128, 8 * 128), idesc,
+                                 (onto || i > 0 || k > 0) ? 1u : 0u);
+                tc::mma_commit(&empty[s]);
+                ++next_use;
+                // refill this stage with chunk next_use + 1 once its MMAs are done
+                ok = tc::mbar_wait(&empty[s], ephase[s]);
+                if (!ok) break;
+                ephase[s] ^= 1u;
+                if (next_load < total_chunks) load_chunk();
+            }
+            if (!ok) {
+                atomicExch(a.err, 1);
+                s_err = 1;
+            }
+            tc::mma_commit(&mbar);
+        }
+        __syncwarp();
+        if (!tc::mbar_wait(&mbar, mphase)) {
+            if (lane == 0) atomicExch(a.err, 2);
+            s_err = 1;
+        }
+        mphase ^= 1u;
+        __syncthreads();
+        tc::tc_fence_after();
+    };
+
+    // this thread's 64 columns of a 256-wide TMEM block at `col`
+    auto ld64 = [&](uint32_t col, float (&v0)[32], float (&v1)[32]) {
+        tc::tmem_ld32(tmem + tq + col + 64 * qr, v0);
+        tc::tmem_ld32(tmem + tq + col + 64 * qr + 32, v1);
+        tc::tmem_wait_ld();
+    };
+
+    // LayerNorm of h (TMEM) into the BF16 A tile; also returns nothing else
+    auto layernorm_to = [&](const float *gam, const float *bet) {
+        float v0[32], v1[32];
+        ld64(HCOL, v0, v1);
+        float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            s1 += v0[j] + v1[j];
+            s2 += v0[j] * v0[j] + v1[j] * v1[j];
+        }
+        xln[(qr * kRows + r) * 2] = s1;
+        xln[(qr * kRows + r) * 2 + 1] = s2;
+        __syncthreads();
+        float t1 = 0.f, t2 = 0.f;
+#pragma unroll
+        for (int q4 = 0; q4 < 4; ++q4) {
+            t1 += xln[(q4 * kRows + r) * 2];
+            t2 += xln[(q4 * kRows + r) * 2 + 1];
+        }
+        const float mean = t1 * (1.0f / D);
+        const float var = fmaxf(t2 * (1.0f / D) - mean * mean, 0.f);
+        const float rs = 1.0f / sqrtf(var + 1e-5f);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            float y[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int d = 64 * qr + 8 * c + j;
+                const float x = c < 4 ? v0[8 * c + j] : v1[8 * (c - 4) + j];
+                y[j] = (x - mean) * rs * __ldg(gam + d) + __ldg(bet + d);
+            }
+            store8(Abuf, r, 64 * qr + 8 * c, KG, y);
+        }
+        tc::fence_async_smem();
+        tc::tc_fence_before();
+        __syncthreads();
+    };
+
+    // append this thread's 64 columns of the accumulator (+bias) to the ring
+    auto append = [&](unsigned char *slot, int part, const float *bias) {
+        float v0[32], v1[32];
+        ld64(ACC, v0, v1);
+        if (!active) return;
+        uint4 *dst = reinterpret_cast<uint4 *>(slot) + (size_t)part * (D / 8) * kRows;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            float x[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                x[j] = (c < 4 ? v0[8 * c + j] : v1[8 * (c - 4) + j]) + __ldg(bias + 64 * qr + 8 * c + j);
+            uint4 q;
+            q.x = pack_bf2(x[0], x[1]);
+            q.y = pack_bf2(x[2], x[3]);
+            q.z = pack_bf2(x[4], x[5]);
+            q.w = pack_bf2(x[6], x[7]);
+            dst[(8 * qr + c) * kRows + r] = q;
+        }
+    };
+
+    float lq = 0.f;
+    const float qscale = 0.17677669529663687f;  // 1 / sqrt(32)
+
+    for (int t = 0; t < a.N && !s_err; ++t) {
+        {   // embedding into the residual columns
+            const float *pos = w + a.o.pos + (size_t)t * (D - a.dt);
+            float v[32];
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int d = 64 * qr + 32 * c + j;
+                    v[j] = d < a.dt ? __ldg(w + a.o.tok + stok[r] * a.dt + d) : __ldg(pos + d - a.dt);
+                }
+                tc::tmem_st32(tmem + tq + HCOL + 64 * qr + 32 * c, v);
+            }
+            tc::tmem_wait_st();
+        }
+        int n_sink, band_lo;
+        visible_ranges(a.mask, a.W, a.S, t, n_sink, band_lo);
+        const int slot_t = bslot(g, a.S, a.W, t);
+        const int nk_all = n_sink + band_count(t, band_lo);  // keys <= t
+        const int nk = active ? nk_all : 0;
+        for (int i = tid; i < nk_all; i += blockDim.x)
+            koff[i] = (uint32_t)bslot(g, a.S, a.W, i < n_sink ? i : band_lo + (i - n_sink)) *
+                      (uint32_t)(slot_bytes / 16);
+        for (int l = 0; l < a.L && !s_err; ++l) {
+            const LayerOff &o = a.o.L[l];
+            const float *bq = wt + a.p.bqkv[l];
+            unsigned char *kvl = kvt + (size_t)l * layer_bytes;
+            unsigned char *slot = kvl + (size_t)slot_t * slot_bytes;
+            layernorm_to(w + o.ln1g, w + o.ln1b);
+            run(Abuf, 4, ACC, false);  // k_t
+            if (s_err) break;
+            append(slot, 0, bq + D);
+            tc::tc_fence_before();
+            __syncthreads();  // every thread has drained the accumulator
+            run(Abuf, 4, ACC, false);  // v_t
+            if (s_err) break;
+            append(slot, 1, bq + 2 * D);
+            tc::tc_fence_before();
+            __syncthreads();
+            run(Abuf, 4, ACC, false);  // q_t stays in TMEM
+            if (s_err) break;
+            // attention: heads 2 qr and 2 qr + 1, keys 0..t from the ring
+            // (this thread wrote row r of key t itself, so it sees it)
+#pragma unroll 1
+            for (int p = 0; p < 2; ++p) {
+                const int hh = 2 * qr + p;
+                float q[DH], acc[DH];
+                __syncwarp();
+                tc::tmem_ld32(tmem + tq + ACC + DH * hh, q);
+                tc::tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < DH; ++j) {
+                    q[j] = (q[j] + __ldg(bq + DH * hh + j)) * qscale;
+                    acc[j] = 0.f;
+                }
+                float m0 = -INFINITY, l0 = 0.f;
+                const uint4 *kb = reinterpret_cast<const uint4 *>(kvl) + (4 * hh) * kRows + r;
+                for (int i = 0; i < nk; ++i) {
+                    const uint4 *pp = kb + koff[i];
+                    uint4 ck[4], cv[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        ck[c] = __ldcg(pp + c * kRows);
+                        cv[c] = __ldcg(pp + (D / 8) * kRows + c * kRows);
+                    }
+                    float s = 0.f;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const uint32_t wk[4] = {ck[c].x, ck[c].y, ck[c].z, ck[c].w};
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            s += q[8 * c + 2 * j] * bf_lo(wk[j]) + q[8 * c + 2 * j + 1] * bf_hi(wk[j]);
+                    }
+                    const float n0 = fmaxf(m0, s);
+                    const float c0 = __expf(m0 - n0), p0 = __expf(s - n0);
+                    m0 = n0;
+                    l0 = l0 * c0 + p0;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const uint32_t wv[4] = {cv[c].x, cv[c].y, cv[c].z, cv[c].w};
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            acc[8 * c + 2 * j] = acc[8 * c + 2 * j] * c0 + p0 * bf_lo(wv[j]);
+                            acc[8 * c + 2 * j + 1] = acc[8 * c + 2 * j + 1] * c0 + p0 * bf_hi(wv[j]);
+                        }
+                    }
+                }
+                __syncwarp();
+                float hv[32];
+                tc::tmem_ld32(tmem + tq + HCOL + DH * hh, hv);
+                tc::tmem_wait_ld();
+                const float inv = active ? 1.0f / l0 : 0.f;
+#pragma unroll
+                for (int j = 0; j < DH; ++j) hv[j] += acc[j] * inv;
+                tc::tmem_st32(tmem + tq + HCOL + DH * hh, hv);
+                tc::tmem_wait_st();
+            }
+            tc::tc_fence_before();
+            __syncthreads();
+            tc::tc_fence_after();
+            layernorm_to(w + o.ln2g, w + o.ln2b);
+            const float *b1 = wt + a.p.b1[l];
+            for (int j = 0; j < 4 && !s_err; ++j) {
+                run(Abuf, 4, ACC, false);  // FFN1 slice j
+                if (s_err) break;
+                {
+                    float v0[32], v1[32];
+                    ld64(ACC, v0, v1);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        float x[8];
+#pragma unroll
+                        for (int jj = 0; jj < 8; ++jj) {
+                            const float z = c < 4 ? v0[8 * c + jj] : v1[8 * (c - 4) + jj];
+                            x[jj] = gelu_f(z + __ldg(b1 + 256 * j + 64 * qr + 8 * c + jj));
+                        }
+                        store8(A2buf, r, 64 * qr + 8 * c, KG, x);
+                    }
+                    tc::fence_async_smem();
+                    tc::tc_fence_before();
+                    __syncthreads();
+                }
+                run(A2buf, 4, HCOL, true);  // FFN2 K-slice j, onto the residual
+            }
+            if (s_err) break;
+            {   // h += b2
+                float v0[32], v1[32];
+                ld64(HCOL, v0, v1);
+                const float *b2 = wt + a.p.b2[l];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    v0[j] += __ldg(b2 + 64 * qr + j);
+                    v1[j] += __ldg(b2 + 64 * qr + 32 + j);
+                }
+                tc::tmem_st32(tmem + tq + HCOL + 64 * qr, v0);
+                tc::tmem_st32(tmem + tq + HCOL + 64 * qr + 32, v1);
+                tc::tmem_wait_st();
+                tc::tc_fence_before();
+                __syncthreads();
+                tc::tc_fence_after();
+            }
+        }
+        if (s_err) break;
+        {   // output head and the draw
+            float v0[32], v1[32];
+            ld64(HCOL, v0, v1);
+            float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                s1 += v0[j] + v1[j];
+                s2 += v0[j] * v0[j] + v1[j] * v1[j];
+            }
+            xln[(qr * kRows + r) * 2] = s1;
+            xln[(qr * kRows + r) * 2 + 1] = s2;
+            __syncthreads();
+            float t1 = 0.f, t2 = 0.f;
+#pragma unroll
+            for (int q4 = 0; q4 < 4; ++q4) {
+                t1 += xln[(q4 * kRows + r) * 2];
+                t2 += xln[(q4 * kRows + r) * 2 + 1];
+            }
+            const float mean = t1 * (1.0f / D);
+            const float var = fmaxf(t2 * (1.0f / D) - mean * mean, 0.f);
+            const float rs = 1.0f / sqrtf(var + 1e-5f);
+            float z0 = 0.f, z1 = 0.f;
+#pragma unroll
+            for (int j = 0; j < 64; ++j) {
+                const int d = 64 * qr + j;
+                const float x = j < 32 ? v0[j] : v1[j - 32];
+                const float y = (x - mean) * rs * __ldg(w + a.o.lnfg + d) + __ldg(w + a.o.lnfb + d);
+                z0 += y * __ldg(w + a.o.Wh + d);
+                z1 += y * __ldg(w + a.o.Wh + D + d);
+            }
+            xhd[(qr * kRows + r) * 2] = z0;
+            xhd[(qr * kRows + r) * 2 + 1] = z1;
+            __syncthreads();
+            if (qr == 0) {
+                z0 = __ldg(w + a.o.bh);
+                z1 = __ldg(w + a.o.bh + 1);
+#pragma unroll
+                for (int q4 = 0; q4 < 4; ++q4) {
+                    z0 += xhd[(q4 * kRows + r) * 2];
+                    z1 += xhd[(q4 * kRows + r) * 2 + 1];
+                }
+                const float ell = z1 - z0;
+                const float p = 1.0f / (1.0f + expf(-ell));
+                const float u = philox_uniform(a.seed, (uint32_t)b, (uint32_t)t, a.sid, 0u);
+                const int sp = u < p ? 1 : -1;
+                lq += log_sigmoid_f((float)sp * ell);
+                stok[r] = (sp + 1) >> 1;
+                if (active) {
+                    a.spins[(size_t)b * a.N + t] = (int8_t)sp;
+                    if (a.flags && fabsf(p - u) < a.band)
+                        a.flags[(size_t)b * nfw + (t >> 5)] |= 1u << (t & 31);
+                    if (!isfinite(ell)) atomicOr(a.err, 4);
+                }
+            }
+            __syncthreads();  // stok is read by every thread of the row
+        }
+    }
+    if (qr == 0 && active) a.logq[b] = lq;
+    if (tid == 0)
+        while (next_use < next_load) {
+            const int s = (int)(next_use % kStages256);
+            if (!tc::mbar_wait(&full[s], fphase[s])) {
+                atomicExch(a.err, 3);
+                break;
+            }
+            fphase[s] ^= 1u;
+            ++next_use;
+        }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
 }  // namespace
 
 sg_status launch_pack_bf16(sg_model *m, cudaStream_t st)
 {
     const sg_config &c = m->cfg;
+    if (c.d == 256) {
+        // 44 chunks of 32 KB per layer and model; models follow one another
+        const size_t per_layer = (size_t)kChunks256 * kChunk256;
+        SG_TRY(ensure_buffer(&m->bf, &m->bf_bytes, per_layer * c.n_layers * m->n_models));
+        if (c.d_ff != 1024) return SG_OK;  // the d = 256 decode needs d_ff = 1024
+        const int64_t n = (int64_t)kChunks256 * 256 * 64;
+        for (int mi = 0; mi < m->n_models; ++mi) {
+            const float *w = m->w + (size_t)mi * m->P1;
+            for (int l = 0; l < c.n_layers; ++l) {
+                const LayerOff &o = m->off.L[l];
+                unsigned char *dst =
+                    (unsigned char *)m->bf + per_layer * ((size_t)mi * c.n_layers + l);
+                pack_chunks256_kernel<<<(unsigned)((n + 255) / 256), 256, 0, ::sg::counted(st)>>>(
+                    w + o.Wqkv, w + o.W1, w + o.W2, reinterpret_cast<__nv_bfloat16 *>(dst));
+            }
+        }
+        return check_launch("pack bf16 chunks (d = 256)");
+    }
     if (c.d == 128) {
         const size_t per_layer = (size_t)kChunksPerLayer * kChunkBytes;
         SG_TRY(ensure_buffer(&m->bf, &m->bf_bytes, per_layer * c.n_layers));
@@ -1249,15 +1703,35 @@ sg_status launch_decode_bf16(sg_model *m, int64_t B, uint64_t seed, uint32_t sid
     const sg_config &c = m->cfg;
     const bool d64 = c.d == 64 && c.n_heads == 4 && c.d_ff == 256 && c.d_token <= 32;
     const bool d128 = c.d == 128 && c.n_heads == 8 && c.d_ff == 512 && c.d_token <= 32;
-    if (!d64 && !d128)
-        return fail(SG_EUNSUPPORTED, "BF16 decode is built for (d, heads, d_ff) = (64, 4, 256) "
-                                     "and (128, 8, 512)");
+    const bool d256 = c.d == 256 && c.n_heads == 8 && c.d_ff == 1024 && c.d_token <= 64;
+    if (!d64 && !d128 && !d256)
+        return fail(SG_EUNSUPPORTED, "BF16 decode is built for (d, heads, d_ff) = (64, 4, 256), "
+                                     "(128, 8, 512) and (256, 8, 1024)");
+    if (m->n_models > 1 && !d256)
+        return fail(SG_EUNSUPPORTED, "grouped models are served by the d = 256 decode");
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // spread the batch over every SM: rows per CTA = ceil(B / SMs), at most 128
+    const int64_t rows_per_model = B / m->n_models;
+    // spread the batch over every SM: rows per CTA = ceil(B / SMs), at most 128;
+    // with grouped models a CTA must not straddle two models, so the rows per
+    // CTA divide the rows per model
     int rows = (int)std::min<int64_t>(kRows, (B + sms - 1) / sms);
     rows = std::max(rows, 1);
+    if (m->n_models > 1) {
+        // the fewest waves over the SMs, then the most CTAs within them
+        int best = 1;
+        int64_t best_waves = INT64_MAX;
+        for (int r = 1; r <= kRows && r <= rows_per_model; ++r) {
+            if (rows_per_model % r) continue;
+            const int64_t waves = ((B / r) + sms - 1) / sms;
+            if (waves < best_waves) {
+                best_waves = waves;
+                best = r;
+            }
+        }
+        rows = best;
+    }
     const int64_t tiles = (B + rows - 1) / rows;
     const Bf16Geom g = bgeom(c.mask_kind, c.N, c.W, c.S);
     const size_t kv_bytes = (size_t)tiles * c.n_layers * g.nslots * 2 * c.d * kRows * 2;
@@ -1291,6 +1765,21 @@ sg_status launch_decode_bf16(sg_model *m, int64_t B, uint64_t seed, uint32_t sid
     a.flags = flags;
     a.kv = (unsigned char *)m->kv;
     a.err = (int *)m->err;
+    a.rows_per_model = rows_per_model;
+    a.stride_w = m->P1;
+    a.stride_wt = m->pack.total;
+    a.stride_bf = (size_t)kChunks256 * kChunk256 * c.n_layers;
+    a.max_keys = g.nslots;
+    if (d256) {
+        const size_t smem256 = 2 * (size_t)kRows * 256 * 2 + (size_t)kStages256 * kChunk256 +
+                               8 * kRows * 2 * sizeof(float) + (size_t)g.nslots * sizeof(uint32_t);
+        if (smem256 > 227 * 1024)
+            return fail(SG_EUNSUPPORTED, "BF16 decode (d = 256) needs at most 6900 visible keys");
+        SG_CUDA_TRY(cudaFuncSetAttribute(decode_bf16_d256_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem256));
+        decode_bf16_d256_kernel<<<(unsigned)tiles, 512, smem256, ::sg::counted(st)>>>(a);
+        return check_launch("decode_bf16_d256_kernel");
+    }
     if (d128) {
         const size_t smem128 = 2 * (size_t)kRows * 128 * 2 + (size_t)kStages * kChunkBytes +
                                8 * kRows * 2 * sizeof(float);

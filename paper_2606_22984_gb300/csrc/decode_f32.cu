@@ -50,23 +50,28 @@ sg_status launch_pack_f32(sg_model *m, cudaStream_t st)
 {
     const sg_config &c = m->cfg;
     const size_t f4 = sizeof(float);
-    for (int l = 0; l < c.n_layers; ++l) {
-        const LayerOff &o = m->off.L[l];
-        transpose(m->w + o.Wqkv, m->wt + m->pack.WqkvT[l], 3 * c.d, c.d, st);
-        transpose(m->w + o.W1, m->wt + m->pack.W1T[l], c.d_ff, c.d, st);
-        transpose(m->w + o.W2, m->wt + m->pack.W2T[l], c.d, c.d_ff, st);
-        SG_CUDA_TRY(cudaMemcpyAsync(m->wt + m->pack.Wqkv[l], m->w + o.Wqkv,
-                                    (size_t)3 * c.d * c.d * f4, cudaMemcpyDeviceToDevice, st));
-        SG_CUDA_TRY(cudaMemcpyAsync(m->wt + m->pack.W1[l], m->w + o.W1,
-                                    (size_t)c.d_ff * c.d * f4, cudaMemcpyDeviceToDevice, st));
-        SG_CUDA_TRY(cudaMemcpyAsync(m->wt + m->pack.W2[l], m->w + o.W2,
-                                    (size_t)c.d * c.d_ff * f4, cudaMemcpyDeviceToDevice, st));
-        SG_CUDA_TRY(cudaMemcpyAsync(m->wt + m->pack.bqkv[l], m->w + o.bqkv, (size_t)3 * c.d * f4,
-                                    cudaMemcpyDeviceToDevice, st));
-        SG_CUDA_TRY(cudaMemcpyAsync(m->wt + m->pack.b1[l], m->w + o.b1, (size_t)c.d_ff * f4,
-                                    cudaMemcpyDeviceToDevice, st));
-        SG_CUDA_TRY(cudaMemcpyAsync(m->wt + m->pack.b2[l], m->w + o.b2, (size_t)c.d * f4,
-                                    cudaMemcpyDeviceToDevice, st));
+    // grouped models: model mi's blob at w + mi * P1, its packed copies at wt + mi * pack.total
+    for (int mi = 0; mi < m->n_models; ++mi) {
+        const float *w = m->w + (size_t)mi * m->P1;
+        float *wt = m->wt + (size_t)mi * m->pack.total;
+        for (int l = 0; l < c.n_layers; ++l) {
+            const LayerOff &o = m->off.L[l];
+            transpose(w + o.Wqkv, wt + m->pack.WqkvT[l], 3 * c.d, c.d, st);
+            transpose(w + o.W1, wt + m->pack.W1T[l], c.d_ff, c.d, st);
+            transpose(w + o.W2, wt + m->pack.W2T[l], c.d, c.d_ff, st);
+            SG_CUDA_TRY(cudaMemcpyAsync(wt + m->pack.Wqkv[l], w + o.Wqkv,
+                                        (size_t)3 * c.d * c.d * f4, cudaMemcpyDeviceToDevice, st));
+            SG_CUDA_TRY(cudaMemcpyAsync(wt + m->pack.W1[l], w + o.W1,
+                                        (size_t)c.d_ff * c.d * f4, cudaMemcpyDeviceToDevice, st));
+            SG_CUDA_TRY(cudaMemcpyAsync(wt + m->pack.W2[l], w + o.W2,
+                                        (size_t)c.d * c.d_ff * f4, cudaMemcpyDeviceToDevice, st));
+            SG_CUDA_TRY(cudaMemcpyAsync(wt + m->pack.bqkv[l], w + o.bqkv, (size_t)3 * c.d * f4,
+                                        cudaMemcpyDeviceToDevice, st));
+            SG_CUDA_TRY(cudaMemcpyAsync(wt + m->pack.b1[l], w + o.b1, (size_t)c.d_ff * f4,
+                                        cudaMemcpyDeviceToDevice, st));
+            SG_CUDA_TRY(cudaMemcpyAsync(wt + m->pack.b2[l], w + o.b2, (size_t)c.d * f4,
+                                        cudaMemcpyDeviceToDevice, st));
+        }
     }
     return check_launch("pack transposed weights");
 }
@@ -449,6 +454,7 @@ extern "C" sg_status sg_sample_noalloc(const sg_config *cfg, const float *weight
     const sg_config &c = *cfg;
     if (c.precision != SG_FP32)
         return fail(SG_EUNSUPPORTED, "sg_sample_noalloc serves the FP32 path only");
+    if (c.n_models > 1) return fail(SG_EUNSUPPORTED, "sg_sample_noalloc serves single models");
     const int dh = c.d / c.n_heads;
     const bool shape_ok = (c.d == 32 && (dh == 8 || dh == 16)) || (c.d == 64 && (dh == 8 || dh == 16)) ||
                           (c.d == 128 && (dh == 16 || dh == 32));

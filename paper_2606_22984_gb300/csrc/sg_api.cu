@@ -118,8 +118,11 @@ static sg_status validate(const sg_config *c)
         return fail(SG_EINVAL, "band W and sink S must be >= 0");
     if (c->precision != SG_FP32 && c->precision != SG_BF16)
         return fail(SG_EINVAL, "precision must be SG_FP32 or SG_BF16");
+    if (c->n_models < 0 || c->n_models > 64) return fail(SG_EINVAL, "n_models must be in [0, 64]");
     return SG_OK;
 }
+
+static int models_of(const sg_config &c) { return c.n_models > 1 ? c.n_models : 1; }
 
 }  // namespace sg
 
@@ -134,7 +137,7 @@ int64_t sg_launch_count(void) { return g_launches.load(std::memory_order_relaxed
 int64_t sg_param_count(const sg_config *cfg)
 {
     if (validate(cfg) != SG_OK) return -1;
-    return blob_offsets(*cfg).total;
+    return blob_offsets(*cfg).total * models_of(*cfg);
 }
 
 sg_status sg_model_create(const sg_config *cfg, const float *weights_host, int64_t n_weights,
@@ -142,7 +145,7 @@ sg_status sg_model_create(const sg_config *cfg, const float *weights_host, int64
 {
     SG_TRY(validate(cfg));
     if (!weights_host || !out) return fail(SG_EINVAL, "NULL weights or out pointer");
-    const int64_t P = blob_offsets(*cfg).total;
+    const int64_t P = blob_offsets(*cfg).total * models_of(*cfg);
     if (n_weights != P)
         return fail(SG_EINVAL, "weight blob has " + std::to_string(n_weights) +
                                    " floats, config needs " + std::to_string(P));
@@ -153,13 +156,17 @@ sg_status sg_model_create(const sg_config *cfg, const float *weights_host, int64
     if (!m) return fail(SG_ENOMEM, "host allocation failed");
     m->cfg = *cfg;
     m->P = P;
+    m->n_models = models_of(*cfg);
+    m->P1 = P / m->n_models;
     m->off = blob_offsets(*cfg);
     m->pack = pack_offsets(*cfg);
     cudaGetDevice(&m->device);
     size_t have = 0;
     sg_status s = ensure_buffer((void **)&m->w, &have, (size_t)P * sizeof(float));
     have = 0;
-    if (s == SG_OK) s = ensure_buffer((void **)&m->wt, &have, (size_t)m->pack.total * sizeof(float));
+    if (s == SG_OK)
+        s = ensure_buffer((void **)&m->wt, &have,
+                          (size_t)m->pack.total * m->n_models * sizeof(float));
     if (s == SG_OK && cudaMemcpy(m->w, weights_host, (size_t)P * sizeof(float),
                                  cudaMemcpyHostToDevice) != cudaSuccess)
         s = fail(SG_ECUDA, "copying weights to the device failed");
@@ -223,6 +230,10 @@ sg_status sg_sample(sg_model *m, int64_t B, double beta, uint64_t seed, uint32_t
     (void)beta;
     if (!m || !spins || !logq) return fail(SG_EINVAL, "NULL model or output");
     if (B < 1 || B >= (int64_t)1 << 32) return fail(SG_EINVAL, "B must be in [1, 2^32)");
+    if (m->n_models > 1 && B % m->n_models)
+        return fail(SG_EINVAL, "B must be a multiple of n_models");
+    if (m->n_models > 1 && !(m->cfg.precision == SG_BF16 && m->cfg.d == 256))
+        return fail(SG_EUNSUPPORTED, "grouped models are served by the BF16 d = 256 decode");
     if (flag_band <= 0.f) flag_band = m->cfg.precision == SG_BF16 ? 1e-2f : 1e-5f;
     cudaStream_t st = (cudaStream_t)stream;
     if (flags)
@@ -237,6 +248,7 @@ sg_status sg_logprob(sg_model *m, const int8_t *spins, int64_t B, float *logq, s
 {
     if (!m || !spins || !logq) return fail(SG_EINVAL, "NULL model or pointer");
     if (B < 1) return fail(SG_EINVAL, "B must be >= 1");
+    if (m->n_models > 1) return fail(SG_EUNSUPPORTED, "sg_logprob serves single models");
     return launch_logprob_f32(m, spins, B, logq, (cudaStream_t)stream);
 }
 
@@ -245,6 +257,7 @@ sg_status sg_grad(sg_model *m, const int8_t *spins, const float *coeff, int64_t 
 {
     if (!m || !spins || !coeff || !grad) return fail(SG_EINVAL, "NULL model or pointer");
     if (B < 1) return fail(SG_EINVAL, "B must be >= 1");
+    if (m->n_models > 1) return fail(SG_EUNSUPPORTED, "sg_grad serves single models");
     return launch_grad_f32(m, spins, coeff, B, grad, logq, (cudaStream_t)stream);
 }
 

@@ -155,7 +155,9 @@ __host__ __device__ __forceinline__ bool key_visible(int mask, int W, int S, int
 // ---------------------------------------------------------------------------
 struct sg_model {
     sg_config cfg;
-    int64_t P;
+    int64_t P;                // floats of all models' blobs
+    int64_t P1 = 0;           // floats of one model's blob
+    int n_models = 1;
     int device;
     sg::BlobOff off;
     sg::PackOff pack;

@@ -129,6 +129,12 @@ def make_ferro(D: int, L: int, periodic: bool = True) -> Instance:
     return Instance("ea", N, np.ones((N, D), np.float32), D=D, L=L, periodic=periodic, pm=True)
 
 
+def make_group_weights(m: ModelShape, seed: int, n: int, scale: float = 1.0) -> np.ndarray:
+    """Blobs of a group of n models of one shape, concatenated; model i
+    draws its weights from seed + 7919 i."""
+    return np.concatenate([make_weights(m, seed + 7919 * i, scale) for i in range(n)])
+
+
 def random_spins(B: int, N: int, seed: int) -> np.ndarray:
     rng = _rng(seed, 4)
     return np.where(rng.random((B, N)) < 0.5, 1, -1).astype(np.int8)
@@ -151,6 +157,10 @@ class Workload:
 
     def weights(self, scale: float = 1.0) -> np.ndarray:
         return make_weights(self.model, self.seed, scale)
+
+    def group_weights(self, scale: float = 1.0) -> np.ndarray:
+        """One model per beta, blobs concatenated (model i seeded seed + 7919 i)."""
+        return make_group_weights(self.model, self.seed, len(self.betas), scale)
 
 
 def lattice_mask(D: int, L: int):

@@ -34,7 +34,7 @@ class SgError(RuntimeError):
 
 class SgConfig(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in ("N", "n_layers", "d", "n_heads", "d_token", "d_ff",
-                                              "mask_kind", "W", "S", "precision")]
+                                              "mask_kind", "W", "S", "precision", "n_models")]
 
 
 _P, _I64, _I32, _U32, _U64, _D, _F = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
@@ -112,9 +112,9 @@ def launch_count() -> int:
     return int(lib().sg_launch_count())
 
 
-def config(shape: _inputs.ModelShape, precision: int = SG_FP32) -> SgConfig:
+def config(shape: _inputs.ModelShape, precision: int = SG_FP32, n_models: int = 1) -> SgConfig:
     return SgConfig(shape.N, shape.n_layers, shape.d, shape.n_heads, shape.d_token, shape.d_ff,
-                    shape.mask_kind, shape.W, shape.S, precision)
+                    shape.mask_kind, shape.W, shape.S, precision, n_models)
 
 
 def param_count(shape: _inputs.ModelShape, precision: int = SG_FP32) -> int:
@@ -122,13 +122,16 @@ def param_count(shape: _inputs.ModelShape, precision: int = SG_FP32) -> int:
 
 
 class Model:
-    """Owns an sg_model.  ``weights`` is the float32 blob (host numpy array)."""
+    """Owns an sg_model.  ``weights`` is the float32 blob (host numpy array);
+    for a group of ``n_models`` models, their blobs concatenated."""
 
-    def __init__(self, shape: _inputs.ModelShape, weights: np.ndarray, precision: int = SG_FP32):
+    def __init__(self, shape: _inputs.ModelShape, weights: np.ndarray, precision: int = SG_FP32,
+                 n_models: int = 1):
         self.shape = shape
         self.precision = precision
+        self.n_models = n_models
         w = np.ascontiguousarray(weights, dtype=np.float32)
-        self._cfg = config(shape, precision)
+        self._cfg = config(shape, precision, n_models)
         h = ctypes.c_void_p()
         _check("sg_model_create",
                lib().sg_model_create(ctypes.byref(self._cfg), w.ctypes.data_as(_P), w.size,

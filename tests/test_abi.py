@@ -40,6 +40,16 @@ def test_param_count_agrees_with_blob_layouts(lib):
         assert n == inputs.param_count(m) == oracle.param_count(oracle.ModelCfg(**vars(m)))
 
 
+def test_grouped_param_count(lib):
+    m = inputs.workloads()["ea2d64"].model
+    one = lib.sg_param_count(ctypes.byref(sg.config(m)))
+    assert lib.sg_param_count(ctypes.byref(sg.config(m, n_models=8))) == 8 * one
+    assert lib.sg_param_count(ctypes.byref(sg.config(m, n_models=0))) == one
+    assert inputs.make_group_weights(m, 5, 2).size == 2 * one
+    assert lib.sg_param_count(ctypes.byref(sg.config(m, n_models=65))) == -1
+    assert lib.sg_param_count(ctypes.byref(sg.config(m, n_models=-1))) == -1
+
+
 @pytest.mark.parametrize("bad", [dict(N=0), dict(n_heads=5), dict(d_token=32), dict(n_layers=17),
                                  dict(mask_kind=3)])
 def test_invalid_config_rejected(lib, bad):

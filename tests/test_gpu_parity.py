@@ -75,6 +75,9 @@ BF16_CASES = {
     "dense_d128": (inputs.ModelShape(40, 2, 128, 8), 200, 1.0),
     "ring_d128": (inputs.ModelShape(64, 3, 128, 8, mask_kind=1, W=6, S=9), 300, 1.0),
     "tiny_d128": (inputs.ModelShape(3, 1, 128, 8), 7, 1.0),
+    "ring_d256": (inputs.ModelShape(40, 2, 256, 8, mask_kind=1, W=5, S=3), 200, 1.0),
+    "dense_d256": (inputs.ModelShape(24, 1, 256, 8), 130, 1.0),
+    "tiny_d256": (inputs.ModelShape(2, 1, 256, 8), 3, 1.0),
 }
 
 
@@ -120,6 +123,77 @@ def test_bf16_sampling_matches_oracle(name):
     model.check()
     assert frac < 0.05
     print(f"{name}: flagged {frac:.4f} of draws, max |dlogq|/N {dl.max() / m.N:.2e}")
+
+
+@pytest.mark.parametrize("n_models,per_model", [(3, 100), (2, 1000)])
+def test_bf16_grouped_models_match_oracle(n_models, per_model):
+    """A group of d = 256 models in one launch: sample b uses model
+    b // per_model (its own weights), Philox counters keep the global row."""
+    m = inputs.ModelShape(30, 2, 256, 8, mask_kind=1, W=4, S=5)
+    w = inputs.make_group_weights(m, 11, n_models)
+    P1 = w.size // n_models
+    B = n_models * per_model
+    model = sg.Model(m, w, sg.SG_BF16, n_models=n_models)
+    spins, logq, flags = model.sample(B, seed=99, with_flags=True)
+    model.check()
+    s, lq, fl = _np(spins), _np(logq), _np(flags)
+    assert unpack_flags(fl, m.N).mean() < 0.05
+    for i in range(n_models):
+        rows = np.arange(i * per_model, (i + 1) * per_model)
+        rows = rows if per_model <= 100 else rows[[0, 1, per_model // 2, per_model - 1]]
+        so, lqo, _, _ = oracle_replay(m, w[i * P1:(i + 1) * P1], 99, s, fl, rows=rows)
+        assert np.array_equal(so, s[rows]), f"model {i}: spins differ"
+        assert np.abs(lqo - lq[rows]).max() <= BF16_LOGQ_TOL * m.N
+    # rows of model 0 are bit-identical to a single-model launch of model 0
+    # (per-row arithmetic does not depend on how rows are grouped into CTAs)
+    single = sg.Model(m, w[:P1], sg.SG_BF16)
+    s1, l1 = single.sample(per_model, seed=99)
+    assert np.array_equal(s[:per_model], _np(s1))
+    assert np.array_equal(lq[:per_model], _np(l1))
+
+
+def test_grouped_models_rejected_outside_d256():
+    m = inputs.ModelShape(20, 1, 64, 4)
+    w = inputs.make_group_weights(m, 1, 2)
+    with pytest.raises(sg.SgError):
+        sg.Model(m, w, sg.SG_FP32, n_models=2).sample(8, seed=1)
+    g = sg.Model(inputs.ModelShape(8, 1, 256, 8), inputs.make_group_weights(
+        inputs.ModelShape(8, 1, 256, 8), 1, 2), sg.SG_BF16, n_models=2)
+    with pytest.raises(sg.SgError):
+        g.sample(7, seed=1)  # B not a multiple of n_models
+    with pytest.raises(sg.SgError):
+        g.logprob(torch.ones(2, 8, dtype=torch.int8, device="cuda"))
+
+
+def test_full_size_ea2d64_grouped_bf16_sampled_rows():
+    """2D EA L=64 (N=4096), 8 layers d=256, one model per beta (8 betas x
+    B=1024) in one launch: sampled rows of three models against the oracle,
+    and the Gaussian energies of the samples."""
+    import time
+    wl = inputs.workloads()["ea2d64"]
+    m, nb = wl.model, len(wl.betas)
+    w = wl.group_weights()
+    P1 = w.size // nb
+    B = nb * wl.B
+    model = sg.Model(m, w, sg.SG_BF16, n_models=nb)
+    model.sample(256 * nb, seed=5)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    spins, logq, flags = model.sample(B, seed=2026, with_flags=True)
+    model.check()
+    dt = time.perf_counter() - t0
+    print(f"ea2d64 grouped BF16 decode: {B} samples x {m.N} spins in {dt:.2f} s "
+          f"({B / dt:.0f} configs/s)")
+    s, lq, fl = _np(spins), _np(logq), _np(flags)
+    assert np.all(np.isin(s, (-1, 1)))
+    assert unpack_flags(fl, m.N).mean() < 0.05
+    for i, rows in ((0, [0, 1023]), (3, [3 * 1024 + 17]), (7, [B - 1])):
+        so, lqo, _, _ = oracle_replay(m, w[i * P1:(i + 1) * P1], 2026, s, fl, rows=rows)
+        assert np.array_equal(so, s[rows]), f"model {i}: spins differ"
+        assert np.abs(lqo - lq[rows]).max() <= BF16_LOGQ_TOL * m.N
+    inst = wl.instance()
+    E = _np(sg.Instance(inst).energy(spins[:64]))
+    assert np.allclose(E, oracle.energy(inst, s[:64]), rtol=1e-5, atol=1e-2)
 
 
 def test_full_size_ea2d16_bf16_sampled_rows():
