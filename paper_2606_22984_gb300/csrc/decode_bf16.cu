@@ -95,6 +95,7 @@ struct DecodeArgs {
     int64_t stride_w, stride_wt;  // floats between consecutive models' blobs
     size_t stride_bf;             // bytes between consecutive models' packed chunks
     int max_keys;                 // capacity of the per-step key-offset table
+    int kv_stages;                // d = 64: keys in flight per thread (2 or 3)
 };
 
 // Element (r, k) of a core-matrix tile as a 16-byte group store of 8 bf16.
@@ -478,6 +479,7 @@ __global__ void __launch_bounds__(kThreads, 1) decode_bf16_kernel(const __grid_c
 // threads per row do, and split the LayerNorm and GELU epilogues four ways.
 // Weights stream per layer into three buffers exactly as in the kernel above.
 // ---------------------------------------------------------------------------
+template <int NST>  // keys in flight per thread in the attention (2 or 3)
 __global__ void __launch_bounds__(512, 1) decode_bf16_d64_kernel(const __grid_constant__ DecodeArgs a)
 {
     constexpr int D = 64, DFF = 256, DH = 16, KG = D / 8, KG2 = DFF / 8;
@@ -494,6 +496,9 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d64_kernel(const __grid_co
     float *xln = reinterpret_cast<float *>(W2s + W2_BYTES);  // [4][128][2]
     float *xhd = xln + 4 * kRows * 2;                          // [4][128][2]
     uint32_t *koff = reinterpret_cast<uint32_t *>(xhd + 4 * kRows * 2);  // [N]
+    // spare 32 KB KV stage after the key table (rounded to 1 KB), when it fits
+    unsigned char *kvspare = reinterpret_cast<unsigned char *>(koff) + ((a.N * 4 + 1023) / 1024) * 1024;
+    constexpr int nst = NST;
     __shared__ uint64_t wbar[3], mbar;
     __shared__ uint32_t tslot;
     __shared__ int s_err;
@@ -675,25 +680,35 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d64_kernel(const __grid_co
                         dv[(2 * qr + c) * kRows + r] = y;
                     }
                 }
-                // keys < t of head qr straight from the ring, one key prefetched
+                // keys < t of head qr, staged through shared memory by cp.async:
+                // kv_stages keys in flight per thread without holding registers.
+                // Stages 0 and 1 are the A2 tile (idle until the GELU epilogue),
+                // stage 2 the spare tile; each stage holds, per thread, K pieces
+                // at +0, +8 KB and V pieces at +16 KB, +24 KB (conflict-free: the
+                // 512 threads' 16-byte pieces are consecutive).
                 const uint4 *kb = reinterpret_cast<const uint4 *>(kvl) + (2 * qr) * kRows + r;
-                uint4 ck[2], cv[2];
-                if (nk > 0) {
-                    const uint4 *p = kb + koff[0];
-                    ck[0] = __ldcg(p);
-                    ck[1] = __ldcg(p + kRows);
-                    cv[0] = __ldcg(p + (D / 8) * kRows);
-                    cv[1] = __ldcg(p + (D / 8) * kRows + kRows);
-                }
+                auto stage = [&](int s) { return (s < 2 ? A2buf + s * 32768 : kvspare) + tid * 16; };
+                auto fetch = [&](int i, int s) {
+                    const uint4 *p = kb + koff[i];
+                    unsigned char *dst = stage(s);
+                    tc::cp_async16(dst, p);
+                    tc::cp_async16(dst + 8192, p + kRows);
+                    tc::cp_async16(dst + 16384, p + (D / 8) * kRows);
+                    tc::cp_async16(dst + 24576, p + (D / 8) * kRows + kRows);
+                    tc::cp_async_commit();
+                };
+                for (int i = 0; i < nk && i < nst; ++i) fetch(i, i);
                 for (int i = 0; i < nk; ++i) {
-                    uint4 nk2[2], nv2[2];
-                    if (i + 1 < nk) {
-                        const uint4 *p = kb + koff[i + 1];
-                        nk2[0] = __ldcg(p);
-                        nk2[1] = __ldcg(p + kRows);
-                        nv2[0] = __ldcg(p + (D / 8) * kRows);
-                        nv2[1] = __ldcg(p + (D / 8) * kRows + kRows);
-                    }
+                    if (nst == 3 && i + 2 < nk) tc::cp_async_wait<2>();
+                    else if (i + 1 < nk) tc::cp_async_wait<1>();
+                    else tc::cp_async_wait<0>();
+                    const int si = i % nst;
+                    const unsigned char *src = stage(si);
+                    uint4 ck[2], cv[2];
+                    ck[0] = *reinterpret_cast<const uint4 *>(src);
+                    ck[1] = *reinterpret_cast<const uint4 *>(src + 8192);
+                    cv[0] = *reinterpret_cast<const uint4 *>(src + 16384);
+                    cv[1] = *reinterpret_cast<const uint4 *>(src + 24576);
                     float s = 0.f;
 #pragma unroll
                     for (int c = 0; c < 2; ++c) {
@@ -715,10 +730,8 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d64_kernel(const __grid_co
                             acc[8 * c + 2 * j + 1] = acc[8 * c + 2 * j + 1] * c0 + p0 * bf_hi(wv[j]);
                         }
                     }
-                    ck[0] = nk2[0];
-                    ck[1] = nk2[1];
-                    cv[0] = nv2[0];
-                    cv[1] = nv2[1];
+                    // the stage is refilled only after its data has been consumed
+                    if (i + nst < nk) fetch(i + nst, si);
                 }
                 const float inv = 1.0f / l0;
 #pragma unroll
@@ -864,6 +877,9 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d128_kernel(const __grid_c
     unsigned char *ring = A2buf + A_BYTES;
     float *xln = reinterpret_cast<float *>(ring + kStages * kChunkBytes);  // [4][128][2]
     float *xhd = xln + 4 * kRows * 2;                                     // [4][128][2]
+    uint32_t *koff = reinterpret_cast<uint32_t *>(xhd + 4 * kRows * 2);   // [max_keys]
+    // spare 32 KB KV stage after the key table (rounded to 1 KB)
+    unsigned char *kvspare = reinterpret_cast<unsigned char *>(koff) + ((a.max_keys * 4 + 1023) / 1024) * 1024;
     __shared__ uint64_t full[kStages], mbar;
     __shared__ uint32_t tslot;
     __shared__ int s_err;
@@ -998,7 +1014,13 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d128_kernel(const __grid_c
         int n_sink, band_lo;
         visible_ranges(a.mask, a.W, a.S, t, n_sink, band_lo);
         const int slot_t = bslot(g, a.S, a.W, t);
-        const int nk = active ? n_sink + band_count(t, band_lo) - 1 : 0;  // keys < t
+        const int nk_all = n_sink + band_count(t, band_lo) - 1;  // keys < t
+        const int nk = active ? nk_all : 0;
+        // ring offsets (16-byte units) of this step's visible keys, the same for
+        // every row, head and layer (the first LayerNorm's barrier orders them)
+        for (int i = tid; i < nk_all; i += blockDim.x)
+            koff[i] = (uint32_t)bslot(g, a.S, a.W, i < n_sink ? i : band_lo + (i - n_sink)) *
+                      (uint32_t)(slot_bytes / 16);
         for (int l = 0; l < a.L; ++l) {
             const LayerOff &o = a.o.L[l];
             layernorm_to(a.w + o.ln1g, a.w + o.ln1b);
@@ -1062,26 +1084,35 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d128_kernel(const __grid_c
 #pragma unroll
                     for (int j = 0; j < DH; ++j)
                         acc[j] = round_bf(kk[DH * p + j] + __ldg(bq + 2 * D + DH * hh + j));
+                    // keys < t staged through shared memory by cp.async, three keys
+                    // in flight per thread: stages are the A and A2 tiles (idle
+                    // during attention) and the spare tile; per thread, K pieces at
+                    // +0, +8 KB and V pieces at +16 KB, +24 KB of a stage.
                     const uint4 *kb = reinterpret_cast<const uint4 *>(kvl) + (2 * hh) * kRows + r;
-                    auto key_of = [&](int i) { return i < n_sink ? i : band_lo + (i - n_sink); };
-                    uint4 ck[2], cv[2];
-                    if (nk > 0) {
-                        const uint4 *pp = kb + (size_t)bslot(g, a.S, a.W, key_of(0)) * (slot_bytes / 16);
-                        ck[0] = __ldcg(pp);
-                        ck[1] = __ldcg(pp + kRows);
-                        cv[0] = __ldcg(pp + (D / 8) * kRows);
-                        cv[1] = __ldcg(pp + (D / 8) * kRows + kRows);
-                    }
+                    auto stage = [&](int s) {
+                        return (s == 0 ? Abuf : (s == 1 ? A2buf : kvspare)) + tid * 16;
+                    };
+                    auto fetch = [&](int i, int s) {
+                        const uint4 *pp = kb + koff[i];
+                        unsigned char *dst = stage(s);
+                        tc::cp_async16(dst, pp);
+                        tc::cp_async16(dst + 8192, pp + kRows);
+                        tc::cp_async16(dst + 16384, pp + (D / 8) * kRows);
+                        tc::cp_async16(dst + 24576, pp + (D / 8) * kRows + kRows);
+                        tc::cp_async_commit();
+                    };
+                    for (int i = 0; i < nk && i < 3; ++i) fetch(i, i);
                     for (int i = 0; i < nk; ++i) {
-                        uint4 nk2[2], nv2[2];
-                        if (i + 1 < nk) {
-                            const uint4 *pp =
-                                kb + (size_t)bslot(g, a.S, a.W, key_of(i + 1)) * (slot_bytes / 16);
-                            nk2[0] = __ldcg(pp);
-                            nk2[1] = __ldcg(pp + kRows);
-                            nv2[0] = __ldcg(pp + (D / 8) * kRows);
-                            nv2[1] = __ldcg(pp + (D / 8) * kRows + kRows);
-                        }
+                        if (i + 2 < nk) tc::cp_async_wait<2>();
+                        else if (i + 1 < nk) tc::cp_async_wait<1>();
+                        else tc::cp_async_wait<0>();
+                        const int si = i % 3;
+                        const unsigned char *src = stage(si);
+                        uint4 ck[2], cv[2];
+                        ck[0] = *reinterpret_cast<const uint4 *>(src);
+                        ck[1] = *reinterpret_cast<const uint4 *>(src + 8192);
+                        cv[0] = *reinterpret_cast<const uint4 *>(src + 16384);
+                        cv[1] = *reinterpret_cast<const uint4 *>(src + 24576);
                         float s = 0.f;
 #pragma unroll
                         for (int c = 0; c < 2; ++c) {
@@ -1103,10 +1134,8 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d128_kernel(const __grid_c
                                 acc[8 * c + 2 * j + 1] = acc[8 * c + 2 * j + 1] * c0 + p0 * bf_hi(wv[j]);
                             }
                         }
-                        ck[0] = nk2[0];
-                        ck[1] = nk2[1];
-                        cv[0] = nv2[0];
-                        cv[1] = nv2[1];
+                        // the stage is refilled only after its data has been consumed
+                        if (i + 3 < nk) fetch(i + 3, si);
                     }
                     const float inv = 1.0f / l0;
 #pragma unroll
@@ -1488,19 +1517,31 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d256_kernel(const __grid_c
                     acc[j] = 0.f;
                 }
                 float m0 = -INFINITY, l0 = 0.f;
+                // keys 0..t staged through shared memory by cp.async, two keys
+                // in flight per thread: the stages are the A and A2 tiles (idle
+                // during attention); per thread, K pieces at +0..+24 KB and V
+                // pieces at +32..+56 KB of a stage, 8 KB apart (conflict-free).
                 const uint4 *kb = reinterpret_cast<const uint4 *>(kvl) + (4 * hh) * kRows + r;
-                for (int i = 0; i < nk; ++i) {
+                auto fetch = [&](int i, int s) {
                     const uint4 *pp = kb + koff[i];
-                    uint4 ck[4], cv[4];
+                    unsigned char *dst = (s == 0 ? Abuf : A2buf) + tid * 16;
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
-                        ck[c] = __ldcg(pp + c * kRows);
-                        cv[c] = __ldcg(pp + (D / 8) * kRows + c * kRows);
+                        tc::cp_async16(dst + c * 8192, pp + c * kRows);
+                        tc::cp_async16(dst + 32768 + c * 8192, pp + (D / 8) * kRows + c * kRows);
                     }
+                    tc::cp_async_commit();
+                };
+                for (int i = 0; i < nk && i < 2; ++i) fetch(i, i);
+                for (int i = 0; i < nk; ++i) {
+                    if (i + 1 < nk) tc::cp_async_wait<1>();
+                    else tc::cp_async_wait<0>();
+                    const unsigned char *src = ((i & 1) ? A2buf : Abuf) + tid * 16;
                     float s = 0.f;
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
-                        const uint32_t wk[4] = {ck[c].x, ck[c].y, ck[c].z, ck[c].w};
+                        const uint4 ck = *reinterpret_cast<const uint4 *>(src + c * 8192);
+                        const uint32_t wk[4] = {ck.x, ck.y, ck.z, ck.w};
 #pragma unroll
                         for (int j = 0; j < 4; ++j)
                             s += q[8 * c + 2 * j] * bf_lo(wk[j]) + q[8 * c + 2 * j + 1] * bf_hi(wk[j]);
@@ -1511,13 +1552,16 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d256_kernel(const __grid_c
                     l0 = l0 * c0 + p0;
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
-                        const uint32_t wv[4] = {cv[c].x, cv[c].y, cv[c].z, cv[c].w};
+                        const uint4 cv = *reinterpret_cast<const uint4 *>(src + 32768 + c * 8192);
+                        const uint32_t wv[4] = {cv.x, cv.y, cv.z, cv.w};
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
                             acc[8 * c + 2 * j] = acc[8 * c + 2 * j] * c0 + p0 * bf_lo(wv[j]);
                             acc[8 * c + 2 * j + 1] = acc[8 * c + 2 * j + 1] * c0 + p0 * bf_hi(wv[j]);
                         }
                     }
+                    // the stage is refilled only after its data has been consumed
+                    if (i + 2 < nk) fetch(i + 2, i & 1);
                 }
                 __syncwarp();
                 float hv[32];
@@ -1782,7 +1826,10 @@ sg_status launch_decode_bf16(sg_model *m, int64_t B, uint64_t seed, uint32_t sid
     }
     if (d128) {
         const size_t smem128 = 2 * (size_t)kRows * 128 * 2 + (size_t)kStages * kChunkBytes +
-                               8 * kRows * 2 * sizeof(float);
+                               8 * kRows * 2 * sizeof(float) +
+                               (size_t)((g.nslots * 4 + 1023) / 1024) * 1024 + 32768;
+        if (smem128 > 227 * 1024)
+            return fail(SG_EUNSUPPORTED, "BF16 decode (d = 128) needs at most 12000 visible keys");
         SG_CUDA_TRY(cudaFuncSetAttribute(decode_bf16_d128_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem128));
         decode_bf16_d128_kernel<<<(unsigned)tiles, 512, smem128, ::sg::counted(st)>>>(a);
@@ -1790,12 +1837,15 @@ sg_status launch_decode_bf16(sg_model *m, int64_t B, uint64_t seed, uint32_t sid
     }
     if (c.d_token <= 16) {
         // four threads per sample (16 warps): the default for d = 64
-        const size_t smem4 = smem + 4 * kRows * 2 * sizeof(float) + (size_t)c.N * sizeof(uint32_t);
+        size_t smem4 = smem + 4 * kRows * 2 * sizeof(float) + (size_t)((c.N * 4 + 1023) / 1024) * 1024;
         if (smem4 > 227 * 1024)
             return fail(SG_EUNSUPPORTED, "BF16 decode (d = 64) needs N <= 11000");
-        SG_CUDA_TRY(cudaFuncSetAttribute(decode_bf16_d64_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem4));
-        decode_bf16_d64_kernel<<<(unsigned)tiles, 512, smem4, ::sg::counted(st)>>>(a);
+        // a third KV stage (32 KB) when shared memory allows it
+        a.kv_stages = smem4 + 32768 <= 227 * 1024 ? 3 : 2;
+        if (a.kv_stages == 3) smem4 += 32768;
+        auto k64 = a.kv_stages == 3 ? decode_bf16_d64_kernel<3> : decode_bf16_d64_kernel<2>;
+        SG_CUDA_TRY(cudaFuncSetAttribute(k64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem4));
+        k64<<<(unsigned)tiles, 512, smem4, ::sg::counted(st)>>>(a);
         return check_launch("decode_bf16_d64_kernel");
     }
     SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

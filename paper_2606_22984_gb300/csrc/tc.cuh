@@ -80,6 +80,24 @@ __device__ __forceinline__ void bulk_g2s(void *smem_dst, const void *gmem_src, u
         : "memory");
 }
 
+// ------------------------------------------- per-thread async copies (16 B)
+// global -> shared through L2 only, no registers held while in flight; each
+// commit closes a group, wait<n> returns once at most n groups are pending.
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)),
+                 "l"(gmem_src)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Make generic-proxy shared-memory writes visible to the async proxy (MMA
 // operand reads, bulk copies).
 __device__ __forceinline__ void fence_async_smem()
