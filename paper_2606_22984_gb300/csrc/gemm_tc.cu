@@ -4,7 +4,8 @@
 // persistent CTA walks row blocks of 128; warp 0 streams A tiles by bulk copy
 // into two shared-memory stages, warp 1 issues the MMAs into one of two TMEM
 // accumulators, warps 2-5 drain the other accumulator through the epilogue.
-// B (the weights, <= 256 x 256) stays resident in shared memory.
+// B (the weights, <= 256 x 256) stays resident in shared memory.  Larger
+// weights go through tile_gemm_kernel (column blocks of 256, A and B streamed).
 //
 // wgrad_kernel: C[M][N] += A[M][Kr] B[N][Kr]^T, a split-K reduction over the
 // batch rows for weight gradients: each CTA owns one 128-row block of C and a
@@ -201,16 +202,143 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) row_gemm_kernel(const 
     if (warp == 1) tc::tmem_dealloc(tmem, 512);
 }
 
+// tile_gemm_kernel: the same product and epilogues for any N (a multiple of
+// 32) and any K.  Output tiles of 128 rows x up to 256 columns are walked by
+// persistent CTAs (column blocks of one row block consecutively, so the A
+// tiles are reused from L2); per K chunk of 64 a stage holds the A tile and
+// the one or two B tiles of the column block, through four stages.
+constexpr int kTStages = 4;
+
+template <int EPI>
+__global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) tile_gemm_kernel(const __grid_constant__ RowGemm g)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    constexpr uint32_t stage_bytes = 3 * kTileBytes;
+    __shared__ uint64_t full[kTStages], empty[kTStages], tfull[2], tempty[2];
+    __shared__ uint32_t tslot;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kTStages; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            tc::mbar_init(&tfull[s], 1);
+            tc::mbar_init(&tempty[s], kEpiWarps);
+        }
+        tc::fence_mbar_init();
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(&tslot, 512);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = tslot;
+    const int ncb = (g.N + 255) / 256;
+    const int64_t ntiles = g.RB * ncb;
+    const int64_t my_n = (int64_t)blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    auto cols_of = [&](int cb) { return min(256, g.N - 256 * cb); };
+
+    if (warp == 0 && lane == 0) {
+        int64_t j = 0;  // chunks issued
+        bool ok = true;
+        for (int64_t i = 0; i < my_n && ok; ++i) {
+            const int64_t t = blockIdx.x + i * gridDim.x, rb = t / ncb;
+            const int cb = (int)(t % ncb), nbc = (cols_of(cb) + 127) / 128;
+            for (int kc = 0; kc < g.KC; ++kc) {
+                const int s = (int)(j % kTStages);
+                if (j >= kTStages && !tc::mbar_wait(&empty[s], (uint32_t)((j / kTStages - 1) & 1))) {
+                    atomicExch(g.err, 14);
+                    ok = false;
+                    break;
+                }
+                unsigned char *dst = smem + (size_t)s * stage_bytes;
+                tc::mbar_arrive_expect_tx(&full[s], (uint32_t)(1 + nbc) * kTileBytes);
+                tc::bulk_g2s(dst, g.A + ((size_t)(kc * g.RB + rb) << 14), kTileBytes, &full[s]);
+                tc::bulk_g2s(dst + kTileBytes, g.Bw + ((size_t)(kc * g.NBw + 2 * cb) << 14),
+                             (uint32_t)nbc * kTileBytes, &full[s]);
+                ++j;
+            }
+        }
+        // no bulk copy may be in flight when the CTA exits (the last stages'
+        // phases complete when their copies land; earlier ones already have)
+        for (int64_t jj = j > kTStages ? j - kTStages : 0; jj < j; ++jj)
+            if (!tc::mbar_wait(&full[jj % kTStages], (uint32_t)((jj / kTStages) & 1))) break;
+    } else if (warp == 1 && lane == 0) {
+        int64_t j = 0;
+        bool ok = true;
+        for (int64_t i = 0; i < my_n && ok; ++i) {
+            const int acc = (int)(i & 1);
+            const int64_t t = blockIdx.x + i * gridDim.x;
+            const int cb = (int)(t % ncb);
+            if (i >= 2 && !tc::mbar_wait(&tempty[acc], (uint32_t)(((i >> 1) - 1) & 1))) {
+                ok = false;
+                break;
+            }
+            const uint32_t idesc = tc::idesc_bf16(128, cols_of(cb));
+            for (int kc = 0; kc < g.KC; ++kc, ++j) {
+                const int s = (int)(j % kTStages);
+                if (!tc::mbar_wait(&full[s], (uint32_t)((j / kTStages) & 1))) {
+                    ok = false;
+                    break;
+                }
+                tc::tc_fence_after();
+                const uint32_t sa = tc::smem_u32(smem + (size_t)s * stage_bytes);
+                const uint32_t sb = sa + kTileBytes;
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks)
+                    tc::mma_bf16(tmem + acc * 256, tc::smem_desc(sa + 256 * ks, 128, 1024),
+                                 tc::smem_desc(sb + 256 * ks, 128, 1024), idesc,
+                                 (kc | ks) != 0 ? 1u : 0u);
+                tc::mma_commit(&empty[s]);
+            }
+            if (ok) tc::mma_commit(&tfull[acc]);
+        }
+        if (!ok) atomicExch(g.err, 15);
+    } else if (warp >= 2) {
+        const int q = warp & 3, half = (warp - 2) >> 2, row = 32 * q + lane;
+        for (int64_t i = 0; i < my_n; ++i) {
+            const int acc = (int)(i & 1);
+            const int64_t t = blockIdx.x + i * gridDim.x, rb = t / ncb;
+            const int cb = (int)(t % ncb);
+            if (!tc::mbar_wait(&tfull[acc], (uint32_t)((i >> 1) & 1))) {
+                if (lane == 0) atomicExch(g.err, 16);
+                break;
+            }
+            tc::tc_fence_after();
+            const int64_t r = rb * 128 + row;
+            const bool valid = r < g.R;
+            for (int c = half; c < cols_of(cb) / 32; c += 2) {
+                float v[32];
+                tc::tmem_ld32(tmem + acc * 256 + ((uint32_t)(32 * q) << 16) + 32 * c, v);
+                tc::tmem_wait_ld();
+                row_epilogue<EPI>(g, v, r, 256 * cb + 32 * c, valid);
+            }
+            tc::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&tempty[acc]);
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) tc::tmem_dealloc(tmem, 512);
+}
+
 constexpr int kWStages = 4;
 
 __global__ void __launch_bounds__(192, 1) wgrad_kernel(const __grid_constant__ WgradGemm g)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    const uint32_t stage_bytes = (uint32_t)(1 + g.NB) * kTileBytes;
+    const uint32_t stage_bytes = (uint32_t)(1 + min(g.NB, 2)) * kTileBytes;
     __shared__ uint64_t full[kWStages], empty[kWStages], tfull;
     __shared__ uint32_t tslot;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t mb = blockIdx.x % g.MB, split = blockIdx.x / g.MB;
+    const int ncb = (g.N + 255) / 256;
+    const int64_t mb = blockIdx.x % g.MB, split = blockIdx.x / g.MB / ncb;
+    const int cb = (int)((blockIdx.x / g.MB) % ncb);
+    const int nc = min(256, g.N - 256 * cb), nbc = (nc + 127) / 128;
     const int64_t kc0 = split * g.kc_per_cta;
     const int64_t kc1 = kc0 + g.kc_per_cta < g.KCtot ? kc0 + g.kc_per_cta : g.KCtot;
     const int64_t n = kc1 > kc0 ? kc1 - kc0 : 0;
@@ -239,14 +367,13 @@ __global__ void __launch_bounds__(192, 1) wgrad_kernel(const __grid_constant__ W
                 break;
             }
             unsigned char *dst = smem + (size_t)s * stage_bytes;
-            tc::mbar_arrive_expect_tx(&full[s], stage_bytes);
+            tc::mbar_arrive_expect_tx(&full[s], (uint32_t)(1 + nbc) * kTileBytes);
             tc::bulk_g2s(dst, g.A + ((size_t)(kc * g.MB + mb) << 14), kTileBytes, &full[s]);
-            for (int nb = 0; nb < g.NB; ++nb)
-                tc::bulk_g2s(dst + (size_t)(1 + nb) * kTileBytes,
-                             g.Bm + ((size_t)(kc * g.NB + nb) << 14), kTileBytes, &full[s]);
+            tc::bulk_g2s(dst + kTileBytes, g.Bm + ((size_t)(kc * g.NB + 2 * cb) << 14),
+                         (uint32_t)nbc * kTileBytes, &full[s]);
         }
     } else if (warp == 1 && lane == 0) {
-        const uint32_t idesc = tc::idesc_bf16(128, g.N);
+        const uint32_t idesc = tc::idesc_bf16(128, nc);
         bool ok = true;
         for (int64_t j = 0; j < n; ++j) {
             const int s = (int)(j % kWStages);
@@ -271,13 +398,13 @@ __global__ void __launch_bounds__(192, 1) wgrad_kernel(const __grid_constant__ W
         const int64_t m = mb * 128 + 32 * q + lane;
         if (tc::mbar_wait(&tfull, 0)) {
             tc::tc_fence_after();
-            for (int c = 0; c < g.N / 32; ++c) {
+            for (int c = 0; c < nc / 32; ++c) {
                 float v[32];
                 tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + 32 * c, v);
                 tc::tmem_wait_ld();
                 if (m < g.M)
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) atomicAdd(g.C + m * g.N + 32 * c + j, v[j]);
+                    for (int j = 0; j < 32; ++j) atomicAdd(g.C + m * g.N + 256 * cb + 32 * c + j, v[j]);
             }
         } else if (lane == 0) {
             atomicExch(g.err, 23);
@@ -374,35 +501,50 @@ sg_status launch_pack_tiled(const float *W, int rows, int K, unsigned char *dst,
 
 sg_status launch_row_gemm(const RowGemm &g, int epi, cudaStream_t st)
 {
-    if (g.N % 32 || g.N > 256 || g.N > g.NBw * 128 || g.KC < 1 || g.KC > 4)
-        return fail(SG_EUNSUPPORTED, "row GEMM needs N a multiple of 32, N <= 256, K <= 256");
+    if (g.N % 32 || g.N < 32 || g.N > g.NBw * 128 || g.KC < 1)
+        return fail(SG_EUNSUPPORTED, "tensor-core GEMM needs N a multiple of 32");
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t smem = (size_t)(g.NBw * g.KC + 2 * g.KC) * kTileBytes;
-    const unsigned grid = (unsigned)std::min<int64_t>(g.RB, sms);
+    // weights that fit stay resident (row_gemm_kernel); otherwise column
+    // blocks of 256 with A and B streamed per K chunk (tile_gemm_kernel)
+    const bool resident = g.N <= 256 && g.KC <= 4;
+    const size_t smem = resident ? (size_t)(g.NBw * g.KC + 2 * g.KC) * kTileBytes
+                                 : (size_t)kTStages * 3 * kTileBytes;
+    const int64_t units = resident ? g.RB : g.RB * ((g.N + 255) / 256);
+    const unsigned grid = (unsigned)std::min<int64_t>(units, sms);
     auto go = [&](auto kern) -> sg_status {
         SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kern<<<grid, 64 + 32 * kEpiWarps, smem, ::sg::counted(st)>>>(g);
-        return check_launch("row_gemm_kernel");
+        return check_launch(resident ? "row_gemm_kernel" : "tile_gemm_kernel");
     };
+    if (resident) {
+        switch (epi) {
+        case TE_STORE_F32: return go(row_gemm_kernel<TE_STORE_F32>);
+        case TE_RESID_F32: return go(row_gemm_kernel<TE_RESID_F32>);
+        case TE_GELU_T: return go(row_gemm_kernel<TE_GELU_T>);
+        case TE_GELU_BWD_T: return go(row_gemm_kernel<TE_GELU_BWD_T>);
+        default: return go(row_gemm_kernel<TE_STORE_F32_T>);
+        }
+    }
     switch (epi) {
-    case TE_STORE_F32: return go(row_gemm_kernel<TE_STORE_F32>);
-    case TE_RESID_F32: return go(row_gemm_kernel<TE_RESID_F32>);
-    case TE_GELU_T: return go(row_gemm_kernel<TE_GELU_T>);
-    case TE_GELU_BWD_T: return go(row_gemm_kernel<TE_GELU_BWD_T>);
-    default: return go(row_gemm_kernel<TE_STORE_F32_T>);
+    case TE_STORE_F32: return go(tile_gemm_kernel<TE_STORE_F32>);
+    case TE_RESID_F32: return go(tile_gemm_kernel<TE_RESID_F32>);
+    case TE_GELU_T: return go(tile_gemm_kernel<TE_GELU_T>);
+    case TE_GELU_BWD_T: return go(tile_gemm_kernel<TE_GELU_BWD_T>);
+    default: return go(tile_gemm_kernel<TE_STORE_F32_T>);
     }
 }
 
 sg_status launch_wgrad_gemm(const WgradGemm &g, cudaStream_t st)
 {
-    if (g.N % 32 || g.N > 256 || g.N > g.NB * 128)
-        return fail(SG_EUNSUPPORTED, "weight-gradient GEMM needs N a multiple of 32, <= 256");
-    const size_t smem = (size_t)kWStages * (1 + g.NB) * kTileBytes;
+    if (g.N % 32 || g.N < 32 || g.N > g.NB * 128)
+        return fail(SG_EUNSUPPORTED, "weight-gradient GEMM needs N a multiple of 32");
+    const size_t smem = (size_t)kWStages * (1 + std::min(g.NB, 2)) * kTileBytes;
     const int64_t splits = (g.KCtot + g.kc_per_cta - 1) / g.kc_per_cta;
+    const int64_t ncb = (g.N + 255) / 256;
     SG_CUDA_TRY(cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    wgrad_kernel<<<(unsigned)(g.MB * splits), 192, smem, ::sg::counted(st)>>>(g);
+    wgrad_kernel<<<(unsigned)(g.MB * ncb * splits), 192, smem, ::sg::counted(st)>>>(g);
     return check_launch("wgrad_kernel");
 }
 

@@ -45,7 +45,7 @@ struct RowGemm {
     int KC;                   // K chunks of 64
     const unsigned char *Bw;  // T(N, K): NBw row blocks
     int NBw;
-    int N;                    // output columns (multiple of 32, <= 256)
+    int N;                    // output columns (multiple of 32)
     int64_t R;                // valid rows
     const float *bias;        // [N] or nullptr
     float *out_f32;
@@ -62,7 +62,7 @@ struct WgradGemm {
     const unsigned char *A;   // T(M, Kr): rows = M output features, K = rows of the batch
     int64_t MB;               // row blocks of A
     const unsigned char *Bm;  // T(N, Kr)
-    int NB;                   // row blocks of B (N <= 256)
+    int NB;                   // row blocks of B
     int N;
     int M;
     int64_t KCtot;            // K chunks (ceil(Kr / 64))

@@ -608,12 +608,11 @@ struct LayerBufs {
     unsigned char *A1t, *A2t, *Gt, *F1t;
 };
 
-// The BF16 model runs its teacher-forced GEMMs on tcgen05 when every GEMM
-// fits the row-GEMM kernel (N <= 256 columns, K <= 256).
+// The BF16 model runs its teacher-forced GEMMs on tcgen05 (every output
+// width a multiple of 32).
 bool use_tc(const sg_config &c)
 {
-    return c.precision == SG_BF16 && c.d % 32 == 0 && 3 * c.d <= 256 && c.d_ff % 32 == 0 &&
-           c.d_ff <= 256;
+    return c.precision == SG_BF16 && c.d % 32 == 0 && c.d_ff % 32 == 0;
 }
 
 // out[j] += sum_r T[r][j] over a tiled BF16 matrix T(R, F)
@@ -1246,7 +1245,7 @@ sg_status launch_grad_f32(sg_model *m, const int8_t *spins, const float *coeff, 
                 WgradGemm g{};
                 g.A = A; g.MB = tl_blocks(M); g.Bm = Bm; g.NB = (int)tl_blocks(N); g.N = N; g.M = M;
                 g.KCtot = KCr;
-                const int64_t splits = std::max<int64_t>(1, 304 / g.MB);
+                const int64_t splits = std::max<int64_t>(1, 304 / (g.MB * ((N + 255) / 256)));
                 g.kc_per_cta = (KCr + splits - 1) / splits;
                 g.C = C; g.err = (int *)m->err;
                 launch_wgrad_gemm(g, st);

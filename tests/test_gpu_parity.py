@@ -103,6 +103,10 @@ def test_full_size_d128_sampled_rows(name, precision, rows):
     assert np.array_equal(so, s[rows])
     assert np.abs(lqo - lq[rows]).max() <= tol * m.N
     assert unpack_flags(fl, m.N).mean() < (0.05 if precision == "bf16" else 0.01)
+    if precision == "bf16":
+        # the teacher-forced BF16 pass (tcgen05 GEMMs) scores the same spins
+        tf = _np(model.logprob(spins[:256]))
+        assert np.abs(tf - lq[:256]).max() <= tol * m.N
     if inst.pm:
         _, Ei = gi.energy(spins, want_int=True)
         assert np.array_equal(_np(Ei).astype(np.float64), oracle.energy(inst, s))
@@ -345,7 +349,11 @@ def test_fp32_grad_matches_oracle(m):
 
 BF16_TF_MODELS = [inputs.ModelShape(20, 2, 32, 4), inputs.ModelShape(40, 2, 64, 4),
                   inputs.ModelShape(70, 3, 64, 4, mask_kind=1, W=8, S=9),
-                  inputs.ModelShape(33, 1, 64, 4, mask_kind=1, W=3, S=2)]
+                  inputs.ModelShape(33, 1, 64, 4, mask_kind=1, W=3, S=2),
+                  # weights beyond 256 x 256: column-blocked tile GEMM, split wgrad
+                  inputs.ModelShape(24, 2, 128, 8),
+                  inputs.ModelShape(30, 1, 96, 6, mask_kind=1, W=5, S=4),
+                  inputs.ModelShape(20, 1, 256, 8, mask_kind=1, W=6, S=3)]
 
 
 @pytest.mark.parametrize("m", BF16_TF_MODELS)
