@@ -72,7 +72,7 @@ __device__ __forceinline__ void row_epilogue(const RowGemm &g, const float (&v)[
 #pragma unroll
             for (int j = 0; j < 32; ++j) o[j] = valid ? o[j] : 0.f;
 #pragma unroll
-            for (int c = 0; c < 4; ++c) st8(g.out_t, tl_offset(r, col0 + 8 * c, g.RB), o + 8 * c);
+            for (int c = 0; c < 4; ++c) st8(g.out_t, wl_offset(r, col0 + 8 * c, g.N), o + 8 * c);
         }
     } else if (EPI == TE_GELU_T) {
         float x[32], y[32];
@@ -83,20 +83,20 @@ __device__ __forceinline__ void row_epilogue(const RowGemm &g, const float (&v)[
         }
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            st8(g.out_t, tl_offset(r, col0 + 8 * c, g.RB), y + 8 * c);
-            st8(g.out_t2, tl_offset(r, col0 + 8 * c, g.RB), x + 8 * c);
+            st8(g.out_t, wl_offset(r, col0 + 8 * c, g.N), y + 8 * c);
+            st8(g.out_t2, wl_offset(r, col0 + 8 * c, g.N), x + 8 * c);
         }
     } else {  // TE_GELU_BWD_T
         float y[32];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             float f1[8];
-            ld8(g.aux_t, tl_offset(r, col0 + 8 * c, g.RB), f1);
+            ld8(g.aux_t, wl_offset(r, col0 + 8 * c, g.N), f1);
 #pragma unroll
             for (int j = 0; j < 8; ++j) y[8 * c + j] = valid ? v[8 * c + j] * gelu_grad_f(f1[j]) : 0.f;
         }
 #pragma unroll
-        for (int c = 0; c < 4; ++c) st8(g.out_t, tl_offset(r, col0 + 8 * c, g.RB), y + 8 * c);
+        for (int c = 0; c < 4; ++c) st8(g.out_t, wl_offset(r, col0 + 8 * c, g.N), y + 8 * c);
     }
 }
 
@@ -106,7 +106,7 @@ template <int EPI>
 __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) row_gemm_kernel(const __grid_constant__ RowGemm g)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    const uint32_t stage_bytes = (uint32_t)g.KC * kTileBytes;
+    const uint32_t stage_bytes = (uint32_t)wl_block_bytes(g.K);  // one row block of A
     unsigned char *Bs = smem;
     unsigned char *As = smem + (size_t)g.NBw * g.KC * kTileBytes;
     __shared__ uint64_t full[2], empty[2], tfull[2], tempty[2], wfull;
@@ -146,9 +146,8 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) row_gemm_kernel(const 
                 break;
             }
             tc::mbar_arrive_expect_tx(&full[s], stage_bytes);
-            for (int kc = 0; kc < g.KC; ++kc)
-                tc::bulk_g2s(As + (size_t)s * stage_bytes + (size_t)kc * kTileBytes,
-                             g.A + ((size_t)(kc * g.RB + rb) << 14), kTileBytes, &full[s]);
+            tc::bulk_g2s(As + (size_t)s * stage_bytes, g.A + (size_t)rb * stage_bytes, stage_bytes,
+                         &full[s]);
         }
     } else if (warp == 1 && lane == 0) {
         bool ok = tc::mbar_wait(&wfull, 0);
@@ -159,14 +158,11 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) row_gemm_kernel(const 
             if (ok && i >= 2) ok = tc::mbar_wait(&tempty[acc], (uint32_t)(((i >> 1) - 1) & 1));
             if (!ok) break;
             tc::tc_fence_after();
-            for (int kc = 0; kc < g.KC; ++kc) {
-                const uint32_t sa = tc::smem_u32(As + (size_t)s * stage_bytes + (size_t)kc * kTileBytes);
-                const uint32_t sb = tc::smem_u32(Bs + (size_t)kc * g.NBw * kTileBytes);
-#pragma unroll
-                for (int ks = 0; ks < 4; ++ks)
-                    tc::mma_bf16(tmem + acc * 256, tc::smem_desc(sa + 256 * ks, 128, 1024),
-                                 tc::smem_desc(sb + 256 * ks, 128, 1024), idesc,
-                                 (kc | ks) != 0 ? 1u : 0u);
+            const uint32_t sa = tc::smem_u32(As + (size_t)s * stage_bytes);
+            for (int ks = 0; ks < g.K / 16; ++ks) {
+                const uint32_t sb = tc::smem_u32(Bs + (size_t)(ks >> 2) * g.NBw * kTileBytes) + 256 * (ks & 3);
+                tc::mma_bf16(tmem + acc * 256, tc::smem_desc(sa + 256 * ks, 128, 16 * g.K),
+                             tc::smem_desc(sb, 128, 1024), idesc, ks != 0 ? 1u : 0u);
             }
             tc::mma_commit(&empty[s]);
             tc::mma_commit(&tfull[acc]);
@@ -255,8 +251,12 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) tile_gemm_kernel(const
                     break;
                 }
                 unsigned char *dst = smem + (size_t)s * stage_bytes;
-                tc::mbar_arrive_expect_tx(&full[s], (uint32_t)(1 + nbc) * kTileBytes);
-                tc::bulk_g2s(dst, g.A + ((size_t)(kc * g.RB + rb) << 14), kTileBytes, &full[s]);
+                // K chunk kc of A: in each 8-row group, core groups 8 kc .. of the row block
+                const uint32_t kw = (uint32_t)min(64, g.K - 64 * kc);
+                tc::mbar_arrive_expect_tx(&full[s], 16u * 16u * kw + (uint32_t)nbc * kTileBytes);
+                const unsigned char *arow = g.A + (size_t)rb * wl_block_bytes(g.K) + (size_t)kc * 1024;
+                for (int rg = 0; rg < 16; ++rg)
+                    tc::bulk_g2s(dst + rg * 1024, arow + (size_t)rg * 16 * g.K, 16u * kw, &full[s]);
                 tc::bulk_g2s(dst + kTileBytes, g.Bw + ((size_t)(kc * g.NBw + 2 * cb) << 14),
                              (uint32_t)nbc * kTileBytes, &full[s]);
                 ++j;
@@ -287,8 +287,8 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) tile_gemm_kernel(const
                 tc::tc_fence_after();
                 const uint32_t sa = tc::smem_u32(smem + (size_t)s * stage_bytes);
                 const uint32_t sb = sa + kTileBytes;
-#pragma unroll
-                for (int ks = 0; ks < 4; ++ks)
+                const int nks = min(4, (g.K - 64 * kc) / 16);  // only k-steps inside K
+                for (int ks = 0; ks < nks; ++ks)
                     tc::mma_bf16(tmem + acc * 256, tc::smem_desc(sa + 256 * ks, 128, 1024),
                                  tc::smem_desc(sb + 256 * ks, 128, 1024), idesc,
                                  (kc | ks) != 0 ? 1u : 0u);
@@ -326,24 +326,32 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) tile_gemm_kernel(const
     if (warp == 1) tc::tmem_dealloc(tmem, 512);
 }
 
-constexpr int kWStages = 4;
-
-__global__ void __launch_bounds__(192, 1) wgrad_kernel(const __grid_constant__ WgradGemm g)
+// wgrad_kernel: C (+)= A^T B over the rows of two wide activations.  CTA
+// (mt, nb, split) owns C rows 128 mt .. (features of A) and columns 256 nb ..
+// (features of B) and a range of row blocks.  Per row block a stage holds the
+// A window [128 rows x 128 features] and the B window [128 rows x nw
+// features], gathered per 8-row group by bulk copies; both are read MN-major
+// (instruction-descriptor bits 15 and 16), 8 MMAs of 16 rows each.  The TMEM
+// accumulator is added to C with atomics.  A window that overhangs the
+// features of A reads the next row group (or the slack tail); those
+// accumulator rows are never stored.
+__global__ void __launch_bounds__(192, 1) wgrad_kernel(const __grid_constant__ WgradGemm g, int stages)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    const uint32_t stage_bytes = (uint32_t)(1 + min(g.NB, 2)) * kTileBytes;
-    __shared__ uint64_t full[kWStages], empty[kWStages], tfull;
+    const int nbn = (g.N + 255) / 256, nmt = (g.M + 127) / 128;
+    const int mt = (int)(blockIdx.x % nmt), nb = (int)((blockIdx.x / nmt) % nbn);
+    const int64_t split = blockIdx.x / nmt / nbn;
+    const int nw = min(256, g.N - 256 * nb);
+    const uint32_t a_bytes = 128 * 128 * 2, b_bytes = (uint32_t)(128 * nw * 2);
+    const uint32_t stage_bytes = a_bytes + b_bytes;
+    const int64_t rb0 = split * g.rb_per_cta;
+    const int64_t rb1 = rb0 + g.rb_per_cta < g.RB ? rb0 + g.rb_per_cta : g.RB;
+    const int64_t n = rb1 > rb0 ? rb1 - rb0 : 0;
+    __shared__ uint64_t full[4], empty[4], tfull;
     __shared__ uint32_t tslot;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ncb = (g.N + 255) / 256;
-    const int64_t mb = blockIdx.x % g.MB, split = blockIdx.x / g.MB / ncb;
-    const int cb = (int)((blockIdx.x / g.MB) % ncb);
-    const int nc = min(256, g.N - 256 * cb), nbc = (nc + 127) / 128;
-    const int64_t kc0 = split * g.kc_per_cta;
-    const int64_t kc1 = kc0 + g.kc_per_cta < g.KCtot ? kc0 + g.kc_per_cta : g.KCtot;
-    const int64_t n = kc1 > kc0 ? kc1 - kc0 : 0;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kWStages; ++s) {
+        for (int s = 0; s < stages; ++s) {
             tc::mbar_init(&full[s], 1);
             tc::mbar_init(&empty[s], 1);
         }
@@ -359,35 +367,45 @@ __global__ void __launch_bounds__(192, 1) wgrad_kernel(const __grid_constant__ W
     tc::tc_fence_after();
     const uint32_t tmem = tslot;
     if (warp == 0 && lane == 0) {
-        for (int64_t j = 0; j < n; ++j) {
-            const int s = (int)(j % kWStages);
-            const int64_t kc = kc0 + j;
-            if (j >= kWStages && !tc::mbar_wait(&empty[s], (uint32_t)((j / kWStages - 1) & 1))) {
+        // A window: 16 KB... per 8-row group 16 core matrices (2 KB) of A's row group;
+        // B window: nw / 8 core matrices of B's row group
+        const uint32_t a_row = (uint32_t)min(2048, 16 * (g.M - 128 * mt));
+        int64_t j = 0;
+        for (; j < n; ++j) {
+            const int s = (int)(j % stages);
+            if (j >= stages && !tc::mbar_wait(&empty[s], (uint32_t)((j / stages - 1) & 1))) {
                 atomicExch(g.err, 21);
                 break;
             }
+            const int64_t rb = rb0 + j;
             unsigned char *dst = smem + (size_t)s * stage_bytes;
-            tc::mbar_arrive_expect_tx(&full[s], (uint32_t)(1 + nbc) * kTileBytes);
-            tc::bulk_g2s(dst, g.A + ((size_t)(kc * g.MB + mb) << 14), kTileBytes, &full[s]);
-            tc::bulk_g2s(dst + kTileBytes, g.Bm + ((size_t)(kc * g.NB + 2 * cb) << 14),
-                         (uint32_t)nbc * kTileBytes, &full[s]);
+            tc::mbar_arrive_expect_tx(&full[s], 16 * a_row + b_bytes);
+            const unsigned char *ab = g.A + (size_t)rb * wl_block_bytes(g.M) + (size_t)mt * 2048;
+            const unsigned char *bb = g.Bm + (size_t)rb * wl_block_bytes(g.N) + (size_t)nb * 4096;
+            for (int rg = 0; rg < 16; ++rg) {
+                tc::bulk_g2s(dst + rg * 2048, ab + (size_t)rg * 16 * g.M, a_row, &full[s]);
+                tc::bulk_g2s(dst + a_bytes + rg * 16 * nw, bb + (size_t)rg * 16 * g.N, 16u * nw, &full[s]);
+            }
         }
+        // no bulk copy may be in flight when the CTA exits
+        for (int64_t jj = j > stages ? j - stages : 0; jj < j; ++jj)
+            if (!tc::mbar_wait(&full[jj % stages], (uint32_t)((jj / stages) & 1))) break;
     } else if (warp == 1 && lane == 0) {
-        const uint32_t idesc = tc::idesc_bf16(128, nc);
+        const uint32_t idesc = tc::idesc_bf16(128, nw) | (1u << 15) | (1u << 16);  // A, B MN-major
         bool ok = true;
         for (int64_t j = 0; j < n; ++j) {
-            const int s = (int)(j % kWStages);
-            if (!tc::mbar_wait(&full[s], (uint32_t)((j / kWStages) & 1))) {
+            const int s = (int)(j % stages);
+            if (!tc::mbar_wait(&full[s], (uint32_t)((j / stages) & 1))) {
                 ok = false;
                 break;
             }
             tc::tc_fence_after();
             const uint32_t sa = tc::smem_u32(smem + (size_t)s * stage_bytes);
-            const uint32_t sb = sa + kTileBytes;
+            const uint32_t sb = sa + a_bytes;
 #pragma unroll
-            for (int ks = 0; ks < 4; ++ks)
-                tc::mma_bf16(tmem, tc::smem_desc(sa + 256 * ks, 128, 1024),
-                             tc::smem_desc(sb + 256 * ks, 128, 1024), idesc,
+            for (int ks = 0; ks < 8; ++ks)  // 16 rows = two 8-row groups per MMA
+                tc::mma_bf16(tmem, tc::smem_desc(sa + ks * 2 * 2048, 2048, 128),
+                             tc::smem_desc(sb + ks * 2 * 16 * nw, 16 * nw, 128), idesc,
                              (j | ks) != 0 ? 1u : 0u);
             tc::mma_commit(&empty[s]);
         }
@@ -395,16 +413,22 @@ __global__ void __launch_bounds__(192, 1) wgrad_kernel(const __grid_constant__ W
         tc::mma_commit(&tfull);
     } else if (warp >= 2 && n > 0) {
         const int q = warp & 3;
-        const int64_t m = mb * 128 + 32 * q + lane;
+        const int m = mt * 128 + 32 * q + lane;
         if (tc::mbar_wait(&tfull, 0)) {
             tc::tc_fence_after();
-            for (int c = 0; c < nc / 32; ++c) {
+            for (int c = 0; c < nw / 32; ++c) {
                 float v[32];
                 tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + 32 * c, v);
                 tc::tmem_wait_ld();
-                if (m < g.M)
+                if (m < g.M) {
+                    const int n0 = nb * 256 + 32 * c;
+                    if (g.transpose_out)
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) atomicAdd(g.C + m * g.N + 256 * cb + 32 * c + j, v[j]);
+                        for (int jj = 0; jj < 32; ++jj) atomicAdd(g.C + (size_t)(n0 + jj) * g.ldc + m, v[jj]);
+                    else
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj) atomicAdd(g.C + (size_t)m * g.ldc + n0 + jj, v[jj]);
+                }
             }
         } else if (lane == 0) {
             atomicExch(g.err, 23);
@@ -447,27 +471,27 @@ __global__ void to_tiled_kernel(const float *__restrict__ X, int64_t R, int F, i
     st8(dst, tl_offset(rt, (int)(kg * 8), RBt), v);
 }
 
-// T(R, F) -> T(F, R).  Thread = (tiled output row f, 8-group of R).
-__global__ void tiled_transpose_kernel(const unsigned char *__restrict__ src, int64_t R, int F,
-                                       unsigned char *__restrict__ dst)
+// FP32 row-major [R][F] -> W(R, F).  Thread = (row, 8-wide group); rows past
+// R up to the end of the last row block are written as zeros.
+__global__ void to_wide_kernel(const float *__restrict__ X, int64_t R, int F,
+                               unsigned char *__restrict__ dst)
 {
-    const int64_t RBs = tl_blocks(R), RBd = tl_blocks(F);
-    const int64_t groups = ((R + 63) >> 6) * 8;
+    const int groups = F >> 3;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= RBd * 128 * groups) return;
-    const int64_t f = i % (RBd * 128), rg = i / (RBd * 128);
+    if (i >= tl_blocks(R) * 128 * groups) return;
+    const int64_t r = i / groups;
+    const int kg = (int)(i % groups);
     float v[8];
+    if (r < R) {
+        const float4 a = *reinterpret_cast<const float4 *>(X + r * F + 8 * kg);
+        const float4 b = *reinterpret_cast<const float4 *>(X + r * F + 8 * kg + 4);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const int64_t r = rg * 8 + j;
-        float x = 0.f;
-        if (f < F && r < R) {
-            const uint16_t b = *reinterpret_cast<const uint16_t *>(src + tl_offset(r, (int)f, RBs));
-            x = __uint_as_float((uint32_t)b << 16);
-        }
-        v[j] = x;
+        for (int j = 0; j < 8; ++j) v[j] = 0.f;
     }
-    st8(dst, tl_offset(f, (int)(rg * 8), RBd), v);
+    st8(dst, wl_offset(r, 8 * kg, F), v);
 }
 
 unsigned grid_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
@@ -484,12 +508,11 @@ sg_status launch_to_tiled(const float *X, int64_t R, int F, int ldx, unsigned ch
     return check_launch("to_tiled_kernel");
 }
 
-sg_status launch_tiled_transpose(const unsigned char *src, int64_t R, int F, unsigned char *dst,
-                                 cudaStream_t st)
+sg_status launch_to_wide(const float *X, int64_t R, int F, unsigned char *dst, cudaStream_t st)
 {
-    const int64_t n = tl_blocks(F) * 128 * (((R + 63) >> 6) * 8);
-    tiled_transpose_kernel<<<grid_for(n, 256), 256, 0, ::sg::counted(st)>>>(src, R, F, dst);
-    return check_launch("tiled_transpose_kernel");
+    const int64_t n = tl_blocks(R) * 128 * (F >> 3);
+    to_wide_kernel<<<grid_for(n, 256), 256, 0, ::sg::counted(st)>>>(X, R, F, dst);
+    return check_launch("to_wide_kernel");
 }
 
 sg_status launch_pack_tiled(const float *W, int rows, int K, unsigned char *dst, bool transpose,
@@ -508,8 +531,10 @@ sg_status launch_row_gemm(const RowGemm &g, int epi, cudaStream_t st)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     // weights that fit stay resident (row_gemm_kernel); otherwise column
     // blocks of 256 with A and B streamed per K chunk (tile_gemm_kernel)
+    if (g.K % 16 || g.KC != (g.K + 63) / 64)
+        return fail(SG_EUNSUPPORTED, "tensor-core GEMM needs K a multiple of 16");
     const bool resident = g.N <= 256 && g.KC <= 4;
-    const size_t smem = resident ? (size_t)(g.NBw * g.KC + 2 * g.KC) * kTileBytes
+    const size_t smem = resident ? (size_t)g.NBw * g.KC * kTileBytes + 2 * wl_block_bytes(g.K)
                                  : (size_t)kTStages * 3 * kTileBytes;
     const int64_t units = resident ? g.RB : g.RB * ((g.N + 255) / 256);
     const unsigned grid = (unsigned)std::min<int64_t>(units, sms);
@@ -538,13 +563,16 @@ sg_status launch_row_gemm(const RowGemm &g, int epi, cudaStream_t st)
 
 sg_status launch_wgrad_gemm(const WgradGemm &g, cudaStream_t st)
 {
-    if (g.N % 32 || g.N < 32 || g.N > g.NB * 128)
-        return fail(SG_EUNSUPPORTED, "weight-gradient GEMM needs N a multiple of 32");
-    const size_t smem = (size_t)kWStages * (1 + std::min(g.NB, 2)) * kTileBytes;
-    const int64_t splits = (g.KCtot + g.kc_per_cta - 1) / g.kc_per_cta;
-    const int64_t ncb = (g.N + 255) / 256;
+    if (g.N % 16 || g.M % 16 || g.N < 16 || g.M < 16)
+        return fail(SG_EUNSUPPORTED, "weight-gradient GEMM needs feature counts that are multiples of 16");
+    const int nw = std::min(256, g.N);
+    const size_t stage = (size_t)128 * 128 * 2 + (size_t)128 * nw * 2;
+    const int stages = (int)std::min<size_t>(4, (200 * 1024) / stage);
+    const int64_t splits = (g.RB + g.rb_per_cta - 1) / g.rb_per_cta;
+    const int64_t ctas = (int64_t)((g.M + 127) / 128) * ((g.N + 255) / 256) * splits;
+    const size_t smem = stage * stages;
     SG_CUDA_TRY(cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    wgrad_kernel<<<(unsigned)(g.MB * ncb * splits), 192, smem, ::sg::counted(st)>>>(g);
+    wgrad_kernel<<<(unsigned)ctas, 192, smem, ::sg::counted(st)>>>(g, stages);
     return check_launch("wgrad_kernel");
 }
 

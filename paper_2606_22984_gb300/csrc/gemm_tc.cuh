@@ -31,6 +31,27 @@ __host__ __device__ __forceinline__ size_t tl_offset(int64_t r, int k, int64_t R
            tc::cm_offset((int)(r & 127), k & 63, 8);
 }
 
+// Wide layout W(R, F) of activations: row block rb (128 rows) is one [128 x F]
+// core-matrix tile (KG = F / 8) at byte rb * 256 F, so a row block is one
+// bulk copy.  Read K-major (K = F) by the row GEMMs: descriptor strides 128 B
+// along K and 16 F bytes between 8-row groups.  Read MN-major (MN = F, K =
+// rows) by the weight-gradient GEMM: 128 B along MN and 16 F bytes along K.
+// Rows past R up to the block end are zero; a slack tail lets a 128-wide
+// operand window that overhangs F stay inside the buffer.  F is a multiple of 16.
+constexpr size_t kWideSlack = 4096;
+
+__host__ __device__ __forceinline__ size_t wl_block_bytes(int F) { return (size_t)256 * F; }
+
+__host__ __device__ __forceinline__ size_t wl_bytes(int64_t R, int F)
+{
+    return (size_t)tl_blocks(R) * wl_block_bytes(F) + kWideSlack;
+}
+
+__host__ __device__ __forceinline__ size_t wl_offset(int64_t r, int f, int F)
+{
+    return (size_t)(r >> 7) * wl_block_bytes(F) + tc::cm_offset((int)(r & 127), f, F >> 3);
+}
+
 enum TcEpilogue {
     TE_STORE_F32 = 0,   // out_f32 = acc (+ bias)
     TE_RESID_F32 = 1,   // out_f32 = resid + acc + bias
@@ -40,9 +61,10 @@ enum TcEpilogue {
 };
 
 struct RowGemm {
-    const unsigned char *A;   // T(R, K)
-    int64_t RB;               // row blocks of A (and of tiled outputs)
-    int KC;                   // K chunks of 64
+    const unsigned char *A;   // W(R, K)
+    int64_t RB;               // row blocks of A (and of the wide outputs)
+    int K;                    // reduction length (multiple of 16)
+    int KC;                   // K chunks of 64 of the weights
     const unsigned char *Bw;  // T(N, K): NBw row blocks
     int NBw;
     int N;                    // output columns (multiple of 32)
@@ -52,22 +74,24 @@ struct RowGemm {
     int ld_out;
     const float *resid;
     int ld_resid;
-    unsigned char *out_t;     // T(R, N)
-    unsigned char *out_t2;    // T(R, N)
-    const unsigned char *aux_t;
+    unsigned char *out_t;     // W(R, N)
+    unsigned char *out_t2;    // W(R, N)
+    const unsigned char *aux_t;  // W(R, N)
     int *err;
 };
 
+// C += A^T B over the rows of two wide activations (both operands MN-major):
+// C[m][n] = sum_r A[r][m] B[r][n], or stored at C[n][m] when transpose_out.
 struct WgradGemm {
-    const unsigned char *A;   // T(M, Kr): rows = M output features, K = rows of the batch
-    int64_t MB;               // row blocks of A
-    const unsigned char *Bm;  // T(N, Kr)
-    int NB;                   // row blocks of B
-    int N;
+    const unsigned char *A;   // W(R, M)
     int M;
-    int64_t KCtot;            // K chunks (ceil(Kr / 64))
-    int64_t kc_per_cta;
-    float *C;                 // [M][N] accumulated with atomics
+    const unsigned char *Bm;  // W(R, N)
+    int N;
+    int64_t RB;               // row blocks (the reduction, 128 rows each)
+    int64_t rb_per_cta;       // row blocks per split
+    float *C;
+    int ldc;
+    int transpose_out;
     int *err;
 };
 
@@ -77,9 +101,8 @@ sg_status launch_wgrad_gemm(const WgradGemm &g, cudaStream_t st);
 // FP32 row-major [R][F] -> T(R, F) or the transpose T(F, R) (zero padding).
 sg_status launch_to_tiled(const float *X, int64_t R, int F, int ldx, unsigned char *dst,
                           bool transpose, cudaStream_t st);
-// T(R, F) -> T(F, R)
-sg_status launch_tiled_transpose(const unsigned char *src, int64_t R, int F, unsigned char *dst,
-                                 cudaStream_t st);
+// FP32 row-major [R][F] -> W(R, F) (rows past R zero).
+sg_status launch_to_wide(const float *X, int64_t R, int F, unsigned char *dst, cudaStream_t st);
 // FP32 row-major W[rows][K] -> T(rows, K) (weights), or of W^T when transpose.
 sg_status launch_pack_tiled(const float *W, int rows, int K, unsigned char *dst, bool transpose,
                             cudaStream_t st);

@@ -82,7 +82,12 @@ __global__ void ln_fwd_kernel(const float *__restrict__ X, const float *__restri
 {
     const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (r >= R) return;
+    if (r >= R) {  // padding rows of the wide copy's last row block are zero
+        if (At && r < tl_blocks(R) * 128)
+            for (int j = 2 * lane; j < D; j += 64)
+                *reinterpret_cast<__nv_bfloat162 *>(At + wl_offset(r, j, D)) = __floats2bfloat162_rn(0.f, 0.f);
+        return;
+    }
     const float *x = X + r * D;
     float s = 0.f;
     for (int j = lane; j < D; j += 32) s += x[j];
@@ -95,12 +100,11 @@ __global__ void ln_fwd_kernel(const float *__restrict__ X, const float *__restri
     const float r_s = 1.0f / sqrtf(wsum(q) / D + 1e-5f);
     if (Y)
         for (int j = lane; j < D; j += 32) Y[r * D + j] = (x[j] - mean) * r_s * g[j] + b[j];
-    if (At) {  // tiled BF16 copy, two columns per lane (D even)
-        const int64_t RB = tl_blocks(R);
+    if (At) {  // wide BF16 copy, two columns per lane (D even)
         for (int j = 2 * lane; j < D; j += 64) {
             const __nv_bfloat162 v = __floats2bfloat162_rn((x[j] - mean) * r_s * g[j] + b[j],
                                                            (x[j + 1] - mean) * r_s * g[j + 1] + b[j + 1]);
-            *reinterpret_cast<__nv_bfloat162 *>(At + tl_offset(r, j, RB)) = v;
+            *reinterpret_cast<__nv_bfloat162 *>(At + wl_offset(r, j, D)) = v;
         }
     }
     if (lane == 0 && mu) {
@@ -615,19 +619,18 @@ bool use_tc(const sg_config &c)
     return c.precision == SG_BF16 && c.d % 32 == 0 && c.d_ff % 32 == 0;
 }
 
-// out[j] += sum_r T[r][j] over a tiled BF16 matrix T(R, F)
+// out[j] += sum_r T[r][j] over a wide BF16 matrix W(R, F)
 __global__ void colsum_tiled_kernel(const unsigned char *__restrict__ T, int64_t R, int F,
                                     float *__restrict__ out, int64_t rows_per_block)
 {
     __shared__ float red[8][33];
     const int j = blockIdx.x * 32 + threadIdx.x;
-    const int64_t RB = tl_blocks(R);
     const int64_t rb0 = (int64_t)blockIdx.y * rows_per_block;
     const int64_t re = rb0 + rows_per_block < R ? rb0 + rows_per_block : R;
     float s = 0.f;
     if (j < F)
         for (int64_t r = rb0 + threadIdx.y; r < re; r += 8) {
-            const uint16_t b = *reinterpret_cast<const uint16_t *>(T + tl_offset(r, j, RB));
+            const uint16_t b = *reinterpret_cast<const uint16_t *>(T + wl_offset(r, j, F));
             s += __uint_as_float((uint32_t)b << 16);
         }
     red[threadIdx.y][threadIdx.x] = s;
@@ -661,6 +664,32 @@ __device__ __forceinline__ void stage_rows(float *dst, const float *__restrict__
         *reinterpret_cast<float4 *>(dst + t * DP + 4 * c) =
             *reinterpret_cast<const float4 *>(src + (size_t)t * stride_src + 4 * c);
     }
+}
+
+// Shared-memory row (16-byte aligned) into registers with 128-bit loads.
+template <int DH>
+__device__ __forceinline__ void row_regs(const float *row, float (&r)[DH])
+{
+#pragma unroll
+    for (int c = 0; c < DH / 4; ++c) {
+        const float4 x = *reinterpret_cast<const float4 *>(row + 4 * c);
+        r[4 * c] = x.x;
+        r[4 * c + 1] = x.y;
+        r[4 * c + 2] = x.z;
+        r[4 * c + 3] = x.w;
+    }
+}
+
+template <int DH>
+__device__ __forceinline__ float dot_regs(const float (&a)[DH], const float (&b)[DH])
+{
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+    for (int j = 0; j < DH; j += 2) {
+        s0 += a[j] * b[j];
+        s1 += a[j + 1] * b[j + 1];
+    }
+    return s0 + s1;
 }
 
 template <int DH>
@@ -801,10 +830,13 @@ attn_bwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ O,
         const int nk = n_sink + band_count(t, band_lo);
         for (int i = 0; i < nk; ++i) {
             const int k = i < n_sink ? i : band_lo + (i - n_sink);
-            const float p = __expf(dot_row<DH>(q, Ks + k * DP) - lse);
-            const float ds = p * (dot_row<DH>(g, Vs + k * DP) - dd) * scale;
+            float kr[DH], vr[DH];  // each row read once, with 128-bit loads
+            row_regs<DH>(Ks + k * DP, kr);
+            row_regs<DH>(Vs + k * DP, vr);
+            const float p = __expf(dot_regs<DH>(q, kr) - lse);
+            const float ds = p * (dot_regs<DH>(g, vr) - dd) * scale;
 #pragma unroll
-            for (int j = 0; j < DH; ++j) dq[j] += ds * Ks[k * DP + j];
+            for (int j = 0; j < DH; ++j) dq[j] += ds * kr[j];
         }
 #pragma unroll
         for (int j = 0; j < DH; ++j) Os[t * DP + j] = dq[j];  // own row
@@ -829,12 +861,15 @@ attn_bwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ O,
         }
         const int t_hi = min(N - 1, k + W);
         for (int t = k; t <= t_hi; ++t) {
-            const float p = __expf(dot_row<DH>(key, Qs + t * DP) - Ls[t]);
-            const float ds = p * (dot_row<DH>(val, Gs + t * DP) - Ds[t]) * scale;
+            float qr[DH], gr[DH];
+            row_regs<DH>(Qs + t * DP, qr);
+            row_regs<DH>(Gs + t * DP, gr);
+            const float p = __expf(dot_regs<DH>(key, qr) - Ls[t]);
+            const float ds = p * (dot_regs<DH>(val, gr) - Ds[t]) * scale;
 #pragma unroll
             for (int j = 0; j < DH; ++j) {
-                dk[j] += ds * Qs[t * DP + j];
-                dv[j] += p * Gs[t * DP + j];
+                dk[j] += ds * qr[j];
+                dv[j] += p * gr[j];
             }
         }
 #pragma unroll
@@ -852,12 +887,15 @@ attn_bwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ O,
             dk[j] = dv[j] = 0.f;
         }
         for (int t = k + lane; t < N; t += 32) {
-            const float p = __expf(dot_row<DH>(key, Qs + t * DP) - Ls[t]);
-            const float ds = p * (dot_row<DH>(val, Gs + t * DP) - Ds[t]) * scale;
+            float qr[DH], gr[DH];
+            row_regs<DH>(Qs + t * DP, qr);
+            row_regs<DH>(Gs + t * DP, gr);
+            const float p = __expf(dot_regs<DH>(key, qr) - Ls[t]);
+            const float ds = p * (dot_regs<DH>(val, gr) - Ds[t]) * scale;
 #pragma unroll
             for (int j = 0; j < DH; ++j) {
-                dk[j] += ds * Qs[t * DP + j];
-                dv[j] += p * Gs[t * DP + j];
+                dk[j] += ds * qr[j];
+                dv[j] += p * gr[j];
             }
         }
 #pragma unroll
@@ -937,8 +975,12 @@ void attn_bwd(const float *QKV, const float *O, const float *dO, const float *LS
 bool dh_supported(int dh) { return dh == 8 || dh == 16 || dh == 32; }
 
 void attn_fwd_dispatch(int dh, const float *QKV, const float *Hin, float *O, float *Hmid,
-                       float *LSE, int Bc, const sg_config &c, cudaStream_t st)
+                       float *LSE, int Bc, const sg_config &c, cudaStream_t st, int *err)
 {
+    if (attn_tc_supported(c)) {  // BF16 model: tcgen05 attention
+        launch_attn_fwd_tc(c, QKV, Hin, O, Hmid, LSE, Bc, err, st);
+        return;
+    }
     if (dh == 8) attn_fwd<8>(QKV, Hin, O, Hmid, LSE, Bc, c, st);
     else if (dh == 16) attn_fwd<16>(QKV, Hin, O, Hmid, LSE, Bc, c, st);
     else attn_fwd<32>(QKV, Hin, O, Hmid, LSE, Bc, c, st);
@@ -946,8 +988,12 @@ void attn_fwd_dispatch(int dh, const float *QKV, const float *Hin, float *O, flo
 
 void attn_bwd_dispatch(int dh, const float *QKV, const float *O, const float *dO,
                        const float *LSE, float *dQKV, float *Dt, int Bc, const sg_config &c,
-                       cudaStream_t st)
+                       cudaStream_t st, int *err)
 {
+    if (attn_tc_supported(c)) {
+        launch_attn_bwd_tc(c, QKV, O, dO, LSE, dQKV, Dt, Bc, err, st);
+        return;
+    }
     if (dh == 8) attn_bwd<8>(QKV, O, dO, LSE, dQKV, Dt, Bc, c, st);
     else if (dh == 16) attn_bwd<16>(QKV, O, dO, LSE, dQKV, Dt, Bc, c, st);
     else attn_bwd<32>(QKV, O, dO, LSE, dQKV, Dt, Bc, c, st);
@@ -994,8 +1040,8 @@ struct Work {
     std::vector<LayerBufs> layers;
     float *Hfin, *muf, *rsf, *Y, *ell, *lp, *Hping;
     float *dH, *dHmid, *dA, *dQKV, *dF1, *Dt;
-    // tensor-core backward scratch (tiled BF16; T* = transposed operands)
-    unsigned char *dHt, *dF1t, *dQKVt, *TdH, *TG, *TdF1, *TA2, *TdQKV, *TA1;
+    // tensor-core backward scratch (wide BF16)
+    unsigned char *dHt, *dF1t, *dQKVt;
     int64_t total_floats;
 };
 
@@ -1010,8 +1056,8 @@ Work carve(const sg_config &c, float *base, int64_t R, bool bwd)
         off += (n + 3) & ~int64_t(3);
         return q;
     };
-    auto take_t = [&](int64_t rows, int64_t K) {  // tiled BF16 T(rows, K)
-        return reinterpret_cast<unsigned char *>(take((int64_t)(tl_bytes(rows, (int)K) / 4)));
+    auto take_t = [&](int64_t rows, int64_t F) {  // wide BF16 W(rows, F)
+        return reinterpret_cast<unsigned char *>(take((int64_t)((wl_bytes(rows, (int)F) + 3) / 4)));
     };
     const int nl = bwd ? c.n_layers : 1;
     for (int l = 0; l < nl; ++l) {
@@ -1042,12 +1088,6 @@ Work carve(const sg_config &c, float *base, int64_t R, bool bwd)
         w.dHt = take_t(R, D);
         w.dF1t = take_t(R, F);
         w.dQKVt = take_t(R, 3 * D);
-        w.TdH = take_t(D, R);
-        w.TG = take_t(F, R);
-        w.TdF1 = take_t(F, R);
-        w.TA2 = take_t(D, R);
-        w.TdQKV = take_t(3 * D, R);
-        w.TA1 = take_t(D, R);
     }
     w.Hfin = take(R * D);
     w.Hping = take(R * D);
@@ -1105,7 +1145,7 @@ void forward_chunk(sg_model *m, const int8_t *spins, int Bc, Work &w, bool keep,
         float *Hout = keep ? (l + 1 < c.n_layers ? w.layers[l + 1].Hin : w.Hfin)
                            : (H == w.Hping ? w.Hfin : w.Hping);
         const bool tcp = use_tc(c);
-        ln_fwd_kernel<<<blocks_for(R, 8), 256, 0, ::sg::counted(st)>>>(
+        ln_fwd_kernel<<<blocks_for(tcp ? tl_blocks(R) * 128 : R, 8), 256, 0, ::sg::counted(st)>>>(
             Hin, W + o.ln1g, W + o.ln1b, tcp ? nullptr : L.A1, L.mu1, L.rs1, R, D,
             tcp ? L.A1t : nullptr);
         if (tcp) {
@@ -1113,17 +1153,17 @@ void forward_chunk(sg_model *m, const int8_t *spins, int Bc, Work &w, bool keep,
             // the tiled A operands directly
             const unsigned char *bt = (const unsigned char *)m->bt;
             RowGemm g{};
-            g.A = L.A1t; g.RB = tl_blocks(R); g.KC = (D + 63) / 64; g.R = R; g.err = (int *)m->err;
+            g.A = L.A1t; g.RB = tl_blocks(R); g.K = D; g.KC = (D + 63) / 64; g.R = R; g.err = (int *)m->err;
             g.Bw = bt + m->bt_off[l][0]; g.NBw = (int)tl_blocks(3 * D); g.N = 3 * D;
             g.bias = m->wt + m->pack.bqkv[l]; g.out_f32 = L.QKV; g.ld_out = 3 * D;
             launch_row_gemm(g, TE_STORE_F32, st);
-            attn_fwd_dispatch(dh, L.QKV, Hin, L.O, L.Hmid, L.LSE, Bc, c, st);
-            ln_fwd_kernel<<<blocks_for(R, 8), 256, 0, ::sg::counted(st)>>>(
+            attn_fwd_dispatch(dh, L.QKV, Hin, L.O, L.Hmid, L.LSE, Bc, c, st, (int *)m->err);
+            ln_fwd_kernel<<<blocks_for(tl_blocks(R) * 128, 8), 256, 0, ::sg::counted(st)>>>(
                 L.Hmid, W + o.ln2g, W + o.ln2b, nullptr, L.mu2, L.rs2, R, D, L.A2t);
             g.A = L.A2t; g.Bw = bt + m->bt_off[l][1]; g.NBw = (int)tl_blocks(F); g.N = F;
             g.bias = m->wt + m->pack.b1[l]; g.out_t = L.Gt; g.out_t2 = L.F1t;
             launch_row_gemm(g, TE_GELU_T, st);
-            g.A = L.Gt; g.KC = (F + 63) / 64; g.Bw = bt + m->bt_off[l][2]; g.NBw = (int)tl_blocks(D);
+            g.A = L.Gt; g.K = F; g.KC = (F + 63) / 64; g.Bw = bt + m->bt_off[l][2]; g.NBw = (int)tl_blocks(D);
             g.N = D; g.bias = m->wt + m->pack.b2[l]; g.out_f32 = Hout; g.ld_out = D;
             g.resid = L.Hmid; g.ld_resid = D;
             launch_row_gemm(g, TE_RESID_F32, st);
@@ -1132,7 +1172,7 @@ void forward_chunk(sg_model *m, const int8_t *spins, int Bc, Work &w, bool keep,
         }
         gemm<G_STORE>(L.A1, D, m->wt + m->pack.WqkvT[l], 3 * D, m->wt + m->pack.bqkv[l], L.QKV, 3 * D, R,
                       3 * D, D, st);
-        attn_fwd_dispatch(dh, L.QKV, Hin, L.O, L.Hmid, L.LSE, Bc, c, st);
+        attn_fwd_dispatch(dh, L.QKV, Hin, L.O, L.Hmid, L.LSE, Bc, c, st, (int *)m->err);
         ln_fwd_kernel<<<blocks_for(R, 8), 256, 0, ::sg::counted(st)>>>(L.Hmid, W + o.ln2g, W + o.ln2b, L.A2,
                                                         L.mu2, L.rs2, R, D);
         if (keep)
@@ -1236,53 +1276,49 @@ sg_status launch_grad_f32(sg_model *m, const int8_t *spins, const float *coeff, 
             grad + O.Wh, grad + O.bh, grad + O.lnfg, grad + O.lnfb, R, c.N, D, 256);
         for (int l = c.n_layers - 1; l >= 0 && use_tc(c); --l) {
             // tensor-core backward: dX GEMMs by row_gemm, weight gradients by
-            // split-K wgrad over tiled (transposed) BF16 operands
+            // split wgrad reading the wide BF16 activations MN-major
             LayerBufs &L = w.layers[l];
             const LayerOff &o = O.L[l];
             const unsigned char *bt = (const unsigned char *)m->bt;
-            const int64_t RB = tl_blocks(R), KCr = (R + 63) / 64;
-            auto wgrad = [&](const unsigned char *A, int M, const unsigned char *Bm, int N, float *C) {
+            const int64_t RB = tl_blocks(R);
+            // C (+)= A^T B over the rows; A has the wider feature count
+            auto wgrad = [&](const unsigned char *A, int M, const unsigned char *Bm, int N, float *C,
+                             int ldc, bool transpose_out) {
                 WgradGemm g{};
-                g.A = A; g.MB = tl_blocks(M); g.Bm = Bm; g.NB = (int)tl_blocks(N); g.N = N; g.M = M;
-                g.KCtot = KCr;
-                const int64_t splits = std::max<int64_t>(1, 304 / (g.MB * ((N + 255) / 256)));
-                g.kc_per_cta = (KCr + splits - 1) / splits;
-                g.C = C; g.err = (int *)m->err;
+                g.A = A; g.M = M; g.Bm = Bm; g.N = N; g.RB = RB;
+                const int64_t per_split = (int64_t)((M + 127) / 128) * ((N + 255) / 256);
+                const int64_t splits = std::max<int64_t>(1, std::min<int64_t>(RB, 304 / per_split));
+                g.rb_per_cta = (RB + splits - 1) / splits;
+                g.C = C; g.ldc = ldc; g.transpose_out = transpose_out ? 1 : 0; g.err = (int *)m->err;
                 launch_wgrad_gemm(g, st);
             };
             RowGemm g{};
             g.RB = RB; g.R = R; g.err = (int *)m->err;
             // FFN: H = Hmid + W2 G + b2, G = gelu(F1), F1 = W1 A2 + b1
-            launch_to_tiled(w.dH, R, D, D, w.dHt, false, st);
-            launch_to_tiled(w.dH, R, D, D, w.TdH, true, st);
-            g.A = w.dHt; g.KC = (D + 63) / 64; g.Bw = bt + m->bt_off[l][3]; g.NBw = (int)tl_blocks(F);
-            g.N = F; g.aux_t = L.F1t; g.out_t = w.dF1t;
+            launch_to_wide(w.dH, R, D, w.dHt, st);
+            g.A = w.dHt; g.K = D; g.KC = (D + 63) / 64; g.Bw = bt + m->bt_off[l][3];
+            g.NBw = (int)tl_blocks(F); g.N = F; g.aux_t = L.F1t; g.out_t = w.dF1t;
             launch_row_gemm(g, TE_GELU_BWD_T, st);
-            launch_tiled_transpose(L.Gt, R, F, w.TG, st);
-            wgrad(w.TdH, D, w.TG, F, grad + o.W2);
+            wgrad(L.Gt, F, w.dHt, D, grad + o.W2, F, true);        // dW2[d][f] = sum dH[d] G[f]
             colsum(w.dH, D, R, D, grad + o.b2, st);
-            launch_tiled_transpose(w.dF1t, R, F, w.TdF1, st);
-            launch_tiled_transpose(L.A2t, R, D, w.TA2, st);
-            wgrad(w.TdF1, F, w.TA2, D, grad + o.W1);
+            wgrad(w.dF1t, F, L.A2t, D, grad + o.W1, D, false);     // dW1[f][d] = sum dF1[f] A2[d]
             {
                 const int64_t rpb = 4096;
                 dim3 grid((F + 31) / 32, (unsigned)((R + rpb - 1) / rpb)), block(32, 8);
                 colsum_tiled_kernel<<<grid, block, 0, ::sg::counted(st)>>>(w.dF1t, R, F, grad + o.b1, rpb);
             }
-            g.A = w.dF1t; g.KC = (F + 63) / 64; g.Bw = bt + m->bt_off[l][4]; g.NBw = (int)tl_blocks(D);
-            g.N = D; g.out_f32 = w.dA; g.ld_out = D;
+            g.A = w.dF1t; g.K = F; g.KC = (F + 63) / 64; g.Bw = bt + m->bt_off[l][4];
+            g.NBw = (int)tl_blocks(D); g.N = D; g.out_f32 = w.dA; g.ld_out = D;
             launch_row_gemm(g, TE_STORE_F32, st);
             cudaMemcpyAsync(w.dHmid, w.dH, (size_t)R * D * sizeof(float), cudaMemcpyDeviceToDevice, st);
             ln_bwd(w.dA, L.Hmid, L.mu2, L.rs2, W + o.ln2g, w.dHmid, 1, grad + o.ln2g, grad + o.ln2b,
                    R, D, st);
             // attention: Hmid = Hin + O(QKV)
-            attn_bwd_dispatch(dh, L.QKV, L.O, w.dHmid, L.LSE, w.dQKV, w.Dt, Bc, c, st);
-            launch_to_tiled(w.dQKV, R, 3 * D, 3 * D, w.dQKVt, false, st);
-            launch_to_tiled(w.dQKV, R, 3 * D, 3 * D, w.TdQKV, true, st);
-            launch_tiled_transpose(L.A1t, R, D, w.TA1, st);
-            wgrad(w.TdQKV, 3 * D, w.TA1, D, grad + o.Wqkv);
+            attn_bwd_dispatch(dh, L.QKV, L.O, w.dHmid, L.LSE, w.dQKV, w.Dt, Bc, c, st, (int *)m->err);
+            launch_to_wide(w.dQKV, R, 3 * D, w.dQKVt, st);
+            wgrad(w.dQKVt, 3 * D, L.A1t, D, grad + o.Wqkv, D, false);  // dWqkv[j][d] = sum dQKV[j] A1[d]
             colsum(w.dQKV, 3 * D, R, 3 * D, grad + o.bqkv, st);
-            g.A = w.dQKVt; g.KC = (3 * D + 63) / 64; g.Bw = bt + m->bt_off[l][5];
+            g.A = w.dQKVt; g.K = 3 * D; g.KC = (3 * D + 63) / 64; g.Bw = bt + m->bt_off[l][5];
             g.NBw = (int)tl_blocks(D); g.N = D; g.out_f32 = w.dA; g.ld_out = D;
             launch_row_gemm(g, TE_STORE_F32, st);
             cudaMemcpyAsync(w.dH, w.dHmid, (size_t)R * D * sizeof(float), cudaMemcpyDeviceToDevice, st);
@@ -1304,7 +1340,7 @@ sg_status launch_grad_f32(sg_model *m, const int8_t *spins, const float *coeff, 
             ln_bwd(w.dA, L.Hmid, L.mu2, L.rs2, W + o.ln2g, w.dHmid, 1, grad + o.ln2g,
                    grad + o.ln2b, R, D, st);
             // attention: Hmid = Hin + O(QKV)
-            attn_bwd_dispatch(dh, L.QKV, L.O, w.dHmid, L.LSE, w.dQKV, w.Dt, Bc, c, st);
+            attn_bwd_dispatch(dh, L.QKV, L.O, w.dHmid, L.LSE, w.dQKV, w.Dt, Bc, c, st, (int *)m->err);
             gemm_tn_acc(w.dQKV, 3 * D, L.A1, D, grad + o.Wqkv, R, 3 * D, D, st);
             colsum(w.dQKV, 3 * D, R, 3 * D, grad + o.bqkv, st);
             gemm<G_STORE>(w.dQKV, 3 * D, m->wt + m->pack.Wqkv[l], D, nullptr, w.dA, D, R, D, 3 * D, st);

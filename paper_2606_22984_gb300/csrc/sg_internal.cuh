@@ -221,6 +221,12 @@ sg_status launch_metropolis(const sg_instance *inst, int8_t *spins, int64_t R, i
                             double beta, uint64_t seed, double *E, float *trace,
                             cudaStream_t st);
 sg_status launch_overlap(const int8_t *spins, int64_t B, int N, int64_t *hist, cudaStream_t st);
+bool attn_tc_supported(const sg_config &c);
+sg_status launch_attn_fwd_tc(const sg_config &c, const float *QKV, const float *Hin, float *O,
+                             float *Hmid, float *LSE, int Bc, int *err, cudaStream_t st);
+sg_status launch_attn_bwd_tc(const sg_config &c, const float *QKV, const float *O, const float *dO,
+                             const float *LSE, float *dQKV, float *Dt, int Bc, int *err,
+                             cudaStream_t st);
 sg_status launch_adam(float *w, const float *g, float *m, float *v, int64_t n, float lr,
                       float b1, float b2, float eps, int64_t step, cudaStream_t st);
 }  // namespace sg

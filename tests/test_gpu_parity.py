@@ -353,7 +353,13 @@ BF16_TF_MODELS = [inputs.ModelShape(20, 2, 32, 4), inputs.ModelShape(40, 2, 64, 
                   # weights beyond 256 x 256: column-blocked tile GEMM, split wgrad
                   inputs.ModelShape(24, 2, 128, 8),
                   inputs.ModelShape(30, 1, 96, 6, mask_kind=1, W=5, S=4),
-                  inputs.ModelShape(20, 1, 256, 8, mask_kind=1, W=6, S=3)]
+                  inputs.ModelShape(20, 1, 256, 8, mask_kind=1, W=6, S=3),
+                  # attention on the tensor cores (a query sees >= 64 keys):
+                  # dense over two query tiles with a ragged tail, a band
+                  # crossing tile edges with its sink, d_h = 32
+                  inputs.ModelShape(160, 2, 64, 4),
+                  inputs.ModelShape(300, 1, 64, 4, mask_kind=1, W=70, S=9),
+                  inputs.ModelShape(140, 1, 256, 8)]
 
 
 @pytest.mark.parametrize("m", BF16_TF_MODELS)
