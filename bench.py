@@ -240,7 +240,7 @@ def run_ours(args):
     import torch.distributed as dist
 
     from paper_2606_22984_gb300 import build as _build
-    from paper_2606_22984_gb300 import inputs, sg
+    from paper_2606_22984_gb300 import inputs, replicas, sg
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -287,7 +287,7 @@ def run_ours(args):
     ev = []
 
     def step(model, inst, bufs, i, timed):
-        seed = (rank << 32) + 1000 + i
+        seed = replicas.replica_seed(rank, i)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -329,18 +329,15 @@ def run_ours(args):
             t1.record(stream)
             torch.cuda.synchronize()
         launches = sg.launch_count() - n0
-        ms = t0.elapsed_time(t1)
+        ms = replicas.max_over_ranks(t0.elapsed_time(t1), dist, dev)
         if world > 1:
-            x = torch.tensor([ms], device=dev)
-            dist.all_reduce(x, op=dist.ReduceOp.MAX)
-            ms = float(x.item())
             dist.barrier()
         dec_ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
         return model, inst, bufs, ms, dec_ms, launches, sampler.summary()
 
     model, inst, bufs, ms, dec_ms, launches, clocks = timed_run(prec, True)
     ms_step = ms / args.steps
-    value = B * world * args.steps / (ms / 1e3)
+    value = replicas.whole_job_throughput(B, world, args.steps, ms / 1e3)
 
     # end to end through the public API with host buffers: each step copies a
     # control block (seed, beta) host -> device and reads the sampled
@@ -364,12 +361,9 @@ def run_ours(args):
         h_E.copy_(bufs["E"], non_blocking=True)
         h_F.copy_(bufs["F"], non_blocking=True)
         torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        x = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(x, op=dist.ReduceOp.MAX)
-        e2e_s = float(x.item())
-    e2e = {"value": B * world * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16,
+    e2e_s = replicas.max_over_ranks(time.perf_counter() - t0, dist, dev)
+    e2e = {"value": replicas.whole_job_throughput(B, world, args.steps, e2e_s), "unit": UNIT,
+           "h2d_bytes_per_step": 16,
            "d2h_bytes_per_step": int(B * m.N + 8 * B + 24)}
 
     elem = 2 if prec == sg.SG_BF16 else 4
@@ -401,7 +395,7 @@ def run_ours(args):
         F32 = bufs32["F"].cpu().numpy()
         alg32 = decode_bytes_per_sample(m, 4) * B
         line["fp32_plain"] = {
-            "value": B * world * args.steps / (ms32 / 1e3), "unit": UNIT,
+            "value": replicas.whole_job_throughput(B, world, args.steps, ms32 / 1e3), "unit": UNIT,
             "ms_per_step": ms32 / args.steps, "decode_ms": dec32,
             "decode_roofline_frac": alg32 / (dec32 / 1e3) / 1e9 / peak,
             "F_IS_per_spin_last_step": F32[1] / m.N}
