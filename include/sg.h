@@ -237,6 +237,25 @@ sg_status sg_free_energy(const float *E, const float *logq, int64_t B, double be
                          float *coeff, sg_stream stream);
 
 /*
+ * REINFORCE weights of a general per-sample loss, reduced in FP64 on the
+ * device:  L_b = a E_b + c ln q_b,  coeff_b = (L_b - mean L - w) / B,
+ * so that sg_grad with these weights gives (1/B) sum_b (L_b - mean L) grad ln q
+ * - (w/B) sum_b grad ln q.  The cases:
+ *   (a, c, w) = (beta, 1, 0)  Eq. loss1, the free energy F_q;
+ *   (a, c, w) = (1, T, 0)     the ground-state form of Methods "Variational
+ *                             annealing", L = E + T ln q, which stays
+ *                             bounded as T -> 0;
+ *   w > 0                     Eq. loss2, the likelihood (self-distillation)
+ *                             term on configurations refined by local Monte
+ *                             Carlo before scoring.
+ *   E, logq dev float [B]; coeff dev float [B] out;
+ *   mean    dev double [2] out or NULL: mean L, mean E.
+ * Errors: SG_EINVAL on NULL inputs, B < 1 or non-finite a, c, w.
+ */
+sg_status sg_loss_coeff(const float *E, const float *logq, int64_t B, double a, double c,
+                        double w, double *mean, float *coeff, sg_stream stream);
+
+/*
  * Independence Metropolis-Hastings with the model as proposal (the paper's
  * Monte Carlo + generative-model combination; not an algorithm it prints).
  * Chain c (of C, B % C == 0) consumes proposals p = j*C + c, j = 0..B/C-1,

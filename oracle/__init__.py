@@ -94,6 +94,7 @@ def lib():
         L.or_energy_sk.argtypes = [_I, _P, _I64, _P, _P]
         L.or_energy_ea.argtypes = [_I, _I, _I, _P, _I64, _P, _P]
         L.or_free_energy.argtypes = [_I64, _P, _P, _D, _P]
+        L.or_loss_coeff.argtypes = [_I64, _P, _P, _D, _D, _D, _P, _P]
         L.or_enumerate.argtypes = [ctypes.POINTER(OrCfg), _P, _I, _I, _I, _I, _P, _D, _P, _I]
         L.or_mh.argtypes = [_I64, _I, _P, _P, _D, _U64, _D, _P, _P, _P, _P, _P, _P, _P]
         L.or_metropolis.argtypes = [_I, _I, _I, _I, _I, _P, _I64, _I, _D, _U64, _P, _P, _P, _P]
@@ -220,6 +221,17 @@ def free_energy(E, logq, beta):
     out = np.zeros(3, np.float64)
     lib().or_free_energy(E.shape[0], _ptr(E), _ptr(lq), beta, _ptr(out))
     return float(out[0]), float(out[1]), float(out[2])
+
+
+def loss_coeff(E, logq, a, c, w=0.0):
+    """REINFORCE weights (a E + c ln q - mean - w) / B of Eqs. loss1 / loss2;
+    returns (coeff, mean L, mean E)."""
+    E = _f64(E)
+    lq = _f64(logq)
+    coeff = np.zeros(E.shape[0], np.float64)
+    mean = np.zeros(2, np.float64)
+    lib().or_loss_coeff(E.shape[0], _ptr(E), _ptr(lq), a, c, w, _ptr(mean), _ptr(coeff))
+    return coeff, float(mean[0]), float(mean[1])
 
 
 def enumerate_exact(cfg: ModelCfg, weights, inst, beta, n_threads=0):

@@ -765,6 +765,28 @@ void or_free_energy(int64_t B, const double *E, const double *logq, double beta,
 }
 
 /* ------------------------------------------------------------------------ */
+/* REINFORCE weights of a per-sample loss L_b = a E_b + c ln q_b (Eq. loss1  */
+/* with (a, c) = (beta, 1); the ground-state form L = E + T ln q of Methods  */
+/* "Variational annealing" with (1, T)) and the likelihood term of Eq. loss2 */
+/* with weight w:  the gradient (1/B) sum (L - mean L) grad ln q - (w/B) sum */
+/* grad ln q is sum_b coeff_b grad ln q_b with coeff_b = (L_b - mean L - w)/B. */
+/* mean_out = {mean L, mean E}.                                              */
+/* ------------------------------------------------------------------------ */
+void or_loss_coeff(int64_t B, const double *E, const double *logq, double a, double c, double w,
+                   double *mean_out, double *coeff)
+{
+    long double sumL = 0.0L, sumE = 0.0L;
+    for (int64_t b = 0; b < B; ++b) {
+        sumL += a * E[b] + c * logq[b];
+        sumE += E[b];
+    }
+    const double meanL = (double)(sumL / B);
+    mean_out[0] = meanL;
+    mean_out[1] = (double)(sumE / B);
+    for (int64_t b = 0; b < B; ++b) coeff[b] = (a * E[b] + c * logq[b] - meanL - w) / (double)B;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Exhaustive enumeration over all 2^N configurations by a prefix-tree walk: */
 /* each tree node costs one decode step (Algorithm 2) and its two children   */
 /* reuse its KV cache.  Gives sum_sigma q (=1 by construction, Sec.          */

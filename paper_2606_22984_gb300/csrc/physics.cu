@@ -183,6 +183,29 @@ free_energy_kernel(const float *__restrict__ E, const float *__restrict__ lq, in
         }
 }
 
+// REINFORCE weights of L_b = a E_b + c ln q_b with the likelihood term w:
+// coeff_b = (L_b - mean L - w) / B, one block, FP64 sums.
+__global__ void __launch_bounds__(1024)
+loss_coeff_kernel(const float *__restrict__ E, const float *__restrict__ lq, int64_t B, double a,
+                  double c, double w, double *__restrict__ mean, float *__restrict__ coeff)
+{
+    __shared__ double sh[1024];
+    double sl = 0.0, se = 0.0;
+    for (int64_t b = threadIdx.x; b < B; b += blockDim.x) {
+        sl += a * (double)E[b] + c * (double)lq[b];
+        se += (double)E[b];
+    }
+    sl = block_reduce(sl, sh, false);
+    se = block_reduce(se, sh, false);
+    const double ml = sl / (double)B;
+    if (threadIdx.x == 0 && mean) {
+        mean[0] = ml;
+        mean[1] = se / (double)B;
+    }
+    for (int64_t b = threadIdx.x; b < B; b += blockDim.x)
+        coeff[b] = (float)((a * (double)E[b] + c * (double)lq[b] - ml - w) / (double)B);
+}
+
 // ---------------------------------------------------------------------------
 // Independence MH: one thread per chain, proposals consumed in order.  The
 // log-acceptance is formed in FP64 with explicitly rounded operations (no
@@ -356,6 +379,13 @@ sg_status launch_free_energy(const float *E, const float *logq, int64_t B, doubl
 {
     free_energy_kernel<<<1, 1024, 0, ::sg::counted(st)>>>(E, logq, B, beta, out, coeff);
     return check_launch("free_energy_kernel");
+}
+
+sg_status launch_loss_coeff(const float *E, const float *logq, int64_t B, double a, double c,
+                            double w, double *mean, float *coeff, cudaStream_t st)
+{
+    loss_coeff_kernel<<<1, 1024, 0, ::sg::counted(st)>>>(E, logq, B, a, c, w, mean, coeff);
+    return check_launch("loss_coeff_kernel");
 }
 
 sg_status launch_mh(const int8_t *prop, const float *E, const float *logq, int64_t B, int N,

@@ -360,6 +360,16 @@ sg_status sg_free_energy(const float *E, const float *logq, int64_t B, double be
     return launch_free_energy(E, logq, B, beta, out, coeff, (cudaStream_t)stream);
 }
 
+sg_status sg_loss_coeff(const float *E, const float *logq, int64_t B, double a, double c,
+                        double w, double *mean, float *coeff, sg_stream stream)
+{
+    if (!E || !logq || !coeff) return fail(SG_EINVAL, "NULL pointer");
+    if (B < 1) return fail(SG_EINVAL, "B must be >= 1");
+    if (!std::isfinite(a) || !std::isfinite(c) || !std::isfinite(w))
+        return fail(SG_EINVAL, "a, c and w must be finite");
+    return launch_loss_coeff(E, logq, B, a, c, w, mean, coeff, (cudaStream_t)stream);
+}
+
 sg_status sg_mh_step(const int8_t *prop_spins, const float *E, const float *logq, int64_t B,
                      int32_t N, int32_t C, double beta, uint64_t seed, int8_t *chain_spins,
                      double *chain_E, double *chain_lq, int64_t *accepts, float *trace_E,

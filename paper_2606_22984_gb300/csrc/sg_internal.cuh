@@ -214,6 +214,8 @@ sg_status launch_energy(const sg_instance *inst, const int8_t *spins, int64_t B,
                         float *E, int32_t *E_int, cudaStream_t st);
 sg_status launch_free_energy(const float *E, const float *logq, int64_t B, double beta,
                              double *out, float *coeff, cudaStream_t st);
+sg_status launch_loss_coeff(const float *E, const float *logq, int64_t B, double a, double c,
+                            double w, double *mean, float *coeff, cudaStream_t st);
 sg_status launch_mh(const int8_t *prop, const float *E, const float *logq, int64_t B, int N,
                     int C, double beta, uint64_t seed, int8_t *cs, double *cE, double *cL,
                     int64_t *acc, float *trace, cudaStream_t st);

@@ -54,6 +54,7 @@ _SIGS = {
     "sg_instance_destroy": ([_P], _I32),
     "sg_energy": ([_P, _P, _I64, _I32, _P, _P, _P], _I32),
     "sg_free_energy": ([_P, _P, _I64, _D, _P, _P, _P], _I32),
+    "sg_loss_coeff": ([_P, _P, _I64, _D, _D, _D, _P, _P, _P], _I32),
     "sg_mh_step": ([_P, _P, _P, _I64, _I32, _I32, _D, _U64, _P, _P, _P, _P, _P, _P], _I32),
     "sg_metropolis": ([_P, _P, _I64, _I32, _D, _U64, _P, _P, _P], _I32),
     "sg_overlap_hist": ([_P, _I64, _I32, _P, _P], _I32),
@@ -262,6 +263,17 @@ def free_energy(E, logq, beta, out=None, coeff=None, want_coeff=False, stream=No
         _dev(E, torch.float32, (B,)), _dev(logq, torch.float32, (B,)), B, beta,
         _dev(out, torch.float64, (3,)), _dev(coeff, torch.float32, (B,)), _stream(stream)))
     return (out, coeff) if want_coeff else out
+
+
+def loss_coeff(E, logq, a, c, w=0.0, coeff=None, mean=None, stream=None):
+    """REINFORCE weights (a E + c ln q - mean - w) / B; returns (coeff, mean[2])."""
+    B = E.shape[0]
+    coeff = torch.empty(B, dtype=torch.float32, device=E.device) if coeff is None else coeff
+    mean = torch.empty(2, dtype=torch.float64, device=E.device) if mean is None else mean
+    _check("sg_loss_coeff", lib().sg_loss_coeff(
+        _dev(E, torch.float32, (B,)), _dev(logq, torch.float32, (B,)), B, a, c, w,
+        _dev(mean, torch.float64, (2,)), _dev(coeff, torch.float32, (B,)), _stream(stream)))
+    return coeff, mean
 
 
 def mh_step(prop_spins, E, logq, C, beta, seed, chain_spins, chain_E, chain_lq, accepts=None,

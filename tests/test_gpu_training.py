@@ -59,3 +59,69 @@ def test_sk20_training_reaches_exact_free_energy(precision):
     assert abs(out[1] - ex["F"]) / N <= 1e-3
     # the batch estimate of F_q agrees with the exact F_q of the trained model
     assert abs(out[0] - ex["Fq"]) / N <= 2e-3
+
+
+def test_loss_coeff_matches_oracle():
+    rng = np.random.default_rng(4)
+    B = 5000
+    E = rng.normal(-10, 3, B).astype(np.float32)
+    lq = (-np.abs(rng.normal(12, 2, B))).astype(np.float32)
+    for a, c, w in ((1.3, 1.0, 0.0), (1.0, 0.25, 0.0), (1.0, 0.1, 0.3), (0.0, 0.0, 1.0)):
+        co, mean = sg.loss_coeff(torch.tensor(E, device="cuda"), torch.tensor(lq, device="cuda"), a, c, w)
+        ref, mL, mE = oracle.loss_coeff(E, lq, a, c, w)
+        assert np.allclose(co.cpu().numpy(), ref, rtol=1e-5, atol=1e-9)
+        mv = mean.cpu().numpy()
+        assert abs(mv[0] - mL) < 1e-9 * max(1.0, abs(mL)) and abs(mv[1] - mE) < 1e-9 * max(1.0, abs(mE))
+    with pytest.raises(sg.SgError):
+        sg.loss_coeff(torch.tensor(E, device="cuda"), torch.tensor(lq, device="cuda"), float("nan"), 1.0)
+
+
+def test_annealing_reaches_the_sk20_ground_state():
+    """Methods "Variational annealing": training on L = E + T ln q while T is
+    lowered to 0 concentrates q on the ground state of SK N=20, whose energy
+    the oracle finds by enumerating all 2^20 states."""
+    from paper_2606_22984_gb300.train import TrainConfig, Trainer, anneal_temperature
+    wl = inputs.workloads()["sk20"]
+    m, inst = wl.model, wl.instance()
+    model = sg.Model(m, inputs.make_weights(m, 2), sg.SG_FP32)
+    gi = sg.Instance(inst)
+    sched = lambda i: anneal_temperature(i, 1.0, 100, 20, 15)
+    tr = Trainer(model, gi, TrainConfig(B=2048, steps=401, lr=3e-3, schedule=sched, log_every=100))
+    log = tr.run()
+    assert log.T[-1] == 0.0
+    ex = oracle.enumerate_exact(ocfg(m), model.weights().cpu().numpy().astype(np.float64), inst, 1.0)
+    spins, _ = model.sample(8192, seed=77)
+    E = gi.energy(spins).cpu().numpy()
+    print(f"E_min exact {ex['Emin']:.4f}  sampled min {E.min():.4f}  mean {E.mean():.4f}")
+    assert abs(E.min() - ex["Emin"]) < 1e-3
+    assert E.mean() < 0.9 * ex["Emin"]
+
+
+def test_lmc_refinement_with_self_distillation_trains_toward_ground_state():
+    """Eq. loss2: samples refined by local Monte Carlo before scoring, plus the
+    likelihood term w, on a 2D EA L=4 +-J instance (N=16, band + sink mask);
+    the refinement lowers the batch energy at low T, and the annealed training
+    reaches the exact ground state (enumeration of 2^16 states)."""
+    from paper_2606_22984_gb300.train import TrainConfig, Trainer, anneal_temperature
+    inst = inputs.make_ea(2, 4, 9, pm=True)
+    W, S = inputs.lattice_mask(2, 4)
+    m = inputs.ModelShape(16, 2, 64, 4, mask_kind=1, W=W, S=S)
+    model = sg.Model(m, inputs.make_weights(m, 3), sg.SG_BF16)
+    gi = sg.Instance(inst)
+    # one refinement at low temperature lowers the mean energy of raw samples
+    spins, _ = model.sample(4096, seed=5)
+    E0 = gi.energy(spins).cpu().numpy().mean()
+    gi.metropolis(spins, 2, 1.0 / 0.2, 6)
+    E1 = gi.energy(spins).cpu().numpy().mean()
+    assert E1 < E0
+    sched = lambda i: anneal_temperature(i, 1.5, 80, 20, 10)
+    cfg = TrainConfig(B=1024, steps=300, lr=3e-3, schedule=sched, lmc_sweeps=2, w=0.05,
+                      log_every=100)
+    log = Trainer(model, gi, cfg).run()
+    ex = oracle.enumerate_exact(ocfg(m), model.weights().cpu().numpy().astype(np.float64), inst, 1.0)
+    spins, _ = model.sample(8192, seed=78)
+    E = gi.energy(spins).cpu().numpy()
+    print(f"E_min exact {ex['Emin']:.1f}  sampled min {E.min():.1f}  mean {E.mean():.2f}  "
+          f"log mean_E {log.mean_E}")
+    assert abs(E.min() - ex["Emin"]) < 1e-3
+    assert E.mean() < 0.8 * ex["Emin"]

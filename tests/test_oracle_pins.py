@@ -427,3 +427,70 @@ def test_overlap_histogram():
     h = oracle.overlap_hist(pairs)
     q = (np.arange(17) * 2 - 16) / 16
     assert h.sum() == 1000 and abs((h * q).sum() / 1000) < 0.05
+
+
+# --------------------------------------------------------------------------
+# Loss weights of Eq. loss1 / loss2 and the ground-state form (Methods)
+# --------------------------------------------------------------------------
+
+def test_ground_state_form_weights_estimate_exact_gradient():
+    """L = E + T ln q (Methods "Variational annealing"): the REINFORCE estimate
+    with the oracle's weights matches sum_sigma q grad ln q (E + T ln q) by
+    enumeration, and the likelihood term (w > 0) adds a zero-mean term under q."""
+    N, T = 8, 0.7
+    m = inputs.ModelShape(N, 1, 8, 2, d_ff=16)
+    w = inputs.make_weights(m, 4)
+    inst = inputs.make_sk(N, 5)
+    states = all_states(N)
+    lq = oracle.logprob(ocfg(m), w, states)
+    E = oracle.energy(inst, states)
+    exact, _ = oracle.grad(ocfg(m), w, states, np.exp(lq) * (E + T * lq))
+    K, M = 12, 3000
+    ests = []
+    for k in range(K):
+        s, lqs, _, _ = oracle.sample(ocfg(m), w, M, seed=300 + k)
+        coeff, mL, mE = oracle.loss_coeff(oracle.energy(inst, s), lqs, 1.0, T, 0.5)
+        assert abs(coeff.sum() + 0.5) < 1e-12          # sum of the weights is -w
+        assert abs(mE - oracle.energy(inst, s).mean()) < 1e-12
+        g, _ = oracle.grad(ocfg(m), w, s, coeff)
+        ests.append(g)
+    ests = np.array(ests)
+    mean, se = ests.mean(0), ests.std(0, ddof=1) / math.sqrt(K)
+    big = np.abs(exact) > 1e-8
+    z = np.abs(mean - exact)[big] / np.maximum(se[big], 1e-12)
+    assert np.mean(z < 4) > 0.97
+    assert np.linalg.norm(mean - exact) < 0.15 * np.linalg.norm(exact)
+
+
+def test_loss_weights_scale_and_shift():
+    """The ground-state weights at temperature T are T times the free-energy
+    weights at beta = 1/T; a constant energy shift leaves the weights unchanged."""
+    rng = np.random.default_rng(3)
+    E = rng.normal(0, 5, 257)
+    lq = -np.abs(rng.normal(10, 2, 257))
+    T = 0.37
+    c_gs, _, _ = oracle.loss_coeff(E, lq, 1.0, T, 0.0)
+    c_fe, _, _ = oracle.loss_coeff(E, lq, 1.0 / T, 1.0, 0.0)
+    assert np.allclose(c_gs, T * c_fe, rtol=1e-12, atol=1e-15)
+    c_sh, _, _ = oracle.loss_coeff(E + 123.0, lq, 1.0, T, 0.2)
+    c_0, _, _ = oracle.loss_coeff(E, lq, 1.0, T, 0.2)
+    assert np.allclose(c_sh, c_0, rtol=1e-9, atol=1e-12)
+
+
+def test_likelihood_term_ascends_the_batch_log_likelihood():
+    """Eq. loss2's extra term alone (a = c = 0, w = 1): the weights -1/B make
+    sg_grad's sum equal minus the gradient of the mean log-likelihood of the
+    batch, checked against central finite differences of the oracle's log q."""
+    m = inputs.ModelShape(6, 1, 8, 2, d_ff=16)
+    w = inputs.make_weights(m, 6)
+    s = inputs.random_spins(5, m.N, 7)
+    coeff, _, _ = oracle.loss_coeff(np.zeros(5), np.zeros(5), 0.0, 0.0, 1.0)
+    g, _ = oracle.grad(ocfg(m), w, s, coeff)
+    rng = np.random.default_rng(1)
+    for idx in rng.choice(w.size, 12, replace=False):
+        h = 1e-6
+        wp, wm = w.astype(np.float64).copy(), w.astype(np.float64).copy()
+        wp[idx] += h
+        wm[idx] -= h
+        fd = (oracle.logprob(ocfg(m), wp, s).mean() - oracle.logprob(ocfg(m), wm, s).mean()) / (2 * h)
+        assert abs(g[idx] + fd) < 1e-6 + 1e-5 * abs(fd)
