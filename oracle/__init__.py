@@ -75,6 +75,7 @@ _I64 = ctypes.c_int64
 _D = ctypes.c_double
 _U64 = ctypes.c_uint64
 _U32 = ctypes.c_uint32
+_I32 = ctypes.c_int32
 _I = ctypes.c_int
 
 
@@ -95,6 +96,8 @@ def lib():
         L.or_energy_ea.argtypes = [_I, _I, _I, _P, _I64, _P, _P]
         L.or_free_energy.argtypes = [_I64, _P, _P, _D, _P]
         L.or_loss_coeff.argtypes = [_I64, _P, _P, _D, _D, _D, _P, _P]
+        L.or_newton_schulz.argtypes = [_P, _I32, _I32, _I32, _P]
+        L.or_muon_step.argtypes = [_P, _P, _P, _P, _P, _P, _D, _D, _D, _I32, _I64]
         L.or_enumerate.argtypes = [ctypes.POINTER(OrCfg), _P, _I, _I, _I, _I, _P, _D, _P, _I]
         L.or_mh.argtypes = [_I64, _I, _P, _P, _D, _U64, _D, _P, _P, _P, _P, _P, _P, _P]
         L.or_metropolis.argtypes = [_I, _I, _I, _I, _I, _P, _I64, _I, _D, _U64, _P, _P, _P, _P]
@@ -232,6 +235,24 @@ def loss_coeff(E, logq, a, c, w=0.0):
     mean = np.zeros(2, np.float64)
     lib().or_loss_coeff(E.shape[0], _ptr(E), _ptr(lq), a, c, w, _ptr(mean), _ptr(coeff))
     return coeff, float(mean[0]), float(mean[1])
+
+
+def newton_schulz(M, steps=5):
+    """The quintic Newton-Schulz orthogonalisation of Muon (FP64)."""
+    M = _f64(M)
+    O = np.zeros_like(M)
+    lib().or_newton_schulz(_ptr(M), M.shape[0], M.shape[1], steps, _ptr(O))
+    return O
+
+
+def muon_step(cfg: ModelCfg, w, g, mom, am, av, lr, mu, wd, ns_steps, step):
+    """One Muon step on the blob (matrices) with AdamW on the rest; arrays
+    updated in place (float64)."""
+    for a in (w, mom, am, av):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    g = _f64(g)
+    lib().or_muon_step(ctypes.byref(cfg.c()), _ptr(w), _ptr(g), _ptr(mom), _ptr(am), _ptr(av), lr, mu,
+                       wd, ns_steps, step)
 
 
 def enumerate_exact(cfg: ModelCfg, weights, inst, beta, n_threads=0):

@@ -787,6 +787,108 @@ void or_loss_coeff(int64_t B, const double *E, const double *logq, double a, dou
 }
 
 /* ------------------------------------------------------------------------ */
+/* Muon (Methods "Comparison on optimizers"): for each weight matrix         */
+/* (Wqkv, W1, W2 of every layer) with gradient G: M = mu M + G; O = k        */
+/* quintic Newton-Schulz steps on X = M / (|M|_F + 1e-7), taken on M^T when  */
+/* it has more rows than columns: X <- a X + (b A + c A A) X, A = X X^T,     */
+/* (a, b, c) = (3.4445, -4.7750, 2.0315) (Jordan et al. 2024); then          */
+/* W -= lr (s O + wd W) with the RMS alignment s = 0.2 sqrt(max(r, c)) and   */
+/* decoupled weight decay (Liu et al. 2025).  Every other parameter takes an */
+/* AdamW step (beta1 0.9, beta2 0.999, eps 1e-8, same lr and wd).            */
+/* ------------------------------------------------------------------------ */
+static void ns_orthogonalise(const double *M, int rows, int cols, int steps, double *O)
+{
+    const int tr = rows > cols;
+    const int p = tr ? cols : rows, q = tr ? rows : cols;  /* X is p x q, p <= q */
+    double *X = (double *)malloc((size_t)p * q * sizeof(double));
+    double *Y = (double *)malloc((size_t)p * q * sizeof(double));
+    double *A = (double *)malloc((size_t)p * p * sizeof(double));
+    double *Bm = (double *)malloc((size_t)p * p * sizeof(double));
+    double ss = 0.0;
+    for (size_t i = 0; i < (size_t)rows * cols; ++i) ss += M[i] * M[i];
+    const double inv = 1.0 / (sqrt(ss) + 1e-7);
+    for (int i = 0; i < rows; ++i)
+        for (int j = 0; j < cols; ++j) {
+            const double v = M[(size_t)i * cols + j] * inv;
+            if (tr) X[(size_t)j * q + i] = v;
+            else X[(size_t)i * q + j] = v;
+        }
+    const double a = 3.4445, b = -4.7750, c = 2.0315;
+    for (int it = 0; it < steps; ++it) {
+        for (int i = 0; i < p; ++i)          /* A = X X^T */
+            for (int j = 0; j < p; ++j) {
+                double acc = 0.0;
+                for (int k = 0; k < q; ++k) acc += X[(size_t)i * q + k] * X[(size_t)j * q + k];
+                A[(size_t)i * p + j] = acc;
+            }
+        for (int i = 0; i < p; ++i)          /* Bm = b A + c A A */
+            for (int j = 0; j < p; ++j) {
+                double acc = 0.0;
+                for (int k = 0; k < p; ++k) acc += A[(size_t)i * p + k] * A[(size_t)k * p + j];
+                Bm[(size_t)i * p + j] = b * A[(size_t)i * p + j] + c * acc;
+            }
+        for (int i = 0; i < p; ++i)          /* Y = a X + Bm X */
+            for (int j = 0; j < q; ++j) {
+                double acc = 0.0;
+                for (int k = 0; k < p; ++k) acc += Bm[(size_t)i * p + k] * X[(size_t)k * q + j];
+                Y[(size_t)i * q + j] = a * X[(size_t)i * q + j] + acc;
+            }
+        double *t = X; X = Y; Y = t;
+    }
+    for (int i = 0; i < rows; ++i)
+        for (int j = 0; j < cols; ++j)
+            O[(size_t)i * cols + j] = tr ? X[(size_t)j * q + i] : X[(size_t)i * q + j];
+    free(X); free(Y); free(A); free(Bm);
+}
+
+void or_newton_schulz(const double *M, int rows, int cols, int steps, double *O)
+{
+    ns_orthogonalise(M, rows, cols, steps, O);
+}
+
+static void adamw_range(double *w, const double *g, double *m, double *v, size_t n, double lr,
+                        double wd, double bc1, double bc2)
+{
+    for (size_t i = 0; i < n; ++i) {
+        m[i] = 0.9 * m[i] + 0.1 * g[i];
+        v[i] = 0.999 * v[i] + 0.001 * g[i] * g[i];
+        w[i] -= lr * ((m[i] / bc1) / (sqrt(v[i] / bc2) + 1e-8) + wd * w[i]);
+    }
+}
+
+void or_muon_step(const or_cfg *c, double *w, const double *g, double *mom, double *am, double *av,
+                  double lr, double mu, double wd, int ns_steps, int64_t step)
+{
+    const size_t d = (size_t)c->d, f = (size_t)c->d_ff;
+    const double bc1 = 1.0 - pow(0.9, (double)step), bc2 = 1.0 - pow(0.999, (double)step);
+    size_t off = 0;
+    /* walk the blob in layout order: matrices get Muon, the rest AdamW */
+#define OR_ADAMW(n) do { adamw_range(w + off, g + off, am + off, av + off, (n), lr, wd, bc1, bc2); off += (n); } while (0)
+#define OR_MUON(r, cc) do { \
+        const size_t n_ = (size_t)(r) * (cc); \
+        for (size_t i_ = 0; i_ < n_; ++i_) mom[off + i_] = mu * mom[off + i_] + g[off + i_]; \
+        double *O_ = (double *)malloc(n_ * sizeof(double)); \
+        ns_orthogonalise(mom + off, (int)(r), (int)(cc), ns_steps, O_); \
+        const double s_ = 0.2 * sqrt((double)((r) > (cc) ? (r) : (cc))); \
+        for (size_t i_ = 0; i_ < n_; ++i_) w[off + i_] -= lr * (s_ * O_[i_] + wd * w[off + i_]); \
+        free(O_); off += n_; } while (0)
+    OR_ADAMW(2 * (size_t)c->d_token);
+    OR_ADAMW((size_t)c->N * (d - (size_t)c->d_token));
+    for (int l = 0; l < c->n_layers; ++l) {
+        OR_ADAMW(2 * d);          /* ln1 gain, bias */
+        OR_MUON(3 * d, d);        /* Wqkv */
+        OR_ADAMW(3 * d + 2 * d);  /* bqkv, ln2 gain, bias */
+        OR_MUON(f, d);            /* W1 */
+        OR_ADAMW(f);              /* b1 */
+        OR_MUON(d, f);            /* W2 */
+        OR_ADAMW(d);              /* b2 */
+    }
+    OR_ADAMW(2 * d + 2 * d + 2);  /* LN_f, head */
+#undef OR_ADAMW
+#undef OR_MUON
+}
+
+/* ------------------------------------------------------------------------ */
 /* Exhaustive enumeration over all 2^N configurations by a prefix-tree walk: */
 /* each tree node costs one decode step (Algorithm 2) and its two children   */
 /* reuse its KV cache.  Gives sum_sigma q (=1 by construction, Sec.          */

@@ -494,3 +494,61 @@ def test_likelihood_term_ascends_the_batch_log_likelihood():
         wm[idx] -= h
         fd = (oracle.logprob(ocfg(m), wp, s).mean() - oracle.logprob(ocfg(m), wm, s).mean()) / (2 * h)
         assert abs(g[idx] + fd) < 1e-6 + 1e-5 * abs(fd)
+
+
+# --------------------------------------------------------------------------
+# Muon (Methods "Comparison on optimizers")
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape", [(48, 16), (16, 40), (24, 24)])
+def test_newton_schulz_acts_on_singular_values_only(shape):
+    """Each quintic step maps every singular value s of X to a s + b s^3 + c s^5
+    and keeps the singular vectors: NS_k(M) = U phi^k(S / |M|_F) V^T, checked
+    against numpy's SVD for both orientations."""
+    rng = np.random.default_rng(sum(shape))
+    M = rng.normal(size=shape)
+    a, b, c = 3.4445, -4.7750, 2.0315
+    U, S, Vt = np.linalg.svd(M, full_matrices=False)
+    s = S / (np.linalg.norm(M) + 1e-7)
+    for _ in range(5):
+        s = a * s + b * s ** 3 + c * s ** 5
+    O = oracle.newton_schulz(M, 5)
+    assert np.allclose(O, (U * s) @ Vt, atol=1e-10)
+    sv = np.linalg.svd(O, compute_uv=False)
+    assert sv.min() > 0.6 and sv.max() < 1.2  # approximately orthogonal
+
+
+def test_muon_step_matrices_and_adamw_rest():
+    """One step from zero state: every weight matrix moves by
+    -lr (0.2 sqrt(max(r, c)) NS(G) + wd W); every other parameter takes the
+    torch.optim.AdamW step; momentum holds G on the matrices."""
+    m = inputs.ModelShape(10, 1, 16, 2, d_ff=32)
+    cfg = ocfg(m)
+    w0 = inputs.make_weights(m, 2).astype(np.float64)
+    g = np.random.default_rng(5).normal(0, 1e-2, w0.size)
+    w, mom, am, av = w0.copy(), np.zeros_like(w0), np.zeros_like(w0), np.zeros_like(w0)
+    lr, mu, wd = 2e-3, 0.95, 0.1
+    oracle.muon_step(cfg, w, g, mom, am, av, lr, mu, wd, 5, 1)
+    d, f = m.d, m.d_ff
+    off = 2 * m.d_token + m.N * (d - m.d_token)
+    mats = []
+    off += 2 * d
+    mats.append((off, 3 * d, d)); off += 3 * d * d + 3 * d + 2 * d
+    mats.append((off, f, d)); off += f * d + f
+    mats.append((off, d, f)); off += d * f + d
+    is_mat = np.zeros(w0.size, bool)
+    for o, r, cc in mats:
+        n = r * cc
+        is_mat[o:o + n] = True
+        G = g[o:o + n].reshape(r, cc)
+        exp = w0[o:o + n] - lr * (0.2 * np.sqrt(max(r, cc)) * oracle.newton_schulz(G, 5).ravel()
+                                   + wd * w0[o:o + n])
+        assert np.allclose(w[o:o + n], exp, atol=1e-12)
+        assert np.allclose(mom[o:o + n], g[o:o + n])
+    p = torch.nn.Parameter(torch.tensor(w0[~is_mat]))
+    opt = torch.optim.AdamW([p], lr=lr, betas=(0.9, 0.999), eps=1e-8, weight_decay=wd)
+    p.grad = torch.tensor(g[~is_mat])
+    opt.step()
+    # torch applies the decay as w (1 - lr wd) before the Adam step: the same to O(lr^2 wd)
+    assert np.allclose(w[~is_mat], p.detach().numpy(), atol=1e-7)
+    assert np.all(mom[~is_mat] == 0)
