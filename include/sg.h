@@ -298,6 +298,28 @@ sg_status sg_overlap_hist(const int8_t *spins, int64_t B, int32_t N, int64_t *hi
 sg_status sg_adam_step(float *w, const float *g, float *m, float *v, int64_t n, float lr,
                        float beta1, float beta2, float eps, int64_t step, sg_stream stream);
 
+/*
+ * Muon update of a model's weight blob (Methods "Comparison on optimizers":
+ * the optimiser of Jordan et al. 2024 with the weight decay and RMS alignment
+ * of Liu et al. 2025).  For each weight matrix (per layer Wqkv [3d][d],
+ * W1 [d_ff][d], W2 [d][d_ff]) with gradient G:
+ *   M = mu M + G;  O = NS(M);  W -= lr (0.2 sqrt(max(rows, cols)) O + wd W),
+ * NS = ns_steps quintic Newton-Schulz steps on X = M / (|M|_F + 1e-7), taken
+ * on M^T when rows > cols: X <- a X + (b A + c A A) X, A = X X^T,
+ * (a, b, c) = (3.4445, -4.7750, 2.0315).  Every other parameter (embeddings,
+ * LayerNorm gains and biases, biases, output head) takes an AdamW step
+ * (beta1 0.9, beta2 0.999, eps 1e-8, same lr, decoupled decay wd).
+ *   weights, grad, momentum, adam_m, adam_v: dev float [sg_param_count];
+ *   momentum is used on the matrix entries, adam_m/adam_v on the others;
+ *   step >= 1 (AdamW bias correction); 0 <= ns_steps <= 32.
+ * Scratch is the model's workspace.  Errors: SG_EINVAL (pointers, values),
+ * SG_EUNSUPPORTED (grouped models).  The paper prints no counterpart of the
+ * AdamW split; it is the usual practice for the non-matrix parameters.
+ */
+sg_status sg_muon_step(sg_model *m, float *weights, const float *grad, float *momentum,
+                       float *adam_m, float *adam_v, double lr, double mu, double weight_decay,
+                       int32_t ns_steps, int64_t step, sg_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -55,6 +55,7 @@ _SIGS = {
     "sg_energy": ([_P, _P, _I64, _I32, _P, _P, _P], _I32),
     "sg_free_energy": ([_P, _P, _I64, _D, _P, _P, _P], _I32),
     "sg_loss_coeff": ([_P, _P, _I64, _D, _D, _D, _P, _P, _P], _I32),
+    "sg_muon_step": ([_P, _P, _P, _P, _P, _P, _D, _D, _D, _I32, _I64, _P], _I32),
     "sg_mh_step": ([_P, _P, _P, _I64, _I32, _I32, _D, _U64, _P, _P, _P, _P, _P, _P], _I32),
     "sg_metropolis": ([_P, _P, _I64, _I32, _D, _U64, _P, _P, _P], _I32),
     "sg_overlap_hist": ([_P, _I64, _I32, _P, _P], _I32),
@@ -175,6 +176,16 @@ class Model:
             self.handle, B, beta, seed, stream_id, flag_band, _dev(spins, torch.int8, (B, N)),
             _dev(logq, torch.float32, (B,)), _dev(flags, torch.int32), _stream(stream)))
         return (spins, logq, flags) if with_flags else (spins, logq)
+
+    def muon_step(self, grad, momentum, adam_m, adam_v, lr, step, mu=0.95, weight_decay=0.0,
+                  ns_steps=5, stream=None):
+        """Muon on the weight matrices, AdamW on the rest, in place on weights()."""
+        n = self.n_params
+        _check("sg_muon_step", lib().sg_muon_step(
+            self.handle, _dev(self.weights(), torch.float32, (n,)), _dev(grad, torch.float32, (n,)),
+            _dev(momentum, torch.float32, (n,)), _dev(adam_m, torch.float32, (n,)),
+            _dev(adam_v, torch.float32, (n,)), lr, mu, weight_decay, ns_steps, step,
+            _stream(stream)))
 
     def logprob(self, spins, logq=None, stream=None):
         B = spins.shape[0]

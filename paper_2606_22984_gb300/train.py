@@ -10,7 +10,8 @@ One step (Methods "Training strategy", "Variational annealing"; Eq. loss2):
   3. energies (sg_energy);
   4. REINFORCE weights of L = E + T ln q (or beta E + ln q at a fixed beta),
      with the likelihood term w of Eq. loss2 (sg_loss_coeff);
-  5. gradient (sg_grad) and optimiser step (sg_adam_step), weights repacked
+  5. gradient (sg_grad) and optimiser step (sg_adam_step, or sg_muon_step:
+     Muon on the weight matrices, AdamW on the rest), weights repacked
      (sg_model_refresh).
 """
 from dataclasses import dataclass, field
@@ -44,6 +45,9 @@ class TrainConfig:
     lmc_sweeps: int = 0                   # local Monte Carlo sweeps on the samples (0: off)
     w: float = 0.0                        # likelihood (self-distillation) weight of Eq. loss2
     T_floor: float = 1e-3                 # temperature used by the local Monte Carlo at T = 0
+    optimizer: str = "adam"               # "adam", or "muon" (Muon + AdamW, sg_muon_step)
+    momentum: float = 0.95                # Muon momentum
+    weight_decay: float = 0.0             # Muon / AdamW decoupled weight decay
     seed: int = 1
     log_every: int = 50
 
@@ -58,15 +62,18 @@ class TrainLog:
 
 
 class Trainer:
-    """REINFORCE training of one model on one instance with Adam."""
+    """REINFORCE training of one model on one instance (Adam or Muon)."""
 
     def __init__(self, model: "sg.Model", inst: "sg.Instance", cfg: TrainConfig):
         if (cfg.beta is None) == (cfg.schedule is None):
             raise ValueError("give exactly one of beta (fixed) or schedule (temperature)")
+        if cfg.optimizer not in ("adam", "muon"):
+            raise ValueError("optimizer must be 'adam' or 'muon'")
         self.model, self.inst, self.cfg = model, inst, cfg
         w = model.weights()
         self.m = torch.zeros_like(w)
         self.v = torch.zeros_like(w)
+        self.mom = torch.zeros_like(w) if cfg.optimizer == "muon" else None
         self.grad = torch.empty_like(w)
         self.log = TrainLog()
 
@@ -89,7 +96,11 @@ class Trainer:
             a, cc = 1.0, T
         coeff, mean = sg.loss_coeff(E, logq, a, cc, c.w)
         model.grad(spins, coeff, grad=self.grad)
-        sg.adam_step(model.weights(), self.grad, self.m, self.v, c.lr, i + 1)
+        if self.mom is None:
+            sg.adam_step(model.weights(), self.grad, self.m, self.v, c.lr, i + 1)
+        else:
+            model.muon_step(self.grad, self.mom, self.m, self.v, c.lr, i + 1, mu=c.momentum,
+                            weight_decay=c.weight_decay)
         model.refresh()
         if i % c.log_every == 0 or i == c.steps - 1:
             mv = mean.cpu().numpy()

@@ -125,3 +125,50 @@ def test_lmc_refinement_with_self_distillation_trains_toward_ground_state():
           f"log mean_E {log.mean_E}")
     assert abs(E.min() - ex["Emin"]) < 1e-3
     assert E.mean() < 0.8 * ex["Emin"]
+
+
+@pytest.mark.parametrize("shape", [inputs.ModelShape(12, 2, 32, 4),
+                                   inputs.ModelShape(20, 1, 64, 4, d_ff=96),
+                                   inputs.ModelShape(8, 1, 128, 8)])
+def test_muon_step_matches_oracle(shape):
+    """Three Muon steps (Newton-Schulz in FP32 on the GPU, FP64 in the oracle):
+    the weight updates agree to 1e-3 relative, matrices and AdamW parameters."""
+    m = shape
+    w0 = inputs.make_weights(m, 8)
+    model = sg.Model(m, w0, sg.SG_FP32)
+    n = model.n_params
+    dev = torch.device("cuda")
+    mom, am, av = (torch.zeros(n, device=dev) for _ in range(3))
+    w, mo, amo, avo = (w0.astype(np.float64).copy(), np.zeros(n), np.zeros(n), np.zeros(n))
+    rng = np.random.default_rng(9)
+    for step in range(1, 4):
+        g = rng.normal(0, 1e-2, n).astype(np.float32)
+        model.muon_step(torch.tensor(g, device=dev), mom, am, av, 2e-3, step, mu=0.95,
+                        weight_decay=0.1)
+        oracle.muon_step(ocfg(m), w, g, mo, amo, avo, 2e-3, 0.95, 0.1, 5, step)
+    model.check()
+    wg = model.weights().cpu().numpy().astype(np.float64)
+    dg, do = wg - w0, w - w0
+    rel = np.linalg.norm(dg - do) / np.linalg.norm(do)
+    print(f"d={m.d}: Muon update rel err {rel:.2e}")
+    assert rel < 1e-3
+    assert np.allclose(mom.cpu().numpy(), mo, rtol=1e-5, atol=1e-7)
+
+
+def test_sk20_training_with_muon_reaches_exact_free_energy():
+    """The paper's optimiser: REINFORCE (Eq. loss1) with Muon on the weight
+    matrices, SK N=20 at beta = 1; F_IS/N within 1e-3 of the enumerated F/N."""
+    from paper_2606_22984_gb300.train import TrainConfig, Trainer
+    wl = inputs.workloads()["sk20"]
+    m, inst = wl.model, wl.instance()
+    model = sg.Model(m, inputs.make_weights(m, 1), sg.SG_FP32)
+    gi = sg.Instance(inst)
+    log = Trainer(model, gi, TrainConfig(B=4096, steps=400, lr=4e-3, beta=1.0,
+                                         optimizer="muon", log_every=100)).run()
+    ex = oracle.enumerate_exact(ocfg(m), model.weights().cpu().numpy().astype(np.float64), inst, 1.0)
+    spins, logq = model.sample(65536, seed=999)
+    out = sg.free_energy(gi.energy(spins), logq, 1.0).cpu().numpy()
+    print(f"Muon: F/N exact {ex['F'] / m.N:.6f}  F_IS/N {out[1] / m.N:.6f}  F_q/N {out[0] / m.N:.6f}"
+          f"  exact (F_q - F)/N {(ex['Fq'] - ex['F']) / m.N:.2e}")
+    assert abs(out[1] - ex["F"]) / m.N <= 1e-3
+    assert 0 <= (ex["Fq"] - ex["F"]) / m.N < 2e-3  # the variational gap (KL / beta N)
