@@ -160,6 +160,128 @@ __global__ void ln_bwd_kernel(const float *__restrict__ dY, const float *__restr
     }
 }
 
+// LayerNorm backward for D = 32 VPL (VPL values per lane, contiguous, vector
+// loads): dX = dres + rs (dY g - m1 - xhat m2) (dres may be null), with
+// m1 = mean(dY g), m2 = mean(dY g xhat); dg += sum dY xhat, db += sum dY.
+// A warp walks RPW rows at a time so that their loads are in flight together;
+// per-lane partials of dg, db are reduced per block and added with atomics.
+template <int VPL>
+__device__ __forceinline__ void ld_vec(const float *p, float (&v)[VPL])
+{
+    if (VPL % 4 == 0) {
+#pragma unroll
+        for (int c = 0; c < VPL / 4; ++c) {
+            const float4 x = *reinterpret_cast<const float4 *>(p + 4 * c);
+            v[4 * c] = x.x; v[4 * c + 1] = x.y; v[4 * c + 2] = x.z; v[4 * c + 3] = x.w;
+        }
+    } else if (VPL % 2 == 0) {
+#pragma unroll
+        for (int c = 0; c < VPL / 2; ++c) {
+            const float2 x = *reinterpret_cast<const float2 *>(p + 2 * c);
+            v[2 * c] = x.x; v[2 * c + 1] = x.y;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < VPL; ++c) v[c] = p[c];
+    }
+}
+
+template <int VPL>
+__device__ __forceinline__ void st_vec(float *p, const float (&v)[VPL])
+{
+    if (VPL % 4 == 0) {
+#pragma unroll
+        for (int c = 0; c < VPL / 4; ++c)
+            *reinterpret_cast<float4 *>(p + 4 * c) = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+    } else if (VPL % 2 == 0) {
+#pragma unroll
+        for (int c = 0; c < VPL / 2; ++c)
+            *reinterpret_cast<float2 *>(p + 2 * c) = make_float2(v[2 * c], v[2 * c + 1]);
+    } else {
+#pragma unroll
+        for (int c = 0; c < VPL; ++c) p[c] = v[c];
+    }
+}
+
+template <int VPL, int RPW>
+__global__ void __launch_bounds__(256)
+ln_bwd_rows_kernel(const float *__restrict__ dY, const float *__restrict__ X,
+                   const float *__restrict__ mu, const float *__restrict__ rs,
+                   const float *__restrict__ g, const float *__restrict__ dres,
+                   float *__restrict__ dX, float *__restrict__ dg, float *__restrict__ db, int64_t R)
+{
+    constexpr int D = 32 * VPL;
+    __shared__ float red[2][D];
+    for (int j = threadIdx.x; j < 2 * D; j += blockDim.x) (&red[0][0])[j] = 0.f;
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    float gl[VPL], pg[VPL], pb[VPL];
+    ld_vec<VPL>(g + lane * VPL, gl);
+#pragma unroll
+    for (int j = 0; j < VPL; ++j) pg[j] = pb[j] = 0.f;
+    __syncthreads();
+    for (int64_t r0 = gw * RPW; r0 < R; r0 += nw * RPW) {
+        float x[RPW][VPL], dy[RPW][VPL], m[RPW], s[RPW], m1[RPW], m2[RPW];
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+            const int64_t r = r0 + q < R ? r0 + q : R - 1;  // duplicate a row past the end, never stored
+            m[q] = mu[r];
+            s[q] = rs[r];
+            ld_vec<VPL>(X + r * D + lane * VPL, x[q]);
+            ld_vec<VPL>(dY + r * D + lane * VPL, dy[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+            float a = 0.f, b = 0.f;
+#pragma unroll
+            for (int j = 0; j < VPL; ++j) {
+                x[q][j] = (x[q][j] - m[q]) * s[q];  // xhat
+                const float dxh = dy[q][j] * gl[j];
+                a += dxh;
+                b += dxh * x[q][j];
+            }
+            m1[q] = a;
+            m2[q] = b;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < RPW; ++q) {
+                m1[q] += __shfl_xor_sync(0xffffffffu, m1[q], o);
+                m2[q] += __shfl_xor_sync(0xffffffffu, m2[q], o);
+            }
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+            if (r0 + q >= R) break;
+            const int64_t r = r0 + q;
+            float out[VPL];
+            if (dres) ld_vec<VPL>(dres + r * D + lane * VPL, out);
+            else {
+#pragma unroll
+                for (int j = 0; j < VPL; ++j) out[j] = 0.f;
+            }
+#pragma unroll
+            for (int j = 0; j < VPL; ++j) {
+                out[j] += s[q] * (dy[q][j] * gl[j] - m1[q] * (1.0f / D) - x[q][j] * m2[q] * (1.0f / D));
+                pg[j] += dy[q][j] * x[q][j];
+                pb[j] += dy[q][j];
+            }
+            st_vec<VPL>(dX + r * D + lane * VPL, out);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < VPL; ++j) {
+        atomicAdd(&red[0][lane * VPL + j], pg[j]);
+        atomicAdd(&red[1][lane * VPL + j], pb[j]);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < D; j += blockDim.x) {
+        atomicAdd(dg + j, red[0][j]);
+        atomicAdd(db + j, red[1][j]);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // GEMM C[M][N] = A[M][K] * B[K][N] (+bias) with a fused epilogue.  64x64 block
 // tile, 16-deep k tiles, 4x4 outputs per thread.  K, N, lda, ldb multiples of 4.
@@ -1028,13 +1150,32 @@ void colsum(const float *A, int lda, int64_t M, int N, float *out, cudaStream_t 
     colsum_kernel<<<grid, block, 0, ::sg::counted(st)>>>(A, lda, M, N, out, rpb);
 }
 
-void ln_bwd(const float *dY, const float *X, const float *mu, const float *rs, const float *g,
-            float *dX, int accumulate, float *dg, float *db, int64_t R, int D, cudaStream_t st)
+// dX = dres + LN'(X)^T dY (dres may alias nothing or be null), dg/db accumulated
+void ln_bwd_res(const float *dY, const float *X, const float *mu, const float *rs, const float *g,
+                const float *dres, float *dX, float *dg, float *db, int64_t R, int D, cudaStream_t st)
 {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    constexpr int RPW = 4;
+    const int64_t want = (R + 8 * RPW - 1) / (8 * RPW);
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 8));
+    auto go = [&](auto kern) { kern<<<blocks, 256, 0, ::sg::counted(st)>>>(dY, X, mu, rs, g, dres, dX, dg, db, R); };
+    switch (D) {
+    case 32: go(ln_bwd_rows_kernel<1, RPW>); return;
+    case 64: go(ln_bwd_rows_kernel<2, RPW>); return;
+    case 96: go(ln_bwd_rows_kernel<3, RPW>); return;
+    case 128: go(ln_bwd_rows_kernel<4, RPW>); return;
+    case 256: go(ln_bwd_rows_kernel<8, RPW>); return;
+    default: break;
+    }
+    // other widths: copy the residual, then the generic kernel accumulates
+    if (dres) cudaMemcpyAsync(dX, dres, (size_t)R * D * sizeof(float), cudaMemcpyDeviceToDevice, st);
     const int rpb = 256;
     ln_bwd_kernel<<<blocks_for(R, rpb), 256, 2 * D * sizeof(float), ::sg::counted(st)>>>(
-        dY, X, mu, rs, g, dX, accumulate, dg, db, R, D, rpb);
+        dY, X, mu, rs, g, dX, dres ? 1 : 0, dg, db, R, D, rpb);
 }
+
 
 struct Work {
     std::vector<LayerBufs> layers;
@@ -1310,9 +1451,8 @@ sg_status launch_grad_f32(sg_model *m, const int8_t *spins, const float *coeff, 
             g.A = w.dF1t; g.K = F; g.KC = (F + 63) / 64; g.Bw = bt + m->bt_off[l][4];
             g.NBw = (int)tl_blocks(D); g.N = D; g.out_f32 = w.dA; g.ld_out = D;
             launch_row_gemm(g, TE_STORE_F32, st);
-            cudaMemcpyAsync(w.dHmid, w.dH, (size_t)R * D * sizeof(float), cudaMemcpyDeviceToDevice, st);
-            ln_bwd(w.dA, L.Hmid, L.mu2, L.rs2, W + o.ln2g, w.dHmid, 1, grad + o.ln2g, grad + o.ln2b,
-                   R, D, st);
+            ln_bwd_res(w.dA, L.Hmid, L.mu2, L.rs2, W + o.ln2g, w.dH, w.dHmid, grad + o.ln2g,
+                       grad + o.ln2b, R, D, st);
             // attention: Hmid = Hin + O(QKV)
             attn_bwd_dispatch(dh, L.QKV, L.O, w.dHmid, L.LSE, w.dQKV, w.Dt, Bc, c, st, (int *)m->err);
             launch_to_wide(w.dQKV, R, 3 * D, w.dQKVt, st);
@@ -1321,9 +1461,8 @@ sg_status launch_grad_f32(sg_model *m, const int8_t *spins, const float *coeff, 
             g.A = w.dQKVt; g.K = 3 * D; g.KC = (3 * D + 63) / 64; g.Bw = bt + m->bt_off[l][5];
             g.NBw = (int)tl_blocks(D); g.N = D; g.out_f32 = w.dA; g.ld_out = D;
             launch_row_gemm(g, TE_STORE_F32, st);
-            cudaMemcpyAsync(w.dH, w.dHmid, (size_t)R * D * sizeof(float), cudaMemcpyDeviceToDevice, st);
-            ln_bwd(w.dA, L.Hin, L.mu1, L.rs1, W + o.ln1g, w.dH, 1, grad + o.ln1g, grad + o.ln1b,
-                   R, D, st);
+            ln_bwd_res(w.dA, L.Hin, L.mu1, L.rs1, W + o.ln1g, w.dHmid, w.dH, grad + o.ln1g,
+                       grad + o.ln1b, R, D, st);
         }
         for (int l = c.n_layers - 1; l >= 0 && !use_tc(c); --l) {
             LayerBufs &L = w.layers[l];
@@ -1335,19 +1474,15 @@ sg_status launch_grad_f32(sg_model *m, const int8_t *spins, const float *coeff, 
             gemm_tn_acc(w.dF1, F, L.A2, D, grad + o.W1, R, F, D, st);
             colsum(w.dF1, F, R, F, grad + o.b1, st);
             gemm<G_STORE>(w.dF1, F, m->wt + m->pack.W1[l], D, nullptr, w.dA, D, R, D, F, st);
-            cudaMemcpyAsync(w.dHmid, w.dH, (size_t)R * D * sizeof(float),
-                            cudaMemcpyDeviceToDevice, st);
-            ln_bwd(w.dA, L.Hmid, L.mu2, L.rs2, W + o.ln2g, w.dHmid, 1, grad + o.ln2g,
-                   grad + o.ln2b, R, D, st);
+            ln_bwd_res(w.dA, L.Hmid, L.mu2, L.rs2, W + o.ln2g, w.dH, w.dHmid, grad + o.ln2g,
+                       grad + o.ln2b, R, D, st);
             // attention: Hmid = Hin + O(QKV)
             attn_bwd_dispatch(dh, L.QKV, L.O, w.dHmid, L.LSE, w.dQKV, w.Dt, Bc, c, st, (int *)m->err);
             gemm_tn_acc(w.dQKV, 3 * D, L.A1, D, grad + o.Wqkv, R, 3 * D, D, st);
             colsum(w.dQKV, 3 * D, R, 3 * D, grad + o.bqkv, st);
             gemm<G_STORE>(w.dQKV, 3 * D, m->wt + m->pack.Wqkv[l], D, nullptr, w.dA, D, R, D, 3 * D, st);
-            cudaMemcpyAsync(w.dH, w.dHmid, (size_t)R * D * sizeof(float),
-                            cudaMemcpyDeviceToDevice, st);
-            ln_bwd(w.dA, L.Hin, L.mu1, L.rs1, W + o.ln1g, w.dH, 1, grad + o.ln1g, grad + o.ln1b,
-                   R, D, st);
+            ln_bwd_res(w.dA, L.Hin, L.mu1, L.rs1, W + o.ln1g, w.dHmid, w.dH, grad + o.ln1g,
+                       grad + o.ln1b, R, D, st);
         }
         embed_bwd_kernel<<<blocks_for((int64_t)c.N * D, 256), 256, 0, ::sg::counted(st)>>>(
             w.dH, sp, Bc, c.N, D, c.d_token, grad + O.tok, grad + O.pos);
