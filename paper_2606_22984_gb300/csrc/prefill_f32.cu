@@ -814,6 +814,59 @@ __device__ __forceinline__ float dot_regs(const float (&a)[DH], const float (&b)
     return s0 + s1;
 }
 
+// Rows staged in shared memory as FP32 (FP32 model) or BF16 (BF16 model:
+// half the shared-memory bytes per row read; values as the tensor-core paths
+// see them).  Row pitch in elements: FP32 DH + 4, BF16 DH + 8 (24 for DH = 8),
+// so 8 consecutive rows' 16-byte pieces fall in distinct banks.
+template <int DH, typename TS>
+struct Pitch {
+    static constexpr int value = sizeof(TS) == 4 ? DH + 4 : (DH == 8 ? 24 : DH + 8);
+};
+
+template <int DH, typename TS>
+__device__ __forceinline__ void stage_rows_t(TS *dst, const float *__restrict__ src, int N,
+                                             int stride_src)
+{
+    constexpr int DP = Pitch<DH, TS>::value;
+    if constexpr (sizeof(TS) == 4) {
+        for (int e = threadIdx.x; e < N * (DH / 4); e += blockDim.x) {
+            const int t = e / (DH / 4), c = e % (DH / 4);
+            *reinterpret_cast<float4 *>(dst + t * DP + 4 * c) =
+                *reinterpret_cast<const float4 *>(src + (size_t)t * stride_src + 4 * c);
+        }
+    } else {
+        for (int e = threadIdx.x; e < N * (DH / 8); e += blockDim.x) {
+            const int t = e / (DH / 8), c = e % (DH / 8);
+            const float4 a = *reinterpret_cast<const float4 *>(src + (size_t)t * stride_src + 8 * c);
+            const float4 b = *reinterpret_cast<const float4 *>(src + (size_t)t * stride_src + 8 * c + 4);
+            __nv_bfloat162 h[4] = {__floats2bfloat162_rn(a.x, a.y), __floats2bfloat162_rn(a.z, a.w),
+                                   __floats2bfloat162_rn(b.x, b.y), __floats2bfloat162_rn(b.z, b.w)};
+            *reinterpret_cast<uint4 *>(dst + t * DP + 8 * c) = *reinterpret_cast<const uint4 *>(h);
+        }
+    }
+}
+
+template <int DH>
+__device__ __forceinline__ void row_regs_t(const float *row, float (&r)[DH])
+{
+    row_regs<DH>(row, r);
+}
+
+template <int DH>
+__device__ __forceinline__ void row_regs_t(const __nv_bfloat16 *row, float (&r)[DH])
+{
+#pragma unroll
+    for (int c = 0; c < DH / 8; ++c) {
+        const uint4 x = *reinterpret_cast<const uint4 *>(row + 8 * c);
+        const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            r[8 * c + 2 * j] = __uint_as_float(w[j] << 16);
+            r[8 * c + 2 * j + 1] = __uint_as_float(w[j] & 0xffff0000u);
+        }
+    }
+}
+
 template <int DH>
 __device__ __forceinline__ float dot_row(const float *q, const float *row)
 {
@@ -826,22 +879,22 @@ __device__ __forceinline__ float dot_row(const float *q, const float *row)
     return s;
 }
 
-template <int DH>
+template <int DH, typename TS>
 __global__ void __launch_bounds__(256)
 attn_fwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ Hin,
                      float *__restrict__ O, float *__restrict__ Hmid, float *__restrict__ LSE,
                      int N, int D, int NH, int mask, int W, int S)
 {
-    constexpr int DP = DH + 4;
+    constexpr int DP = DH + 4, DPS = Pitch<DH, TS>::value;
     extern __shared__ float4 sm4[];
-    float *Qs = reinterpret_cast<float *>(sm4);  // Q in, attention output out
-    float *Ks = Qs + N * DP;
-    float *Vs = Ks + N * DP;
+    float *Qs = reinterpret_cast<float *>(sm4);  // Q in, attention output out (FP32)
+    TS *Ks = reinterpret_cast<TS *>(Qs + N * DP);
+    TS *Vs = Ks + N * DPS;
     const int b = blockIdx.x / NH, hh = blockIdx.x % NH;
     const float *base = QKV + (size_t)b * N * 3 * D;
     stage_rows<DH>(Qs, base + hh * DH, N, 3 * D);
-    stage_rows<DH>(Ks, base + D + hh * DH, N, 3 * D);
-    stage_rows<DH>(Vs, base + 2 * D + hh * DH, N, 3 * D);
+    stage_rows_t<DH, TS>(Ks, base + D + hh * DH, N, 3 * D);
+    stage_rows_t<DH, TS>(Vs, base + 2 * D + hh * DH, N, 3 * D);
     __syncthreads();
     const float scale = rsqrtf((float)DH);
     for (int t = threadIdx.x; t < N; t += blockDim.x) {
@@ -858,20 +911,16 @@ attn_fwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ Hi
         float mx = -INFINITY, den = 0.f;
         for (int i = 0; i < nk; ++i) {
             const int k = i < n_sink ? i : band_lo + (i - n_sink);
-            const float sc = dot_row<DH>(q, Ks + k * DP);
+            float kr[DH], vr[DH];
+            row_regs_t<DH>(Ks + k * DPS, kr);
+            row_regs_t<DH>(Vs + k * DPS, vr);
+            const float sc = dot_regs<DH>(q, kr);
             const float mn = fmaxf(mx, sc);
             const float corr = __expf(mx - mn), p = __expf(sc - mn);
             mx = mn;
             den = den * corr + p;
-            const float *vr = Vs + k * DP;
 #pragma unroll
-            for (int c = 0; c < DH / 4; ++c) {
-                const float4 v = *reinterpret_cast<const float4 *>(vr + 4 * c);
-                acc[4 * c] = acc[4 * c] * corr + p * v.x;
-                acc[4 * c + 1] = acc[4 * c + 1] * corr + p * v.y;
-                acc[4 * c + 2] = acc[4 * c + 2] * corr + p * v.z;
-                acc[4 * c + 3] = acc[4 * c + 3] * corr + p * v.w;
-            }
+            for (int j = 0; j < DH; ++j) acc[j] = acc[j] * corr + p * vr[j];
         }
         const float inv = 1.0f / den;
 #pragma unroll
@@ -895,36 +944,41 @@ attn_fwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ Hi
 // key threads (each sees at most W + 1 queries); sink keys (and every key of
 // a dense mask) by warps, lanes striding over the queries with a shuffle
 // reduction.
-template <int DH>
+template <int DH, typename TS>
 __global__ void __launch_bounds__(256)
 attn_bwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ O,
                      const float *__restrict__ dO, const float *__restrict__ LSE,
                      float *__restrict__ dQKV, int N, int D, int NH, int mask, int W, int S)
 {
-    constexpr int DP = DH + 4;
+    constexpr int DP = DH + 4, DPS = Pitch<DH, TS>::value;
+    constexpr bool kF32 = sizeof(TS) == 4;
     extern __shared__ float4 sm4[];
-    float *Qs = reinterpret_cast<float *>(sm4);
-    float *Ks = Qs + N * DP;
-    float *Vs = Ks + N * DP;
-    float *Gs = Vs + N * DP;  // dO
-    float *Os = Gs + N * DP;  // O in; then the dQ, dK, dV rows out
-    float *Ls = Os + N * DP;  // LSE
-    float *Ds = Ls + N;       // D_t = dO_t . O_t
+    float *Os = reinterpret_cast<float *>(sm4);  // O in; then the dQ, dK, dV rows out
+    float *Ls = Os + N * DP;                     // LSE
+    float *Ds = Ls + N;                          // D_t = dO_t . O_t
+    // FP32 rows for the dV of sink keys (the FP32 model parks them in Vs)
+    float *Pk = Ds + N;
+    // the staged rows start 16-byte aligned after the FP32 arrays
+    const int f32_floats = (N * DP + 2 * N + (kF32 ? 0 : N * DP) + 3) & ~3;
+    TS *Qs = reinterpret_cast<TS *>(reinterpret_cast<float *>(sm4) + f32_floats);
+    TS *Ks = Qs + N * DPS;
+    TS *Vs = Ks + N * DPS;
+    TS *Gs = Vs + N * DPS;  // dO
     const int b = blockIdx.x / NH, hh = blockIdx.x % NH;
     const float *base = QKV + (size_t)b * N * 3 * D;
-    stage_rows<DH>(Qs, base + hh * DH, N, 3 * D);
-    stage_rows<DH>(Ks, base + D + hh * DH, N, 3 * D);
-    stage_rows<DH>(Vs, base + 2 * D + hh * DH, N, 3 * D);
-    stage_rows<DH>(Gs, dO + (size_t)b * N * D + hh * DH, N, D);
+    stage_rows_t<DH, TS>(Qs, base + hh * DH, N, 3 * D);
+    stage_rows_t<DH, TS>(Ks, base + D + hh * DH, N, 3 * D);
+    stage_rows_t<DH, TS>(Vs, base + 2 * D + hh * DH, N, 3 * D);
+    stage_rows_t<DH, TS>(Gs, dO + (size_t)b * N * D + hh * DH, N, D);
     stage_rows<DH>(Os, O + (size_t)b * N * D + hh * DH, N, D);
     for (int t = threadIdx.x; t < N; t += blockDim.x) Ls[t] = LSE[((size_t)b * N + t) * NH + hh];
     __syncthreads();
     const float scale = rsqrtf((float)DH);
     for (int t = threadIdx.x; t < N; t += blockDim.x) {
-        float dd = 0.f;
-#pragma unroll
-        for (int j = 0; j < DH; ++j) dd += Gs[t * DP + j] * Os[t * DP + j];
-        Ds[t] = dd;
+        float gr[DH], orr[DH];
+        row_regs_t<DH>(Gs + t * DPS, gr);
+        row_regs<DH>(Os + t * DP, orr);
+        Ds[t] = dot_regs<DH>(gr, orr);
     }
     __syncthreads();
     // out_part 0/1/2 = q/k/v columns of dQKV: coalesced float4 rows from Os
@@ -940,10 +994,11 @@ attn_bwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ O,
     // dQ_t = scale * sum_k P_tk (dP_tk - D_t) k_k
     for (int t = threadIdx.x; t < N; t += blockDim.x) {
         float q[DH], g[DH], dq[DH];
+        row_regs_t<DH>(Qs + t * DPS, q);
+        row_regs_t<DH>(Gs + t * DPS, g);
 #pragma unroll
         for (int j = 0; j < DH; ++j) {
-            q[j] = Qs[t * DP + j] * scale;
-            g[j] = Gs[t * DP + j];
+            q[j] *= scale;
             dq[j] = 0.f;
         }
         const float lse = Ls[t], dd = Ds[t];
@@ -953,8 +1008,8 @@ attn_bwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ O,
         for (int i = 0; i < nk; ++i) {
             const int k = i < n_sink ? i : band_lo + (i - n_sink);
             float kr[DH], vr[DH];  // each row read once, with 128-bit loads
-            row_regs<DH>(Ks + k * DP, kr);
-            row_regs<DH>(Vs + k * DP, vr);
+            row_regs_t<DH>(Ks + k * DPS, kr);
+            row_regs_t<DH>(Vs + k * DPS, vr);
             const float p = __expf(dot_regs<DH>(q, kr) - lse);
             const float ds = p * (dot_regs<DH>(g, vr) - dd) * scale;
 #pragma unroll
@@ -975,17 +1030,18 @@ attn_bwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ O,
     int kk_i = 0;
     for (int k = k_band0 + threadIdx.x; k < N; k += blockDim.x, ++kk_i) {
         float key[DH], val[DH], dk[DH], dv[DH];
+        row_regs_t<DH>(Ks + k * DPS, key);
+        row_regs_t<DH>(Vs + k * DPS, val);
 #pragma unroll
         for (int j = 0; j < DH; ++j) {
-            key[j] = Ks[k * DP + j] * scale;
-            val[j] = Vs[k * DP + j];
+            key[j] *= scale;
             dk[j] = dv[j] = 0.f;
         }
         const int t_hi = min(N - 1, k + W);
         for (int t = k; t <= t_hi; ++t) {
             float qr[DH], gr[DH];
-            row_regs<DH>(Qs + t * DP, qr);
-            row_regs<DH>(Gs + t * DP, gr);
+            row_regs_t<DH>(Qs + t * DPS, qr);
+            row_regs_t<DH>(Gs + t * DPS, gr);
             const float p = __expf(dot_regs<DH>(key, qr) - Ls[t]);
             const float ds = p * (dot_regs<DH>(val, gr) - Ds[t]) * scale;
 #pragma unroll
@@ -1002,16 +1058,17 @@ attn_bwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ O,
     }
     for (int k = warp; k < k_band0; k += nw) {
         float key[DH], val[DH], dk[DH], dv[DH];
+        row_regs_t<DH>(Ks + k * DPS, key);
+        row_regs_t<DH>(Vs + k * DPS, val);
 #pragma unroll
         for (int j = 0; j < DH; ++j) {
-            key[j] = Ks[k * DP + j] * scale;
-            val[j] = Vs[k * DP + j];
+            key[j] *= scale;
             dk[j] = dv[j] = 0.f;
         }
         for (int t = k + lane; t < N; t += 32) {
             float qr[DH], gr[DH];
-            row_regs<DH>(Qs + t * DP, qr);
-            row_regs<DH>(Gs + t * DP, gr);
+            row_regs_t<DH>(Qs + t * DPS, qr);
+            row_regs_t<DH>(Gs + t * DPS, gr);
             const float p = __expf(dot_regs<DH>(key, qr) - Ls[t]);
             const float ds = p * (dot_regs<DH>(val, gr) - Ds[t]) * scale;
 #pragma unroll
@@ -1025,13 +1082,15 @@ attn_bwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ O,
             dk[j] = wsum(dk[j]);
             dv[j] = wsum(dv[j]);
         }
-        // dK to the output buffer; dV parked in row k of Vs, which nothing
-        // reads again (the dQ phase is over and key k is owned by this warp)
+        // dK to the output buffer; dV parked in row k of Vs (FP32 model: nothing
+        // reads it again, the dQ phase is over and key k is owned by this warp)
+        // or of the FP32 rows Pk (BF16 model)
         if (lane == 0)
 #pragma unroll
             for (int j = 0; j < DH; ++j) {
                 Os[k * DP + j] = dk[j];
-                Vs[k * DP + j] = dv[j];
+                if constexpr (kF32) Vs[k * DPS + j] = dv[j];
+                else Pk[k * DP + j] = dv[j];
             }
     }
     flush(1);
@@ -1043,31 +1102,46 @@ attn_bwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ O,
     for (int k = warp; k < k_band0; k += nw)
         if (lane == 0)
 #pragma unroll
-            for (int j = 0; j < DH; ++j) Os[k * DP + j] = Vs[k * DP + j];
+            for (int j = 0; j < DH; ++j) {
+                if constexpr (kF32) Os[k * DP + j] = Vs[k * DPS + j];
+                else Os[k * DP + j] = Pk[k * DP + j];
+            }
     flush(2);
 }
 
 constexpr size_t kAttnSmemMax = 200 * 1024;
 
-template <int DH>
+template <int DH, typename TS>
 size_t attn_bwd_smem_bytes(int N)
 {
-    // Q, K, V, dO, O/out rows + LSE, D.  The backward keeps at most two band
-    // keys' dV per thread in registers, so it serves N <= 512 (256 threads).
+    // Q, K, V, dO rows (TS) + O/out rows, LSE, D (+ sink dV rows for BF16).
+    // The backward keeps at most two band keys' dV per thread in registers,
+    // so it serves N <= 512 (256 threads).
     if (N > 512) return (size_t)1 << 40;
-    return ((size_t)5 * N * (DH + 4) + 2 * N) * sizeof(float);
+    const size_t f32 = (((size_t)(sizeof(TS) == 4 ? 1 : 2) * N * (DH + 4) + 2 * N + 3) & ~(size_t)3) *
+                       sizeof(float);
+    return f32 + (size_t)4 * N * Pitch<DH, TS>::value * sizeof(TS);
+}
+
+template <int DH, typename TS>
+void attn_fwd_t(const float *QKV, const float *Hin, float *O, float *Hmid, float *LSE, int Bc,
+                const sg_config &c, cudaStream_t st)
+{
+    const size_t fwd_smem = (size_t)c.N * (DH + 4) * sizeof(float) +
+                            (size_t)2 * c.N * Pitch<DH, TS>::value * sizeof(TS);
+    cudaFuncSetAttribute(attn_fwd_smem_kernel<DH, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)fwd_smem);
+    attn_fwd_smem_kernel<DH, TS><<<(unsigned)(Bc * c.n_heads), 256, fwd_smem, ::sg::counted(st)>>>(
+        QKV, Hin, O, Hmid, LSE, c.N, c.d, c.n_heads, c.mask_kind, c.W, c.S);
 }
 
 template <int DH>
 void attn_fwd(const float *QKV, const float *Hin, float *O, float *Hmid, float *LSE, int Bc,
               const sg_config &c, cudaStream_t st)
 {
-    const size_t fwd_smem = (size_t)3 * c.N * (DH + 4) * sizeof(float);
-    if (attn_bwd_smem_bytes<DH>(c.N) <= kAttnSmemMax) {
-        cudaFuncSetAttribute(attn_fwd_smem_kernel<DH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)fwd_smem);
-        attn_fwd_smem_kernel<DH><<<(unsigned)(Bc * c.n_heads), 256, fwd_smem, ::sg::counted(st)>>>(
-            QKV, Hin, O, Hmid, LSE, c.N, c.d, c.n_heads, c.mask_kind, c.W, c.S);
+    if (attn_bwd_smem_bytes<DH, float>(c.N) <= kAttnSmemMax) {
+        if (c.precision == SG_BF16) attn_fwd_t<DH, __nv_bfloat16>(QKV, Hin, O, Hmid, LSE, Bc, c, st);
+        else attn_fwd_t<DH, float>(QKV, Hin, O, Hmid, LSE, Bc, c, st);
         return;
     }
     const int warps = Bc * c.n_heads * ((c.N + 31) / 32);
@@ -1079,12 +1153,16 @@ template <int DH>
 void attn_bwd(const float *QKV, const float *O, const float *dO, const float *LSE, float *dQKV,
               float *Dt, int Bc, const sg_config &c, cudaStream_t st)
 {
-    const size_t smem = attn_bwd_smem_bytes<DH>(c.N);
-    if (smem <= kAttnSmemMax) {
-        cudaFuncSetAttribute(attn_bwd_smem_kernel<DH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        attn_bwd_smem_kernel<DH><<<(unsigned)(Bc * c.n_heads), 256, smem, ::sg::counted(st)>>>(
-            QKV, O, dO, LSE, dQKV, c.N, c.d, c.n_heads, c.mask_kind, c.W, c.S);
+    if (attn_bwd_smem_bytes<DH, float>(c.N) <= kAttnSmemMax) {
+        auto go = [&](auto kern, size_t smem) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            kern<<<(unsigned)(Bc * c.n_heads), 256, smem, ::sg::counted(st)>>>(
+                QKV, O, dO, LSE, dQKV, c.N, c.d, c.n_heads, c.mask_kind, c.W, c.S);
+        };
+        if (c.precision == SG_BF16)
+            go(attn_bwd_smem_kernel<DH, __nv_bfloat16>, attn_bwd_smem_bytes<DH, __nv_bfloat16>(c.N));
+        else
+            go(attn_bwd_smem_kernel<DH, float>, attn_bwd_smem_bytes<DH, float>(c.N));
         return;
     }
     const int warps = Bc * c.n_heads * ((c.N + 31) / 32);
