@@ -100,7 +100,8 @@ __device__ __forceinline__ void row_epilogue(const RowGemm &g, const float (&v)[
     }
 }
 
-constexpr int kEpiWarps = 8;  // two epilogue warps per TMEM lane quadrant
+constexpr int kEpiWarps = 16;  // four epilogue warps per TMEM lane quadrant
+constexpr int kEpiPerQuad = kEpiWarps / 4;
 
 template <int EPI>
 __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) row_gemm_kernel(const __grid_constant__ RowGemm g)
@@ -170,7 +171,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) row_gemm_kernel(const 
         if (!ok) atomicExch(g.err, 12);
     } else if (warp >= 2) {
         const int q = warp & 3;             // TMEM lane quadrant of this warp
-        const int half = (warp - 2) >> 2;   // which alternate 32-column chunks
+        const int part = (warp - 2) >> 2;   // which interleaved 32-column chunks
         const int row = 32 * q + lane;
         for (int64_t i = 0; i < my_n; ++i) {
             const int acc = (int)(i & 1);
@@ -182,7 +183,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) row_gemm_kernel(const 
             tc::tc_fence_after();
             const int64_t r = rb * 128 + row;
             const bool valid = r < g.R;
-            for (int c = half; c < g.N / 32; c += 2) {
+            for (int c = part; c < g.N / 32; c += kEpiPerQuad) {
                 float v[32];
                 tc::tmem_ld32(tmem + acc * 256 + ((uint32_t)(32 * q) << 16) + 32 * c, v);
                 tc::tmem_wait_ld();
@@ -298,7 +299,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) tile_gemm_kernel(const
         }
         if (!ok) atomicExch(g.err, 15);
     } else if (warp >= 2) {
-        const int q = warp & 3, half = (warp - 2) >> 2, row = 32 * q + lane;
+        const int q = warp & 3, part = (warp - 2) >> 2, row = 32 * q + lane;
         for (int64_t i = 0; i < my_n; ++i) {
             const int acc = (int)(i & 1);
             const int64_t t = blockIdx.x + i * gridDim.x, rb = t / ncb;
@@ -310,7 +311,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) tile_gemm_kernel(const
             tc::tc_fence_after();
             const int64_t r = rb * 128 + row;
             const bool valid = r < g.R;
-            for (int c = half; c < cols_of(cb) / 32; c += 2) {
+            for (int c = part; c < cols_of(cb) / 32; c += kEpiPerQuad) {
                 float v[32];
                 tc::tmem_ld32(tmem + acc * 256 + ((uint32_t)(32 * q) << 16) + 32 * c, v);
                 tc::tmem_wait_ld();
