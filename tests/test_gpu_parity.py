@@ -78,6 +78,11 @@ BF16_CASES = {
     "ring_d256": (inputs.ModelShape(40, 2, 256, 8, mask_kind=1, W=5, S=3), 200, 1.0),
     "dense_d256": (inputs.ModelShape(24, 1, 256, 8), 130, 1.0),
     "tiny_d256": (inputs.ModelShape(2, 1, 256, 8), 3, 1.0),
+    "one_spin_d128": (inputs.ModelShape(1, 1, 128, 8), 1, 1.0),
+    "one_spin_d256": (inputs.ModelShape(1, 2, 256, 8), 2, 1.0),
+    "one_sample_d64": (inputs.ModelShape(45, 2, 64, 4, mask_kind=1, W=5, S=6), 1, 1.0),
+    # N beyond the three-stage shared-memory budget: the two-stage d = 64 kernel
+    "two_stage_d64": (inputs.ModelShape(5000, 1, 64, 4, mask_kind=1, W=8, S=9), 24, 1.0),
 }
 
 
@@ -154,6 +159,23 @@ def test_bf16_grouped_models_match_oracle(n_models, per_model):
     s1, l1 = single.sample(per_model, seed=99)
     assert np.array_equal(s[:per_model], _np(s1))
     assert np.array_equal(lq[:per_model], _np(l1))
+
+
+def test_bf16_grouped_models_at_the_group_limit():
+    """64 models (the limit) of one sample each, and 65 rejected."""
+    m = inputs.ModelShape(6, 1, 256, 8, mask_kind=1, W=2, S=1)
+    w = inputs.make_group_weights(m, 21, 64)
+    P1 = w.size // 64
+    model = sg.Model(m, w, sg.SG_BF16, n_models=64)
+    spins, logq, flags = model.sample(64, seed=5, with_flags=True)
+    model.check()
+    s, lq, fl = _np(spins), _np(logq), _np(flags)
+    for i in (0, 31, 63):
+        so, lqo, _, _ = oracle_replay(m, w[i * P1:(i + 1) * P1], 5, s, fl, rows=[i])
+        assert np.array_equal(so, s[[i]])
+        assert abs(lqo[0] - lq[i]) <= BF16_LOGQ_TOL * m.N
+    with pytest.raises(sg.SgError):
+        sg.Model(m, inputs.make_group_weights(m, 21, 65), sg.SG_BF16, n_models=65)
 
 
 def test_grouped_models_rejected_outside_d256():
