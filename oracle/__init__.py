@@ -45,7 +45,8 @@ def build(force: bool = False) -> str:
 
 class OrCfg(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in
-                ("N", "n_layers", "d", "n_heads", "d_token", "d_ff", "mask_kind", "W", "S")]
+                ("N", "n_layers", "d", "n_heads", "d_token", "d_ff", "mask_kind", "W", "S",
+                 "patch", "lat_D", "lat_L")]
 
 
 @dataclass
@@ -57,9 +58,12 @@ class ModelCfg:
     n_heads: int
     d_token: int = 2
     d_ff: int = 0          # 0 -> 4 d
-    mask_kind: int = 0     # 0 dense causal, 1 band + sink
+    mask_kind: int = 0     # 0 dense causal, 1 band + sink (W, S in tokens)
     W: int = 0
     S: int = 0
+    patch: int = 1         # spins per token (2^D for a lattice of dimension D)
+    lat_D: int = 0         # lattice of the patch map (0: consecutive spins)
+    lat_L: int = 0
 
     def __post_init__(self):
         if self.d_ff == 0:
@@ -67,7 +71,7 @@ class ModelCfg:
 
     def c(self) -> OrCfg:
         return OrCfg(self.N, self.n_layers, self.d, self.n_heads, self.d_token, self.d_ff,
-                     self.mask_kind, self.W, self.S)
+                     self.mask_kind, self.W, self.S, self.patch, self.lat_D, self.lat_L)
 
 
 _P = ctypes.c_void_p

@@ -41,7 +41,47 @@ typedef struct {
     int32_t mask_kind;  /* 0 = dense causal, 1 = sliding band + sink       */
     int32_t W;          /* band: key k visible to query t iff t-k <= W     */
     int32_t S;          /* sink: keys k < S always visible                 */
+    int32_t patch;      /* spins per token P (0 or 1: one spin per token)  */
+    int32_t lat_D;      /* lattice dimension for the patch map (0: chain)  */
+    int32_t lat_L;      /* lattice side                                     */
 } or_cfg;
+
+/* ------------------------------------------------------------------------ */
+/* Patching (Methods / SI: the EA lattice is cut into non-overlapping        */
+/* patches of 2^D spins, one token per patch, sequence length (L/2)^D).      */
+/* Readings: patches in raster order of the patch grid; bit j of a token is  */
+/* the spin at offset delta = (j & 1, (j >> 1) & 1, ...) from the patch's    */
+/* even corner (x0 fastest), value (sigma + 1) / 2; token = sum_j bit_j 2^j; */
+/* the head is a softmax over K = 2^P classes; without a lattice, token t    */
+/* holds spins tP .. tP + P - 1.  P = 1 is the unpatched model.               */
+/* ------------------------------------------------------------------------ */
+static int n_spt(const or_cfg *c) { return c->patch > 1 ? c->patch : 1; }
+static int n_tok(const or_cfg *c) { return c->N / n_spt(c); }
+static int n_cls(const or_cfg *c) { return 1 << n_spt(c); }
+
+/* site (raster index) of bit j of token t */
+static int patch_site(const or_cfg *c, int t, int j)
+{
+    const int P = n_spt(c);
+    if (P == 1) return t;
+    if (c->lat_D == 0) return t * P + j;
+    const int D = c->lat_D, L = c->lat_L, M = L / 2;
+    int site = 0, stride = 1, rem = t;
+    for (int k = 0; k < D; ++k) {
+        const int pk = rem % M;
+        rem /= M;
+        site += (2 * pk + ((j >> k) & 1)) * stride;
+        stride *= L;
+    }
+    return site;
+}
+
+static int token_of(const or_cfg *c, const int8_t *s, int t)
+{
+    int tok = 0;
+    for (int j = 0; j < n_spt(c); ++j) tok |= ((s[patch_site(c, t, j)] + 1) / 2) << j;
+    return tok;
+}
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), written from the       */
@@ -84,10 +124,10 @@ double or_uniform(uint64_t seed, uint32_t a, uint32_t b, uint32_t stream, uint32
 /* ------------------------------------------------------------------------ */
 /* Weight blob: one flat array (float32 on the device, passed here widened). */
 /* Order (all row-major, "out x in" for linear maps):                        */
-/*   tok[2][d_token]  pos[N][d - d_token]                                   */
+/*   tok[K][d_token]  pos[T][d - d_token]   (K = 2^P classes, T = N / P)     */
 /*   per layer: ln1_g[d] ln1_b[d] Wqkv[3d][d] bqkv[3d] ln2_g[d] ln2_b[d]     */
 /*              W1[d_ff][d] b1[d_ff] W2[d][d_ff] b2[d]                        */
-/*   lnf_g[d] lnf_b[d] Wh[2][d] bh[2]                                        */
+/*   lnf_g[d] lnf_b[d] Wh[K][d] bh[K]                                        */
 /* ------------------------------------------------------------------------ */
 typedef struct {
     double *ln1g, *ln1b, *Wqkv, *bqkv, *ln2g, *ln2b, *W1, *b1, *W2, *b2;
@@ -109,9 +149,9 @@ static size_t layer_params(const or_cfg *c)
 
 int64_t or_param_count(const or_cfg *c)
 {
-    size_t d = (size_t)c->d;
-    return (int64_t)(2 * (size_t)c->d_token + (size_t)c->N * (d - (size_t)c->d_token)
-                     + (size_t)c->n_layers * layer_params(c) + 2 * d + 2 * d + 2);
+    size_t d = (size_t)c->d, K = (size_t)n_cls(c), T = (size_t)n_tok(c);
+    return (int64_t)(K * (size_t)c->d_token + T * (d - (size_t)c->d_token)
+                     + (size_t)c->n_layers * layer_params(c) + 2 * d + K * d + K);
 }
 
 /* Lay views over a double buffer of or_param_count() entries. */
@@ -120,8 +160,8 @@ static void model_views(const or_cfg *c, double *p, or_model *m)
     size_t d = (size_t)c->d, f = (size_t)c->d_ff;
     m->base = p;
     m->n = (size_t)or_param_count(c);
-    m->tok = p; p += 2 * (size_t)c->d_token;
-    m->pos = p; p += (size_t)c->N * (d - (size_t)c->d_token);
+    m->tok = p; p += (size_t)n_cls(c) * c->d_token;
+    m->pos = p; p += (size_t)n_tok(c) * (d - (size_t)c->d_token);
     for (int l = 0; l < c->n_layers; ++l) {
         or_layer *L = &m->L[l];
         L->ln1g = p; p += d;
@@ -137,8 +177,8 @@ static void model_views(const or_cfg *c, double *p, or_model *m)
     }
     m->lnfg = p; p += d;
     m->lnfb = p; p += d;
-    m->Wh = p; p += 2 * d;
-    m->bh = p; p += 2;
+    m->Wh = p; p += (size_t)n_cls(c) * d;
+    m->bh = p; p += (size_t)n_cls(c);
 }
 
 static int model_load(const or_cfg *c, const double *w, or_model *m)
@@ -245,10 +285,10 @@ static double head_logit(const or_cfg *c, const or_model *m, const double *h, do
 /* appended before attention so the query sees its own token.  Returns the   */
 /* logit l_t.  work: at least 6*d + d_ff doubles.                            */
 /* ------------------------------------------------------------------------ */
-static double decode_step(const or_cfg *c, const or_model *m, double *K, double *V, int t,
-                          int tok, double *work)
+static void decode_logits(const or_cfg *c, const or_model *m, double *K, double *V, int t,
+                          int tok, double *work, double *z)
 {
-    int d = c->d, nh = c->n_heads, dh = d / nh, N = c->N;
+    int d = c->d, nh = c->n_heads, dh = d / nh, N = n_tok(c);
     double *h = work, *a = h + d, *qkv = a + d, *o = qkv + 3 * d, *f = o + d;
     double inv_sqrt = 1.0 / sqrt((double)dh);
     embed(c, m, t, tok, h);
@@ -288,7 +328,27 @@ static double decode_step(const or_cfg *c, const or_model *m, double *K, double 
         linear(L->W2, L->b2, f, c->d_ff, d, o);
         for (int i = 0; i < d; ++i) h[i] += o[i];
     }
-    return head_logit(c, m, h, a, NULL, NULL);
+    layernorm(h, m->lnfg, m->lnfb, d, a, NULL, NULL);
+    linear(m->Wh, m->bh, a, d, n_cls(c), z);
+}
+
+/* One spin per token: the logit l_t = z1 - z0 of q(+1 | past) = sigmoid(l). */
+static double decode_step(const or_cfg *c, const or_model *m, double *K, double *V, int t,
+                          int tok, double *work)
+{
+    double z[2];
+    decode_logits(c, m, K, V, t, tok, work, z);
+    return z[1] - z[0];
+}
+
+/* log softmax of z[K] into lp[K] */
+static void log_softmax(const double *z, int K, double *lp)
+{
+    double mx = -INFINITY, s = 0.0;
+    for (int k = 0; k < K; ++k) if (z[k] > mx) mx = z[k];
+    for (int k = 0; k < K; ++k) s += exp(z[k] - mx);
+    const double lse = mx + log(s);
+    for (int k = 0; k < K; ++k) lp[k] = z[k] - lse;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -326,6 +386,41 @@ int or_sample(const or_cfg *c, const double *weights, int64_t B, const int64_t *
 #pragma omp for schedule(dynamic, 1)
 #endif
             for (int64_t b = 0; b < B; ++b) {
+              if (n_spt(c) > 1) {
+                /* patched: a categorical draw over K classes by the inverse
+                 * CDF of u (classes in index order); flagged when u lies
+                 * within flag_band of a CDF boundary */
+                const int T = n_tok(c), Kc = n_cls(c), P = n_spt(c);
+                double z[256], lp[256];
+                double lq = 0.0;
+                int tok = 0; /* start token */
+                for (int t = 0; t < T; ++t) {
+                    decode_logits(c, &m, K, V, t, tok, work, z);
+                    log_softmax(z, Kc, lp);
+                    double u = or_uniform(seed, (uint32_t)(row_ids ? row_ids[b] : b), (uint32_t)t,
+                                          stream, 0);
+                    /* the first class whose cumulative probability exceeds u */
+                    double cdf = 0.0, near = INFINITY;
+                    int k = Kc - 1, found = 0;
+                    for (int j = 0; j < Kc - 1; ++j) {
+                        cdf += exp(lp[j]);
+                        if (fabs(u - cdf) < near) near = fabs(u - cdf);
+                        if (!found && u < cdf) { k = j; found = 1; }
+                    }
+                    size_t bt = (size_t)b * N + t;
+                    if (override_mask && override_mask[bt])
+                        k = token_of(c, override_spins + (size_t)b * N, t);
+                    for (int j = 0; j < P; ++j)
+                        spins[(size_t)b * N + patch_site(c, t, j)] = (int8_t)(((k >> j) & 1) ? 1 : -1);
+                    if (pplus) pplus[bt] = exp(lp[k]);
+                    if (flags) flags[bt] = (uint8_t)(near < flag_band);
+                    lq += lp[k];
+                    tok = k;
+                }
+                logq[b] = lq;
+                continue;
+              }
+              {
                 double lq = 0.0;
                 int tok = 0; /* start token */
                 for (int t = 0; t < N; ++t) {
@@ -344,6 +439,7 @@ int or_sample(const or_cfg *c, const double *weights, int64_t B, const int64_t *
                     tok = (s + 1) / 2;
                 }
                 logq[b] = lq;
+              }
             }
         }
         free(K); free(V); free(work);
@@ -371,6 +467,7 @@ typedef struct {
     double *Hfin;  /* [N][d]                                                  */
     double *Xf, *Rf, *Yf;
     double *logit; /* [N]                                                     */
+    double *z;     /* [T][K] logits of a patched model (NULL when P = 1)      */
 } or_tape;
 
 static int tape_alloc(const or_cfg *c, or_tape *T)
@@ -393,15 +490,17 @@ static int tape_alloc(const or_cfg *c, or_tape *T)
     T->Rf = malloc(N * sizeof(double));
     T->Yf = malloc(N * d * sizeof(double));
     T->logit = malloc(N * sizeof(double));
+    T->z = n_spt(c) > 1 ? malloc((size_t)n_tok(c) * n_cls(c) * sizeof(double)) : NULL;
     return (T->Hin && T->X1 && T->R1 && T->A1 && T->QKV && T->Hmid && T->X2 && T->R2 && T->A2
-            && T->F1 && T->G && T->Hfin && T->Xf && T->Rf && T->Yf && T->logit) ? 0 : -1;
+            && T->F1 && T->G && T->Hfin && T->Xf && T->Rf && T->Yf && T->logit
+            && (n_spt(c) == 1 || T->z)) ? 0 : -1;
 }
 
 static void tape_free(or_tape *T)
 {
     free(T->Hin); free(T->X1); free(T->R1); free(T->A1); free(T->QKV); free(T->Hmid);
     free(T->X2); free(T->R2); free(T->A2); free(T->F1); free(T->G); free(T->Hfin);
-    free(T->Xf); free(T->Rf); free(T->Yf); free(T->logit);
+    free(T->Xf); free(T->Rf); free(T->Yf); free(T->logit); free(T->z);
 }
 
 /* Attention probabilities of query t, head hh over keys 0..t (zero where the
@@ -434,10 +533,10 @@ static void attn_probs(const or_cfg *c, const double *QKV, int t, int hh, double
 static double tf_forward(const or_cfg *c, const or_model *m, const int8_t *s, or_tape *T,
                          double *prob)
 {
-    int N = c->N, d = c->d, f = c->d_ff, nh = c->n_heads, dh = d / nh;
+    int N = n_tok(c), d = c->d, f = c->d_ff, nh = c->n_heads, dh = d / nh;
     size_t Nd = (size_t)N * d;
-    double *H = T->Hfin; /* running residual stream [N][d] */
-    for (int t = 0; t < N; ++t) embed(c, m, t, t == 0 ? 0 : (s[t - 1] + 1) / 2, H + (size_t)t * d);
+    double *H = T->Hfin; /* running residual stream [T][d] */
+    for (int t = 0; t < N; ++t) embed(c, m, t, t == 0 ? 0 : token_of(c, s, t - 1), H + (size_t)t * d);
     for (int l = 0; l < c->n_layers; ++l) {
         const or_layer *L = &m->L[l];
         double *Hin = T->Hin + l * Nd, *X1 = T->X1 + l * Nd, *A1 = T->A1 + l * Nd;
@@ -474,6 +573,19 @@ static double tf_forward(const or_cfg *c, const or_model *m, const int8_t *s, or
         }
     }
     double lq = 0.0;
+    if (n_spt(c) > 1) {  /* log softmax of the token's class */
+        const int Kc = n_cls(c);
+        double lp[256];
+        for (int t = 0; t < N; ++t) {
+            double *z = T->z + (size_t)t * Kc;
+            layernorm(H + (size_t)t * d, m->lnfg, m->lnfb, d, T->Yf + (size_t)t * d,
+                      T->Xf + (size_t)t * d, T->Rf + t);
+            linear(m->Wh, m->bh, T->Yf + (size_t)t * d, d, Kc, z);
+            log_softmax(z, Kc, lp);
+            lq += lp[token_of(c, s, t)];
+        }
+        return lq;
+    }
     for (int t = 0; t < N; ++t) {
         T->logit[t] = head_logit(c, m, H + (size_t)t * d, T->Yf + (size_t)t * d,
                                  T->Xf + (size_t)t * d, T->Rf + t);
@@ -503,7 +615,13 @@ int or_logprob(const or_cfg *c, const double *weights, int64_t B, const int8_t *
 #endif
             for (int64_t b = 0; b < B; ++b) {
                 logq[b] = tf_forward(c, &m, spins + (size_t)b * N, &T, prob);
-                if (pplus)
+                if (pplus && n_spt(c) > 1) {
+                    double lp[256];
+                    for (int t = 0; t < n_tok(c); ++t) {
+                        log_softmax(T.z + (size_t)t * n_cls(c), n_cls(c), lp);
+                        pplus[(size_t)b * N + t] = exp(lp[token_of(c, spins + (size_t)b * N, t)]);
+                    }
+                } else if (pplus)
                     for (int t = 0; t < N; ++t) pplus[(size_t)b * N + t] = sigmoid(T.logit[t]);
             }
         }
@@ -537,7 +655,7 @@ static void layernorm_bwd(const double *dy, const double *xhat, double rstd, con
 static void backward_one(const or_cfg *c, const or_model *m, const int8_t *s, double coeff,
                          or_tape *T, or_model *gm, double *prob, double *dprob, double *buf)
 {
-    int N = c->N, d = c->d, f = c->d_ff, nh = c->n_heads, dh = d / nh;
+    int N = n_tok(c), d = c->d, f = c->d_ff, nh = c->n_heads, dh = d / nh;
     size_t Nd = (size_t)N * d;
     double inv_sqrt = 1.0 / sqrt((double)dh);
     double *dH = buf;                    /* [N][d] gradient w.r.t. residual stream */
@@ -546,8 +664,26 @@ static void backward_one(const or_cfg *c, const or_model *m, const int8_t *s, do
     double *tmp = dQKV + 3 * Nd;         /* [max(d_ff, 3d)] */
     double *dA = tmp + (f > 3 * d ? f : 3 * d); /* [d] */
     memset(dH, 0, Nd * sizeof(double));
+    /* patched head: d log softmax(z)[tok] / dz = onehot(tok) - softmax(z) */
+    for (int t = 0; t < N && n_spt(c) > 1; ++t) {
+        const int Kc = n_cls(c), tok = token_of(c, s, t);
+        double lp[256];
+        log_softmax(T->z + (size_t)t * Kc, Kc, lp);
+        const double *y = T->Yf + (size_t)t * d;
+        for (int i = 0; i < d; ++i) dA[i] = 0.0;
+        for (int k = 0; k < Kc; ++k) {
+            const double dz = coeff * ((k == tok ? 1.0 : 0.0) - exp(lp[k]));
+            gm->bh[k] += dz;
+            for (int i = 0; i < d; ++i) {
+                gm->Wh[(size_t)k * d + i] += dz * y[i];
+                dA[i] += dz * m->Wh[(size_t)k * d + i];
+            }
+        }
+        layernorm_bwd(dA, T->Xf + (size_t)t * d, T->Rf[t], m->lnfg, d, dH + (size_t)t * d,
+                      gm->lnfg, gm->lnfb);
+    }
     /* head: log sigmoid(s l) -> d/dl = s * sigmoid(-s l) */
-    for (int t = 0; t < N; ++t) {
+    for (int t = 0; t < N && n_spt(c) == 1; ++t) {
         double sl = (double)s[t];
         double dl = coeff * sl * sigmoid(-sl * T->logit[t]);
         double dz[2] = {-dl, dl};
@@ -640,7 +776,7 @@ static void backward_one(const or_cfg *c, const or_model *m, const int8_t *s, do
     /* concatenated embedding */
     int dt = c->d_token, dp = d - dt;
     for (int t = 0; t < N; ++t) {
-        int tok = t == 0 ? 0 : (s[t - 1] + 1) / 2;
+        int tok = t == 0 ? 0 : token_of(c, s, t - 1);
         for (int i = 0; i < dt; ++i) gm->tok[tok * dt + i] += dH[(size_t)t * d + i];
         for (int i = 0; i < dp; ++i) gm->pos[(size_t)t * dp + i] += dH[(size_t)t * d + dt + i];
     }
@@ -956,14 +1092,30 @@ static void enum_rec(enum_ctx *x, int t, double lq)
     enum_rec(x, t + 1, lq + log_sigmoid(-l));
 }
 
+/* patched models: the tree has K children per token */
+static void enum_rec_tok(enum_ctx *x, int t, int tok_prev, double lq)
+{
+    const or_cfg *c = x->c;
+    if (t == n_tok(c)) { enum_leaf(x, lq); return; }
+    double z[256], lp[256];
+    decode_logits(c, x->m, x->K, x->V, t, tok_prev, x->work, z);
+    log_softmax(z, n_cls(c), lp);
+    for (int k = 0; k < n_cls(c); ++k) {
+        for (int j = 0; j < n_spt(c); ++j)
+            x->s[patch_site(c, t, j)] = (int8_t)(((k >> j) & 1) ? 1 : -1);
+        enum_rec_tok(x, t + 1, k, lq + lp[k]);
+    }
+}
+
 int or_enumerate(const or_cfg *c, const double *weights, int kind, int D, int L, int periodic,
                  const float *J, double beta, double *out, int n_threads)
 {
     or_model m;
     if (model_load(c, weights, &m)) return -1;
     int N = c->N, d = c->d;
-    int split = N < 6 ? N : 6; /* 2^split independent subtrees */
-    int64_t nsub = (int64_t)1 << split;
+    const int patched = n_spt(c) > 1;
+    int split = N < 6 ? N : 6; /* 2^split independent subtrees (K for a patched model) */
+    int64_t nsub = patched ? (int64_t)n_cls(c) : (int64_t)1 << split;
     double sum_q = 0.0, fq = 0.0, emin = INFINITY;
     double *lzm = (double *)malloc((size_t)nsub * sizeof(double));
     double *lzs = (double *)malloc((size_t)nsub * sizeof(double));
@@ -993,6 +1145,17 @@ int or_enumerate(const or_cfg *c, const double *weights, int kind, int D, int L,
             for (int64_t sub = 0; sub < nsub; ++sub) {
                 x.sum_q = x.sum_q_c = x.fq = x.fq_c = 0.0;
                 x.lz_max = -INFINITY; x.lz_sum = 0.0; x.emin = INFINITY;
+                if (patched) {  /* subtree: the class of token 0 */
+                    double z[256], lp[256];
+                    decode_logits(c, &m, x.K, x.V, 0, 0, x.work, z);
+                    log_softmax(z, n_cls(c), lp);
+                    for (int j = 0; j < n_spt(c); ++j)
+                        x.s[patch_site(c, 0, j)] = (int8_t)(((sub >> j) & 1) ? 1 : -1);
+                    enum_rec_tok(&x, 1, (int)sub, lp[sub]);
+                    lzm[sub] = x.lz_max; lzs[sub] = x.lz_sum;
+                    sq[sub] = x.sum_q; sf[sub] = x.fq; em[sub] = x.emin;
+                    continue;
+                }
                 /* walk the prefix of this subtree: bit t of sub = spin t is -1 */
                 double lq = 0.0;
                 for (int t = 0; t < split; ++t) {

@@ -32,13 +32,24 @@ class ModelShape:
     n_heads: int
     d_token: int = 2
     d_ff: int = 0
-    mask_kind: int = 0     # 0 dense causal, 1 band + sink
+    mask_kind: int = 0     # 0 dense causal, 1 band + sink (W, S counted in tokens)
     W: int = 0
     S: int = 0
+    patch: int = 1         # spins per token P (patching: 2^D spins of a lattice cell)
+    lat_D: int = 0         # lattice of the patch map (0: token t holds spins tP..tP+P-1)
+    lat_L: int = 0
 
     def __post_init__(self):
         if self.d_ff == 0:
             self.d_ff = 4 * self.d
+
+    @property
+    def n_tokens(self) -> int:
+        return self.N // max(1, self.patch)
+
+    @property
+    def n_classes(self) -> int:
+        return 1 << max(1, self.patch)
 
 
 @dataclass
@@ -59,8 +70,8 @@ def _rng(seed: int, salt: int) -> np.random.Generator:
 
 def segments(m: ModelShape):
     """(name, shape, init) for every tensor of the blob, in blob order."""
-    d, f = m.d, m.d_ff
-    segs = [("tok", (2, m.d_token), "normal"), ("pos", (m.N, d - m.d_token), "normal")]
+    d, f, K = m.d, m.d_ff, m.n_classes
+    segs = [("tok", (K, m.d_token), "normal"), ("pos", (m.n_tokens, d - m.d_token), "normal")]
     for l in range(m.n_layers):
         segs += [
             (f"l{l}.ln1_g", (d,), "ones"), (f"l{l}.ln1_b", (d,), "zeros"),
@@ -70,7 +81,7 @@ def segments(m: ModelShape):
             (f"l{l}.W2", (d, f), ("unif", f)), (f"l{l}.b2", (d,), ("unif", f)),
         ]
     segs += [("lnf_g", (d,), "ones"), ("lnf_b", (d,), "zeros"),
-             ("Wh", (2, d), ("unif", d)), ("bh", (2,), ("unif", d))]
+             ("Wh", (K, d), ("unif", d)), ("bh", (K,), ("unif", d))]
     return segs
 
 

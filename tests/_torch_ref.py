@@ -12,9 +12,27 @@ import torch.nn.functional as F
 from paper_2606_22984_gb300 import inputs
 
 
+def patch_sites(m: inputs.ModelShape) -> np.ndarray:
+    """[T, P] raster site of bit j of token t: patches of 2^D sites of a
+    periodic lattice in raster order of the patch grid, bit j at offset
+    (j & 1, (j >> 1) & 1, ...) from the even corner; consecutive spins when
+    there is no lattice."""
+    P = max(1, m.patch)
+    T = m.N // P
+    if P == 1 or m.lat_D == 0:
+        return np.arange(T * P).reshape(T, P)
+    D, L = m.lat_D, m.lat_L
+    M = L // 2
+    grid = np.stack(np.unravel_index(np.arange(T), (M,) * D, order="F"), -1)   # [T, D] patch coords
+    offs = np.array([[(j >> k) & 1 for k in range(D)] for j in range(P)])       # [P, D]
+    coords = 2 * grid[:, None, :] + offs[None, :, :]                            # [T, P, D]
+    return np.ravel_multi_index(tuple(coords[..., k] for k in range(D)), (L,) * D, order="F")
+
+
 def allowed_mask(m: inputs.ModelShape) -> torch.Tensor:
-    t = torch.arange(m.N)[:, None]
-    k = torch.arange(m.N)[None, :]
+    T = m.N // max(1, m.patch)
+    t = torch.arange(T)[:, None]
+    k = torch.arange(T)[None, :]
     causal = k <= t
     if m.mask_kind == 0:
         return causal
@@ -29,11 +47,15 @@ def logq(m: inputs.ModelShape, w: torch.Tensor, spins: np.ndarray) -> torch.Tens
         return w[o:o + int(np.prod(shape))].view(*shape)
 
     s = torch.as_tensor(np.asarray(spins, dtype=np.int64))
-    B, N = s.shape
+    B = s.shape[0]
     d, nh = m.d, m.n_heads
     dh = d // nh
+    sites = torch.as_tensor(patch_sites(m))                       # [T, P]
+    N = sites.shape[0]
+    bits = (s[:, sites] + 1) // 2                                 # [B, T, P]
+    tok = (bits * (2 ** torch.arange(sites.shape[1]))).sum(-1)    # [B, T]
     tok_in = torch.zeros(B, N, dtype=torch.int64)
-    tok_in[:, 1:] = (s[:, :-1] + 1) // 2
+    tok_in[:, 1:] = tok[:, :-1]
     h = torch.cat([P("tok")[tok_in], P("pos")[None].expand(B, N, d - m.d_token)], dim=-1)
     mask = allowed_mask(m)
     for l in range(m.n_layers):
@@ -48,5 +70,7 @@ def logq(m: inputs.ModelShape, w: torch.Tensor, spins: np.ndarray) -> torch.Tens
                          P(f"l{l}.b2"))
     y = F.layer_norm(h, (d,), P("lnf_g"), P("lnf_b"), eps=1e-5)
     z = F.linear(y, P("Wh"), P("bh"))
+    if max(1, m.patch) > 1:
+        return torch.log_softmax(z, -1).gather(-1, tok[..., None])[..., 0].sum(-1)
     ell = z[..., 1] - z[..., 0]
     return F.logsigmoid(s.to(torch.float64) * ell).sum(-1)

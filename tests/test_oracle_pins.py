@@ -552,3 +552,81 @@ def test_muon_step_matrices_and_adamw_rest():
     # torch applies the decay as w (1 - lr wd) before the Adam step: the same to O(lr^2 wd)
     assert np.allclose(w[~is_mat], p.detach().numpy(), atol=1e-7)
     assert np.all(mom[~is_mat] == 0)
+
+
+# --------------------------------------------------------------------------
+# Patching: 2^D spins per token, softmax over 2^(2^D) classes
+# --------------------------------------------------------------------------
+
+PATCHED = [
+    inputs.ModelShape(16, 2, 16, 2, d_ff=32, mask_kind=1, W=2, S=3, patch=4, lat_D=2, lat_L=4),
+    inputs.ModelShape(8, 1, 8, 2, d_ff=16, patch=2),                       # chain, 4 classes
+    inputs.ModelShape(8, 1, 8, 2, d_ff=16, patch=8, lat_D=3, lat_L=2),     # one 2x2x2 patch
+]
+
+
+@pytest.mark.parametrize("m", PATCHED)
+def test_patched_model_matches_torch_and_is_normalised(m):
+    """Teacher-forced log q against the torch composition (tokens from the
+    patch map, K-way head); sampled = teacher-forced; sum over all 2^N
+    configurations of q = 1 by enumeration; F_q >= F."""
+    w = inputs.make_weights(m, 13, scale=1.3)
+    spins = inputs.random_spins(6, m.N, 3)
+    lq = oracle.logprob(ocfg(m), w, spins)
+    ref = _torch_ref.logq(m, torch.tensor(w, dtype=torch.float64), spins).numpy()
+    assert np.allclose(lq, ref, rtol=1e-12, atol=1e-12)
+    s, lqs, _, _ = oracle.sample(ocfg(m), w, 20, seed=4)
+    assert np.allclose(oracle.logprob(ocfg(m), w, s), lqs, rtol=1e-12, atol=1e-12)
+    inst = inputs.make_ea(2, 4, 1, pm=True) if m.N == 16 else inputs.make_sk(m.N, 2)
+    ex = oracle.enumerate_exact(ocfg(m), w, inst, 0.8)
+    assert abs(ex["sum_q"] - 1.0) < 1e-12
+    assert ex["Fq"] >= ex["F"] - 1e-12
+
+
+def test_patched_zero_model_is_uniform():
+    m = PATCHED[0]
+    w = inputs.make_weights(m, 1) * 0.0
+    o = inputs.offsets(m)
+    for name in o:
+        if name.endswith("_g"):
+            off, shape = o[name]
+            w[off:off + int(np.prod(shape))] = 1.0
+    s, lq, _, _ = oracle.sample(ocfg(m), w, 5, seed=2)
+    assert np.allclose(lq, -m.N * math.log(2), rtol=0, atol=1e-12)
+
+
+def test_patch_bits_land_on_the_patch_map():
+    """A head bias that is a sum over bits, everything else zero: the classes
+    factorise, bit j is +1 with probability sigmoid(a_j), and every site
+    carries the marginal of its bit under the patch map (2D lattice L=4)."""
+    m = PATCHED[0]
+    w = np.zeros(inputs.param_count(m), np.float32)
+    o = inputs.offsets(m)
+    for name in o:
+        if name.endswith("_g"):
+            off, shape = o[name]
+            w[off:off + int(np.prod(shape))] = 1.0
+    a = np.array([1.2, -0.7, 0.3, -1.6])
+    off, _ = o["bh"]
+    w[off:off + 16] = [sum(a[j] for j in range(4) if (k >> j) & 1) for k in range(16)]
+    s, _, _, _ = oracle.sample(ocfg(m), w, 40000, seed=8)
+    sites = _torch_ref.patch_sites(m)
+    p1 = 1 / (1 + np.exp(-a))
+    mean = s.mean(0)
+    for t in range(sites.shape[0]):
+        for j in range(4):
+            assert abs(mean[sites[t, j]] - (2 * p1[j] - 1)) < 0.02
+    # the four bits of a patch are one 2x2 cell of the lattice
+    x, y = sites % 4, sites // 4
+    assert np.all(x.max(1) - x.min(1) == 1) and np.all(y.max(1) - y.min(1) == 1)
+
+
+@pytest.mark.parametrize("m", PATCHED[:2])
+def test_patched_grad_matches_torch_autograd(m):
+    w = inputs.make_weights(m, 21)
+    s = inputs.random_spins(4, m.N, 6)
+    c = np.array([0.3, -1.1, 0.7, 0.25])
+    g, _ = oracle.grad(ocfg(m), w, s, c)
+    wt = torch.tensor(w, dtype=torch.float64, requires_grad=True)
+    (torch.tensor(c) * _torch_ref.logq(m, wt, s)).sum().backward()
+    assert np.allclose(g, wt.grad.numpy(), rtol=1e-9, atol=1e-11)
