@@ -22,11 +22,12 @@
  *     al., SC'11) keyed by the 64-bit seed; the uniform of counter
  *     (a, b, stream, e) is ((x0 >> 8) + 0.5) * 2^-24.
  *
- * Weight blob (sg_param_count floats), row-major, linear maps "out x in":
- *   tok[2][d_token]  pos[N][d - d_token]
+ * Weight blob (sg_param_count floats), row-major, linear maps "out x in";
+ * K = 2^P token classes and T = N / P tokens (K = 2, T = N without patching):
+ *   tok[K][d_token]  pos[T][d - d_token]
  *   per layer: ln1_g[d] ln1_b[d] Wqkv[3d][d] bqkv[3d] ln2_g[d] ln2_b[d]
  *              W1[d_ff][d] b1[d_ff] W2[d][d_ff] b2[d]
- *   lnf_g[d] lnf_b[d] Wh[2][d] bh[2]
+ *   lnf_g[d] lnf_b[d] Wh[K][d] bh[K]
  * Rows of Wqkv: queries, keys, values, each head-major (head h owns
  * columns h*d_h .. h*d_h + d_h - 1 of its block).
  */
@@ -79,13 +80,28 @@ typedef enum { SG_SK_DENSE = 0, SG_EA_LATTICE = 1 } sg_instance_kind;
  *              sg_sample, sample b of B uses model b / (B / n).  Grouped
  *              models are served by the BF16 decode for d = 256; other calls
  *              return SG_EUNSUPPORTED for n > 1.
- * Key position k holds the token of spin k-1; key 0 holds the start token 0.
+ *   patch      spins per token P (patching, Methods: the EA lattice cut into
+ *              cells of 2^D spins, one token per cell).  0 or 1: one spin per
+ *              token.  P > 1: the head is a softmax over K = 2^P classes and
+ *              the draw is categorical, class k chosen by the inverse CDF of
+ *              the uniform (classes in index order); token = sum_j bit_j 2^j,
+ *              bit_j = (s + 1) / 2 of the cell's j-th spin.  W, S count tokens.
+ *   lat_D, lat_L  the patch map: lat_D = 0: token t holds spins tP .. tP+P-1;
+ *              lat_D > 0 (P = 2^lat_D, even lat_L, N = lat_L^lat_D): tokens are
+ *              the cells of the lattice in raster order of the cell grid, bit
+ *              j at offset (j & 1, (j >> 1) & 1, ...) from the cell's even
+ *              corner (x0 fastest).  Spins stay in lattice raster order.
+ *              Patched models are served by the FP32 decode, the BF16 decode
+ *              for d = 64 and the teacher-forced pass; others return
+ *              SG_EUNSUPPORTED.
+ * Key position k holds the token of position k-1; key 0 holds the start token 0.
  */
 typedef struct {
     int32_t N, n_layers, d, n_heads, d_token, d_ff;
     int32_t mask_kind, W, S;
     int32_t precision;
     int32_t n_models;
+    int32_t patch, lat_D, lat_L;
 } sg_config;
 
 typedef struct sg_model sg_model;
@@ -137,9 +153,11 @@ sg_status sg_model_check(sg_model *m, sg_stream stream);
  * configurations in one persistent kernel launch.
  *   spins  dev int8 [B][N]   out: sampled spins.
  *   logq   dev float [B]     out: log q(sigma) = sum_t log sigmoid(sigma_t l_t).
- *   flags  dev uint32 [B][(N+31)/32] or NULL   out: bit t set where the draw
- *          was flagged, |p+ - u| < flag_band (flag_band <= 0 selects 1e-5 for
- *          FP32 and 1e-2 for BF16).
+ *   flags  dev uint32 [B][(T+31)/32] or NULL   out: bit t set where the draw
+ *          of token position t was flagged, |p+ - u| < flag_band (patched:
+ *          u within flag_band of a boundary of the cumulative class
+ *          probabilities); flag_band <= 0 selects 1e-5 for FP32 and 1e-2 for
+ *          BF16.  T = N / patch (T = N without patching).
  * Sample b, step t uses u = uniform(seed, counter (b, t, stream_id, 0)) and
  * takes sigma_t = +1 iff u < p+ = sigmoid(l_t), l_t = z1 - z0 of the output
  * head.  beta is recorded only (sampling does not depend on it).

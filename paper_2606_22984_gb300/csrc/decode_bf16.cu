@@ -96,6 +96,7 @@ struct DecodeArgs {
     size_t stride_bf;             // bytes between consecutive models' packed chunks
     int max_keys;                 // capacity of the per-step key-offset table
     int kv_stages;                // d = 64: keys in flight per thread (2 or 3)
+    int P, K, Nspins, latD, latL; // patching (d = 64 decode): spins per token, classes
 };
 
 // Element (r, k) of a core-matrix tile as a 16-byte group store of 8 bf16.
@@ -793,6 +794,61 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d64_kernel(const __grid_co
             const float mean = t1 * (1.0f / D);
             const float var = fmaxf(t2 * (1.0f / D) - mean * mean, 0.f);
             const float rs = 1.0f / sqrtf(var + 1e-5f);
+            if (a.P > 1) {
+                // patched: K logits; this quarter's partial sums over its 16
+                // dims go to the A2 tile (idle until the next step's attention)
+                float y[DH];
+#pragma unroll
+                for (int j = 0; j < DH; ++j) {
+                    const int d = DH * qr + j;
+                    y[j] = (h[j] - mean) * rs * __ldg(a.w + a.o.lnfg + d) + __ldg(a.w + a.o.lnfb + d);
+                }
+                float *zp = reinterpret_cast<float *>(A2buf);  // [4][128][K]
+                for (int k = 0; k < a.K; ++k) {
+                    float zk = 0.f;
+#pragma unroll
+                    for (int j = 0; j < DH; ++j) zk += y[j] * __ldg(a.w + a.o.Wh + (size_t)k * D + DH * qr + j);
+                    zp[((size_t)qr * kRows + r) * a.K + k] = zk;
+                }
+                __syncthreads();
+                if (qr == 0) {
+                    auto logit = [&](int k) {
+                        float zk = __ldg(a.w + a.o.bh + k);
+#pragma unroll
+                        for (int q4 = 0; q4 < 4; ++q4) zk += zp[((size_t)q4 * kRows + r) * a.K + k];
+                        return zk;
+                    };
+                    float mx = -INFINITY;
+                    for (int k = 0; k < a.K; ++k) mx = fmaxf(mx, logit(k));
+                    float se = 0.f;
+                    for (int k = 0; k < a.K; ++k) se += expf(logit(k) - mx);
+                    const float lse = mx + logf(se);
+                    const float u = philox_uniform(a.seed, (uint32_t)b, (uint32_t)t, a.sid, 0u);
+                    float cdf = 0.f, near = INFINITY;
+                    int cls = a.K - 1;
+                    bool found = false;
+                    for (int k = 0; k < a.K - 1; ++k) {
+                        cdf += expf(logit(k) - lse);
+                        near = fminf(near, fabsf(u - cdf));
+                        if (!found && u < cdf) {
+                            cls = k;
+                            found = true;
+                        }
+                    }
+                    const float zc = logit(cls);
+                    lq += zc - lse;
+                    tok = cls;
+                    if (active) {
+                        for (int j = 0; j < a.P; ++j)
+                            a.spins[(size_t)b * a.Nspins + patch_site(t, j, a.P, a.latD, a.latL)] =
+                                (int8_t)(((cls >> j) & 1) ? 1 : -1);
+                        if (a.flags && near < a.band)
+                            a.flags[(size_t)b * nfw + (t >> 5)] |= 1u << (t & 31);
+                        if (!isfinite(zc - lse)) atomicOr(a.err, 4);
+                    }
+                }
+                continue;
+            }
             float z0 = 0.f, z1 = 0.f;
 #pragma unroll
             for (int j = 0; j < DH; ++j) {
@@ -1744,7 +1800,8 @@ sg_status launch_pack_bf16(sg_model *m, cudaStream_t st)
 sg_status launch_decode_bf16(sg_model *m, int64_t B, uint64_t seed, uint32_t sid, float band,
                              int8_t *spins, float *logq, uint32_t *flags, cudaStream_t st)
 {
-    const sg_config &c = m->cfg;
+    const sg_config &c = m->seq;  // N = tokens
+    const int P = spins_per_token(c);
     const bool d64 = c.d == 64 && c.n_heads == 4 && c.d_ff == 256 && c.d_token <= 32;
     const bool d128 = c.d == 128 && c.n_heads == 8 && c.d_ff == 512 && c.d_token <= 32;
     const bool d256 = c.d == 256 && c.n_heads == 8 && c.d_ff == 1024 && c.d_token <= 64;
@@ -1753,6 +1810,9 @@ sg_status launch_decode_bf16(sg_model *m, int64_t B, uint64_t seed, uint32_t sid
                                      "(128, 8, 512) and (256, 8, 1024)");
     if (m->n_models > 1 && !d256)
         return fail(SG_EUNSUPPORTED, "grouped models are served by the d = 256 decode");
+    if (P > 1 && !(d64 && c.d_token <= 16 && (1 << P) <= 32))
+        return fail(SG_EUNSUPPORTED, "patched BF16 decode is built for d = 64 with at most 32 "
+                                     "classes (2D cells); use SG_FP32");
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1814,6 +1874,11 @@ sg_status launch_decode_bf16(sg_model *m, int64_t B, uint64_t seed, uint32_t sid
     a.stride_wt = m->pack.total;
     a.stride_bf = (size_t)kChunks256 * kChunk256 * c.n_layers;
     a.max_keys = g.nslots;
+    a.P = P;
+    a.K = 1 << P;
+    a.Nspins = m->cfg.N;
+    a.latD = c.lat_D;
+    a.latL = c.lat_L;
     if (d256) {
         const size_t smem256 = 2 * (size_t)kRows * 256 * 2 + (size_t)kStages256 * kChunk256 +
                                8 * kRows * 2 * sizeof(float) + (size_t)g.nslots * sizeof(uint32_t);

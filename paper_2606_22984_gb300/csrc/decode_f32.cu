@@ -207,7 +207,8 @@ decode_f32_kernel(const __grid_constant__ DevModel m, int64_t B, uint64_t seed, 
     constexpr int NH = D / DH;
     constexpr int MS = 256 / NH;
     constexpr int RS = D + 4;  // row stride of h / a (floats); RS/4 odd
-    const int US = (3 * D > m.dff ? 3 * D : m.dff) + 4;
+    int US = (3 * D > m.dff ? 3 * D : m.dff) + 4;
+    if (US < m.K + 4) US = m.K + 4;
 
     extern __shared__ float4 smem4[];
     float *h = reinterpret_cast<float *>(smem4);
@@ -317,7 +318,49 @@ decode_f32_kernel(const __grid_constant__ DevModel m, int64_t B, uint64_t seed, 
             __syncthreads();
         }
         // output head and the draw
-        for (int r = warp; r < MS; r += 8) {
+        for (int r = warp; r < MS && m.P > 1; r += 8) {
+            // patched: K logits (a softmax over the token classes), the class
+            // by the inverse CDF of u; the cell's P spins land on the patch map
+            ln_row<D>(h + r * RS, m.w + m.o.lnfg, m.w + m.o.lnfb, a + r * RS, lane);
+            __syncwarp();
+            float *z = u + r * US;
+            for (int k = 0; k < m.K; ++k) {
+                float zk = 0.f;
+                for (int j = lane; j < D; j += 32) zk += a[r * RS + j] * __ldg(m.w + m.o.Wh + (size_t)k * D + j);
+                zk = warp_sum(zk);
+                if (lane == 0) z[k] = zk + __ldg(m.w + m.o.bh + k);
+            }
+            __syncwarp();
+            if (lane == 0) {
+                float mx = -INFINITY;
+                for (int k = 0; k < m.K; ++k) mx = fmaxf(mx, z[k]);
+                float se = 0.f;
+                for (int k = 0; k < m.K; ++k) se += expf(z[k] - mx);
+                const float lse = mx + logf(se);
+                const int64_t b = b0 + r;
+                const float uu = philox_uniform(seed, (uint32_t)b, (uint32_t)t, sid, 0u);
+                float cdf = 0.f, near = INFINITY;
+                int cls = m.K - 1;
+                bool found = false;
+                for (int k = 0; k < m.K - 1; ++k) {
+                    cdf += expf(z[k] - lse);
+                    near = fminf(near, fabsf(uu - cdf));
+                    if (!found && uu < cdf) {
+                        cls = k;
+                        found = true;
+                    }
+                }
+                lq[r] += z[cls] - lse;
+                tok[r] = cls;
+                if (b < B) {
+                    for (int j = 0; j < m.P; ++j)
+                        spins[(size_t)b * m.Nspins + patch_site(t, j, m.P, m.latD, m.latL)] =
+                            (int8_t)(((cls >> j) & 1) ? 1 : -1);
+                    if (flags && near < band) flags[(size_t)b * nfw + (t >> 5)] |= 1u << (t & 31);
+                }
+            }
+        }
+        for (int r = warp; r < MS && m.P == 1; r += 8) {
             ln_row<D>(h + r * RS, m.w + m.o.lnfg, m.w + m.o.lnfb, a + r * RS, lane);
             __syncwarp();
             float z0 = 0.f, z1 = 0.f;
@@ -355,17 +398,19 @@ static sg_status run_decode(sg_model *m, int64_t B, uint64_t seed, uint32_t sid,
 {
     constexpr int NH = D / DH;
     constexpr int MS = 256 / NH;
-    const sg_config &c = m->cfg;
+    const sg_config &c = m->seq;  // N = tokens
+    const int P = spins_per_token(c), K = 1 << P;
     const RingGeom g = ring_geom(c.mask_kind, c.N, c.W, c.S);
     const int64_t tiles = (B + MS - 1) / MS;
     const size_t kv_bytes = (size_t)tiles * c.n_layers * g.nslots * 2 * D * MS * sizeof(float);
     SG_TRY(ensure_buffer(&m->kv, &m->kv_bytes, kv_bytes));
-    const int US = (3 * D > c.d_ff ? 3 * D : c.d_ff) + 4;
+    int US = (3 * D > c.d_ff ? 3 * D : c.d_ff) + 4;
+    if (US < K + 4) US = K + 4;  // the head's K logits per sample reuse u
     const size_t smem = ((size_t)MS * (2 * (D + 4) + US) + 2 * MS) * sizeof(float);
     auto kern = decode_f32_kernel<D, DH>;
     SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     DevModel dm{c.N, c.n_layers, c.d, c.n_heads, c.d_token, c.d_ff, c.mask_kind, c.W, c.S,
-                m->w, m->wt, m->off, m->pack};
+                P, K, m->cfg.N, c.lat_D, c.lat_L, m->w, m->wt, m->off, m->pack};
     kern<<<(unsigned)tiles, 256, smem, ::sg::counted(st)>>>(dm, B, seed, sid, band, spins, logq, flags,
                                              (float *)m->kv);
     return check_launch("decode_f32_kernel");
@@ -433,7 +478,7 @@ static sg_status run_decode_noalloc(const sg_config &c, const float *w, const Bl
     auto kern = decode_f32_kernel<D, DH>;
     SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     DevModel dm{c.N, c.n_layers, c.d, c.n_heads, c.d_token, c.d_ff, c.mask_kind, c.W, c.S,
-                w, wt, off, pack};
+                1, 2, c.N, 0, 0, w, wt, off, pack};
     kern<<<(unsigned)tiles, 256, smem, ::sg::counted(st)>>>(dm, B, seed, sid, band, spins, logq,
                                                             flags, kv);
     return check_launch("decode_f32_kernel (no-alloc)");
@@ -455,6 +500,7 @@ extern "C" sg_status sg_sample_noalloc(const sg_config *cfg, const float *weight
     if (c.precision != SG_FP32)
         return fail(SG_EUNSUPPORTED, "sg_sample_noalloc serves the FP32 path only");
     if (c.n_models > 1) return fail(SG_EUNSUPPORTED, "sg_sample_noalloc serves single models");
+    if (c.patch > 1) return fail(SG_EUNSUPPORTED, "sg_sample_noalloc serves unpatched models");
     const int dh = c.d / c.n_heads;
     const bool shape_ok = (c.d == 32 && (dh == 8 || dh == 16)) || (c.d == 64 && (dh == 8 || dh == 16)) ||
                           (c.d == 128 && (dh == 16 || dh == 32));

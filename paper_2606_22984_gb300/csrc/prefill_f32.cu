@@ -73,6 +73,197 @@ __global__ void embed_bwd_kernel(const float *__restrict__ dH, const int8_t *__r
 }
 
 // ---------------------------------------------------------------------------
+// Patched models (sg_config.patch > 1): one token of P spins per position,
+// a softmax head over K = 2^P classes.  Rows r = b T + t of a chunk.
+// ---------------------------------------------------------------------------
+__global__ void spins_to_tokens_kernel(const int8_t *__restrict__ spins, int64_t R, int T, int Ns,
+                                       int P, int latD, int latL, uint8_t *__restrict__ tok)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= R) return;
+    const int64_t b = i / T;
+    const int t = (int)(i % T);
+    int v = 0;
+    for (int j = 0; j < P; ++j) v |= ((spins[b * Ns + patch_site(t, j, P, latD, latL)] + 1) >> 1) << j;
+    tok[i] = (uint8_t)v;
+}
+
+__global__ void embed_tok_kernel(const uint8_t *__restrict__ tok, int64_t R, int T, int D, int dt,
+                                 const float *__restrict__ tokE, const float *__restrict__ pos,
+                                 float *__restrict__ H)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= R * D) return;
+    const int64_t r = i / D;
+    const int j = (int)(i % D), t = (int)(r % T);
+    if (j < dt) H[i] = tokE[(t == 0 ? 0 : tok[r - 1]) * dt + j];
+    else H[i] = pos[(size_t)t * (D - dt) + (j - dt)];
+}
+
+__global__ void embed_bwd_tok_kernel(const float *__restrict__ dH, const uint8_t *__restrict__ tok,
+                                     int Bc, int T, int D, int dt, float *__restrict__ gtok,
+                                     float *__restrict__ gpos)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)T * D) return;
+    const int t = (int)(i / D), j = (int)(i % D);
+    if (j >= dt) {
+        float s = 0.f;
+        for (int b = 0; b < Bc; ++b) s += dH[((size_t)b * T + t) * D + j];
+        atomicAdd(gpos + (size_t)t * (D - dt) + (j - dt), s);
+    } else {
+        for (int b = 0; b < Bc; ++b) {
+            const size_t r = (size_t)b * T + t;
+            const int tk = t == 0 ? 0 : tok[r - 1];
+            atomicAdd(gtok + tk * dt + j, dH[r * D + j]);
+        }
+    }
+}
+
+// Warp per row: LN_f, the K logits, log-sum-exp; lp = z[tok] - lse.  Saves
+// Y, mu, rs and lse for the backward (which recomputes the logits from Y).
+__global__ void head_fwd_cat_kernel(const float *__restrict__ H, const float *__restrict__ g,
+                                    const float *__restrict__ bb, const float *__restrict__ Wh,
+                                    const float *__restrict__ bh, const uint8_t *__restrict__ tok,
+                                    float *__restrict__ Y, float *__restrict__ mu,
+                                    float *__restrict__ rs, float *__restrict__ lse_out,
+                                    float *__restrict__ lp, int64_t R, int D, int K)
+{
+    const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= R) return;
+    const float *x = H + r * D;
+    float s = 0.f;
+    for (int j = lane; j < D; j += 32) s += x[j];
+    const float mean = wsum(s) / D;
+    float q = 0.f;
+    for (int j = lane; j < D; j += 32) {
+        const float dv = x[j] - mean;
+        q += dv * dv;
+    }
+    const float r_s = 1.0f / sqrtf(wsum(q) / D + 1e-5f);
+    float yv[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int j = lane + 32 * i;
+        yv[i] = j < D ? (x[j] - mean) * r_s * g[j] + bb[j] : 0.f;
+        if (Y && j < D) Y[r * D + j] = yv[i];
+    }
+    const int tk = tok[r];
+    float mx = -INFINITY, se = 0.f, zt = 0.f;
+    for (int k = 0; k < K; ++k) {
+        float zk = 0.f;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int j = lane + 32 * i;
+            if (j < D) zk += yv[i] * Wh[(size_t)k * D + j];
+        }
+        zk = wsum(zk) + bh[k];
+        const float mn = fmaxf(mx, zk);
+        se = se * expf(mx - mn) + expf(zk - mn);
+        mx = mn;
+        if (k == tk) zt = zk;
+    }
+    if (lane == 0) {
+        const float lse = mx + logf(se);
+        if (lse_out) lse_out[r] = lse;
+        if (mu) {
+            mu[r] = mean;
+            rs[r] = r_s;
+        }
+        lp[r] = zt - lse;
+    }
+}
+
+// dz_k = c_b (onehot(tok) - softmax(z)_k), then LN_f backward into dH and the
+// head / LN_f weight gradients (shared-memory partial sums when K D fits).
+__global__ void head_bwd_cat_kernel(const float *__restrict__ H, const float *__restrict__ mu,
+                                    const float *__restrict__ rs, const float *__restrict__ Y,
+                                    const float *__restrict__ lse, const uint8_t *__restrict__ tok,
+                                    const float *__restrict__ coeff, const float *__restrict__ g,
+                                    const float *__restrict__ Wh, const float *__restrict__ bh,
+                                    float *__restrict__ dH, float *__restrict__ gWh,
+                                    float *__restrict__ gbh, float *__restrict__ glnfg,
+                                    float *__restrict__ glnfb, int64_t R, int T, int D, int K,
+                                    int rows_per_block, int shared_sums)
+{
+    extern __shared__ float red[];  // [K][D] Wh, [D] lnf_g, [D] lnf_b, [K] bh
+    float *rW = red, *rg = red + (size_t)K * D, *rb = rg + D, *rh = rb + D;
+    if (shared_sums)
+        for (int j = threadIdx.x; j < K * D + 2 * D + K; j += blockDim.x) red[j] = 0.f;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+    for (int64_t r = r0 + warp; r < R && r < r0 + rows_per_block; r += nw) {
+        const float c = coeff[r / T];
+        const int tk = tok[r];
+        float yv[16], dy[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int j = lane + 32 * i;
+            yv[i] = j < D ? Y[r * D + j] : 0.f;
+            dy[i] = 0.f;
+        }
+        for (int k = 0; k < K; ++k) {
+            float zk = 0.f;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int j = lane + 32 * i;
+                if (j < D) zk += yv[i] * Wh[(size_t)k * D + j];
+            }
+            zk = wsum(zk) + bh[k];
+            const float dz = c * ((k == tk ? 1.f : 0.f) - expf(zk - lse[r]));
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int j = lane + 32 * i;
+                if (j >= D) break;
+                dy[i] += dz * Wh[(size_t)k * D + j];
+                if (shared_sums) atomicAdd(rW + (size_t)k * D + j, dz * yv[i]);
+                else atomicAdd(gWh + (size_t)k * D + j, dz * yv[i]);
+            }
+            if (lane == 0) {
+                if (shared_sums) atomicAdd(rh + k, dz);
+                else atomicAdd(gbh + k, dz);
+            }
+        }
+        const float m = mu[r], s = rs[r];
+        float m1 = 0.f, m2 = 0.f, xh[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int j = lane + 32 * i;
+            xh[i] = j < D ? (H[r * D + j] - m) * s : 0.f;
+            if (j < D) {
+                const float dxh = dy[i] * g[j];
+                m1 += dxh;
+                m2 += dxh * xh[i];
+                if (shared_sums) {
+                    atomicAdd(rg + j, dy[i] * xh[i]);
+                    atomicAdd(rb + j, dy[i]);
+                } else {
+                    atomicAdd(glnfg + j, dy[i] * xh[i]);
+                    atomicAdd(glnfb + j, dy[i]);
+                }
+            }
+        }
+        m1 = wsum(m1) / D;
+        m2 = wsum(m2) / D;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int j = lane + 32 * i;
+            if (j < D) dH[r * D + j] = s * (dy[i] * g[j] - m1 - xh[i] * m2);
+        }
+    }
+    if (!shared_sums) return;
+    __syncthreads();
+    for (int j = threadIdx.x; j < K * D; j += blockDim.x) atomicAdd(gWh + j, rW[j]);
+    for (int j = threadIdx.x; j < D; j += blockDim.x) {
+        atomicAdd(glnfg + j, rg[j]);
+        atomicAdd(glnfb + j, rb[j]);
+    }
+    for (int j = threadIdx.x; j < K; j += blockDim.x) atomicAdd(gbh + j, rh[j]);
+}
+
+// ---------------------------------------------------------------------------
 // LayerNorm forward / backward, one warp per row (eps 1e-5, biased variance).
 // ---------------------------------------------------------------------------
 __global__ void ln_fwd_kernel(const float *__restrict__ X, const float *__restrict__ g,
@@ -1261,6 +1452,7 @@ struct Work {
     float *dH, *dHmid, *dA, *dQKV, *dF1, *Dt;
     // tensor-core backward scratch (wide BF16)
     unsigned char *dHt, *dF1t, *dQKVt;
+    uint8_t *tok8;  // patched models: the token class of every row
     int64_t total_floats;
 };
 
@@ -1315,6 +1507,7 @@ Work carve(const sg_config &c, float *base, int64_t R, bool bwd)
     w.Y = take(R * D);
     w.ell = take(R);
     w.lp = take(R);
+    if (spins_per_token(c) > 1) w.tok8 = reinterpret_cast<uint8_t *>(take((R + 3) / 4));
     if (bwd) {
         w.dH = take(R * D);
         w.dHmid = take(R * D);
@@ -1329,7 +1522,7 @@ Work carve(const sg_config &c, float *base, int64_t R, bool bwd)
 
 sg_status plan_chunks(sg_model *m, int64_t B, bool bwd, Plan &p, size_t &bytes)
 {
-    const sg_config &c = m->cfg;
+    const sg_config &c = m->seq;  // N = tokens
     // floats per sample from a dry run of carve() over one sample's rows
     const size_t per_sample = (size_t)carve(c, nullptr, c.N, bwd).total_floats * sizeof(float);
     size_t free_b = 0, total_b = 0;
@@ -1350,11 +1543,18 @@ sg_status plan_chunks(sg_model *m, int64_t B, bool bwd, Plan &p, size_t &bytes)
 // and writes its output into the next layer's Hin (or Hfin after the last).
 void forward_chunk(sg_model *m, const int8_t *spins, int Bc, Work &w, bool keep, cudaStream_t st)
 {
-    const sg_config &c = m->cfg;
+    const sg_config &c = m->seq;  // N = tokens
     const int64_t R = (int64_t)Bc * c.N;
+    const int P = spins_per_token(c), K = 1 << P;
     const int D = c.d, F = c.d_ff, dh = c.d / c.n_heads;
     const float *W = m->w;
     float *H = keep ? w.layers[0].Hin : w.Hping;
+    if (P > 1) {
+        spins_to_tokens_kernel<<<blocks_for(R, 256), 256, 0, ::sg::counted(st)>>>(
+            spins, R, c.N, m->cfg.N, P, c.lat_D, c.lat_L, w.tok8);
+        embed_tok_kernel<<<blocks_for(R * D, 256), 256, 0, ::sg::counted(st)>>>(
+            w.tok8, R, c.N, D, c.d_token, W + m->off.tok, W + m->off.pos, H);
+    } else
     embed_kernel<<<blocks_for(R * D, 256), 256, 0, ::sg::counted(st)>>>(spins, R, c.N, D, c.d_token,
                                                          W + m->off.tok, W + m->off.pos, H);
     for (int l = 0; l < c.n_layers; ++l) {
@@ -1406,6 +1606,12 @@ void forward_chunk(sg_model *m, const int8_t *spins, int Bc, Work &w, bool keep,
     // ensure the final stream lives in Hfin
     if (H != w.Hfin)
         cudaMemcpyAsync(w.Hfin, H, (size_t)R * D * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    if (P > 1)
+        head_fwd_cat_kernel<<<blocks_for(R, 8), 256, 0, ::sg::counted(st)>>>(
+            w.Hfin, W + m->off.lnfg, W + m->off.lnfb, W + m->off.Wh, W + m->off.bh, w.tok8,
+            keep ? w.Y : nullptr, keep ? w.muf : nullptr, keep ? w.rsf : nullptr,
+            keep ? w.ell : nullptr, w.lp, R, D, K);
+    else
     head_fwd_kernel<<<blocks_for(R, 8), 256, 0, ::sg::counted(st)>>>(
         w.Hfin, W + m->off.lnfg, W + m->off.lnfb, W + m->off.Wh, W + m->off.bh, spins,
         keep ? w.Y : nullptr, keep ? w.muf : nullptr, keep ? w.rsf : nullptr,
@@ -1448,7 +1654,7 @@ sg_status launch_pack_tiled_weights(sg_model *m, cudaStream_t st)
 sg_status launch_logprob_f32(sg_model *m, const int8_t *spins, int64_t B, float *logq,
                              cudaStream_t st)
 {
-    const sg_config &c = m->cfg;
+    const sg_config &c = m->seq;  // N = tokens
     if (!dh_supported(c.d / c.n_heads))
         return fail(SG_EUNSUPPORTED, "prefill attention is built for d_h in {8, 16, 32}");
     if (c.d % 4 || c.d_ff % 4) return fail(SG_EUNSUPPORTED, "d and d_ff must be multiples of 4");
@@ -1459,7 +1665,7 @@ sg_status launch_logprob_f32(sg_model *m, const int8_t *spins, int64_t B, float 
     for (int64_t b0 = 0; b0 < B; b0 += p.Bc) {
         const int Bc = (int)std::min<int64_t>(p.Bc, B - b0);
         Work w = carve(c, (float *)m->ws, (int64_t)Bc * c.N, false);
-        const int8_t *sp = spins + b0 * c.N;
+        const int8_t *sp = spins + b0 * m->cfg.N;
         forward_chunk(m, sp, Bc, w, false, st);
         seg_sum_kernel<<<Bc, 256, 0, ::sg::counted(st)>>>(w.lp, c.N, logq + b0);
     }
@@ -1469,11 +1675,12 @@ sg_status launch_logprob_f32(sg_model *m, const int8_t *spins, int64_t B, float 
 sg_status launch_grad_f32(sg_model *m, const int8_t *spins, const float *coeff, int64_t B,
                           float *grad, float *logq, cudaStream_t st)
 {
-    const sg_config &c = m->cfg;
+    const sg_config &c = m->seq;  // N = tokens
     if (!dh_supported(c.d / c.n_heads))
         return fail(SG_EUNSUPPORTED, "prefill attention is built for d_h in {8, 16, 32}");
     if (c.d % 4 || c.d_ff % 4) return fail(SG_EUNSUPPORTED, "d and d_ff must be multiples of 4");
     if (c.d > 512) return fail(SG_EUNSUPPORTED, "backward is built for d <= 512");
+    const int P = spins_per_token(c), K = 1 << P;
     Plan p;
     size_t bytes;
     SG_TRY(plan_chunks(m, B, true, p, bytes));
@@ -1486,10 +1693,18 @@ sg_status launch_grad_f32(sg_model *m, const int8_t *spins, const float *coeff, 
         const int Bc = (int)std::min<int64_t>(p.Bc, B - b0);
         const int64_t R = (int64_t)Bc * c.N;
         Work w = carve(c, (float *)m->ws, R, true);
-        const int8_t *sp = spins + b0 * c.N;
+        const int8_t *sp = spins + b0 * m->cfg.N;
         forward_chunk(m, sp, Bc, w, true, st);
         if (logq) seg_sum_kernel<<<Bc, 256, 0, ::sg::counted(st)>>>(w.lp, c.N, logq + b0);
         // head + LN_f
+        if (P > 1) {
+            const size_t red = ((size_t)K * D + 2 * D + K) * sizeof(float);
+            const int shared = red <= 48 * 1024;
+            head_bwd_cat_kernel<<<blocks_for(R, 256), 256, shared ? red : 0, ::sg::counted(st)>>>(
+                w.Hfin, w.muf, w.rsf, w.Y, w.ell, w.tok8, coeff + b0, W + O.lnfg, W + O.Wh,
+                W + O.bh, w.dH, grad + O.Wh, grad + O.bh, grad + O.lnfg, grad + O.lnfb, R, c.N, D,
+                K, 256, shared);
+        } else
         head_bwd_kernel<<<blocks_for(R, 256), 256, (4 * D + 2) * sizeof(float), ::sg::counted(st)>>>(
             w.Hfin, w.muf, w.rsf, w.Y, w.ell, sp, coeff + b0, W + O.lnfg, W + O.Wh, w.dH,
             grad + O.Wh, grad + O.bh, grad + O.lnfg, grad + O.lnfb, R, c.N, D, 256);
@@ -1562,6 +1777,10 @@ sg_status launch_grad_f32(sg_model *m, const int8_t *spins, const float *coeff, 
             ln_bwd_res(w.dA, L.Hin, L.mu1, L.rs1, W + o.ln1g, w.dHmid, w.dH, grad + o.ln1g,
                        grad + o.ln1b, R, D, st);
         }
+        if (P > 1)
+            embed_bwd_tok_kernel<<<blocks_for((int64_t)c.N * D, 256), 256, 0, ::sg::counted(st)>>>(
+                w.dH, w.tok8, Bc, c.N, D, c.d_token, grad + O.tok, grad + O.pos);
+        else
         embed_bwd_kernel<<<blocks_for((int64_t)c.N * D, 256), 256, 0, ::sg::counted(st)>>>(
             w.dH, sp, Bc, c.N, D, c.d_token, grad + O.tok, grad + O.pos);
     }

@@ -60,8 +60,9 @@ BlobOff blob_offsets(const sg_config &c)
     BlobOff o{};
     const int64_t d = c.d, f = c.d_ff;
     int64_t p = 0;
-    o.tok = p; p += 2 * (int64_t)c.d_token;
-    o.pos = p; p += (int64_t)c.N * (d - c.d_token);
+    const int64_t K = (int64_t)1 << spins_per_token(c), T = c.N / spins_per_token(c);
+    o.tok = p; p += K * (int64_t)c.d_token;
+    o.pos = p; p += T * (d - c.d_token);
     for (int l = 0; l < c.n_layers; ++l) {
         LayerOff &L = o.L[l];
         L.ln1g = p; p += d;
@@ -77,8 +78,8 @@ BlobOff blob_offsets(const sg_config &c)
     }
     o.lnfg = p; p += d;
     o.lnfb = p; p += d;
-    o.Wh = p; p += 2 * d;
-    o.bh = p; p += 2;
+    o.Wh = p; p += K * d;
+    o.bh = p; p += K;
     o.total = p;
     return o;
 }
@@ -119,6 +120,20 @@ static sg_status validate(const sg_config *c)
     if (c->precision != SG_FP32 && c->precision != SG_BF16)
         return fail(SG_EINVAL, "precision must be SG_FP32 or SG_BF16");
     if (c->n_models < 0 || c->n_models > 64) return fail(SG_EINVAL, "n_models must be in [0, 64]");
+    if (c->patch < 0 || c->patch > 8 || (c->patch > 1 && (c->patch & (c->patch - 1))))
+        return fail(SG_EINVAL, "patch must be 0, 1, 2, 4 or 8 spins per token");
+    const int P = spins_per_token(*c);
+    if (P > 1) {
+        if (c->lat_D == 0) {
+            if (c->N % P) return fail(SG_EINVAL, "N must be a multiple of patch");
+        } else {
+            int64_t n = 1;
+            for (int k = 0; k < c->lat_D; ++k) n *= c->lat_L;
+            if (c->lat_D < 1 || c->lat_D > 3 || (1 << c->lat_D) != P || c->lat_L < 2 ||
+                c->lat_L % 2 || n != c->N)
+                return fail(SG_EINVAL, "patch map needs patch = 2^lat_D, even lat_L, N = lat_L^lat_D");
+        }
+    }
     return SG_OK;
 }
 
@@ -155,6 +170,8 @@ sg_status sg_model_create(const sg_config *cfg, const float *weights_host, int64
     sg_model *m = new (std::nothrow) sg_model();
     if (!m) return fail(SG_ENOMEM, "host allocation failed");
     m->cfg = *cfg;
+    m->seq = *cfg;
+    m->seq.N = cfg->N / spins_per_token(*cfg);
     m->P = P;
     m->n_models = models_of(*cfg);
     m->P1 = P / m->n_models;
@@ -238,7 +255,7 @@ sg_status sg_sample(sg_model *m, int64_t B, double beta, uint64_t seed, uint32_t
     cudaStream_t st = (cudaStream_t)stream;
     if (flags)
         SG_CUDA_TRY(cudaMemsetAsync(flags, 0,
-                                    (size_t)B * ((m->cfg.N + 31) / 32) * sizeof(uint32_t), st));
+                                    (size_t)B * ((m->seq.N + 31) / 32) * sizeof(uint32_t), st));
     if (m->cfg.precision == SG_BF16)
         return launch_decode_bf16(m, B, seed, stream_id, flag_band, spins, logq, flags, st);
     return launch_decode_f32(m, B, seed, stream_id, flag_band, spins, logq, flags, st);

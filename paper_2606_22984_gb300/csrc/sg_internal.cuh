@@ -100,6 +100,28 @@ struct BlobOff {
 
 BlobOff blob_offsets(const sg_config &c);
 
+// Patching (see sg_config): spins per token, tokens, classes.
+__host__ __device__ __forceinline__ int spins_per_token(const sg_config &c)
+{
+    return c.patch > 1 ? c.patch : 1;
+}
+
+// Raster site of bit j of token t (patch map of sg_config).
+__host__ __device__ __forceinline__ int patch_site(int t, int j, int P, int latD, int latL)
+{
+    if (P == 1) return t;
+    if (latD == 0) return t * P + j;
+    const int M = latL >> 1;
+    int site = 0, stride = 1, rem = t;
+    for (int k = 0; k < latD; ++k) {
+        const int cell = rem % M;
+        rem /= M;
+        site += (2 * cell + ((j >> k) & 1)) * stride;
+        stride *= latL;
+    }
+    return site;
+}
+
 // Offsets of the 16-byte aligned FP32 copies read with vector loads by the
 // CUDA-core GEMMs: k-major (transposed) WqkvT [d][3d], W1T [d][d_ff],
 // W2T [d_ff][d]; the row-major Wqkv, W1, W2 of the backward; and the biases.
@@ -114,7 +136,8 @@ PackOff pack_offsets(const sg_config &c);
 
 // Everything a kernel needs about the model, passed by value.
 struct DevModel {
-    int N, L, d, nh, dt, dff, mask, W, S;
+    int N, L, d, nh, dt, dff, mask, W, S;   // N: tokens (the sequence length)
+    int P, K, Nspins, latD, latL;           // patching: spins per token, classes
     const float *w;    // master FP32 blob
     const float *wt;   // transposed FP32 copies
     BlobOff o;
@@ -155,6 +178,7 @@ __host__ __device__ __forceinline__ bool key_visible(int mask, int W, int S, int
 // ---------------------------------------------------------------------------
 struct sg_model {
     sg_config cfg;
+    sg_config seq;            // cfg with N = tokens (the sequence the transformer sees)
     int64_t P;                // floats of all models' blobs
     int64_t P1 = 0;           // floats of one model's blob
     int n_models = 1;

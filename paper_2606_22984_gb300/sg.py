@@ -34,7 +34,8 @@ class SgError(RuntimeError):
 
 class SgConfig(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in ("N", "n_layers", "d", "n_heads", "d_token", "d_ff",
-                                              "mask_kind", "W", "S", "precision", "n_models")]
+                                              "mask_kind", "W", "S", "precision", "n_models",
+                                              "patch", "lat_D", "lat_L")]
 
 
 _P, _I64, _I32, _U32, _U64, _D, _F = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
@@ -116,7 +117,8 @@ def launch_count() -> int:
 
 def config(shape: _inputs.ModelShape, precision: int = SG_FP32, n_models: int = 1) -> SgConfig:
     return SgConfig(shape.N, shape.n_layers, shape.d, shape.n_heads, shape.d_token, shape.d_ff,
-                    shape.mask_kind, shape.W, shape.S, precision, n_models)
+                    shape.mask_kind, shape.W, shape.S, precision, n_models,
+                    getattr(shape, "patch", 1), getattr(shape, "lat_D", 0), getattr(shape, "lat_L", 0))
 
 
 def param_count(shape: _inputs.ModelShape, precision: int = SG_FP32) -> int:
@@ -170,7 +172,8 @@ class Model:
         dev = torch.device("cuda")
         spins = torch.empty((B, N), dtype=torch.int8, device=dev) if spins is None else spins
         logq = torch.empty(B, dtype=torch.float32, device=dev) if logq is None else logq
-        flags = (torch.empty((B, (N + 31) // 32), dtype=torch.int32, device=dev)
+        T = N // max(1, getattr(self.shape, "patch", 1))  # flags: one bit per token position
+        flags = (torch.empty((B, (T + 31) // 32), dtype=torch.int32, device=dev)
                  if with_flags else None)
         _check("sg_sample", lib().sg_sample(
             self.handle, B, beta, seed, stream_id, flag_band, _dev(spins, torch.int8, (B, N)),

@@ -22,6 +22,9 @@ def oracle_replay(m, w, seed, gpu_spins, gpu_flags, rows=None, stream=0, n_threa
     GPU's decision at every draw the GPU flagged (the protocol for draws with
     |p+ - u| inside the flag band).  Returns spins, logq, pplus, oracle flags."""
     rows = np.arange(gpu_spins.shape[0]) if rows is None else np.asarray(rows, np.int64)
-    fl = unpack_flags(gpu_flags[rows], m.N)
+    T = m.N // max(1, getattr(m, "patch", 1))  # flags are per token position
+    fl = unpack_flags(gpu_flags[rows], T)
+    if T < m.N:
+        fl = np.pad(fl, ((0, 0), (0, m.N - T)))
     return oracle.sample(ocfg(m), w, len(rows), seed, stream, override_mask=fl,
                          override_spins=gpu_spins[rows], n_threads=n_threads, rows=rows)

@@ -101,3 +101,15 @@ def test_call_argument_validation_on_host(lib):
     assert lib.sg_mh_step(P(1), P(1), P(1), 10, 4, 3, 1.0, 1, P(1), P(1), P(1), P(1), None,
                           None) == 1
     assert lib.sg_adam_step(P(1), P(1), P(1), P(1), 5, 1e-3, 0.9, 0.999, 1e-8, 0, None) == 1
+
+
+def test_patched_param_count_and_validation(lib):
+    m = inputs.ModelShape(64, 2, 32, 4, d_token=16, patch=4, lat_D=2, lat_L=8)
+    assert lib.sg_param_count(ctypes.byref(sg.config(m))) == inputs.param_count(m) == \
+        oracle.param_count(oracle.ModelCfg(**vars(m)))
+    for bad in (dict(patch=3), dict(patch=4, lat_D=3), dict(patch=4, lat_L=7),
+                dict(patch=16), dict(patch=4, lat_D=2, lat_L=6)):
+        b = inputs.ModelShape(64, 2, 32, 4, d_token=16, patch=4, lat_D=2, lat_L=8)
+        for k, v in bad.items():
+            setattr(b, k, v)
+        assert lib.sg_param_count(ctypes.byref(sg.config(b))) == -1

@@ -178,6 +178,51 @@ def test_bf16_grouped_models_at_the_group_limit():
         sg.Model(m, inputs.make_group_weights(m, 21, 65), sg.SG_BF16, n_models=65)
 
 
+PATCHED_CASES = {
+    # name: (shape, B, precision)
+    "lat2d_p4_fp32": (inputs.ModelShape(64, 2, 32, 4, d_token=16, mask_kind=1, W=4, S=5,
+                                        patch=4, lat_D=2, lat_L=8), 200, sg.SG_FP32),
+    "chain_p2_fp32": (inputs.ModelShape(40, 1, 32, 4, patch=2), 130, sg.SG_FP32),
+    "lat3d_p8_fp32": (inputs.ModelShape(64, 1, 32, 4, d_token=8, patch=8, lat_D=3, lat_L=4), 70,
+                      sg.SG_FP32),
+    "lat2d_p4_bf16": (inputs.ModelShape(256, 2, 64, 4, d_token=16, mask_kind=1, W=8, S=9,
+                                        patch=4, lat_D=2, lat_L=16), 300, sg.SG_BF16),
+}
+
+
+@pytest.mark.parametrize("name", list(PATCHED_CASES))
+def test_patched_sampling_and_scoring_match_oracle(name):
+    """Patching: spins of every token cell equal to the oracle outside flagged
+    draws, sampled log q within the per-token bound, teacher-forced log q and
+    the REINFORCE gradient against the oracle."""
+    m, B, prec = PATCHED_CASES[name]
+    w = inputs.make_weights(m, 17)
+    tol = BF16_LOGQ_TOL if prec == sg.SG_BF16 else FP32_LOGQ_TOL
+    model = sg.Model(m, w, prec)
+    spins, logq, flags = model.sample(B, seed=31, with_flags=True)
+    model.check()
+    s, lq, fl = _np(spins), _np(logq), _np(flags)
+    assert np.all(np.isin(s, (-1, 1)))
+    so, lqo, _, _ = oracle_replay(m, w, 31, s, fl)
+    assert np.array_equal(so, s), "spins differ from the oracle outside flagged draws"
+    assert np.abs(lqo - lq).max() <= tol * m.N
+    tf = _np(model.logprob(spins))
+    assert np.abs(tf - lqo).max() <= tol * m.N
+    c = np.random.default_rng(1).normal(0, 1, B).astype(np.float32) / B
+    g = _np(model.grad(spins, torch.tensor(c, device="cuda")))
+    go, _ = oracle.grad(ocfg(m), w, s, c.astype(np.float64))
+    rel = np.linalg.norm(g - go) / np.linalg.norm(go)
+    print(f"{name}: flagged {unpack_flags(fl, m.N // m.patch).mean():.4f}, grad rel err {rel:.2e}")
+    assert rel < (2e-2 if prec == sg.SG_BF16 else 1e-4)
+
+
+def test_patched_bf16_rejected_where_not_built():
+    m = inputs.ModelShape(64, 1, 128, 8, d_token=16, patch=4, lat_D=2, lat_L=8)
+    model = sg.Model(m, inputs.make_weights(m, 1), sg.SG_BF16)
+    with pytest.raises(sg.SgError):
+        model.sample(8, seed=1)
+
+
 def test_grouped_models_rejected_outside_d256():
     m = inputs.ModelShape(20, 1, 64, 4)
     w = inputs.make_group_weights(m, 1, 2)
