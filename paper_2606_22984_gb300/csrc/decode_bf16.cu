@@ -480,7 +480,8 @@ __global__ void __launch_bounds__(kThreads, 1) decode_bf16_kernel(const __grid_c
 // threads per row do, and split the LayerNorm and GELU epilogues four ways.
 // Weights stream per layer into three buffers exactly as in the kernel above.
 // ---------------------------------------------------------------------------
-template <int NST>  // keys in flight per thread in the attention (2 or 3)
+// NST: keys in flight per thread in the attention (2 or 3); PATCH: K-way head
+template <int NST, bool PATCH>
 __global__ void __launch_bounds__(512, 1) decode_bf16_d64_kernel(const __grid_constant__ DecodeArgs a)
 {
     constexpr int D = 64, DFF = 256, DH = 16, KG = D / 8, KG2 = DFF / 8;
@@ -794,7 +795,7 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d64_kernel(const __grid_co
             const float mean = t1 * (1.0f / D);
             const float var = fmaxf(t2 * (1.0f / D) - mean * mean, 0.f);
             const float rs = 1.0f / sqrtf(var + 1e-5f);
-            if (a.P > 1) {
+            if constexpr (PATCH) {
                 // patched: K logits; this quarter's partial sums over its 16
                 // dims go to the A2 tile (idle until the next step's attention)
                 float y[DH];
@@ -847,8 +848,7 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d64_kernel(const __grid_co
                         if (!isfinite(zc - lse)) atomicOr(a.err, 4);
                     }
                 }
-                continue;
-            }
+            } else {
             float z0 = 0.f, z1 = 0.f;
 #pragma unroll
             for (int j = 0; j < DH; ++j) {
@@ -881,6 +881,7 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d64_kernel(const __grid_co
                     if (!isfinite(ell)) atomicOr(a.err, 4);
                 }
             }
+            }  // two-class head
             // tok lives in the qr == 0 thread, which is the only one that
             // reads it (the token columns are in quarter 0)
         }
@@ -1358,8 +1359,16 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d256_kernel(const __grid_c
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int r = 32 * (warp & 3) + lane, qr = warp >> 2;
-    const int64_t b = (int64_t)blockIdx.x * a.rows_per_cta + r;
-    const bool active = r < a.rows_per_cta && b < a.B;
+    // With at most 64 rows per CTA, rows 64..127 mirror rows 0..63 (same
+    // inputs, so every phase computes identical copies in TMEM lanes
+    // 64..127); a row and its mirror (thread tid ^ 64) split the attention's
+    // keys and merge their partial softmax states, doubling the KV loads in
+    // flight.  Only the row itself writes the KV cache, spins and log q.
+    const bool mirror_mode = a.rows_per_cta <= 64;
+    const int rr = mirror_mode ? (r & 63) : r;     // the sample row this thread serves
+    const bool is_mirror = mirror_mode && r >= 64;
+    const int64_t b = (int64_t)blockIdx.x * a.rows_per_cta + rr;
+    const bool active = rr < a.rows_per_cta && b < a.B;
     const int64_t mdl = ((int64_t)blockIdx.x * a.rows_per_cta) / a.rows_per_model;
     const float *w = a.w + mdl * a.stride_w;
     const float *wt = a.wt + mdl * a.stride_wt;
@@ -1497,7 +1506,7 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d256_kernel(const __grid_c
     auto append = [&](unsigned char *slot, int part, const float *bias) {
         float v0[32], v1[32];
         ld64(ACC, v0, v1);
-        if (!active) return;
+        if (!active || is_mirror) return;
         uint4 *dst = reinterpret_cast<uint4 *>(slot) + (size_t)part * (D / 8) * kRows;
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
@@ -1526,7 +1535,7 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d256_kernel(const __grid_c
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const int d = 64 * qr + 32 * c + j;
-                    v[j] = d < a.dt ? __ldg(w + a.o.tok + stok[r] * a.dt + d) : __ldg(pos + d - a.dt);
+                    v[j] = d < a.dt ? __ldg(w + a.o.tok + stok[rr] * a.dt + d) : __ldg(pos + d - a.dt);
                 }
                 tc::tmem_st32(tmem + tq + HCOL + 64 * qr + 32 * c, v);
             }
@@ -1559,7 +1568,7 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d256_kernel(const __grid_c
             run(Abuf, 4, ACC, false);  // q_t stays in TMEM
             if (s_err) break;
             // attention: heads 2 qr and 2 qr + 1, keys 0..t from the ring
-            // (this thread wrote row r of key t itself, so it sees it)
+            // (key t of row rr was written before the barriers of the q run)
 #pragma unroll 1
             for (int p = 0; p < 2; ++p) {
                 const int hh = 2 * qr + p;
@@ -1577,7 +1586,31 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d256_kernel(const __grid_c
                 // in flight per thread: the stages are the A and A2 tiles (idle
                 // during attention); per thread, K pieces at +0..+24 KB and V
                 // pieces at +32..+56 KB of a stage, 8 KB apart (conflict-free).
-                const uint4 *kb = reinterpret_cast<const uint4 *>(kvl) + (4 * hh) * kRows + r;
+                const uint4 *kb = reinterpret_cast<const uint4 *>(kvl) + (4 * hh) * kRows + rr;
+                // Every row reduces its keys as two halves, [0, half) and
+                // [half, nk), each an online softmax from the empty state,
+                // merged as (first half, second half).  In mirror mode the
+                // row's thread takes the first half and its mirror the second;
+                // otherwise one thread runs both and parks the first half's
+                // state.  The arithmetic is the same either way, so a row's
+                // results do not depend on how many rows share its CTA.
+                const int half = (nk + 1) >> 1;
+                const int i0 = !mirror_mode ? 0 : (is_mirror ? half : 0);
+                const int i1 = !mirror_mode ? nk : (is_mirror ? nk : half);
+                float sm = -INFINITY, sl = 0.f, sacc[DH];  // the parked first half
+#pragma unroll
+                for (int j = 0; j < DH; ++j) sacc[j] = 0.f;
+                auto park = [&]() {
+                    sm = m0;
+                    sl = l0;
+#pragma unroll
+                    for (int j = 0; j < DH; ++j) {
+                        sacc[j] = acc[j];
+                        acc[j] = 0.f;
+                    }
+                    m0 = -INFINITY;
+                    l0 = 0.f;
+                };
                 auto fetch = [&](int i, int s) {
                     const uint4 *pp = kb + koff[i];
                     unsigned char *dst = (s == 0 ? Abuf : A2buf) + tid * 16;
@@ -1588,11 +1621,12 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d256_kernel(const __grid_c
                     }
                     tc::cp_async_commit();
                 };
-                for (int i = 0; i < nk && i < 2; ++i) fetch(i, i);
-                for (int i = 0; i < nk; ++i) {
-                    if (i + 1 < nk) tc::cp_async_wait<1>();
+                for (int i = i0; i < i1 && i < i0 + 2; ++i) fetch(i, i - i0);
+                for (int i = i0; i < i1; ++i) {
+                    if (!mirror_mode && i == half) park();
+                    if (i + 1 < i1) tc::cp_async_wait<1>();
                     else tc::cp_async_wait<0>();
-                    const unsigned char *src = ((i & 1) ? A2buf : Abuf) + tid * 16;
+                    const unsigned char *src = (((i - i0) & 1) ? A2buf : Abuf) + tid * 16;
                     float s = 0.f;
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
@@ -1617,7 +1651,52 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d256_kernel(const __grid_c
                         }
                     }
                     // the stage is refilled only after its data has been consumed
-                    if (i + 2 < nk) fetch(i + 2, i & 1);
+                    if (i + 2 < i1) fetch(i + 2, (i - i0) & 1);
+                }
+                if (!mirror_mode && half >= nk) park();  // nk <= 1: the second half is empty
+                if (mirror_mode) {
+                    // exchange partial states through this thread's own stage
+                    // slots (its copies are complete); the row's thread parks
+                    // the mirror's half, the mirror parks the row's half and
+                    // keeps its own as the second
+                    float *mine = reinterpret_cast<float *>(Abuf + tid * 16);
+                    float *minex = reinterpret_cast<float *>(A2buf + tid * 16);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        *reinterpret_cast<float4 *>(mine + c * 2048) =
+                            make_float4(acc[4 * c], acc[4 * c + 1], acc[4 * c + 2], acc[4 * c + 3]);
+                    *reinterpret_cast<float4 *>(minex) = make_float4(m0, l0, 0.f, 0.f);
+                    __syncthreads();
+                    const int ptid = tid ^ 64;
+                    const float *other = reinterpret_cast<const float *>(Abuf + ptid * 16);
+                    const float4 ox = *reinterpret_cast<const float4 *>(A2buf + ptid * 16);
+                    if (!is_mirror) park();  // own half -> parked, partner's -> current
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const float4 v = *reinterpret_cast<const float4 *>(other + c * 2048);
+                        const float ov[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            if (is_mirror) sacc[4 * c + k] = ov[k];
+                            else acc[4 * c + k] = ov[k];
+                        }
+                    }
+                    if (is_mirror) {
+                        sm = ox.x;
+                        sl = ox.y;
+                    } else {
+                        m0 = ox.x;
+                        l0 = ox.y;
+                    }
+                    __syncthreads();  // the slots are free again for the next head
+                }
+                {   // merge: parked = first half, current = second half
+                    const float mm = fmaxf(sm, m0);
+                    const float ca = sm == -INFINITY ? 0.f : __expf(sm - mm);
+                    const float cb = m0 == -INFINITY ? 0.f : __expf(m0 - mm);
+#pragma unroll
+                    for (int j = 0; j < DH; ++j) acc[j] = __fmaf_rn(sacc[j], ca, __fmul_rn(acc[j], cb));
+                    l0 = __fmaf_rn(sl, ca, __fmul_rn(l0, cb));
                 }
                 __syncwarp();
                 float hv[32];
@@ -1722,7 +1801,7 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d256_kernel(const __grid_c
                 const int sp = u < p ? 1 : -1;
                 lq += log_sigmoid_f((float)sp * ell);
                 stok[r] = (sp + 1) >> 1;
-                if (active) {
+                if (active && !is_mirror) {
                     a.spins[(size_t)b * a.N + t] = (int8_t)sp;
                     if (a.flags && fabsf(p - u) < a.band)
                         a.flags[(size_t)b * nfw + (t >> 5)] |= 1u << (t & 31);
@@ -1732,7 +1811,7 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d256_kernel(const __grid_c
             __syncthreads();  // stok is read by every thread of the row
         }
     }
-    if (qr == 0 && active) a.logq[b] = lq;
+    if (qr == 0 && active && !is_mirror) a.logq[b] = lq;
     if (tid == 0)
         while (next_use < next_load) {
             const int s = (int)(next_use % kStages256);
@@ -1908,7 +1987,8 @@ sg_status launch_decode_bf16(sg_model *m, int64_t B, uint64_t seed, uint32_t sid
         // a third KV stage (32 KB) when shared memory allows it
         a.kv_stages = smem4 + 32768 <= 227 * 1024 ? 3 : 2;
         if (a.kv_stages == 3) smem4 += 32768;
-        auto k64 = a.kv_stages == 3 ? decode_bf16_d64_kernel<3> : decode_bf16_d64_kernel<2>;
+        auto k64 = P > 1 ? (a.kv_stages == 3 ? decode_bf16_d64_kernel<3, true> : decode_bf16_d64_kernel<2, true>)
+                         : (a.kv_stages == 3 ? decode_bf16_d64_kernel<3, false> : decode_bf16_d64_kernel<2, false>);
         SG_CUDA_TRY(cudaFuncSetAttribute(k64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem4));
         k64<<<(unsigned)tiles, 512, smem4, ::sg::counted(st)>>>(a);
         return check_launch("decode_bf16_d64_kernel");
