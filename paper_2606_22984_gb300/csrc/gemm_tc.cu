@@ -51,9 +51,29 @@ __device__ __forceinline__ void ld8(const unsigned char *base, size_t off, float
     }
 }
 
+// Column sums of a warp's 32 x 32 block (lane = row): a reduce-scatter
+// butterfly leaves lane j with the sum of column j (31 shuffles).
+__device__ __forceinline__ float warp_colsum32(float (&y)[32])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const bool upper = lane & o;
+#pragma unroll
+        for (int j = 0; j < o; ++j) {
+            const float send = upper ? y[j] : y[j + o];
+            const float recv = __shfl_xor_sync(0xffffffffu, send, o);
+            y[j] = (upper ? y[j + o] : y[j]) + recv;
+        }
+    }
+    return y[0];
+}
+
+constexpr int kColsumMax = 1024;
+
 template <int EPI>
 __device__ __forceinline__ void row_epilogue(const RowGemm &g, const float (&v)[32], int64_t r,
-                                             int col0, bool valid)
+                                             int col0, bool valid, float *s_col)
 {
     if (EPI == TE_STORE_F32 || EPI == TE_RESID_F32 || EPI == TE_STORE_F32_T) {
         if (!valid && EPI != TE_STORE_F32_T) return;
@@ -97,6 +117,7 @@ __device__ __forceinline__ void row_epilogue(const RowGemm &g, const float (&v)[
         }
 #pragma unroll
         for (int c = 0; c < 4; ++c) st8(g.out_t, wl_offset(r, col0 + 8 * c, g.N), y + 8 * c);
+        if (s_col) atomicAdd(s_col + col0 + (threadIdx.x & 31), warp_colsum32(y));
     }
 }
 
@@ -112,6 +133,10 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) row_gemm_kernel(const 
     unsigned char *As = smem + (size_t)g.NBw * g.KC * kTileBytes;
     __shared__ uint64_t full[2], empty[2], tfull[2], tempty[2], wfull;
     __shared__ uint32_t tslot;
+    __shared__ float s_colbuf[EPI == TE_GELU_BWD_T ? kColsumMax : 1];
+    float *s_col = EPI == TE_GELU_BWD_T && g.colsum ? s_colbuf : nullptr;
+    if (s_col)
+        for (int j = threadIdx.x; j < g.N; j += blockDim.x) s_col[j] = 0.f;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < 2; ++s) {
@@ -187,7 +212,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) row_gemm_kernel(const 
                 float v[32];
                 tc::tmem_ld32(tmem + acc * 256 + ((uint32_t)(32 * q) << 16) + 32 * c, v);
                 tc::tmem_wait_ld();
-                row_epilogue<EPI>(g, v, r, 32 * c, valid);
+                row_epilogue<EPI>(g, v, r, 32 * c, valid, s_col);
             }
             tc::tc_fence_before();
             __syncwarp();
@@ -197,6 +222,8 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) row_gemm_kernel(const 
     tc::tc_fence_before();
     __syncthreads();
     if (warp == 1) tc::tmem_dealloc(tmem, 512);
+    if (s_col)
+        for (int j = threadIdx.x; j < g.N; j += blockDim.x) atomicAdd(g.colsum + j, s_col[j]);
 }
 
 // tile_gemm_kernel: the same product and epilogues for any N (a multiple of
@@ -213,6 +240,10 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) tile_gemm_kernel(const
     constexpr uint32_t stage_bytes = 3 * kTileBytes;
     __shared__ uint64_t full[kTStages], empty[kTStages], tfull[2], tempty[2];
     __shared__ uint32_t tslot;
+    __shared__ float s_colbuf[EPI == TE_GELU_BWD_T ? kColsumMax : 1];
+    float *s_col = EPI == TE_GELU_BWD_T && g.colsum ? s_colbuf : nullptr;
+    if (s_col)
+        for (int j = threadIdx.x; j < g.N; j += blockDim.x) s_col[j] = 0.f;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kTStages; ++s) {
@@ -315,7 +346,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) tile_gemm_kernel(const
                 float v[32];
                 tc::tmem_ld32(tmem + acc * 256 + ((uint32_t)(32 * q) << 16) + 32 * c, v);
                 tc::tmem_wait_ld();
-                row_epilogue<EPI>(g, v, r, 256 * cb + 32 * c, valid);
+                row_epilogue<EPI>(g, v, r, 256 * cb + 32 * c, valid, s_col);
             }
             tc::tc_fence_before();
             __syncwarp();
@@ -325,6 +356,8 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) tile_gemm_kernel(const
     tc::tc_fence_before();
     __syncthreads();
     if (warp == 1) tc::tmem_dealloc(tmem, 512);
+    if (s_col)
+        for (int j = threadIdx.x; j < g.N; j += blockDim.x) atomicAdd(g.colsum + j, s_col[j]);
 }
 
 // wgrad_kernel: C (+)= A^T B over the rows of two wide activations.  CTA
@@ -472,6 +505,16 @@ __global__ void to_tiled_kernel(const float *__restrict__ X, int64_t R, int F, i
     st8(dst, tl_offset(rt, (int)(kg * 8), RBt), v);
 }
 
+// Rows R .. the end of the last row block of W(R, F) set to zero.
+__global__ void zero_wide_tail_kernel(int64_t R, int F, unsigned char *__restrict__ dst)
+{
+    const int groups = F >> 3;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t r = R + i / groups;
+    if (r >= tl_blocks(R) * 128) return;
+    *reinterpret_cast<uint4 *>(dst + wl_offset(r, 8 * (int)(i % groups), F)) = make_uint4(0, 0, 0, 0);
+}
+
 // FP32 row-major [R][F] -> W(R, F).  Thread = (row, 8-wide group); rows past
 // R up to the end of the last row block are written as zeros.
 __global__ void to_wide_kernel(const float *__restrict__ X, int64_t R, int F,
@@ -509,6 +552,13 @@ sg_status launch_to_tiled(const float *X, int64_t R, int F, int ldx, unsigned ch
     return check_launch("to_tiled_kernel");
 }
 
+sg_status launch_zero_wide_tail(int64_t R, int F, unsigned char *dst, cudaStream_t st)
+{
+    const int64_t n = (tl_blocks(R) * 128 - R) * (F >> 3);
+    if (n > 0) zero_wide_tail_kernel<<<(unsigned)((n + 255) / 256), 256, 0, ::sg::counted(st)>>>(R, F, dst);
+    return check_launch("zero_wide_tail_kernel");
+}
+
 sg_status launch_to_wide(const float *X, int64_t R, int F, unsigned char *dst, cudaStream_t st)
 {
     const int64_t n = tl_blocks(R) * 128 * (F >> 3);
@@ -534,6 +584,8 @@ sg_status launch_row_gemm(const RowGemm &g, int epi, cudaStream_t st)
     // blocks of 256 with A and B streamed per K chunk (tile_gemm_kernel)
     if (g.K % 16 || g.KC != (g.K + 63) / 64)
         return fail(SG_EUNSUPPORTED, "tensor-core GEMM needs K a multiple of 16");
+    if (g.colsum && (epi != TE_GELU_BWD_T || g.N > kColsumMax))
+        return fail(SG_EUNSUPPORTED, "fused column sums need the GELU backward and N <= 1024");
     const bool resident = g.N <= 256 && g.KC <= 4;
     const size_t smem = resident ? (size_t)g.NBw * g.KC * kTileBytes + 2 * wl_block_bytes(g.K)
                                  : (size_t)kTStages * 3 * kTileBytes;

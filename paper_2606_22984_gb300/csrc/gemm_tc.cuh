@@ -77,6 +77,7 @@ struct RowGemm {
     unsigned char *out_t;     // W(R, N)
     unsigned char *out_t2;    // W(R, N)
     const unsigned char *aux_t;  // W(R, N)
+    float *colsum;            // TE_GELU_BWD_T: colsum[j] += sum_r out(r, j) (N <= 1024), or nullptr
     int *err;
 };
 
@@ -103,6 +104,8 @@ sg_status launch_to_tiled(const float *X, int64_t R, int F, int ldx, unsigned ch
                           bool transpose, cudaStream_t st);
 // FP32 row-major [R][F] -> W(R, F) (rows past R zero).
 sg_status launch_to_wide(const float *X, int64_t R, int F, unsigned char *dst, cudaStream_t st);
+// Rows past R up to the end of the last row block of W(R, F) set to zero.
+sg_status launch_zero_wide_tail(int64_t R, int F, unsigned char *dst, cudaStream_t st);
 // FP32 row-major W[rows][K] -> T(rows, K) (weights), or of W^T when transpose.
 sg_status launch_pack_tiled(const float *W, int rows, int K, unsigned char *dst, bool transpose,
                             cudaStream_t st);

@@ -47,31 +47,6 @@ __global__ void embed_kernel(const int8_t *__restrict__ spins, int64_t R, int N,
     }
 }
 
-__global__ void embed_bwd_kernel(const float *__restrict__ dH, const int8_t *__restrict__ spins,
-                                 int Bc, int N, int D, int dt, float *__restrict__ gtok,
-                                 float *__restrict__ gpos)
-{
-    // one thread per (t, j); loops over the samples of the chunk
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)N * D) return;
-    const int t = (int)(i / D), j = (int)(i % D);
-    if (j >= dt) {
-        float s = 0.f;
-        for (int b = 0; b < Bc; ++b) s += dH[((size_t)b * N + t) * D + j];
-        atomicAdd(gpos + (size_t)t * (D - dt) + (j - dt), s);
-    } else {
-        float s0 = 0.f, s1 = 0.f;
-        for (int b = 0; b < Bc; ++b) {
-            const size_t r = (size_t)b * N + t;
-            const float v = dH[r * D + j];
-            const int tk = t == 0 ? 0 : (spins[r - 1] + 1) >> 1;
-            if (tk) s1 += v; else s0 += v;
-        }
-        atomicAdd(gtok + j, s0);
-        atomicAdd(gtok + dt + j, s1);
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Patched models (sg_config.patch > 1): one token of P spins per position,
 // a softmax head over K = 2^P classes.  Rows r = b T + t of a chunk.
@@ -348,6 +323,412 @@ __global__ void ln_bwd_kernel(const float *__restrict__ dY, const float *__restr
     for (int j = threadIdx.x; j < D; j += blockDim.x) {
         atomicAdd(dg + j, red[j]);
         atomicAdd(db + j, red[D + j]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Row kernels with 8 contiguous columns per lane (D in {32, 64, 128, 256}):
+// LPR = D / 8 lanes share a row, a warp covers 32 / LPR rows per pass and
+// keeps RPW passes of loads in flight.  Per-row sums reduce over the row's
+// lanes with xor shuffles (offsets below LPR stay inside the lane group), and
+// a lane's 8 columns are one 16-byte piece of the wide BF16 layout.
+// ---------------------------------------------------------------------------
+template <int LPR>
+__device__ __forceinline__ float gsum(float v)
+{
+#pragma unroll
+    for (int o = LPR / 2; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void ld8(const float *p, float (&v)[8])
+{
+    const float4 a = *reinterpret_cast<const float4 *>(p);
+    const float4 b = *reinterpret_cast<const float4 *>(p + 4);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+
+// Parameter vectors (LayerNorm affine, head rows) sit at arbitrary float
+// offsets of the weight blob: scalar loads.
+__device__ __forceinline__ void ld8s(const float *p, float (&v)[8])
+{
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = __ldg(p + j);
+}
+
+__device__ __forceinline__ void st8(float *p, const float (&v)[8])
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    *reinterpret_cast<float4 *>(p + 4) = make_float4(v[4], v[5], v[6], v[7]);
+}
+
+__device__ __forceinline__ uint4 pack8_bf16(const float (&v)[8])
+{
+    uint4 q;
+    __nv_bfloat162 h;
+    h = __floats2bfloat162_rn(v[0], v[1]); q.x = *reinterpret_cast<uint32_t *>(&h);
+    h = __floats2bfloat162_rn(v[2], v[3]); q.y = *reinterpret_cast<uint32_t *>(&h);
+    h = __floats2bfloat162_rn(v[4], v[5]); q.z = *reinterpret_cast<uint32_t *>(&h);
+    h = __floats2bfloat162_rn(v[6], v[7]); q.w = *reinterpret_cast<uint32_t *>(&h);
+    return q;
+}
+
+bool g8_width(int D) { return D == 32 || D == 64 || D == 128 || D == 256; }
+
+// LayerNorm forward: Y (FP32, optional) and/or the wide BF16 copy At (rows
+// past R up to the row-block end zeroed), mean and 1/std per row (optional).
+template <int D, int RPW>
+__global__ void __launch_bounds__(256)
+ln_fwd_g8_kernel(const float *__restrict__ X, const float *__restrict__ g,
+                 const float *__restrict__ b, float *__restrict__ Y, float *__restrict__ mu,
+                 float *__restrict__ rs, int64_t R, unsigned char *__restrict__ At)
+{
+    constexpr int LPR = D / 8, RPP = 32 / LPR, RPI = RPW * RPP;
+    const int lane = threadIdx.x & 31, sub = lane / LPR, c0 = 8 * (lane % LPR);
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t R_end = At ? tl_blocks(R) * 128 : R;
+    float gl[8], bl[8];
+    ld8s(g + c0, gl);
+    ld8s(b + c0, bl);
+    for (int64_t r0 = gw * RPI; r0 < R_end; r0 += nw * RPI) {
+        float x[RPW][8], mean[RPW], r_s[RPW];
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+            const int64_t r = r0 + q * RPP + sub;
+            if (r < R) ld8(X + r * D + c0, x[q]);
+            else
+#pragma unroll
+                for (int j = 0; j < 8; ++j) x[q][j] = 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+            float s = 0.f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) s += x[q][j];
+            mean[q] = gsum<LPR>(s) / D;
+        }
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+            float v = 0.f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float dv = x[q][j] - mean[q];
+                v += dv * dv;
+            }
+            r_s[q] = 1.0f / sqrtf(gsum<LPR>(v) / D + 1e-5f);
+        }
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+            const int64_t r = r0 + q * RPP + sub;
+            if (r >= R_end) break;
+            float y[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) y[j] = r < R ? (x[q][j] - mean[q]) * r_s[q] * gl[j] + bl[j] : 0.f;
+            if (At) *reinterpret_cast<uint4 *>(At + wl_offset(r, c0, D)) = pack8_bf16(y);
+            if (r >= R) continue;
+            if (Y) st8(Y + r * D + c0, y);
+            if (mu && c0 == 0) {
+                mu[r] = mean[q];
+                rs[r] = r_s[q];
+            }
+        }
+    }
+}
+
+// Output head forward (LN_f -> z = Wh y + bh -> l = z1 - z0 -> lp).
+template <int D, int RPW>
+__global__ void __launch_bounds__(256)
+head_fwd_g8_kernel(const float *__restrict__ H, const float *__restrict__ g,
+                   const float *__restrict__ bb, const float *__restrict__ Wh,
+                   const float *__restrict__ bh, const int8_t *__restrict__ spins,
+                   float *__restrict__ mu, float *__restrict__ rs, float *__restrict__ ell,
+                   float *__restrict__ lp, int64_t R)
+{
+    constexpr int LPR = D / 8, RPP = 32 / LPR, RPI = RPW * RPP;
+    const int lane = threadIdx.x & 31, sub = lane / LPR, c0 = 8 * (lane % LPR);
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    float gl[8], bl[8], w0[8], w1[8];
+    ld8s(g + c0, gl);
+    ld8s(bb + c0, bl);
+    ld8s(Wh + c0, w0);
+    ld8s(Wh + D + c0, w1);
+    const float bh0 = bh[0], bh1 = bh[1];
+    for (int64_t r0 = gw * RPI; r0 < R; r0 += nw * RPI) {
+        float x[RPW][8];
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+            const int64_t r = r0 + q * RPP + sub;
+            ld8(H + (r < R ? r : R - 1) * D + c0, x[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+            const int64_t r = r0 + q * RPP + sub;
+            float s = 0.f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) s += x[q][j];
+            const float mean = gsum<LPR>(s) / D;
+            float v = 0.f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float dv = x[q][j] - mean;
+                v += dv * dv;
+            }
+            const float r_s = 1.0f / sqrtf(gsum<LPR>(v) / D + 1e-5f);
+            float z0 = 0.f, z1 = 0.f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float y = (x[q][j] - mean) * r_s * gl[j] + bl[j];
+                z0 += y * w0[j];
+                z1 += y * w1[j];
+            }
+            z0 = gsum<LPR>(z0) + bh0;
+            z1 = gsum<LPR>(z1) + bh1;
+            if (c0 == 0 && r < R) {
+                const float l = z1 - z0;
+                if (ell) ell[r] = l;
+                if (mu) {
+                    mu[r] = mean;
+                    rs[r] = r_s;
+                }
+                lp[r] = log_sigmoid_f((float)spins[r] * l);
+            }
+        }
+    }
+}
+
+// Output head backward: dl = c_b s sigmoid(-s l) per row, y recomputed from
+// H, mean and 1/std; LN_f backward into dH; Wh, bh, lnf gradients reduced
+// per lane, per warp (shuffles over the lanes of a column group), per block
+// (shared memory), then one atomic per value and block.
+template <int D, int RPW>
+__global__ void __launch_bounds__(256)
+head_bwd_g8_kernel(const float *__restrict__ H, const float *__restrict__ mu,
+                   const float *__restrict__ rs, const float *__restrict__ ell,
+                   const int8_t *__restrict__ spins, const float *__restrict__ coeff,
+                   const float *__restrict__ g, const float *__restrict__ bb,
+                   const float *__restrict__ Wh, float *__restrict__ dH, float *__restrict__ gWh,
+                   float *__restrict__ gbh, float *__restrict__ glnfg, float *__restrict__ glnfb,
+                   int64_t R, int N, unsigned char *__restrict__ dHt, float *__restrict__ dcol)
+{
+    constexpr int LPR = D / 8, RPP = 32 / LPR, RPI = RPW * RPP;
+    __shared__ float red[5 * D + 2];
+    for (int j = threadIdx.x; j < 5 * D + 2; j += blockDim.x) red[j] = 0.f;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, sub = lane / LPR, c0 = 8 * (lane % LPR);
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    float gl[8], bl[8], w0[8], w1[8];
+    ld8s(g + c0, gl);
+    ld8s(bb + c0, bl);
+    ld8s(Wh + c0, w0);
+    ld8s(Wh + D + c0, w1);
+    float pw0[8], pw1[8], pg[8], pb[8], pc[8], pz = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) pw0[j] = pw1[j] = pg[j] = pb[j] = pc[j] = 0.f;
+    const int64_t R_end = dHt ? tl_blocks(R) * 128 : R;
+    for (int64_t r0 = gw * RPI; r0 < R_end; r0 += nw * RPI) {
+        float x[RPW][8], s[RPW], dl[RPW];
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+            const int64_t r = r0 + q * RPP + sub, rr = r < R ? r : R - 1;
+            ld8(H + rr * D + c0, x[q]);
+            const float m = mu[rr];
+            s[q] = rs[rr];
+            const float sg = (float)spins[rr];
+            dl[q] = r < R ? coeff[rr / N] * sg / (1.0f + expf(sg * ell[rr])) : 0.f;  // c s sigmoid(-s l)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) x[q][j] = (x[q][j] - m) * s[q];  // xhat
+        }
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+            const int64_t r = r0 + q * RPP + sub;
+            float m1 = 0.f, m2 = 0.f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float xh = x[q][j];
+                const float y = xh * gl[j] + bl[j];
+                const float dy = dl[q] * (w1[j] - w0[j]);  // dz1 = dl, dz0 = -dl
+                pw0[j] -= dl[q] * y;
+                pw1[j] += dl[q] * y;
+                pg[j] += dy * xh;
+                pb[j] += dy;
+                const float dxh = dy * gl[j];
+                m1 += dxh;
+                m2 += dxh * xh;
+            }
+            m1 = gsum<LPR>(m1) / D;
+            m2 = gsum<LPR>(m2) / D;
+            if (c0 == 0) pz += dl[q];
+            float out[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float dxh = dl[q] * (w1[j] - w0[j]) * gl[j];
+                out[j] = r < R ? s[q] * (dxh - m1 - x[q][j] * m2) : 0.f;
+                pc[j] += out[j];
+            }
+            if (r < R) st8(dH + r * D + c0, out);
+            if (dHt && r < R_end) *reinterpret_cast<uint4 *>(dHt + wl_offset(r, c0, D)) = pack8_bf16(out);
+        }
+    }
+    // lanes with the same column group: offsets LPR, 2 LPR, ..., 16
+#pragma unroll
+    for (int o = LPR; o < 32; o <<= 1)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            pw0[j] += __shfl_xor_sync(0xffffffffu, pw0[j], o);
+            pw1[j] += __shfl_xor_sync(0xffffffffu, pw1[j], o);
+            pg[j] += __shfl_xor_sync(0xffffffffu, pg[j], o);
+            pb[j] += __shfl_xor_sync(0xffffffffu, pb[j], o);
+            pc[j] += __shfl_xor_sync(0xffffffffu, pc[j], o);
+        }
+    pz = wsum(pz);
+    if (sub == 0)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            atomicAdd(red + c0 + j, pw0[j]);
+            atomicAdd(red + D + c0 + j, pw1[j]);
+            atomicAdd(red + 2 * D + c0 + j, pg[j]);
+            atomicAdd(red + 3 * D + c0 + j, pb[j]);
+            atomicAdd(red + 4 * D + 2 + c0 + j, pc[j]);
+        }
+    if (lane == 0) atomicAdd(red + 4 * D, pz);
+    __syncthreads();
+    for (int j = threadIdx.x; j < D; j += blockDim.x) {
+        atomicAdd(gWh + j, red[j]);
+        atomicAdd(gWh + D + j, red[D + j]);
+        atomicAdd(glnfg + j, red[2 * D + j]);
+        atomicAdd(glnfb + j, red[3 * D + j]);
+        if (dcol) atomicAdd(dcol + j, red[4 * D + 2 + j]);
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd(gbh, -red[4 * D]);
+        atomicAdd(gbh + 1, red[4 * D]);
+    }
+}
+
+// LayerNorm backward: dX = dres + rs (dY g - m1 - xhat m2) (dres may be
+// null), m1 = mean(dY g), m2 = mean(dY g xhat); dg += sum dY xhat, db += sum
+// dY.  Optionally the wide BF16 copy dXt of dX (rows past R up to the
+// row-block end zeroed) and dcol += sum_r dX (the bias gradient of the layer
+// that produced X's input gradient).
+template <int D, int RPW>
+__global__ void __launch_bounds__(256)
+ln_bwd_g8_kernel(const float *__restrict__ dY, const float *__restrict__ X,
+                 const float *__restrict__ mu, const float *__restrict__ rs,
+                 const float *__restrict__ g, const float *__restrict__ dres,
+                 float *__restrict__ dX, float *__restrict__ dg, float *__restrict__ db, int64_t R,
+                 unsigned char *__restrict__ dXt, float *__restrict__ dcol)
+{
+    constexpr int LPR = D / 8, RPP = 32 / LPR, RPI = RPW * RPP;
+    __shared__ float red[3][D];
+    for (int j = threadIdx.x; j < 3 * D; j += blockDim.x) (&red[0][0])[j] = 0.f;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, sub = lane / LPR, c0 = 8 * (lane % LPR);
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t R_end = dXt ? tl_blocks(R) * 128 : R;
+    float gl[8], pg[8], pb[8], pc[8];
+    ld8s(g + c0, gl);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) pg[j] = pb[j] = pc[j] = 0.f;
+    for (int64_t r0 = gw * RPI; r0 < R_end; r0 += nw * RPI) {
+        float x[RPW][8], dy[RPW][8], s[RPW];
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+            const int64_t r = r0 + q * RPP + sub, rr = r < R ? r : R - 1;
+            const float m = mu[rr];
+            s[q] = rs[rr];
+            ld8(X + rr * D + c0, x[q]);
+            ld8(dY + rr * D + c0, dy[q]);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                x[q][j] = (x[q][j] - m) * s[q];  // xhat
+                if (r >= R) dy[q][j] = 0.f;      // rows past the end add nothing
+            }
+        }
+        float m1[RPW], m2[RPW];  // all lanes shuffle before any row is skipped
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+            float a = 0.f, c = 0.f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float dxh = dy[q][j] * gl[j];
+                a += dxh;
+                c += dxh * x[q][j];
+            }
+            m1[q] = gsum<LPR>(a) * (1.0f / D);
+            m2[q] = gsum<LPR>(c) * (1.0f / D);
+        }
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+            const int64_t r = r0 + q * RPP + sub;
+            if (r >= R_end) break;
+            float out[8];
+            if (dres && r < R) ld8(dres + r * D + c0, out);
+            else
+#pragma unroll
+                for (int j = 0; j < 8; ++j) out[j] = 0.f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (r < R) out[j] += s[q] * (dy[q][j] * gl[j] - m1[q] - x[q][j] * m2[q]);
+                pg[j] += dy[q][j] * x[q][j];
+                pb[j] += dy[q][j];
+                pc[j] += out[j];
+            }
+            if (r < R) st8(dX + r * D + c0, out);
+            if (dXt) *reinterpret_cast<uint4 *>(dXt + wl_offset(r, c0, D)) = pack8_bf16(out);
+        }
+    }
+#pragma unroll
+    for (int o = LPR; o < 32; o <<= 1)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            pg[j] += __shfl_xor_sync(0xffffffffu, pg[j], o);
+            pb[j] += __shfl_xor_sync(0xffffffffu, pb[j], o);
+            pc[j] += __shfl_xor_sync(0xffffffffu, pc[j], o);
+        }
+    if (sub == 0)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            atomicAdd(&red[0][c0 + j], pg[j]);
+            atomicAdd(&red[1][c0 + j], pb[j]);
+            atomicAdd(&red[2][c0 + j], pc[j]);
+        }
+    __syncthreads();
+    for (int j = threadIdx.x; j < D; j += blockDim.x) {
+        atomicAdd(dg + j, red[0][j]);
+        atomicAdd(db + j, red[1][j]);
+        if (dcol) atomicAdd(dcol + j, red[2][j]);
+    }
+}
+
+// Embedding backward over a chunk: thread (t, j) sums dH over the samples of
+// its split (grid.y), one atomic per thread.
+__global__ void embed_bwd_split_kernel(const float *__restrict__ dH, const int8_t *__restrict__ spins,
+                                       int Bc, int N, int D, int dt, int per_split,
+                                       float *__restrict__ gtok, float *__restrict__ gpos)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)N * D) return;
+    const int t = (int)(i / D), j = (int)(i % D);
+    const int b0 = blockIdx.y * per_split, b1 = min(Bc, b0 + per_split);
+    if (j >= dt) {
+        float s = 0.f;
+        for (int b = b0; b < b1; ++b) s += dH[((size_t)b * N + t) * D + j];
+        atomicAdd(gpos + (size_t)t * (D - dt) + (j - dt), s);
+    } else {
+        float s0 = 0.f, s1 = 0.f;
+        for (int b = b0; b < b1; ++b) {
+            const size_t r = (size_t)b * N + t;
+            const float v = dH[r * D + j];
+            const int tk = t == 0 ? 0 : (spins[r - 1] + 1) >> 1;
+            if (tk) s1 += v; else s0 += v;
+        }
+        atomicAdd(gtok + j, s0);
+        atomicAdd(gtok + dt + j, s1);
     }
 }
 
@@ -1139,7 +1520,8 @@ template <int DH, typename TS>
 __global__ void __launch_bounds__(256)
 attn_bwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ O,
                      const float *__restrict__ dO, const float *__restrict__ LSE,
-                     float *__restrict__ dQKV, int N, int D, int NH, int mask, int W, int S)
+                     float *__restrict__ dQKV, int N, int D, int NH, int mask, int W, int S,
+                     unsigned char *__restrict__ dQKVt, float *__restrict__ bsum)
 {
     constexpr int DP = DH + 4, DPS = Pitch<DH, TS>::value;
     constexpr bool kF32 = sizeof(TS) == 4;
@@ -1172,13 +1554,37 @@ attn_bwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ O,
         Ds[t] = dot_regs<DH>(gr, orr);
     }
     __syncthreads();
-    // out_part 0/1/2 = q/k/v columns of dQKV: coalesced float4 rows from Os
+    // out_part 0/1/2 = q/k/v columns of dQKV, from the rows in Os: FP32 rows
+    // (coalesced float4), or 16-byte pieces of the wide BF16 copy plus this
+    // (sample, head)'s column sums (a slice of the bias gradient) in bsum
+    __shared__ float csum[256];
     auto flush = [&](int part) {
         __syncthreads();
-        for (int e = threadIdx.x; e < N * (DH / 4); e += blockDim.x) {
-            const int t = e / (DH / 4), c = e % (DH / 4);
-            *reinterpret_cast<float4 *>(dQKV + ((size_t)b * N + t) * 3 * D + part * D + hh * DH + 4 * c) =
-                *reinterpret_cast<const float4 *>(Os + t * DP + 4 * c);
+        if (dQKVt) {
+            for (int e = threadIdx.x; e < N * (DH / 8); e += blockDim.x) {
+                const int t = e / (DH / 8), c = e % (DH / 8);
+                float v[8];
+                ld8(Os + t * DP + 8 * c, v);
+                *reinterpret_cast<uint4 *>(dQKVt + wl_offset((int64_t)b * N + t, part * D + hh * DH + 8 * c, 3 * D)) =
+                    pack8_bf16(v);
+            }
+            constexpr int SL = 256 / DH;  // row slices (blockDim.x = 256)
+            const int j = threadIdx.x % DH, sl = threadIdx.x / DH;
+            float a = 0.f;
+            for (int t = sl; t < N; t += SL) a += Os[t * DP + j];
+            csum[threadIdx.x] = a;
+            __syncthreads();
+            if (threadIdx.x < DH) {
+                float tot = 0.f;
+                for (int q = 0; q < SL; ++q) tot += csum[q * DH + threadIdx.x];
+                bsum[(size_t)b * 3 * D + part * D + hh * DH + threadIdx.x] = tot;
+            }
+        } else {
+            for (int e = threadIdx.x; e < N * (DH / 4); e += blockDim.x) {
+                const int t = e / (DH / 4), c = e % (DH / 4);
+                *reinterpret_cast<float4 *>(dQKV + ((size_t)b * N + t) * 3 * D + part * D + hh * DH + 4 * c) =
+                    *reinterpret_cast<const float4 *>(Os + t * DP + 4 * c);
+            }
         }
         __syncthreads();
     };
@@ -1340,27 +1746,31 @@ void attn_fwd(const float *QKV, const float *Hin, float *O, float *Hmid, float *
         QKV, Hin, O, Hmid, LSE, Bc, c.N, c.d, c.n_heads, c.mask_kind, c.W, c.S);
 }
 
+// Returns true when the shared-memory kernel wrote the wide copy dQKVt and
+// the per-sample bias sums bsum instead of the FP32 dQKV (dQKVt non-null).
 template <int DH>
-void attn_bwd(const float *QKV, const float *O, const float *dO, const float *LSE, float *dQKV,
-              float *Dt, int Bc, const sg_config &c, cudaStream_t st)
+bool attn_bwd(const float *QKV, const float *O, const float *dO, const float *LSE, float *dQKV,
+              float *Dt, int Bc, const sg_config &c, cudaStream_t st, unsigned char *dQKVt,
+              float *bsum)
 {
     if (attn_bwd_smem_bytes<DH, float>(c.N) <= kAttnSmemMax) {
         auto go = [&](auto kern, size_t smem) {
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             kern<<<(unsigned)(Bc * c.n_heads), 256, smem, ::sg::counted(st)>>>(
-                QKV, O, dO, LSE, dQKV, c.N, c.d, c.n_heads, c.mask_kind, c.W, c.S);
+                QKV, O, dO, LSE, dQKV, c.N, c.d, c.n_heads, c.mask_kind, c.W, c.S, dQKVt, bsum);
         };
         if (c.precision == SG_BF16)
             go(attn_bwd_smem_kernel<DH, __nv_bfloat16>, attn_bwd_smem_bytes<DH, __nv_bfloat16>(c.N));
         else
             go(attn_bwd_smem_kernel<DH, float>, attn_bwd_smem_bytes<DH, float>(c.N));
-        return;
+        return dQKVt != nullptr;
     }
     const int warps = Bc * c.n_heads * ((c.N + 31) / 32);
     attn_bwd_q_kernel<DH><<<blocks_for(warps, 8), 256, 0, ::sg::counted(st)>>>(
         QKV, O, dO, LSE, dQKV, Dt, Bc, c.N, c.d, c.n_heads, c.mask_kind, c.W, c.S);
     attn_bwd_kv_kernel<DH><<<blocks_for(warps, 8), 256, 0, ::sg::counted(st)>>>(
         QKV, dO, LSE, Dt, dQKV, Bc, c.N, c.d, c.n_heads, c.mask_kind, c.W, c.S);
+    return false;
 }
 
 bool dh_supported(int dh) { return dh == 8 || dh == 16 || dh == 32; }
@@ -1377,17 +1787,20 @@ void attn_fwd_dispatch(int dh, const float *QKV, const float *Hin, float *O, flo
     else attn_fwd<32>(QKV, Hin, O, Hmid, LSE, Bc, c, st);
 }
 
-void attn_bwd_dispatch(int dh, const float *QKV, const float *O, const float *dO,
+// dQKV of one layer: FP32 rows, or (returns true) the wide BF16 copy dQKVt
+// and per-sample bias sums bsum [Bc][3 D] where the kernel fuses them.
+bool attn_bwd_dispatch(int dh, const float *QKV, const float *O, const float *dO,
                        const float *LSE, float *dQKV, float *Dt, int Bc, const sg_config &c,
-                       cudaStream_t st, int *err)
+                       cudaStream_t st, int *err, unsigned char *dQKVt = nullptr,
+                       float *bsum = nullptr)
 {
     if (attn_tc_supported(c)) {
         launch_attn_bwd_tc(c, QKV, O, dO, LSE, dQKV, Dt, Bc, err, st);
-        return;
+        return false;
     }
-    if (dh == 8) attn_bwd<8>(QKV, O, dO, LSE, dQKV, Dt, Bc, c, st);
-    else if (dh == 16) attn_bwd<16>(QKV, O, dO, LSE, dQKV, Dt, Bc, c, st);
-    else attn_bwd<32>(QKV, O, dO, LSE, dQKV, Dt, Bc, c, st);
+    if (dh == 8) return attn_bwd<8>(QKV, O, dO, LSE, dQKV, Dt, Bc, c, st, dQKVt, bsum);
+    if (dh == 16) return attn_bwd<16>(QKV, O, dO, LSE, dQKV, Dt, Bc, c, st, dQKVt, bsum);
+    return attn_bwd<32>(QKV, O, dO, LSE, dQKV, Dt, Bc, c, st, dQKVt, bsum);
 }
 
 template <int EPI>
@@ -1419,23 +1832,69 @@ void colsum(const float *A, int lda, int64_t M, int N, float *out, cudaStream_t 
     colsum_kernel<<<grid, block, 0, ::sg::counted(st)>>>(A, lda, M, N, out, rpb);
 }
 
-// dX = dres + LN'(X)^T dY (dres may alias nothing or be null), dg/db accumulated
-void ln_bwd_res(const float *dY, const float *X, const float *mu, const float *rs, const float *g,
-                const float *dres, float *dX, float *dg, float *db, int64_t R, int D, cudaStream_t st)
+int sm_count()
 {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+// Blocks of 256 threads for a row kernel of `rows` rows taking `rows_per_warp`
+// rows per warp pass, at most `per_sm` blocks per SM (grid-stride beyond).
+unsigned row_blocks(int64_t rows, int rows_per_warp, int per_sm)
+{
+    const int64_t warps = (rows + rows_per_warp - 1) / rows_per_warp;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, (int64_t)sm_count() * per_sm));
+}
+
+// LayerNorm forward: Y (FP32) and/or the wide BF16 copy At, mean and 1/std.
+void ln_fwd(const float *X, const float *g, const float *b, float *Y, float *mu, float *rs, int64_t R,
+            int D, unsigned char *At, cudaStream_t st)
+{
+    constexpr int RPW = 4;
+    const int64_t rows = At ? tl_blocks(R) * 128 : R;
+    auto go = [&](auto kern, int lpr) {
+        kern<<<row_blocks(rows, RPW * (32 / lpr), 8), 256, 0, ::sg::counted(st)>>>(X, g, b, Y, mu, rs, R, At);
+    };
+    switch (D) {
+    case 32: go(ln_fwd_g8_kernel<32, RPW>, 4); return;
+    case 64: go(ln_fwd_g8_kernel<64, RPW>, 8); return;
+    case 128: go(ln_fwd_g8_kernel<128, RPW>, 16); return;
+    case 256: go(ln_fwd_g8_kernel<256, RPW>, 32); return;
+    default: break;
+    }
+    ln_fwd_kernel<<<blocks_for(rows, 8), 256, 0, ::sg::counted(st)>>>(X, g, b, Y, mu, rs, R, D, At);
+}
+
+// dX = dres + LN'(X)^T dY (dres may be null), dg/db accumulated; optionally
+// the wide BF16 copy dXt and the column sums dcol += sum_r dX.  Returns false
+// (nothing launched for dXt/dcol) where the width has no fused kernel.
+bool ln_bwd_res(const float *dY, const float *X, const float *mu, const float *rs, const float *g,
+                const float *dres, float *dX, float *dg, float *db, int64_t R, int D, cudaStream_t st,
+                unsigned char *dXt = nullptr, float *dcol = nullptr)
+{
+    if (g8_width(D)) {
+        constexpr int RPW = 2;
+        const int64_t rows = dXt ? tl_blocks(R) * 128 : R;
+        auto go = [&](auto kern, int lpr) {
+            kern<<<row_blocks(rows, RPW * (32 / lpr), 8), 256, 0, ::sg::counted(st)>>>(
+                dY, X, mu, rs, g, dres, dX, dg, db, R, dXt, dcol);
+        };
+        switch (D) {
+        case 32: go(ln_bwd_g8_kernel<32, RPW>, 4); break;
+        case 64: go(ln_bwd_g8_kernel<64, RPW>, 8); break;
+        case 128: go(ln_bwd_g8_kernel<128, RPW>, 16); break;
+        default: go(ln_bwd_g8_kernel<256, RPW>, 32); break;
+        }
+        return true;
+    }
     constexpr int RPW = 4;
     const int64_t want = (R + 8 * RPW - 1) / (8 * RPW);
-    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 8));
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count() * 8));
     auto go = [&](auto kern) { kern<<<blocks, 256, 0, ::sg::counted(st)>>>(dY, X, mu, rs, g, dres, dX, dg, db, R); };
     switch (D) {
-    case 32: go(ln_bwd_rows_kernel<1, RPW>); return;
-    case 64: go(ln_bwd_rows_kernel<2, RPW>); return;
-    case 96: go(ln_bwd_rows_kernel<3, RPW>); return;
-    case 128: go(ln_bwd_rows_kernel<4, RPW>); return;
-    case 256: go(ln_bwd_rows_kernel<8, RPW>); return;
+    case 96: go(ln_bwd_rows_kernel<3, RPW>); return false;
     default: break;
     }
     // other widths: copy the residual, then the generic kernel accumulates
@@ -1443,8 +1902,8 @@ void ln_bwd_res(const float *dY, const float *X, const float *mu, const float *r
     const int rpb = 256;
     ln_bwd_kernel<<<blocks_for(R, rpb), 256, 2 * D * sizeof(float), ::sg::counted(st)>>>(
         dY, X, mu, rs, g, dX, dres ? 1 : 0, dg, db, R, D, rpb);
+    return false;
 }
-
 
 struct Work {
     std::vector<LayerBufs> layers;
@@ -1452,6 +1911,7 @@ struct Work {
     float *dH, *dHmid, *dA, *dQKV, *dF1, *Dt;
     // tensor-core backward scratch (wide BF16)
     unsigned char *dHt, *dF1t, *dQKVt;
+    float *bsum;    // per-sample bias sums of dQKV [R / N][3 D]
     uint8_t *tok8;  // patched models: the token class of every row
     int64_t total_floats;
 };
@@ -1499,12 +1959,13 @@ Work carve(const sg_config &c, float *base, int64_t R, bool bwd)
         w.dHt = take_t(R, D);
         w.dF1t = take_t(R, F);
         w.dQKVt = take_t(R, 3 * D);
+        w.bsum = take((R / c.N + 1) * 3 * D);
     }
     w.Hfin = take(R * D);
     w.Hping = take(R * D);
     w.muf = take(R);
     w.rsf = take(R);
-    w.Y = take(R * D);
+    if (spins_per_token(c) > 1 || !g8_width((int)D)) w.Y = take(R * D);  // patched / generic head
     w.ell = take(R);
     w.lp = take(R);
     if (spins_per_token(c) > 1) w.tok8 = reinterpret_cast<uint8_t *>(take((R + 3) / 4));
@@ -1564,9 +2025,8 @@ void forward_chunk(sg_model *m, const int8_t *spins, int Bc, Work &w, bool keep,
         float *Hout = keep ? (l + 1 < c.n_layers ? w.layers[l + 1].Hin : w.Hfin)
                            : (H == w.Hping ? w.Hfin : w.Hping);
         const bool tcp = use_tc(c);
-        ln_fwd_kernel<<<blocks_for(tcp ? tl_blocks(R) * 128 : R, 8), 256, 0, ::sg::counted(st)>>>(
-            Hin, W + o.ln1g, W + o.ln1b, tcp ? nullptr : L.A1, L.mu1, L.rs1, R, D,
-            tcp ? L.A1t : nullptr);
+        ln_fwd(Hin, W + o.ln1g, W + o.ln1b, tcp ? nullptr : L.A1, L.mu1, L.rs1, R, D,
+               tcp ? L.A1t : nullptr, st);
         if (tcp) {
             // tensor-core GEMMs over tiled BF16 operands; the LayerNorms write
             // the tiled A operands directly
@@ -1577,8 +2037,7 @@ void forward_chunk(sg_model *m, const int8_t *spins, int Bc, Work &w, bool keep,
             g.bias = m->wt + m->pack.bqkv[l]; g.out_f32 = L.QKV; g.ld_out = 3 * D;
             launch_row_gemm(g, TE_STORE_F32, st);
             attn_fwd_dispatch(dh, L.QKV, Hin, L.O, L.Hmid, L.LSE, Bc, c, st, (int *)m->err);
-            ln_fwd_kernel<<<blocks_for(tl_blocks(R) * 128, 8), 256, 0, ::sg::counted(st)>>>(
-                L.Hmid, W + o.ln2g, W + o.ln2b, nullptr, L.mu2, L.rs2, R, D, L.A2t);
+            ln_fwd(L.Hmid, W + o.ln2g, W + o.ln2b, nullptr, L.mu2, L.rs2, R, D, L.A2t, st);
             g.A = L.A2t; g.Bw = bt + m->bt_off[l][1]; g.NBw = (int)tl_blocks(F); g.N = F;
             g.bias = m->wt + m->pack.b1[l]; g.out_t = L.Gt; g.out_t2 = L.F1t;
             launch_row_gemm(g, TE_GELU_T, st);
@@ -1592,8 +2051,7 @@ void forward_chunk(sg_model *m, const int8_t *spins, int Bc, Work &w, bool keep,
         gemm<G_STORE>(L.A1, D, m->wt + m->pack.WqkvT[l], 3 * D, m->wt + m->pack.bqkv[l], L.QKV, 3 * D, R,
                       3 * D, D, st);
         attn_fwd_dispatch(dh, L.QKV, Hin, L.O, L.Hmid, L.LSE, Bc, c, st, (int *)m->err);
-        ln_fwd_kernel<<<blocks_for(R, 8), 256, 0, ::sg::counted(st)>>>(L.Hmid, W + o.ln2g, W + o.ln2b, L.A2,
-                                                        L.mu2, L.rs2, R, D);
+        ln_fwd(L.Hmid, W + o.ln2g, W + o.ln2b, L.A2, L.mu2, L.rs2, R, D, nullptr, st);
         if (keep)
             gemm<G_GELU>(L.A2, D, m->wt + m->pack.W1T[l], F, m->wt + m->pack.b1[l], L.G, F, R, F, D, st,
                          nullptr, F, L.F1);
@@ -1611,11 +2069,24 @@ void forward_chunk(sg_model *m, const int8_t *spins, int Bc, Work &w, bool keep,
             w.Hfin, W + m->off.lnfg, W + m->off.lnfb, W + m->off.Wh, W + m->off.bh, w.tok8,
             keep ? w.Y : nullptr, keep ? w.muf : nullptr, keep ? w.rsf : nullptr,
             keep ? w.ell : nullptr, w.lp, R, D, K);
-    else
-    head_fwd_kernel<<<blocks_for(R, 8), 256, 0, ::sg::counted(st)>>>(
-        w.Hfin, W + m->off.lnfg, W + m->off.lnfb, W + m->off.Wh, W + m->off.bh, spins,
-        keep ? w.Y : nullptr, keep ? w.muf : nullptr, keep ? w.rsf : nullptr,
-        keep ? w.ell : nullptr, w.lp, R, D);
+    else if (g8_width(D)) {
+        constexpr int RPW = 2;
+        auto go = [&](auto kern, int lpr) {
+            kern<<<row_blocks(R, RPW * (32 / lpr), 8), 256, 0, ::sg::counted(st)>>>(
+                w.Hfin, W + m->off.lnfg, W + m->off.lnfb, W + m->off.Wh, W + m->off.bh, spins,
+                keep ? w.muf : nullptr, keep ? w.rsf : nullptr, keep ? w.ell : nullptr, w.lp, R);
+        };
+        switch (D) {
+        case 32: go(head_fwd_g8_kernel<32, RPW>, 4); break;
+        case 64: go(head_fwd_g8_kernel<64, RPW>, 8); break;
+        case 128: go(head_fwd_g8_kernel<128, RPW>, 16); break;
+        default: go(head_fwd_g8_kernel<256, RPW>, 32); break;
+        }
+    } else
+        head_fwd_kernel<<<blocks_for(R, 8), 256, 0, ::sg::counted(st)>>>(
+            w.Hfin, W + m->off.lnfg, W + m->off.lnfb, W + m->off.Wh, W + m->off.bh, spins,
+            keep ? w.Y : nullptr, keep ? w.muf : nullptr, keep ? w.rsf : nullptr,
+            keep ? w.ell : nullptr, w.lp, R, D);
 }
 
 }  // namespace
@@ -1697,6 +2168,7 @@ sg_status launch_grad_f32(sg_model *m, const int8_t *spins, const float *coeff, 
         forward_chunk(m, sp, Bc, w, true, st);
         if (logq) seg_sum_kernel<<<Bc, 256, 0, ::sg::counted(st)>>>(w.lp, c.N, logq + b0);
         // head + LN_f
+        bool dH_fused = false;  // dHt and the top layer's b2 gradient already written
         if (P > 1) {
             const size_t red = ((size_t)K * D + 2 * D + K) * sizeof(float);
             const int shared = red <= 48 * 1024;
@@ -1704,10 +2176,28 @@ sg_status launch_grad_f32(sg_model *m, const int8_t *spins, const float *coeff, 
                 w.Hfin, w.muf, w.rsf, w.Y, w.ell, w.tok8, coeff + b0, W + O.lnfg, W + O.Wh,
                 W + O.bh, w.dH, grad + O.Wh, grad + O.bh, grad + O.lnfg, grad + O.lnfb, R, c.N, D,
                 K, 256, shared);
+        } else if (g8_width(D)) {
+            constexpr int RPW = 2;
+            // the tensor-core backward takes the wide copy of dH and b2's gradient here
+            unsigned char *dHt = use_tc(c) ? w.dHt : nullptr;
+            float *db2 = use_tc(c) ? grad + O.L[c.n_layers - 1].b2 : nullptr;
+            dH_fused = use_tc(c);
+            auto go = [&](auto kern, int lpr) {
+                kern<<<row_blocks(dHt ? tl_blocks(R) * 128 : R, RPW * (32 / lpr), 4), 256, 0,
+                       ::sg::counted(st)>>>(
+                    w.Hfin, w.muf, w.rsf, w.ell, sp, coeff + b0, W + O.lnfg, W + O.lnfb, W + O.Wh,
+                    w.dH, grad + O.Wh, grad + O.bh, grad + O.lnfg, grad + O.lnfb, R, c.N, dHt, db2);
+            };
+            switch (D) {
+            case 32: go(head_bwd_g8_kernel<32, RPW>, 4); break;
+            case 64: go(head_bwd_g8_kernel<64, RPW>, 8); break;
+            case 128: go(head_bwd_g8_kernel<128, RPW>, 16); break;
+            default: go(head_bwd_g8_kernel<256, RPW>, 32); break;
+            }
         } else
-        head_bwd_kernel<<<blocks_for(R, 256), 256, (4 * D + 2) * sizeof(float), ::sg::counted(st)>>>(
-            w.Hfin, w.muf, w.rsf, w.Y, w.ell, sp, coeff + b0, W + O.lnfg, W + O.Wh, w.dH,
-            grad + O.Wh, grad + O.bh, grad + O.lnfg, grad + O.lnfb, R, c.N, D, 256);
+            head_bwd_kernel<<<blocks_for(R, 256), 256, (4 * D + 2) * sizeof(float), ::sg::counted(st)>>>(
+                w.Hfin, w.muf, w.rsf, w.Y, w.ell, sp, coeff + b0, W + O.lnfg, W + O.Wh, w.dH,
+                grad + O.Wh, grad + O.bh, grad + O.lnfg, grad + O.lnfb, R, c.N, D, 256);
         for (int l = c.n_layers - 1; l >= 0 && use_tc(c); --l) {
             // tensor-core backward: dX GEMMs by row_gemm, weight gradients by
             // split wgrad reading the wide BF16 activations MN-major
@@ -1729,14 +2219,19 @@ sg_status launch_grad_f32(sg_model *m, const int8_t *spins, const float *coeff, 
             RowGemm g{};
             g.RB = RB; g.R = R; g.err = (int *)m->err;
             // FFN: H = Hmid + W2 G + b2, G = gelu(F1), F1 = W1 A2 + b1
-            launch_to_wide(w.dH, R, D, w.dHt, st);
+            if (!dH_fused) {
+                launch_to_wide(w.dH, R, D, w.dHt, st);
+                colsum(w.dH, D, R, D, grad + o.b2, st);
+            }
+            // dF1 = (dH W2) gelu'(F1), its column sums (b1's gradient) fused
             g.A = w.dHt; g.K = D; g.KC = (D + 63) / 64; g.Bw = bt + m->bt_off[l][3];
             g.NBw = (int)tl_blocks(F); g.N = F; g.aux_t = L.F1t; g.out_t = w.dF1t;
+            g.colsum = F <= 1024 ? grad + o.b1 : nullptr;
             launch_row_gemm(g, TE_GELU_BWD_T, st);
+            g.colsum = nullptr;
             wgrad(L.Gt, F, w.dHt, D, grad + o.W2, F, true);        // dW2[d][f] = sum dH[d] G[f]
-            colsum(w.dH, D, R, D, grad + o.b2, st);
             wgrad(w.dF1t, F, L.A2t, D, grad + o.W1, D, false);     // dW1[f][d] = sum dF1[f] A2[d]
-            {
+            if (F > 1024) {
                 const int64_t rpb = 4096;
                 dim3 grid((F + 31) / 32, (unsigned)((R + rpb - 1) / rpb)), block(32, 8);
                 colsum_tiled_kernel<<<grid, block, 0, ::sg::counted(st)>>>(w.dF1t, R, F, grad + o.b1, rpb);
@@ -1747,15 +2242,22 @@ sg_status launch_grad_f32(sg_model *m, const int8_t *spins, const float *coeff, 
             ln_bwd_res(w.dA, L.Hmid, L.mu2, L.rs2, W + o.ln2g, w.dH, w.dHmid, grad + o.ln2g,
                        grad + o.ln2b, R, D, st);
             // attention: Hmid = Hin + O(QKV)
-            attn_bwd_dispatch(dh, L.QKV, L.O, w.dHmid, L.LSE, w.dQKV, w.Dt, Bc, c, st, (int *)m->err);
-            launch_to_wide(w.dQKV, R, 3 * D, w.dQKVt, st);
+            if (attn_bwd_dispatch(dh, L.QKV, L.O, w.dHmid, L.LSE, w.dQKV, w.Dt, Bc, c, st,
+                                  (int *)m->err, w.dQKVt, w.bsum)) {
+                if (l == c.n_layers - 1) launch_zero_wide_tail(R, 3 * D, w.dQKVt, st);
+                colsum(w.bsum, 3 * D, Bc, 3 * D, grad + o.bqkv, st);
+            } else {
+                launch_to_wide(w.dQKV, R, 3 * D, w.dQKVt, st);
+                colsum(w.dQKV, 3 * D, R, 3 * D, grad + o.bqkv, st);
+            }
             wgrad(w.dQKVt, 3 * D, L.A1t, D, grad + o.Wqkv, D, false);  // dWqkv[j][d] = sum dQKV[j] A1[d]
-            colsum(w.dQKV, 3 * D, R, 3 * D, grad + o.bqkv, st);
             g.A = w.dQKVt; g.K = 3 * D; g.KC = (3 * D + 63) / 64; g.Bw = bt + m->bt_off[l][5];
             g.NBw = (int)tl_blocks(D); g.N = D; g.out_f32 = w.dA; g.ld_out = D;
             launch_row_gemm(g, TE_STORE_F32, st);
-            ln_bwd_res(w.dA, L.Hin, L.mu1, L.rs1, W + o.ln1g, w.dHmid, w.dH, grad + o.ln1g,
-                       grad + o.ln1b, R, D, st);
+            // dH of layer l - 1: with its wide copy and b2's gradient where fused
+            dH_fused = ln_bwd_res(w.dA, L.Hin, L.mu1, L.rs1, W + o.ln1g, w.dHmid, w.dH, grad + o.ln1g,
+                                  grad + o.ln1b, R, D, st, l > 0 ? w.dHt : nullptr,
+                                  l > 0 ? grad + O.L[l - 1].b2 : nullptr);
         }
         for (int l = c.n_layers - 1; l >= 0 && !use_tc(c); --l) {
             LayerBufs &L = w.layers[l];
@@ -1780,9 +2282,16 @@ sg_status launch_grad_f32(sg_model *m, const int8_t *spins, const float *coeff, 
         if (P > 1)
             embed_bwd_tok_kernel<<<blocks_for((int64_t)c.N * D, 256), 256, 0, ::sg::counted(st)>>>(
                 w.dH, w.tok8, Bc, c.N, D, c.d_token, grad + O.tok, grad + O.pos);
-        else
-        embed_bwd_kernel<<<blocks_for((int64_t)c.N * D, 256), 256, 0, ::sg::counted(st)>>>(
-            w.dH, sp, Bc, c.N, D, c.d_token, grad + O.tok, grad + O.pos);
+        else {
+            // samples split so that about 4 warps per SM-slot are in flight
+            const int64_t nd_blocks = blocks_for((int64_t)c.N * D, 256);
+            const int64_t splits = std::max<int64_t>(
+                1, std::min<int64_t>(Bc, ((int64_t)sm_count() * 8 + nd_blocks - 1) / nd_blocks));
+            const int per_split = (int)((Bc + splits - 1) / splits);
+            embed_bwd_split_kernel<<<dim3((unsigned)nd_blocks, (unsigned)((Bc + per_split - 1) / per_split)),
+                                     256, 0, ::sg::counted(st)>>>(w.dH, sp, Bc, c.N, D, c.d_token,
+                                                                  per_split, grad + O.tok, grad + O.pos);
+        }
     }
     return check_launch("REINFORCE backward");
 }

@@ -161,6 +161,27 @@ def test_bf16_grouped_models_match_oracle(n_models, per_model):
     assert np.array_equal(lq[:per_model], _np(l1))
 
 
+def test_d256_rows_do_not_depend_on_rows_per_cta():
+    """The d = 256 decode pairs each row with a mirror thread when a CTA
+    serves at most 64 rows and runs both key halves in one thread otherwise;
+    the two schedules give bit-identical rows (and match the oracle)."""
+    m = inputs.ModelShape(7, 1, 256, 8, mask_kind=1, W=3, S=2)
+    w = inputs.make_weights(m, 31)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    B = 64 * sms + 1  # 65 rows per CTA: the single-thread schedule
+    model = sg.Model(m, w, sg.SG_BF16)
+    s_big, l_big, f_big = model.sample(B, seed=4, with_flags=True)
+    s_small, l_small = model.sample(100, seed=4)  # one row per CTA: mirrored
+    model.check()
+    assert np.array_equal(_np(s_big[:100]), _np(s_small))
+    assert np.array_equal(_np(l_big[:100]), _np(l_small))
+    s, lq, fl = _np(s_big), _np(l_big), _np(f_big)
+    rows = [0, 64, B - 1]
+    so, lqo, _, _ = oracle_replay(m, w, 4, s, fl, rows=rows)
+    assert np.array_equal(so, s[rows])
+    assert np.abs(lqo - lq[rows]).max() <= BF16_LOGQ_TOL * m.N
+
+
 def test_bf16_grouped_models_at_the_group_limit():
     """64 models (the limit) of one sample each, and 65 rejected."""
     m = inputs.ModelShape(6, 1, 256, 8, mask_kind=1, W=2, S=1)
