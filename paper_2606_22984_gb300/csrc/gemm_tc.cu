@@ -94,6 +94,21 @@ __device__ __forceinline__ void row_epilogue(const RowGemm &g, const float (&v)[
 #pragma unroll
             for (int c = 0; c < 4; ++c) st8(g.out_t, wl_offset(r, col0 + 8 * c, g.N), o + 8 * c);
         }
+    } else if (EPI == TE_STORE_BF16) {
+        if (!valid) return;
+        float o[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) o[j] = v[j] + (g.bias ? __ldg(g.bias + col0 + j) : 0.f);
+        uint4 *dst = reinterpret_cast<uint4 *>(g.out_h + r * g.ld_out + col0);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            uint4 q;
+            q.x = pk2(o[8 * c], o[8 * c + 1]);
+            q.y = pk2(o[8 * c + 2], o[8 * c + 3]);
+            q.z = pk2(o[8 * c + 4], o[8 * c + 5]);
+            q.w = pk2(o[8 * c + 6], o[8 * c + 7]);
+            dst[c] = q;
+        }
     } else if (EPI == TE_GELU_T) {
         float x[32], y[32];
 #pragma unroll
@@ -602,6 +617,7 @@ sg_status launch_row_gemm(const RowGemm &g, int epi, cudaStream_t st)
         case TE_RESID_F32: return go(row_gemm_kernel<TE_RESID_F32>);
         case TE_GELU_T: return go(row_gemm_kernel<TE_GELU_T>);
         case TE_GELU_BWD_T: return go(row_gemm_kernel<TE_GELU_BWD_T>);
+        case TE_STORE_BF16: return go(row_gemm_kernel<TE_STORE_BF16>);
         default: return go(row_gemm_kernel<TE_STORE_F32_T>);
         }
     }
@@ -610,6 +626,7 @@ sg_status launch_row_gemm(const RowGemm &g, int epi, cudaStream_t st)
     case TE_RESID_F32: return go(tile_gemm_kernel<TE_RESID_F32>);
     case TE_GELU_T: return go(tile_gemm_kernel<TE_GELU_T>);
     case TE_GELU_BWD_T: return go(tile_gemm_kernel<TE_GELU_BWD_T>);
+    case TE_STORE_BF16: return go(tile_gemm_kernel<TE_STORE_BF16>);
     default: return go(tile_gemm_kernel<TE_STORE_F32_T>);
     }
 }

@@ -8,6 +8,7 @@
 // adjacent, so a B operand of up to 256 rows is one descriptor.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <stdint.h>
 
 #include "sg_internal.cuh"
@@ -58,6 +59,7 @@ enum TcEpilogue {
     TE_GELU_T = 2,      // v = acc + bias: out_t = gelu(v), out_t2 = v (both tiled BF16)
     TE_GELU_BWD_T = 3,  // out_t = acc * gelu'(aux_t) (tiled BF16)
     TE_STORE_F32_T = 4, // out_f32 = acc + bias and out_t = same (tiled BF16)
+    TE_STORE_BF16 = 5,  // out_h = acc + bias, row-major BF16 (ld_out elements per row)
 };
 
 struct RowGemm {
@@ -75,6 +77,7 @@ struct RowGemm {
     const float *resid;
     int ld_resid;
     unsigned char *out_t;     // W(R, N)
+    __nv_bfloat16 *out_h;     // row-major BF16 [R][ld_out]
     unsigned char *out_t2;    // W(R, N)
     const unsigned char *aux_t;  // W(R, N)
     float *colsum;            // TE_GELU_BWD_T: colsum[j] += sum_r out(r, j) (N <= 1024), or nullptr

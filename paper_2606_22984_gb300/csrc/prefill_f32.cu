@@ -1418,6 +1418,30 @@ __device__ __forceinline__ void stage_rows_t(TS *dst, const float *__restrict__ 
     }
 }
 
+// Rows of a BF16 row-major source (16-byte pieces) into the staged layout:
+// copied as they are (BF16 staging) or widened (FP32 staging).
+template <int DH, typename TS>
+__device__ __forceinline__ void stage_rows_h(TS *dst, const __nv_bfloat16 *__restrict__ src, int N,
+                                             int stride_src)
+{
+    constexpr int DP = sizeof(TS) == 4 ? DH + 4 : Pitch<DH, TS>::value;
+    for (int e = threadIdx.x; e < N * (DH / 8); e += blockDim.x) {
+        const int t = e / (DH / 8), c = e % (DH / 8);
+        const uint4 x = *reinterpret_cast<const uint4 *>(src + (size_t)t * stride_src + 8 * c);
+        if constexpr (sizeof(TS) == 2) {
+            *reinterpret_cast<uint4 *>(dst + t * DP + 8 * c) = x;
+        } else {
+            const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+            float *d = reinterpret_cast<float *>(dst) + t * DP + 8 * c;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                d[2 * j] = __uint_as_float(w[j] << 16);
+                d[2 * j + 1] = __uint_as_float(w[j] & 0xffff0000u);
+            }
+        }
+    }
+}
+
 template <int DH>
 __device__ __forceinline__ void row_regs_t(const float *row, float (&r)[DH])
 {
@@ -1451,11 +1475,57 @@ __device__ __forceinline__ float dot_row(const float *q, const float *row)
     return s;
 }
 
+// Packed FP32 arithmetic (fma.rn.f32x2 on sm_100 and later): a row of DH
+// values as DH / 2 pairs.  The dot product keeps the even and the odd
+// products in the two halves and adds them at the end.
+template <int DH>
+__device__ __forceinline__ void row_pairs(const float *row, float2 (&r)[DH / 2])
+{
+#pragma unroll
+    for (int c = 0; c < DH / 4; ++c) {
+        const float4 x = *reinterpret_cast<const float4 *>(row + 4 * c);
+        r[2 * c] = make_float2(x.x, x.y);
+        r[2 * c + 1] = make_float2(x.z, x.w);
+    }
+}
+
+template <int DH>
+__device__ __forceinline__ void row_pairs(const __nv_bfloat16 *row, float2 (&r)[DH / 2])
+{
+#pragma unroll
+    for (int c = 0; c < DH / 8; ++c) {
+        const uint4 x = *reinterpret_cast<const uint4 *>(row + 8 * c);
+        const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            r[4 * c + j] = make_float2(__uint_as_float(w[j] << 16), __uint_as_float(w[j] & 0xffff0000u));
+    }
+}
+
+template <int DH>
+__device__ __forceinline__ float dot_pairs(const float2 (&a)[DH / 2], const float2 (&b)[DH / 2])
+{
+    float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < DH / 2; ++j) s = __ffma2_rn(a[j], b[j], s);
+    return s.x + s.y;
+}
+
+// acc += w b, pairwise
+template <int DH>
+__device__ __forceinline__ void axpy_pairs(float2 (&acc)[DH / 2], float w, const float2 (&b)[DH / 2])
+{
+    const float2 w2 = make_float2(w, w);
+#pragma unroll
+    for (int j = 0; j < DH / 2; ++j) acc[j] = __ffma2_rn(w2, b[j], acc[j]);
+}
+
 template <int DH, typename TS>
 __global__ void __launch_bounds__(256)
 attn_fwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ Hin,
                      float *__restrict__ O, float *__restrict__ Hmid, float *__restrict__ LSE,
-                     int N, int D, int NH, int mask, int W, int S)
+                     int N, int D, int NH, int mask, int W, int S,
+                     const __nv_bfloat16 *__restrict__ QKVh)
 {
     constexpr int DP = DH + 4, DPS = Pitch<DH, TS>::value;
     extern __shared__ float4 sm4[];
@@ -1463,19 +1533,27 @@ attn_fwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ Hi
     TS *Ks = reinterpret_cast<TS *>(Qs + N * DP);
     TS *Vs = Ks + N * DPS;
     const int b = blockIdx.x / NH, hh = blockIdx.x % NH;
-    const float *base = QKV + (size_t)b * N * 3 * D;
-    stage_rows<DH>(Qs, base + hh * DH, N, 3 * D);
-    stage_rows_t<DH, TS>(Ks, base + D + hh * DH, N, 3 * D);
-    stage_rows_t<DH, TS>(Vs, base + 2 * D + hh * DH, N, 3 * D);
+    if (QKVh) {  // QKV rows in BF16
+        const __nv_bfloat16 *hb = QKVh + (size_t)b * N * 3 * D;
+        stage_rows_h<DH, float>(Qs, hb + hh * DH, N, 3 * D);
+        stage_rows_h<DH, TS>(Ks, hb + D + hh * DH, N, 3 * D);
+        stage_rows_h<DH, TS>(Vs, hb + 2 * D + hh * DH, N, 3 * D);
+    } else {
+        const float *base = QKV + (size_t)b * N * 3 * D;
+        stage_rows<DH>(Qs, base + hh * DH, N, 3 * D);
+        stage_rows_t<DH, TS>(Ks, base + D + hh * DH, N, 3 * D);
+        stage_rows_t<DH, TS>(Vs, base + 2 * D + hh * DH, N, 3 * D);
+    }
     __syncthreads();
     const float scale = rsqrtf((float)DH);
     for (int t = threadIdx.x; t < N; t += blockDim.x) {
         const size_t r = (size_t)b * N + t;
-        float q[DH], acc[DH];
+        float2 q[DH / 2], acc[DH / 2];
+        row_pairs<DH>(Qs + t * DP, q);
 #pragma unroll
-        for (int j = 0; j < DH; ++j) {
-            q[j] = Qs[t * DP + j] * scale;
-            acc[j] = 0.f;
+        for (int j = 0; j < DH / 2; ++j) {
+            q[j] = make_float2(q[j].x * scale, q[j].y * scale);
+            acc[j] = make_float2(0.f, 0.f);
         }
         int n_sink, band_lo;
         visible_ranges(mask, W, S, t, n_sink, band_lo);
@@ -1483,20 +1561,22 @@ attn_fwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ Hi
         float mx = -INFINITY, den = 0.f;
         for (int i = 0; i < nk; ++i) {
             const int k = i < n_sink ? i : band_lo + (i - n_sink);
-            float kr[DH], vr[DH];
-            row_regs_t<DH>(Ks + k * DPS, kr);
-            row_regs_t<DH>(Vs + k * DPS, vr);
-            const float sc = dot_regs<DH>(q, kr);
+            float2 kr[DH / 2], vr[DH / 2];
+            row_pairs<DH>(Ks + k * DPS, kr);
+            row_pairs<DH>(Vs + k * DPS, vr);
+            const float sc = dot_pairs<DH>(q, kr);
             const float mn = fmaxf(mx, sc);
             const float corr = __expf(mx - mn), p = __expf(sc - mn);
             mx = mn;
             den = den * corr + p;
+            const float2 c2 = make_float2(corr, corr), p2 = make_float2(p, p);
 #pragma unroll
-            for (int j = 0; j < DH; ++j) acc[j] = acc[j] * corr + p * vr[j];
+            for (int j = 0; j < DH / 2; ++j) acc[j] = __ffma2_rn(p2, vr[j], __fmul2_rn(acc[j], c2));
         }
         const float inv = 1.0f / den;
 #pragma unroll
-        for (int j = 0; j < DH; ++j) Qs[t * DP + j] = acc[j] * inv;  // own row only
+        for (int j = 0; j < DH / 2; ++j)  // own row only
+            *reinterpret_cast<float2 *>(Qs + t * DP + 2 * j) = make_float2(acc[j].x * inv, acc[j].y * inv);
         LSE[r * NH + hh] = mx + logf(den);
     }
     __syncthreads();
@@ -1521,7 +1601,8 @@ __global__ void __launch_bounds__(256)
 attn_bwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ O,
                      const float *__restrict__ dO, const float *__restrict__ LSE,
                      float *__restrict__ dQKV, int N, int D, int NH, int mask, int W, int S,
-                     unsigned char *__restrict__ dQKVt, float *__restrict__ bsum)
+                     unsigned char *__restrict__ dQKVt, float *__restrict__ bsum,
+                     const __nv_bfloat16 *__restrict__ QKVh)
 {
     constexpr int DP = DH + 4, DPS = Pitch<DH, TS>::value;
     constexpr bool kF32 = sizeof(TS) == 4;
@@ -1538,20 +1619,27 @@ attn_bwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ O,
     TS *Vs = Ks + N * DPS;
     TS *Gs = Vs + N * DPS;  // dO
     const int b = blockIdx.x / NH, hh = blockIdx.x % NH;
-    const float *base = QKV + (size_t)b * N * 3 * D;
-    stage_rows_t<DH, TS>(Qs, base + hh * DH, N, 3 * D);
-    stage_rows_t<DH, TS>(Ks, base + D + hh * DH, N, 3 * D);
-    stage_rows_t<DH, TS>(Vs, base + 2 * D + hh * DH, N, 3 * D);
+    if (QKVh) {  // QKV rows in BF16
+        const __nv_bfloat16 *hb = QKVh + (size_t)b * N * 3 * D;
+        stage_rows_h<DH, TS>(Qs, hb + hh * DH, N, 3 * D);
+        stage_rows_h<DH, TS>(Ks, hb + D + hh * DH, N, 3 * D);
+        stage_rows_h<DH, TS>(Vs, hb + 2 * D + hh * DH, N, 3 * D);
+    } else {
+        const float *base = QKV + (size_t)b * N * 3 * D;
+        stage_rows_t<DH, TS>(Qs, base + hh * DH, N, 3 * D);
+        stage_rows_t<DH, TS>(Ks, base + D + hh * DH, N, 3 * D);
+        stage_rows_t<DH, TS>(Vs, base + 2 * D + hh * DH, N, 3 * D);
+    }
     stage_rows_t<DH, TS>(Gs, dO + (size_t)b * N * D + hh * DH, N, D);
     stage_rows<DH>(Os, O + (size_t)b * N * D + hh * DH, N, D);
     for (int t = threadIdx.x; t < N; t += blockDim.x) Ls[t] = LSE[((size_t)b * N + t) * NH + hh];
     __syncthreads();
     const float scale = rsqrtf((float)DH);
     for (int t = threadIdx.x; t < N; t += blockDim.x) {
-        float gr[DH], orr[DH];
-        row_regs_t<DH>(Gs + t * DPS, gr);
-        row_regs<DH>(Os + t * DP, orr);
-        Ds[t] = dot_regs<DH>(gr, orr);
+        float2 gr[DH / 2], orr[DH / 2];
+        row_pairs<DH>(Gs + t * DPS, gr);
+        row_pairs<DH>(Os + t * DP, orr);
+        Ds[t] = dot_pairs<DH>(gr, orr);
     }
     __syncthreads();
     // out_part 0/1/2 = q/k/v columns of dQKV, from the rows in Os: FP32 rows
@@ -1590,13 +1678,13 @@ attn_bwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ O,
     };
     // dQ_t = scale * sum_k P_tk (dP_tk - D_t) k_k
     for (int t = threadIdx.x; t < N; t += blockDim.x) {
-        float q[DH], g[DH], dq[DH];
-        row_regs_t<DH>(Qs + t * DPS, q);
-        row_regs_t<DH>(Gs + t * DPS, g);
+        float2 q[DH / 2], g[DH / 2], dq[DH / 2];
+        row_pairs<DH>(Qs + t * DPS, q);
+        row_pairs<DH>(Gs + t * DPS, g);
 #pragma unroll
-        for (int j = 0; j < DH; ++j) {
-            q[j] *= scale;
-            dq[j] = 0.f;
+        for (int j = 0; j < DH / 2; ++j) {
+            q[j] = make_float2(q[j].x * scale, q[j].y * scale);
+            dq[j] = make_float2(0.f, 0.f);
         }
         const float lse = Ls[t], dd = Ds[t];
         int n_sink, band_lo;
@@ -1604,16 +1692,15 @@ attn_bwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ O,
         const int nk = n_sink + band_count(t, band_lo);
         for (int i = 0; i < nk; ++i) {
             const int k = i < n_sink ? i : band_lo + (i - n_sink);
-            float kr[DH], vr[DH];  // each row read once, with 128-bit loads
-            row_regs_t<DH>(Ks + k * DPS, kr);
-            row_regs_t<DH>(Vs + k * DPS, vr);
-            const float p = __expf(dot_regs<DH>(q, kr) - lse);
-            const float ds = p * (dot_regs<DH>(g, vr) - dd) * scale;
-#pragma unroll
-            for (int j = 0; j < DH; ++j) dq[j] += ds * kr[j];
+            float2 kr[DH / 2], vr[DH / 2];  // each row read once, with 128-bit loads
+            row_pairs<DH>(Ks + k * DPS, kr);
+            row_pairs<DH>(Vs + k * DPS, vr);
+            const float p = __expf(dot_pairs<DH>(q, kr) - lse);
+            const float ds = p * (dot_pairs<DH>(g, vr) - dd) * scale;
+            axpy_pairs<DH>(dq, ds, kr);
         }
 #pragma unroll
-        for (int j = 0; j < DH; ++j) Os[t * DP + j] = dq[j];  // own row
+        for (int j = 0; j < DH / 2; ++j) *reinterpret_cast<float2 *>(Os + t * DP + 2 * j) = dq[j];  // own row
     }
     flush(0);
     // dK and dV.  Keys seen only through the band: one thread per key, up to
@@ -1623,61 +1710,58 @@ attn_bwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ O,
     const int k_band0 = mask == SG_MASK_DENSE ? N : (S < N ? S : N);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     constexpr int KPT = 2;  // band keys per thread kept in registers (N <= 512)
-    float dv_keep[KPT][DH];
+    float2 dv_keep[KPT][DH / 2];
     int kk_i = 0;
     for (int k = k_band0 + threadIdx.x; k < N; k += blockDim.x, ++kk_i) {
-        float key[DH], val[DH], dk[DH], dv[DH];
-        row_regs_t<DH>(Ks + k * DPS, key);
-        row_regs_t<DH>(Vs + k * DPS, val);
+        float2 key[DH / 2], val[DH / 2], dk[DH / 2], dv[DH / 2];
+        row_pairs<DH>(Ks + k * DPS, key);
+        row_pairs<DH>(Vs + k * DPS, val);
 #pragma unroll
-        for (int j = 0; j < DH; ++j) {
-            key[j] *= scale;
-            dk[j] = dv[j] = 0.f;
+        for (int j = 0; j < DH / 2; ++j) {
+            key[j] = make_float2(key[j].x * scale, key[j].y * scale);
+            dk[j] = dv[j] = make_float2(0.f, 0.f);
         }
         const int t_hi = min(N - 1, k + W);
         for (int t = k; t <= t_hi; ++t) {
-            float qr[DH], gr[DH];
-            row_regs_t<DH>(Qs + t * DPS, qr);
-            row_regs_t<DH>(Gs + t * DPS, gr);
-            const float p = __expf(dot_regs<DH>(key, qr) - Ls[t]);
-            const float ds = p * (dot_regs<DH>(val, gr) - Ds[t]) * scale;
-#pragma unroll
-            for (int j = 0; j < DH; ++j) {
-                dk[j] += ds * qr[j];
-                dv[j] += p * gr[j];
-            }
+            float2 qr[DH / 2], gr[DH / 2];
+            row_pairs<DH>(Qs + t * DPS, qr);
+            row_pairs<DH>(Gs + t * DPS, gr);
+            const float p = __expf(dot_pairs<DH>(key, qr) - Ls[t]);
+            const float ds = p * (dot_pairs<DH>(val, gr) - Ds[t]) * scale;
+            axpy_pairs<DH>(dk, ds, qr);
+            axpy_pairs<DH>(dv, p, gr);
         }
 #pragma unroll
-        for (int j = 0; j < DH; ++j) {
-            Os[k * DP + j] = dk[j];
+        for (int j = 0; j < DH / 2; ++j) {
+            *reinterpret_cast<float2 *>(Os + k * DP + 2 * j) = dk[j];
             if (kk_i < KPT) dv_keep[kk_i][j] = dv[j];
         }
     }
     for (int k = warp; k < k_band0; k += nw) {
-        float key[DH], val[DH], dk[DH], dv[DH];
-        row_regs_t<DH>(Ks + k * DPS, key);
-        row_regs_t<DH>(Vs + k * DPS, val);
+        float2 key[DH / 2], val[DH / 2], dk2[DH / 2], dv2[DH / 2];
+        row_pairs<DH>(Ks + k * DPS, key);
+        row_pairs<DH>(Vs + k * DPS, val);
 #pragma unroll
-        for (int j = 0; j < DH; ++j) {
-            key[j] *= scale;
-            dk[j] = dv[j] = 0.f;
+        for (int j = 0; j < DH / 2; ++j) {
+            key[j] = make_float2(key[j].x * scale, key[j].y * scale);
+            dk2[j] = dv2[j] = make_float2(0.f, 0.f);
         }
         for (int t = k + lane; t < N; t += 32) {
-            float qr[DH], gr[DH];
-            row_regs_t<DH>(Qs + t * DPS, qr);
-            row_regs_t<DH>(Gs + t * DPS, gr);
-            const float p = __expf(dot_regs<DH>(key, qr) - Ls[t]);
-            const float ds = p * (dot_regs<DH>(val, gr) - Ds[t]) * scale;
-#pragma unroll
-            for (int j = 0; j < DH; ++j) {
-                dk[j] += ds * qr[j];
-                dv[j] += p * gr[j];
-            }
+            float2 qr[DH / 2], gr[DH / 2];
+            row_pairs<DH>(Qs + t * DPS, qr);
+            row_pairs<DH>(Gs + t * DPS, gr);
+            const float p = __expf(dot_pairs<DH>(key, qr) - Ls[t]);
+            const float ds = p * (dot_pairs<DH>(val, gr) - Ds[t]) * scale;
+            axpy_pairs<DH>(dk2, ds, qr);
+            axpy_pairs<DH>(dv2, p, gr);
         }
+        float dk[DH], dv[DH];
 #pragma unroll
-        for (int j = 0; j < DH; ++j) {
-            dk[j] = wsum(dk[j]);
-            dv[j] = wsum(dv[j]);
+        for (int j = 0; j < DH / 2; ++j) {
+            dk[2 * j] = wsum(dk2[j].x);
+            dk[2 * j + 1] = wsum(dk2[j].y);
+            dv[2 * j] = wsum(dv2[j].x);
+            dv[2 * j + 1] = wsum(dv2[j].y);
         }
         // dK to the output buffer; dV parked in row k of Vs (FP32 model: nothing
         // reads it again, the dQ phase is over and key k is owned by this warp)
@@ -1695,7 +1779,8 @@ attn_bwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ O,
     kk_i = 0;
     for (int k = k_band0 + threadIdx.x; k < N; k += blockDim.x, ++kk_i)
 #pragma unroll
-        for (int j = 0; j < DH; ++j) Os[k * DP + j] = dv_keep[kk_i < KPT ? kk_i : 0][j];
+        for (int j = 0; j < DH / 2; ++j)
+            *reinterpret_cast<float2 *>(Os + k * DP + 2 * j) = dv_keep[kk_i < KPT ? kk_i : 0][j];
     for (int k = warp; k < k_band0; k += nw)
         if (lane == 0)
 #pragma unroll
@@ -1722,23 +1807,23 @@ size_t attn_bwd_smem_bytes(int N)
 
 template <int DH, typename TS>
 void attn_fwd_t(const float *QKV, const float *Hin, float *O, float *Hmid, float *LSE, int Bc,
-                const sg_config &c, cudaStream_t st)
+                const sg_config &c, cudaStream_t st, const __nv_bfloat16 *QKVh)
 {
     const size_t fwd_smem = (size_t)c.N * (DH + 4) * sizeof(float) +
                             (size_t)2 * c.N * Pitch<DH, TS>::value * sizeof(TS);
     cudaFuncSetAttribute(attn_fwd_smem_kernel<DH, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)fwd_smem);
     attn_fwd_smem_kernel<DH, TS><<<(unsigned)(Bc * c.n_heads), 256, fwd_smem, ::sg::counted(st)>>>(
-        QKV, Hin, O, Hmid, LSE, c.N, c.d, c.n_heads, c.mask_kind, c.W, c.S);
+        QKV, Hin, O, Hmid, LSE, c.N, c.d, c.n_heads, c.mask_kind, c.W, c.S, QKVh);
 }
 
 template <int DH>
 void attn_fwd(const float *QKV, const float *Hin, float *O, float *Hmid, float *LSE, int Bc,
-              const sg_config &c, cudaStream_t st)
+              const sg_config &c, cudaStream_t st, const __nv_bfloat16 *QKVh)
 {
     if (attn_bwd_smem_bytes<DH, float>(c.N) <= kAttnSmemMax) {
-        if (c.precision == SG_BF16) attn_fwd_t<DH, __nv_bfloat16>(QKV, Hin, O, Hmid, LSE, Bc, c, st);
-        else attn_fwd_t<DH, float>(QKV, Hin, O, Hmid, LSE, Bc, c, st);
+        if (c.precision == SG_BF16) attn_fwd_t<DH, __nv_bfloat16>(QKV, Hin, O, Hmid, LSE, Bc, c, st, QKVh);
+        else attn_fwd_t<DH, float>(QKV, Hin, O, Hmid, LSE, Bc, c, st, QKVh);
         return;
     }
     const int warps = Bc * c.n_heads * ((c.N + 31) / 32);
@@ -1751,13 +1836,13 @@ void attn_fwd(const float *QKV, const float *Hin, float *O, float *Hmid, float *
 template <int DH>
 bool attn_bwd(const float *QKV, const float *O, const float *dO, const float *LSE, float *dQKV,
               float *Dt, int Bc, const sg_config &c, cudaStream_t st, unsigned char *dQKVt,
-              float *bsum)
+              float *bsum, const __nv_bfloat16 *QKVh)
 {
     if (attn_bwd_smem_bytes<DH, float>(c.N) <= kAttnSmemMax) {
         auto go = [&](auto kern, size_t smem) {
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             kern<<<(unsigned)(Bc * c.n_heads), 256, smem, ::sg::counted(st)>>>(
-                QKV, O, dO, LSE, dQKV, c.N, c.d, c.n_heads, c.mask_kind, c.W, c.S, dQKVt, bsum);
+                QKV, O, dO, LSE, dQKV, c.N, c.d, c.n_heads, c.mask_kind, c.W, c.S, dQKVt, bsum, QKVh);
         };
         if (c.precision == SG_BF16)
             go(attn_bwd_smem_kernel<DH, __nv_bfloat16>, attn_bwd_smem_bytes<DH, __nv_bfloat16>(c.N));
@@ -1775,16 +1860,31 @@ bool attn_bwd(const float *QKV, const float *O, const float *dO, const float *LS
 
 bool dh_supported(int dh) { return dh == 8 || dh == 16 || dh == 32; }
 
+// The BF16 tensor-core pass writes QKV in BF16 (row-major [R][3 D]) where the
+// shared-memory attention kernels serve the shape (they stage K and V, and the
+// backward also Q, in BF16 anyway); the tcgen05 attention and the
+// global-memory kernels read FP32 QKV.
+bool qkv_bf16(const sg_config &c)
+{
+    const int dh = c.d / c.n_heads;
+    if (!use_tc(c) || attn_tc_supported(c) || !dh_supported(dh)) return false;
+    const size_t need = dh == 8 ? attn_bwd_smem_bytes<8, float>(c.N)
+                      : dh == 16 ? attn_bwd_smem_bytes<16, float>(c.N)
+                                 : attn_bwd_smem_bytes<32, float>(c.N);
+    return need <= kAttnSmemMax;
+}
+
 void attn_fwd_dispatch(int dh, const float *QKV, const float *Hin, float *O, float *Hmid,
-                       float *LSE, int Bc, const sg_config &c, cudaStream_t st, int *err)
+                       float *LSE, int Bc, const sg_config &c, cudaStream_t st, int *err,
+                       const __nv_bfloat16 *QKVh = nullptr)
 {
     if (attn_tc_supported(c)) {  // BF16 model: tcgen05 attention
         launch_attn_fwd_tc(c, QKV, Hin, O, Hmid, LSE, Bc, err, st);
         return;
     }
-    if (dh == 8) attn_fwd<8>(QKV, Hin, O, Hmid, LSE, Bc, c, st);
-    else if (dh == 16) attn_fwd<16>(QKV, Hin, O, Hmid, LSE, Bc, c, st);
-    else attn_fwd<32>(QKV, Hin, O, Hmid, LSE, Bc, c, st);
+    if (dh == 8) attn_fwd<8>(QKV, Hin, O, Hmid, LSE, Bc, c, st, QKVh);
+    else if (dh == 16) attn_fwd<16>(QKV, Hin, O, Hmid, LSE, Bc, c, st, QKVh);
+    else attn_fwd<32>(QKV, Hin, O, Hmid, LSE, Bc, c, st, QKVh);
 }
 
 // dQKV of one layer: FP32 rows, or (returns true) the wide BF16 copy dQKVt
@@ -1792,15 +1892,15 @@ void attn_fwd_dispatch(int dh, const float *QKV, const float *Hin, float *O, flo
 bool attn_bwd_dispatch(int dh, const float *QKV, const float *O, const float *dO,
                        const float *LSE, float *dQKV, float *Dt, int Bc, const sg_config &c,
                        cudaStream_t st, int *err, unsigned char *dQKVt = nullptr,
-                       float *bsum = nullptr)
+                       float *bsum = nullptr, const __nv_bfloat16 *QKVh = nullptr)
 {
     if (attn_tc_supported(c)) {
         launch_attn_bwd_tc(c, QKV, O, dO, LSE, dQKV, Dt, Bc, err, st);
         return false;
     }
-    if (dh == 8) return attn_bwd<8>(QKV, O, dO, LSE, dQKV, Dt, Bc, c, st, dQKVt, bsum);
-    if (dh == 16) return attn_bwd<16>(QKV, O, dO, LSE, dQKV, Dt, Bc, c, st, dQKVt, bsum);
-    return attn_bwd<32>(QKV, O, dO, LSE, dQKV, Dt, Bc, c, st, dQKVt, bsum);
+    if (dh == 8) return attn_bwd<8>(QKV, O, dO, LSE, dQKV, Dt, Bc, c, st, dQKVt, bsum, QKVh);
+    if (dh == 16) return attn_bwd<16>(QKV, O, dO, LSE, dQKV, Dt, Bc, c, st, dQKVt, bsum, QKVh);
+    return attn_bwd<32>(QKV, O, dO, LSE, dQKV, Dt, Bc, c, st, dQKVt, bsum, QKVh);
 }
 
 template <int EPI>
@@ -2034,9 +2134,12 @@ void forward_chunk(sg_model *m, const int8_t *spins, int Bc, Work &w, bool keep,
             RowGemm g{};
             g.A = L.A1t; g.RB = tl_blocks(R); g.K = D; g.KC = (D + 63) / 64; g.R = R; g.err = (int *)m->err;
             g.Bw = bt + m->bt_off[l][0]; g.NBw = (int)tl_blocks(3 * D); g.N = 3 * D;
-            g.bias = m->wt + m->pack.bqkv[l]; g.out_f32 = L.QKV; g.ld_out = 3 * D;
-            launch_row_gemm(g, TE_STORE_F32, st);
-            attn_fwd_dispatch(dh, L.QKV, Hin, L.O, L.Hmid, L.LSE, Bc, c, st, (int *)m->err);
+            g.bias = m->wt + m->pack.bqkv[l]; g.ld_out = 3 * D;
+            const bool hq = qkv_bf16(c);
+            __nv_bfloat16 *QKVh = hq ? reinterpret_cast<__nv_bfloat16 *>(L.QKV) : nullptr;
+            g.out_f32 = L.QKV; g.out_h = QKVh;
+            launch_row_gemm(g, hq ? TE_STORE_BF16 : TE_STORE_F32, st);
+            attn_fwd_dispatch(dh, L.QKV, Hin, L.O, L.Hmid, L.LSE, Bc, c, st, (int *)m->err, QKVh);
             ln_fwd(L.Hmid, W + o.ln2g, W + o.ln2b, nullptr, L.mu2, L.rs2, R, D, L.A2t, st);
             g.A = L.A2t; g.Bw = bt + m->bt_off[l][1]; g.NBw = (int)tl_blocks(F); g.N = F;
             g.bias = m->wt + m->pack.b1[l]; g.out_t = L.Gt; g.out_t2 = L.F1t;
@@ -2243,7 +2346,8 @@ sg_status launch_grad_f32(sg_model *m, const int8_t *spins, const float *coeff, 
                        grad + o.ln2b, R, D, st);
             // attention: Hmid = Hin + O(QKV)
             if (attn_bwd_dispatch(dh, L.QKV, L.O, w.dHmid, L.LSE, w.dQKV, w.Dt, Bc, c, st,
-                                  (int *)m->err, w.dQKVt, w.bsum)) {
+                                  (int *)m->err, w.dQKVt, w.bsum,
+                                  qkv_bf16(c) ? reinterpret_cast<const __nv_bfloat16 *>(L.QKV) : nullptr)) {
                 if (l == c.n_layers - 1) launch_zero_wide_tail(R, 3 * D, w.dQKVt, st);
                 colsum(w.bsum, 3 * D, Bc, 3 * D, grad + o.bqkv, st);
             } else {
