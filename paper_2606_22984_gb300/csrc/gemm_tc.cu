@@ -110,25 +110,29 @@ __device__ __forceinline__ void row_epilogue(const RowGemm &g, const float (&v)[
             dst[c] = q;
         }
     } else if (EPI == TE_GELU_T) {
-        float x[32], y[32];
+        // gelu(v) = v Phi(v) and gelu'(v) = Phi(v) + v phi(v), Phi(v) = (1 + erf(v / sqrt 2)) / 2,
+        // phi the standard normal density: one erf serves both
+        float y[32], d[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-            x[j] = valid ? v[j] + __ldg(g.bias + col0 + j) : 0.f;
-            y[j] = valid ? gelu_f(x[j]) : 0.f;
+            const float x = v[j] + __ldg(g.bias + col0 + j);
+            const float Phi = 0.5f * (1.0f + erff(x * 0.70710678118654752f));
+            y[j] = valid ? x * Phi : 0.f;
+            if (g.out_t2) d[j] = valid ? Phi + x * 0.39894228040143268f * __expf(-0.5f * x * x) : 0.f;
         }
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             st8(g.out_t, wl_offset(r, col0 + 8 * c, g.N), y + 8 * c);
-            st8(g.out_t2, wl_offset(r, col0 + 8 * c, g.N), x + 8 * c);
+            if (g.out_t2) st8(g.out_t2, wl_offset(r, col0 + 8 * c, g.N), d + 8 * c);
         }
     } else {  // TE_GELU_BWD_T
         float y[32];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            float f1[8];
-            ld8(g.aux_t, wl_offset(r, col0 + 8 * c, g.N), f1);
+            float gp[8];
+            ld8(g.aux_t, wl_offset(r, col0 + 8 * c, g.N), gp);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) y[8 * c + j] = valid ? v[8 * c + j] * gelu_grad_f(f1[j]) : 0.f;
+            for (int j = 0; j < 8; ++j) y[8 * c + j] = valid ? v[8 * c + j] * gp[j] : 0.f;
         }
 #pragma unroll
         for (int c = 0; c < 4; ++c) st8(g.out_t, wl_offset(r, col0 + 8 * c, g.N), y + 8 * c);

@@ -56,8 +56,8 @@ __host__ __device__ __forceinline__ size_t wl_offset(int64_t r, int f, int F)
 enum TcEpilogue {
     TE_STORE_F32 = 0,   // out_f32 = acc (+ bias)
     TE_RESID_F32 = 1,   // out_f32 = resid + acc + bias
-    TE_GELU_T = 2,      // v = acc + bias: out_t = gelu(v), out_t2 = v (both tiled BF16)
-    TE_GELU_BWD_T = 3,  // out_t = acc * gelu'(aux_t) (tiled BF16)
+    TE_GELU_T = 2,      // v = acc + bias: out_t = gelu(v), out_t2 = gelu'(v) (both wide BF16; out_t2 optional)
+    TE_GELU_BWD_T = 3,  // out_t = acc * aux_t, aux_t = gelu'(v) from the forward (wide BF16)
     TE_STORE_F32_T = 4, // out_f32 = acc + bias and out_t = same (tiled BF16)
     TE_STORE_BF16 = 5,  // out_h = acc + bias, row-major BF16 (ld_out elements per row)
 };

@@ -1303,7 +1303,7 @@ unsigned blocks_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per)
 struct LayerBufs {
     float *Hin, *mu1, *rs1, *A1, *QKV, *O, *LSE, *Hmid, *mu2, *rs2, *A2, *F1, *G;
     // tensor-core path: tiled BF16 operands kept for the backward
-    unsigned char *A1t, *A2t, *Gt, *F1t;
+    unsigned char *A1t, *A2t, *Gt, *F1t;  // F1t holds gelu'(F1), the GELU derivative
 };
 
 // The BF16 model runs its teacher-forced GEMMs on tcgen05 (every output
@@ -1415,6 +1415,20 @@ __device__ __forceinline__ void stage_rows_t(TS *dst, const float *__restrict__ 
                                    __floats2bfloat162_rn(b.x, b.y), __floats2bfloat162_rn(b.z, b.w)};
             *reinterpret_cast<uint4 *>(dst + t * DP + 8 * c) = *reinterpret_cast<const uint4 *>(h);
         }
+    }
+}
+
+// Rows copied as they are (BF16 -> BF16 or FP32 -> FP32) by cp.async, 16
+// bytes per copy; the caller waits (cp_async_wait<0>) before the barrier.
+// Row pitch DPS elements; 16-byte aligned rows on both sides.
+template <int DH, int DPS, typename T>
+__device__ __forceinline__ void stage_rows_async(T *dst, const T *__restrict__ src, int N, int stride_src)
+{
+    constexpr int PIECES = DH * (int)sizeof(T) / 16;  // 16-byte pieces per row
+    constexpr int PER = 16 / (int)sizeof(T);          // elements per piece
+    for (int e = threadIdx.x; e < N * PIECES; e += blockDim.x) {
+        const int t = e / PIECES, c = e % PIECES;
+        tc::cp_async16(dst + t * DPS + PER * c, src + (size_t)t * stride_src + PER * c);
     }
 }
 
@@ -1533,11 +1547,18 @@ attn_fwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ Hi
     TS *Ks = reinterpret_cast<TS *>(Qs + N * DP);
     TS *Vs = Ks + N * DPS;
     const int b = blockIdx.x / NH, hh = blockIdx.x % NH;
-    if (QKVh) {  // QKV rows in BF16
+    if (QKVh) {  // QKV rows in BF16: K, V copied asynchronously, Q widened
         const __nv_bfloat16 *hb = QKVh + (size_t)b * N * 3 * D;
+        if constexpr (sizeof(TS) == 2) {
+            stage_rows_async<DH, DPS>(Ks, hb + D + hh * DH, N, 3 * D);
+            stage_rows_async<DH, DPS>(Vs, hb + 2 * D + hh * DH, N, 3 * D);
+            tc::cp_async_commit();
+        } else {
+            stage_rows_h<DH, TS>(Ks, hb + D + hh * DH, N, 3 * D);
+            stage_rows_h<DH, TS>(Vs, hb + 2 * D + hh * DH, N, 3 * D);
+        }
         stage_rows_h<DH, float>(Qs, hb + hh * DH, N, 3 * D);
-        stage_rows_h<DH, TS>(Ks, hb + D + hh * DH, N, 3 * D);
-        stage_rows_h<DH, TS>(Vs, hb + 2 * D + hh * DH, N, 3 * D);
+        if constexpr (sizeof(TS) == 2) tc::cp_async_wait<0>();
     } else {
         const float *base = QKV + (size_t)b * N * 3 * D;
         stage_rows<DH>(Qs, base + hh * DH, N, 3 * D);
@@ -1619,11 +1640,21 @@ attn_bwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ O,
     TS *Vs = Ks + N * DPS;
     TS *Gs = Vs + N * DPS;  // dO
     const int b = blockIdx.x / NH, hh = blockIdx.x % NH;
+    bool async = false;
     if (QKVh) {  // QKV rows in BF16
         const __nv_bfloat16 *hb = QKVh + (size_t)b * N * 3 * D;
-        stage_rows_h<DH, TS>(Qs, hb + hh * DH, N, 3 * D);
-        stage_rows_h<DH, TS>(Ks, hb + D + hh * DH, N, 3 * D);
-        stage_rows_h<DH, TS>(Vs, hb + 2 * D + hh * DH, N, 3 * D);
+        if constexpr (sizeof(TS) == 2) {  // copied asynchronously, with O
+            stage_rows_async<DH, DPS>(Qs, hb + hh * DH, N, 3 * D);
+            stage_rows_async<DH, DPS>(Ks, hb + D + hh * DH, N, 3 * D);
+            stage_rows_async<DH, DPS>(Vs, hb + 2 * D + hh * DH, N, 3 * D);
+            stage_rows_async<DH, DP>(Os, O + (size_t)b * N * D + hh * DH, N, D);
+            tc::cp_async_commit();
+            async = true;
+        } else {
+            stage_rows_h<DH, TS>(Qs, hb + hh * DH, N, 3 * D);
+            stage_rows_h<DH, TS>(Ks, hb + D + hh * DH, N, 3 * D);
+            stage_rows_h<DH, TS>(Vs, hb + 2 * D + hh * DH, N, 3 * D);
+        }
     } else {
         const float *base = QKV + (size_t)b * N * 3 * D;
         stage_rows_t<DH, TS>(Qs, base + hh * DH, N, 3 * D);
@@ -1631,8 +1662,9 @@ attn_bwd_smem_kernel(const float *__restrict__ QKV, const float *__restrict__ O,
         stage_rows_t<DH, TS>(Vs, base + 2 * D + hh * DH, N, 3 * D);
     }
     stage_rows_t<DH, TS>(Gs, dO + (size_t)b * N * D + hh * DH, N, D);
-    stage_rows<DH>(Os, O + (size_t)b * N * D + hh * DH, N, D);
+    if (!async) stage_rows<DH>(Os, O + (size_t)b * N * D + hh * DH, N, D);
     for (int t = threadIdx.x; t < N; t += blockDim.x) Ls[t] = LSE[((size_t)b * N + t) * NH + hh];
+    if (async) tc::cp_async_wait<0>();
     __syncthreads();
     const float scale = rsqrtf((float)DH);
     for (int t = threadIdx.x; t < N; t += blockDim.x) {
@@ -2142,7 +2174,8 @@ void forward_chunk(sg_model *m, const int8_t *spins, int Bc, Work &w, bool keep,
             attn_fwd_dispatch(dh, L.QKV, Hin, L.O, L.Hmid, L.LSE, Bc, c, st, (int *)m->err, QKVh);
             ln_fwd(L.Hmid, W + o.ln2g, W + o.ln2b, nullptr, L.mu2, L.rs2, R, D, L.A2t, st);
             g.A = L.A2t; g.Bw = bt + m->bt_off[l][1]; g.NBw = (int)tl_blocks(F); g.N = F;
-            g.bias = m->wt + m->pack.b1[l]; g.out_t = L.Gt; g.out_t2 = L.F1t;
+            // G = gelu(F1) for FFN2, and gelu'(F1) kept for the backward
+            g.bias = m->wt + m->pack.b1[l]; g.out_t = L.Gt; g.out_t2 = keep ? L.F1t : nullptr;
             launch_row_gemm(g, TE_GELU_T, st);
             g.A = L.Gt; g.K = F; g.KC = (F + 63) / 64; g.Bw = bt + m->bt_off[l][2]; g.NBw = (int)tl_blocks(D);
             g.N = D; g.bias = m->wt + m->pack.b2[l]; g.out_f32 = Hout; g.ld_out = D;
