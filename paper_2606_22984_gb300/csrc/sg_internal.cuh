@@ -3,6 +3,8 @@
 // instance objects, and launch helpers.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -253,6 +255,15 @@ sg_status launch_attn_fwd_tc(const sg_config &c, const float *QKV, const float *
 sg_status launch_attn_bwd_tc(const sg_config &c, const float *QKV, const float *O, const float *dO,
                              const float *LSE, float *dQKV, float *Dt, int Bc, int *err,
                              cudaStream_t st);
+// Attention of the BF16 teacher-forced pass on warp-level tensor-core MMAs
+// (head dims 16 and 32), QKV rows in BF16; the backward writes dQKV as wide
+// BF16 and per-sample bias sums bsum [Bc][3 d].
+bool attn_mma_supported(const sg_config &c);
+sg_status launch_attn_fwd_mma(const sg_config &c, const __nv_bfloat16 *QKVh, const float *Hin,
+                              float *O, float *Hmid, float *LSE, int Bc, cudaStream_t st);
+sg_status launch_attn_bwd_mma(const sg_config &c, const __nv_bfloat16 *QKVh, const float *O,
+                              const float *dO, const float *LSE, unsigned char *dQKVt, float *bsum,
+                              int Bc, cudaStream_t st);
 sg_status launch_adam(float *w, const float *g, float *m, float *v, int64_t n, float lr,
                       float b1, float b2, float eps, int64_t step, cudaStream_t st);
 }  // namespace sg
