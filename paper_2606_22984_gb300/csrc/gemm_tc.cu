@@ -492,6 +492,112 @@ __global__ void __launch_bounds__(192, 1) wgrad_kernel(const __grid_constant__ W
     if (warp == 1) tc::tmem_dealloc(tmem, 256);
 }
 
+// wgrad_rows_kernel: the same product when every feature of A (M <= 512,
+// ceil(M / 128) x N <= 512 TMEM columns) and of B (N <= 256) fits one CTA:
+// a stage is one row block of A and one of B, each a single bulk copy
+// (contiguous in the wide layout), two stages in flight.  Per 16-row k-step
+// one MMA per 128 features of A; A's 8-row groups are 16 M bytes apart.  A
+// last 128-feature window that overhangs M reads the next row group (or B's
+// block); those accumulator rows are never stored.
+__global__ void __launch_bounds__(192, 1) wgrad_rows_kernel(const __grid_constant__ WgradGemm g)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    constexpr int stages = 2;
+    const int nmt = (g.M + 127) / 128;
+    const uint32_t a_bytes = (uint32_t)wl_block_bytes(g.M), b_bytes = (uint32_t)wl_block_bytes(g.N);
+    const uint32_t stage_bytes = a_bytes + b_bytes;
+    const int64_t rb0 = (int64_t)blockIdx.x * g.rb_per_cta;
+    const int64_t rb1 = rb0 + g.rb_per_cta < g.RB ? rb0 + g.rb_per_cta : g.RB;
+    const int64_t n = rb1 > rb0 ? rb1 - rb0 : 0;
+    __shared__ uint64_t full[stages], empty[stages], tfull;
+    __shared__ uint32_t tslot;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < stages; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        tc::mbar_init(&tfull, 1);
+        tc::fence_mbar_init();
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(&tslot, 512);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = tslot;
+    if (warp == 0 && lane == 0) {
+        int64_t j = 0;
+        for (; j < n; ++j) {
+            const int s = (int)(j % stages);
+            if (j >= stages && !tc::mbar_wait(&empty[s], (uint32_t)((j / stages - 1) & 1))) {
+                atomicExch(g.err, 24);
+                break;
+            }
+            const int64_t rb = rb0 + j;
+            unsigned char *dst = smem + (size_t)s * stage_bytes;
+            tc::mbar_arrive_expect_tx(&full[s], stage_bytes);
+            tc::bulk_g2s(dst, g.A + (size_t)rb * a_bytes, a_bytes, &full[s]);
+            tc::bulk_g2s(dst + a_bytes, g.Bm + (size_t)rb * b_bytes, b_bytes, &full[s]);
+        }
+        // no bulk copy may be in flight when the CTA exits
+        for (int64_t jj = j > stages ? j - stages : 0; jj < j; ++jj)
+            if (!tc::mbar_wait(&full[jj % stages], (uint32_t)((jj / stages) & 1))) break;
+    } else if (warp == 1 && lane == 0) {
+        const uint32_t idesc = tc::idesc_bf16(128, g.N) | (1u << 15) | (1u << 16);  // A, B MN-major
+        bool ok = true;
+        for (int64_t j = 0; j < n; ++j) {
+            const int s = (int)(j % stages);
+            if (!tc::mbar_wait(&full[s], (uint32_t)((j / stages) & 1))) {
+                ok = false;
+                break;
+            }
+            tc::tc_fence_after();
+            const uint32_t sa = tc::smem_u32(smem + (size_t)s * stage_bytes);
+            const uint32_t sb = sa + a_bytes;
+#pragma unroll 1
+            for (int ks = 0; ks < 8; ++ks)  // 16 rows = two 8-row groups per MMA
+                for (int mt = 0; mt < nmt; ++mt)
+                    tc::mma_bf16(tmem + (uint32_t)(mt * g.N),
+                                 tc::smem_desc(sa + ks * 2 * 16 * g.M + mt * 2048, 16 * g.M, 128),
+                                 tc::smem_desc(sb + ks * 2 * 16 * g.N, 16 * g.N, 128), idesc,
+                                 (j | ks) != 0 ? 1u : 0u);
+            tc::mma_commit(&empty[s]);
+        }
+        if (!ok) atomicExch(g.err, 25);
+        tc::mma_commit(&tfull);
+    } else if (warp >= 2 && n > 0) {
+        const int q = warp & 3;
+        if (tc::mbar_wait(&tfull, 0)) {
+            tc::tc_fence_after();
+            for (int mt = 0; mt < nmt; ++mt) {
+                const int m = mt * 128 + 32 * q + lane;
+                for (int c = 0; c < g.N / 32; ++c) {
+                    float v[32];
+                    tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(mt * g.N + 32 * c), v);
+                    tc::tmem_wait_ld();
+                    if (m < g.M) {
+                        const int n0 = 32 * c;
+                        if (g.transpose_out)
+#pragma unroll
+                            for (int jj = 0; jj < 32; ++jj) atomicAdd(g.C + (size_t)(n0 + jj) * g.ldc + m, v[jj]);
+                        else
+#pragma unroll
+                            for (int jj = 0; jj < 32; ++jj) atomicAdd(g.C + (size_t)m * g.ldc + n0 + jj, v[jj]);
+                    }
+                }
+            }
+        } else if (lane == 0) {
+            atomicExch(g.err, 26);
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) tc::tmem_dealloc(tmem, 512);
+}
+
 // FP32 row-major -> tiled BF16.  Thread = (8-element group along the tiled
 // K axis, tiled row); padding is written as zeros.
 __global__ void to_tiled_kernel(const float *__restrict__ X, int64_t R, int F, int ldx,
@@ -639,6 +745,22 @@ sg_status launch_wgrad_gemm(const WgradGemm &g, cudaStream_t st)
 {
     if (g.N % 16 || g.M % 16 || g.N < 16 || g.M < 16)
         return fail(SG_EUNSUPPORTED, "weight-gradient GEMM needs feature counts that are multiples of 16");
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int nmt = (g.M + 127) / 128;
+    const size_t rows_stage = wl_block_bytes(g.M) + wl_block_bytes(g.N);
+    if (g.N <= 256 && g.N % 32 == 0 && nmt * g.N <= 512 && 2 * rows_stage <= 200 * 1024) {
+        // whole row blocks per stage: one CTA per SM, row blocks split evenly
+        WgradGemm h = g;
+        const int64_t ctas = std::min<int64_t>(g.RB, sms);
+        h.rb_per_cta = (g.RB + ctas - 1) / ctas;
+        const size_t smem = 2 * rows_stage;
+        SG_CUDA_TRY(cudaFuncSetAttribute(wgrad_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        wgrad_rows_kernel<<<(unsigned)((g.RB + h.rb_per_cta - 1) / h.rb_per_cta), 192, smem,
+                            ::sg::counted(st)>>>(h);
+        return check_launch("wgrad_rows_kernel");
+    }
     const int nw = std::min(256, g.N);
     const size_t stage = (size_t)128 * 128 * 2 + (size_t)128 * nw * 2;
     const int stages = (int)std::min<size_t>(4, (200 * 1024) / stage);

@@ -1899,8 +1899,8 @@ bool dh_supported(int dh) { return dh == 8 || dh == 16 || dh == 32; }
 bool qkv_bf16(const sg_config &c)
 {
     const int dh = c.d / c.n_heads;
+    if (use_tc(c) && attn_mma_supported(c)) return true;
     if (!use_tc(c) || attn_tc_supported(c) || !dh_supported(dh)) return false;
-    if (attn_mma_supported(c)) return true;
     const size_t need = dh == 8 ? attn_bwd_smem_bytes<8, float>(c.N)
                       : dh == 16 ? attn_bwd_smem_bytes<16, float>(c.N)
                                  : attn_bwd_smem_bytes<32, float>(c.N);
@@ -1911,12 +1911,12 @@ void attn_fwd_dispatch(int dh, const float *QKV, const float *Hin, float *O, flo
                        float *LSE, int Bc, const sg_config &c, cudaStream_t st, int *err,
                        const __nv_bfloat16 *QKVh = nullptr)
 {
-    if (attn_tc_supported(c)) {  // BF16 model: tcgen05 attention
-        launch_attn_fwd_tc(c, QKV, Hin, O, Hmid, LSE, Bc, err, st);
-        return;
-    }
     if (QKVh && attn_mma_supported(c)) {  // BF16 QKV: warp-level tensor-core MMAs
         launch_attn_fwd_mma(c, QKVh, Hin, O, Hmid, LSE, Bc, st);
+        return;
+    }
+    if (attn_tc_supported(c)) {  // BF16 model: tcgen05 attention
+        launch_attn_fwd_tc(c, QKV, Hin, O, Hmid, LSE, Bc, err, st);
         return;
     }
     if (dh == 8) attn_fwd<8>(QKV, Hin, O, Hmid, LSE, Bc, c, st, QKVh);
@@ -1931,13 +1931,13 @@ bool attn_bwd_dispatch(int dh, const float *QKV, const float *O, const float *dO
                        cudaStream_t st, int *err, unsigned char *dQKVt = nullptr,
                        float *bsum = nullptr, const __nv_bfloat16 *QKVh = nullptr)
 {
-    if (attn_tc_supported(c)) {
-        launch_attn_bwd_tc(c, QKV, O, dO, LSE, dQKV, Dt, Bc, err, st);
-        return false;
-    }
     if (QKVh && dQKVt && attn_mma_supported(c)) {
         launch_attn_bwd_mma(c, QKVh, O, dO, LSE, dQKVt, bsum, Bc, st);
         return true;
+    }
+    if (attn_tc_supported(c)) {
+        launch_attn_bwd_tc(c, QKV, O, dO, LSE, dQKV, Dt, Bc, err, st);
+        return false;
     }
     if (dh == 8) return attn_bwd<8>(QKV, O, dO, LSE, dQKV, Dt, Bc, c, st, dQKVt, bsum, QKVh);
     if (dh == 16) return attn_bwd<16>(QKV, O, dO, LSE, dQKV, Dt, Bc, c, st, dQKVt, bsum, QKVh);

@@ -442,12 +442,15 @@ BF16_TF_MODELS = [inputs.ModelShape(20, 2, 32, 4), inputs.ModelShape(40, 2, 64, 
                   inputs.ModelShape(24, 2, 128, 8),
                   inputs.ModelShape(30, 1, 96, 6, mask_kind=1, W=5, S=4),
                   inputs.ModelShape(20, 1, 256, 8, mask_kind=1, W=6, S=3),
-                  # attention on the tensor cores (a query sees >= 64 keys):
-                  # dense over two query tiles with a ragged tail, a band
-                  # crossing tile edges with its sink, d_h = 32
+                  # warp-level MMA attention with many keys per query: dense
+                  # over several tiles with a ragged tail, a band crossing
+                  # tile edges with its sink, d_h = 32
                   inputs.ModelShape(160, 2, 64, 4),
                   inputs.ModelShape(300, 1, 64, 4, mask_kind=1, W=70, S=9),
-                  inputs.ModelShape(140, 1, 256, 8)]
+                  inputs.ModelShape(140, 1, 256, 8),
+                  # a sequence beyond the MMA kernels' shared memory (d_h = 32):
+                  # the tcgen05 flash attention
+                  inputs.ModelShape(650, 1, 64, 2, mask_kind=1, W=70, S=9)]
 
 
 @pytest.mark.parametrize("m", BF16_TF_MODELS)
