@@ -62,6 +62,31 @@ __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// 2^x (MUFU ex2, relative error about 2^-22); the softmax runs in base 2
+// with log2(e) folded into its scale and into the stored log-sum-exp.
+__device__ __forceinline__ float ex2(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+constexpr float kLog2e = 1.4426950408889634f;
+
+// Query t sees key k iff 0 <= t - k <= lim(k): lim = W for band keys, and
+// unbounded for sink keys (k < S) and under the dense causal mask.
+__device__ __forceinline__ uint32_t key_lim(int mask, int W, int S, int k)
+{
+    return (mask == SG_MASK_DENSE || k < S) ? 0x7fffffffu : (uint32_t)W;
+}
+
+// Every (query, key) of the 16 x 16 block at (t0, k0) is visible.
+__device__ __forceinline__ bool block_full(int mask, int W, int S, int N, int t0, int k0)
+{
+    return t0 >= k0 + 16 && t0 + 16 <= N &&
+           (mask == SG_MASK_DENSE || k0 + 16 <= S || t0 + 15 - k0 <= W);
+}
+
 // Byte offset of 16-byte chunk c of row r in a [rows][DH] BF16 array.
 template <int DH>
 __device__ __forceinline__ uint32_t sw_off(int r, int c)
@@ -198,7 +223,7 @@ attn_fwd_mma_kernel(const __nv_bfloat16 *__restrict__ QKVh, const float *__restr
     __syncthreads();
     const uint32_t sQ = tc::smem_u32(smem), sK = sQ + (uint32_t)part_bytes,
                    sV = sQ + 2 * (uint32_t)part_bytes;
-    const float scale = rsqrtf((float)DH);
+    const float sc2 = rsqrtf((float)DH) * kLog2e;  // softmax scale in base 2
     for (int tile = warp; tile < Npad / 16; tile += kThreads / 32) {
         const int t0 = 16 * tile;
         const int r_lo = t0 + g, r_hi = t0 + g + 8;
@@ -216,16 +241,21 @@ attn_fwd_mma_kernel(const __nv_bfloat16 *__restrict__ QKVh, const float *__restr
             for (int k0 = lo[ri]; k0 < hi[ri]; k0 += 16) {
                 float s[2][4];
                 scores<DH>(s, qa, sK, k0);
+                // scores in base 2: x = log2(e) scale s, masked to -inf
+                const bool full = block_full(mask, W, S, N, t0, k0);
                 float mx_lo = -INFINITY, mx_hi = -INFINITY;
 #pragma unroll
                 for (int nb = 0; nb < 2; ++nb)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int row = j < 2 ? r_lo : r_hi, key = k0 + 8 * nb + 2 * q + (j & 1);
-                        const bool ok = row < N && key_visible(mask, W, S, row, key);
-                        s[nb][j] = ok ? s[nb][j] * scale : -INFINITY;
-                        if (j < 2) mx_lo = fmaxf(mx_lo, s[nb][j]);
-                        else mx_hi = fmaxf(mx_hi, s[nb][j]);
+                    for (int e = 0; e < 2; ++e) {
+                        const int key = k0 + 8 * nb + 2 * q + e;
+                        const uint32_t lim = key_lim(mask, W, S, key);
+                        const bool ok_lo = full || ((uint32_t)(r_lo - key) <= lim && r_lo < N);
+                        const bool ok_hi = full || ((uint32_t)(r_hi - key) <= lim && r_hi < N);
+                        s[nb][e] = ok_lo ? s[nb][e] * sc2 : -INFINITY;
+                        s[nb][2 + e] = ok_hi ? s[nb][2 + e] * sc2 : -INFINITY;
+                        mx_lo = fmaxf(mx_lo, s[nb][e]);
+                        mx_hi = fmaxf(mx_hi, s[nb][2 + e]);
                     }
 #pragma unroll
                 for (int x = 1; x < 4; x <<= 1) {
@@ -234,18 +264,16 @@ attn_fwd_mma_kernel(const __nv_bfloat16 *__restrict__ QKVh, const float *__restr
                 }
                 const float n_lo = fmaxf(m_lo, mx_lo), n_hi = fmaxf(m_hi, mx_hi);
                 // rows with nothing visible yet keep scale 1 and add nothing
-                const float c_lo = n_lo == -INFINITY ? 1.f : __expf(m_lo - n_lo);
-                const float c_hi = n_hi == -INFINITY ? 1.f : __expf(m_hi - n_hi);
+                const float c_lo = n_lo == -INFINITY ? 1.f : ex2(m_lo - n_lo);
+                const float c_hi = n_hi == -INFINITY ? 1.f : ex2(m_hi - n_hi);
                 m_lo = n_lo;
                 m_hi = n_hi;
+                const float z_lo = n_lo == -INFINITY ? 0.f : n_lo, z_hi = n_hi == -INFINITY ? 0.f : n_hi;
                 float p[2][4];
 #pragma unroll
                 for (int nb = 0; nb < 2; ++nb)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const float m = j < 2 ? m_lo : m_hi;
-                        p[nb][j] = s[nb][j] == -INFINITY ? 0.f : __expf(s[nb][j] - m);
-                    }
+                    for (int j = 0; j < 4; ++j) p[nb][j] = ex2(s[nb][j] - (j < 2 ? z_lo : z_hi));  // ex2(-inf) = 0
                 l_lo = l_lo * c_lo + p[0][0] + p[0][1] + p[1][0] + p[1][1];
                 l_hi = l_hi * c_hi + p[0][2] + p[0][3] + p[1][2] + p[1][3];
 #pragma unroll
@@ -283,9 +311,9 @@ attn_fwd_mma_kernel(const __nv_bfloat16 *__restrict__ QKVh, const float *__restr
                 *reinterpret_cast<float2 *>(Hmid + idx) = make_float2(hv.x + ov.x, hv.y + ov.y);
             }
         }
-        if (q == 0) {
-            if (r_lo < N) LSE[((size_t)b * N + r_lo) * NH + hh] = m_lo + logf(l_lo);
-            if (r_hi < N) LSE[((size_t)b * N + r_hi) * NH + hh] = m_hi + logf(l_hi);
+        if (q == 0) {  // natural log-sum-exp: (m + log2 l) ln 2
+            if (r_lo < N) LSE[((size_t)b * N + r_lo) * NH + hh] = (m_lo + log2f(l_lo)) * 0.69314718055994531f;
+            if (r_hi < N) LSE[((size_t)b * N + r_hi) * NH + hh] = (m_hi + log2f(l_hi)) * 0.69314718055994531f;
         }
     }
 }
@@ -373,14 +401,14 @@ attn_bwd_mma_kernel(const __nv_bfloat16 *__restrict__ QKVh, const float *__restr
             for (int c = 0; c < DH / 8; ++c)
                 *reinterpret_cast<uint4 *>(sG + sw_off<DH>(t, c)) = make_uint4(0, 0, 0, 0);
         }
-        Ls[t] = lse;
-        Ds[t] = dd;
+        Ls[t] = lse * kLog2e;             // base-2 log-sum-exp
+        Ds[t] = dd * rsqrtf((float)DH);   // scale D_t
     }
     tc::cp_async_wait<0>();
     __syncthreads();
     const uint32_t sQ = tc::smem_u32(smem), sK = sQ + (uint32_t)part_bytes,
                    sV = sQ + 2 * (uint32_t)part_bytes, sGu = sQ + 3 * (uint32_t)part_bytes;
-    const float scale = rsqrtf((float)DH);
+    const float scale = rsqrtf((float)DH), sc2 = scale * kLog2e;
     const int T = Npad / 16;
     // tasks: key tiles first (those holding sink keys see every later query),
     // then the query tiles; a warp takes the next task when it is done
@@ -399,21 +427,28 @@ attn_bwd_mma_kernel(const __nv_bfloat16 *__restrict__ QKVh, const float *__restr
                 for (int j = 0; j < 4; ++j) dk[nb][j] = dv[nb][j] = 0.f;
             const bool all_q = mask == SG_MASK_DENSE || k0 < S;
             const int q_hi = all_q ? Npad : min(Npad, (k0 + 16 + W + 15) & ~15);
+            const uint32_t lim_lo = key_lim(mask, W, S, key_lo), lim_hi = key_lim(mask, W, S, key_hi);
             for (int t0 = k0; t0 < q_hi; t0 += 16) {
                 float s[2][4], dp[2][4];
                 scores<DH>(s, ka, sQ, t0);   // S^T: keys x queries
                 scores<DH>(dp, va, sGu, t0); // dP^T = V dO^T
+                const bool full = block_full(mask, W, S, N, t0, k0);
                 float p[2][4], ds[2][4];
 #pragma unroll
-                for (int nb = 0; nb < 2; ++nb)
+                for (int nb = 0; nb < 2; ++nb) {
+                    const int tc0 = t0 + 8 * nb + 2 * q;  // this thread's two query columns
+                    const float2 l2 = *reinterpret_cast<const float2 *>(Ls + tc0);
+                    const float2 d2 = *reinterpret_cast<const float2 *>(Ds + tc0);
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        const int key = j < 2 ? key_lo : key_hi, t = t0 + 8 * nb + 2 * q + (j & 1);
-                        const bool ok = t < N && key < N && key_visible(mask, W, S, t, key);
-                        const float pv = ok ? __expf(s[nb][j] * scale - Ls[t]) : 0.f;
+                        const int t = tc0 + (j & 1);
+                        const int key = j < 2 ? key_lo : key_hi;
+                        const bool ok = full || ((uint32_t)(t - key) <= (j < 2 ? lim_lo : lim_hi) && t < N);
+                        const float pv = ok ? ex2(fmaf(s[nb][j], sc2, -((j & 1) ? l2.y : l2.x))) : 0.f;
                         p[nb][j] = pv;
-                        ds[nb][j] = pv * (dp[nb][j] - Ds[t]) * scale;
+                        ds[nb][j] = pv * fmaf(dp[nb][j], scale, -((j & 1) ? d2.y : d2.x));
                     }
+                }
                 uint32_t pa[4], dsa[4];
                 frag_a(p, pa);
                 frag_a(ds, dsa);
@@ -427,6 +462,7 @@ attn_bwd_mma_kernel(const __nv_bfloat16 *__restrict__ QKVh, const float *__restr
             const int t0 = 16 * (task - T);
             const int r_lo = t0 + g, r_hi = t0 + g + 8;
             const float lse_lo = Ls[r_lo], lse_hi = Ls[r_hi], d_lo = Ds[r_lo], d_hi = Ds[r_hi];
+            const bool in_lo = r_lo < N, in_hi = r_hi < N;
             uint32_t qa[DH / 16][4], ga[DH / 16][4];
             load_a<DH>(sQ, t0, qa);
             load_a<DH>(sGu, t0, ga);
@@ -442,15 +478,20 @@ attn_bwd_mma_kernel(const __nv_bfloat16 *__restrict__ QKVh, const float *__restr
                     float s[2][4], dp[2][4];
                     scores<DH>(s, qa, sK, k0);
                     scores<DH>(dp, ga, sV, k0);
+                    const bool full = block_full(mask, W, S, N, t0, k0);
                     float ds[2][4];
 #pragma unroll
                     for (int nb = 0; nb < 2; ++nb)
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            const int row = j < 2 ? r_lo : r_hi, key = k0 + 8 * nb + 2 * q + (j & 1);
-                            const bool ok = row < N && key_visible(mask, W, S, row, key);
-                            const float pv = ok ? __expf(s[nb][j] * scale - (j < 2 ? lse_lo : lse_hi)) : 0.f;
-                            ds[nb][j] = pv * (dp[nb][j] - (j < 2 ? d_lo : d_hi)) * scale;
+                        for (int e = 0; e < 2; ++e) {
+                            const int key = k0 + 8 * nb + 2 * q + e;
+                            const uint32_t lim = key_lim(mask, W, S, key);
+                            const bool ok_lo = full || ((uint32_t)(r_lo - key) <= lim && in_lo);
+                            const bool ok_hi = full || ((uint32_t)(r_hi - key) <= lim && in_hi);
+                            const float p_lo = ok_lo ? ex2(fmaf(s[nb][e], sc2, -lse_lo)) : 0.f;
+                            const float p_hi = ok_hi ? ex2(fmaf(s[nb][2 + e], sc2, -lse_hi)) : 0.f;
+                            ds[nb][e] = p_lo * fmaf(dp[nb][e], scale, -d_lo);
+                            ds[nb][2 + e] = p_hi * fmaf(dp[nb][2 + e], scale, -d_hi);
                         }
                     uint32_t dsa[4];
                     frag_a(ds, dsa);
