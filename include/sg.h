@@ -338,6 +338,17 @@ sg_status sg_muon_step(sg_model *m, float *weights, const float *grad, float *mo
                        float *adam_m, float *adam_v, double lr, double mu, double weight_decay,
                        int32_t ns_steps, int64_t step, sg_stream stream);
 
+/*
+ * Self-check of the GELU the BF16 path evaluates (the "GELU" of the
+ * architecture, Methods "Overall architecture"; erf form): the approximation
+ * of erf by Abramowitz & Stegun formula 7.1.26 against CUDA's erff and expf,
+ * on the current device, over n points evenly spaced in [-12, 12] (n >= 2).
+ *   max_err_gelu: max |gelu_approx(v) - v (1 + erff(v / sqrt 2)) / 2| / max(1, |v|)
+ *   max_err_grad: max |gelu'_approx(v) - (Phi(v) + v expf(-v^2 / 2) / sqrt(2 pi))|
+ * (host doubles).  Synchronous.  Errors: SG_EINVAL (n < 2 or NULL), SG_ECUDA.
+ */
+sg_status sg_gelu_selfcheck(int64_t n, double *max_err_gelu, double *max_err_grad);
+
 #ifdef __cplusplus
 }
 #endif

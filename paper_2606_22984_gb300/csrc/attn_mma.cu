@@ -62,14 +62,9 @@ __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// 2^x (MUFU ex2, relative error about 2^-22); the softmax runs in base 2
-// with log2(e) folded into its scale and into the stored log-sum-exp.
-__device__ __forceinline__ float ex2(float x)
-{
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
+// The softmax runs in base 2 (ex2_approx) with log2(e) folded into its scale
+// and into the stored log-sum-exp.
+__device__ __forceinline__ float ex2(float x) { return ex2_approx(x); }
 
 constexpr float kLog2e = 1.4426950408889634f;
 

@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(kThreads, 1) decode_bf16_kernel(const __grid_c
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
                             const int col = (DFF / 2) * hf + 32 * c + 8 * g8 + j;
-                            x[j] = gelu_f(v[8 * g8 + j] + __ldg(b1 + col));
+                            x[j] = gelu_as(v[8 * g8 + j] + __ldg(b1 + col));
                         }
                         store8(A2buf, r, (DFF / 2) * hf + 32 * c + 8 * g8, KG2, x);
                     }
@@ -755,7 +755,7 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d64_kernel(const __grid_co
                         float x[8];
 #pragma unroll
                         for (int j = 0; j < 8; ++j)
-                            x[j] = gelu_f(v[8 * g8 + j] + __ldg(b1 + 64 * qr + 32 * c + 8 * g8 + j));
+                            x[j] = gelu_as(v[8 * g8 + j] + __ldg(b1 + 64 * qr + 32 * c + 8 * g8 + j));
                         store8(A2buf, r, 64 * qr + 32 * c + 8 * g8, KG2, x);
                     }
                 }
@@ -1213,7 +1213,7 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d128_kernel(const __grid_c
                         float x[8];
 #pragma unroll
                         for (int jj = 0; jj < 8; ++jj)
-                            x[jj] = gelu_f(v[8 * g8 + jj] + __ldg(b1 + 128 * j + Q32 * qr + 8 * g8 + jj));
+                            x[jj] = gelu_as(v[8 * g8 + jj] + __ldg(b1 + 128 * j + Q32 * qr + 8 * g8 + jj));
                         store8(A2buf, r, Q32 * qr + 8 * g8, KG, x);
                     }
                     tc::fence_async_smem();
@@ -1725,7 +1725,7 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d256_kernel(const __grid_c
 #pragma unroll
                         for (int jj = 0; jj < 8; ++jj) {
                             const float z = c < 4 ? v0[8 * c + jj] : v1[8 * (c - 4) + jj];
-                            x[jj] = gelu_f(z + __ldg(b1 + 256 * j + 64 * qr + 8 * c + jj));
+                            x[jj] = gelu_as(z + __ldg(b1 + 256 * j + 64 * qr + 8 * c + jj));
                         }
                         store8(A2buf, r, 64 * qr + 8 * c, KG, x);
                     }

@@ -110,15 +110,15 @@ __device__ __forceinline__ void row_epilogue(const RowGemm &g, const float (&v)[
             dst[c] = q;
         }
     } else if (EPI == TE_GELU_T) {
-        // gelu(v) = v Phi(v) and gelu'(v) = Phi(v) + v phi(v), Phi(v) = (1 + erf(v / sqrt 2)) / 2,
-        // phi the standard normal density: one erf serves both
+        // gelu(v) and gelu'(v) from one evaluation (gelu_as)
         float y[32], d[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
             const float x = v[j] + __ldg(g.bias + col0 + j);
-            const float Phi = 0.5f * (1.0f + erff(x * 0.70710678118654752f));
-            y[j] = valid ? x * Phi : 0.f;
-            if (g.out_t2) d[j] = valid ? Phi + x * 0.39894228040143268f * __expf(-0.5f * x * x) : 0.f;
+            float dx;
+            const float gx = gelu_as(x, &dx);
+            y[j] = valid ? gx : 0.f;
+            d[j] = valid ? dx : 0.f;
         }
 #pragma unroll
         for (int c = 0; c < 4; ++c) {

@@ -2,7 +2,9 @@
 // reduction (Eqs. KL_div, free_energy), independence Metropolis-Hastings,
 // single-spin-flip Metropolis, the overlap histogram (Eq.
 // overlap_distribution) and the Adam update.
+#include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "sg_internal.cuh"
 
@@ -444,3 +446,47 @@ sg_status launch_adam(float *w, const float *g, float *m, float *v, int64_t n, f
 }
 
 }  // namespace sg
+
+// ---------------------------------------------------------------------------
+// GELU self-check: the BF16 path's approximation against erff / expf.
+// ---------------------------------------------------------------------------
+namespace sg {
+namespace {
+
+__global__ void gelu_check_kernel(int64_t n, double *__restrict__ eg, double *__restrict__ ed)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float v = (float)(-12.0 + 24.0 * (double)i / (double)(n - 1));
+    float d;
+    const float g = gelu_as(v, &d);
+    const double Phi = 0.5 * (1.0 + (double)erff(v * 0.70710678118654752f));
+    const double gref = (double)v * Phi;
+    const double dref = Phi + (double)v * 0.3989422804014327 * (double)expf(-0.5f * v * v);
+    eg[i] = fabs((double)g - gref) / fmax(1.0, fabs((double)v));
+    ed[i] = fabs((double)d - dref);
+}
+
+}  // namespace
+}  // namespace sg
+
+extern "C" sg_status sg_gelu_selfcheck(int64_t n, double *max_err_gelu, double *max_err_grad)
+{
+    using namespace sg;
+    if (n < 2 || !max_err_gelu || !max_err_grad) return fail(SG_EINVAL, "n >= 2 and non-NULL outputs");
+    double *buf = nullptr;
+    SG_CUDA_TRY(cudaMalloc(&buf, 2 * (size_t)n * sizeof(double)));
+    gelu_check_kernel<<<(unsigned)((n + 255) / 256), 256, 0, ::sg::counted(nullptr)>>>(n, buf, buf + n);
+    std::vector<double> h(2 * (size_t)n);
+    const cudaError_t e = cudaMemcpy(h.data(), buf, h.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(buf);
+    if (e != cudaSuccess) return fail(SG_ECUDA, cudaGetErrorString(e));
+    double mg = 0.0, md = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        mg = std::max(mg, h[(size_t)i]);
+        md = std::max(md, h[(size_t)n + (size_t)i]);
+    }
+    *max_err_gelu = mg;
+    *max_err_grad = md;
+    return SG_OK;
+}

@@ -87,6 +87,43 @@ __device__ __forceinline__ float gelu_grad_f(float x)
            + x * 0.39894228040143268f * expf(-0.5f * x * x);
 }
 
+// 2^x and 1/x on the special-function unit (relative errors about 2^-22).
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// GELU of the BF16 path: gelu(v) = v Phi(v), gelu'(v) = Phi(v) + v phi(v),
+// with Phi(v) = (1 + erf(v / sqrt 2)) / 2 from the approximation of
+// Abramowitz & Stegun, Handbook of Mathematical Functions, formula 7.1.26
+// (after Hastings): erf(z) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5))))
+// e^{-z^2}, t = 1 / (1 + p z), z >= 0, |error| <= 1.5e-7, odd in z.  Its
+// exponential e^{-v^2/2} is also the normal density phi(v) up to 1/sqrt(2 pi).
+// Every caller rounds the result to BF16 (relative step 2^-8), far coarser
+// than the approximation; sg_gelu_selfcheck() measures it against erff.
+__device__ __forceinline__ float gelu_as(float v, float *dgelu = nullptr)
+{
+    const float e = ex2_approx(v * v * -0.72134752044448170f);  // e^{-v^2/2} = 2^{-v^2 log2(e) / 2}
+    const float z = fabsf(v) * 0.70710678118654752f;
+    const float t = rcp_approx(fmaf(0.3275911f, z, 1.0f));
+    const float poly =
+        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f),
+                 0.254829592f);
+    const float h = 0.5f * poly * e;  // (1 - erf(z)) / 2
+    const float Phi = v >= 0.f ? 1.0f - h : h;
+    if (dgelu) *dgelu = fmaf(v * 0.39894228040143268f, e, Phi);
+    return v * Phi;
+}
+
 // ---------------------------------------------------------------------------
 // Weight-blob offsets (floats), blob layout of include/sg.h.
 // ---------------------------------------------------------------------------

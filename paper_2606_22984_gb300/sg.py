@@ -57,6 +57,7 @@ _SIGS = {
     "sg_free_energy": ([_P, _P, _I64, _D, _P, _P, _P], _I32),
     "sg_loss_coeff": ([_P, _P, _I64, _D, _D, _D, _P, _P, _P], _I32),
     "sg_muon_step": ([_P, _P, _P, _P, _P, _P, _D, _D, _D, _I32, _I64, _P], _I32),
+    "sg_gelu_selfcheck": ([_I64, _P, _P], _I32),
     "sg_mh_step": ([_P, _P, _P, _I64, _I32, _I32, _D, _U64, _P, _P, _P, _P, _P, _P], _I32),
     "sg_metropolis": ([_P, _P, _I64, _I32, _D, _U64, _P, _P, _P], _I32),
     "sg_overlap_hist": ([_P, _I64, _I32, _P, _P], _I32),
@@ -288,6 +289,14 @@ def loss_coeff(E, logq, a, c, w=0.0, coeff=None, mean=None, stream=None):
         _dev(E, torch.float32, (B,)), _dev(logq, torch.float32, (B,)), B, a, c, w,
         _dev(mean, torch.float64, (2,)), _dev(coeff, torch.float32, (B,)), _stream(stream)))
     return coeff, mean
+
+
+def gelu_selfcheck(n=1 << 20):
+    """Largest errors of the BF16 path's GELU and GELU' against erff / expf
+    over n points of [-12, 12] (sg_gelu_selfcheck)."""
+    eg, ed = ctypes.c_double(), ctypes.c_double()
+    _check("sg_gelu_selfcheck", lib().sg_gelu_selfcheck(n, ctypes.byref(eg), ctypes.byref(ed)))
+    return eg.value, ed.value
 
 
 def mh_step(prop_spins, E, logq, C, beta, seed, chain_spins, chain_E, chain_lq, accepts=None,

@@ -121,6 +121,16 @@ def test_full_size_d128_sampled_rows(name, precision, rows):
     del model
 
 
+def test_bf16_gelu_approximation_within_its_bound():
+    """The GELU of the BF16 path (erf by Abramowitz & Stegun 7.1.26, |error|
+    <= 1.5e-7) against CUDA's erff / expf over [-12, 12]: within that bound
+    plus FP32 rounding, far below the BF16 step (2^-8) its results get."""
+    eg, ed = sg.gelu_selfcheck(1 << 20)
+    print(f"gelu max err {eg:.2e}, gelu' max err {ed:.2e}")
+    assert eg <= 4e-7
+    assert ed <= 4e-7
+
+
 @pytest.mark.parametrize("name", list(BF16_CASES))
 def test_bf16_sampling_matches_oracle(name):
     """BF16 decode on tcgen05: spins equal to the oracle once the draws inside
