@@ -143,6 +143,56 @@ __device__ __forceinline__ void row_epilogue(const RowGemm &g, const float (&v)[
 constexpr int kEpiWarps = 16;  // four epilogue warps per TMEM lane quadrant
 constexpr int kEpiPerQuad = kEpiWarps / 4;
 
+// Barrier among the epilogue warps only (named barrier 1).
+__device__ __forceinline__ void epi_sync()
+{
+    asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
+}
+
+// Row-major outputs (FP32 rows, FP32 rows plus residual, BF16 rows) leave
+// through a shared-memory tile: the TMEM drain writes acc + bias there (row
+// pitch N + 4 floats, so 16-byte writes of 8 consecutive rows hit distinct
+// banks), then all epilogue threads read it back with the residual and store
+// with consecutive threads on consecutive 16-byte pieces of a row.
+template <int EPI>
+__device__ __forceinline__ void staged_store(const RowGemm &g, const float *sOut, int64_t rb)
+{
+    const int et = threadIdx.x - 64;  // epilogue thread 0 .. 511
+    const int P = g.N + 4;
+    if (EPI == TE_STORE_BF16) {
+        const int per_row = g.N / 8;
+        for (int e = et; e < 128 * per_row; e += 32 * kEpiWarps) {
+            const int row = e / per_row, c8 = e % per_row;
+            const int64_t r = rb * 128 + row;
+            if (r >= g.R) continue;
+            const float4 a = *reinterpret_cast<const float4 *>(sOut + row * P + 8 * c8);
+            const float4 b = *reinterpret_cast<const float4 *>(sOut + row * P + 8 * c8 + 4);
+            uint4 q;
+            q.x = pk2(a.x, a.y);
+            q.y = pk2(a.z, a.w);
+            q.z = pk2(b.x, b.y);
+            q.w = pk2(b.z, b.w);
+            *reinterpret_cast<uint4 *>(g.out_h + r * g.ld_out + 8 * c8) = q;
+        }
+    } else {
+        const int per_row = g.N / 4;
+        for (int e = et; e < 128 * per_row; e += 32 * kEpiWarps) {
+            const int row = e / per_row, c4 = e % per_row;
+            const int64_t r = rb * 128 + row;
+            if (r >= g.R) continue;
+            float4 v = *reinterpret_cast<const float4 *>(sOut + row * P + 4 * c4);
+            if (EPI == TE_RESID_F32) {
+                const float4 h = *reinterpret_cast<const float4 *>(g.resid + r * g.ld_resid + 4 * c4);
+                v.x += h.x;
+                v.y += h.y;
+                v.z += h.z;
+                v.w += h.w;
+            }
+            *reinterpret_cast<float4 *>(g.out_f32 + r * g.ld_out + 4 * c4) = v;
+        }
+    }
+}
+
 template <int EPI>
 __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) row_gemm_kernel(const __grid_constant__ RowGemm g)
 {
@@ -217,25 +267,49 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) row_gemm_kernel(const 
         const int q = warp & 3;             // TMEM lane quadrant of this warp
         const int part = (warp - 2) >> 2;   // which interleaved 32-column chunks
         const int row = 32 * q + lane;
+        constexpr bool kRowMajor = EPI == TE_STORE_F32 || EPI == TE_RESID_F32 || EPI == TE_STORE_BF16;
+        const bool staged = kRowMajor && g.staged;
+        float *sOut = reinterpret_cast<float *>(As + 2 * (size_t)stage_bytes);
+        bool ok = true;
         for (int64_t i = 0; i < my_n; ++i) {
             const int acc = (int)(i & 1);
             const int64_t rb = blockIdx.x + i * gridDim.x;
-            if (!tc::mbar_wait(&tfull[acc], (uint32_t)((i >> 1) & 1))) {
+            // every epilogue warp takes part in the barriers below: a timed-out
+            // wait records the error and the warp drains nothing further
+            if (ok && !tc::mbar_wait(&tfull[acc], (uint32_t)((i >> 1) & 1))) {
                 if (lane == 0) atomicExch(g.err, 13);
-                break;
+                ok = false;
             }
+            if (!ok && !staged) break;
             tc::tc_fence_after();
             const int64_t r = rb * 128 + row;
             const bool valid = r < g.R;
-            for (int c = part; c < g.N / 32; c += kEpiPerQuad) {
+            for (int c = part; ok && c < g.N / 32; c += kEpiPerQuad) {
                 float v[32];
                 tc::tmem_ld32(tmem + acc * 256 + ((uint32_t)(32 * q) << 16) + 32 * c, v);
                 tc::tmem_wait_ld();
-                row_epilogue<EPI>(g, v, r, 32 * c, valid, s_col);
+                if (staged) {
+                    float4 *d = reinterpret_cast<float4 *>(sOut + row * (g.N + 4) + 32 * c);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        float b[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) b[k] = g.bias ? __ldg(g.bias + 32 * c + 4 * j + k) : 0.f;
+                        d[j] = make_float4(v[4 * j] + b[0], v[4 * j + 1] + b[1], v[4 * j + 2] + b[2],
+                                           v[4 * j + 3] + b[3]);
+                    }
+                } else {
+                    row_epilogue<EPI>(g, v, r, 32 * c, valid, s_col);
+                }
             }
             tc::tc_fence_before();
             __syncwarp();
-            if (lane == 0) tc::mbar_arrive(&tempty[acc]);
+            if (ok && lane == 0) tc::mbar_arrive(&tempty[acc]);
+            if (staged) {
+                epi_sync();  // the tile is complete
+                if (ok) staged_store<EPI>(g, sOut, rb);
+                epi_sync();  // the tile is free for the next row block
+            }
         }
     }
     tc::tc_fence_before();
@@ -712,13 +786,28 @@ sg_status launch_row_gemm(const RowGemm &g, int epi, cudaStream_t st)
     if (g.colsum && (epi != TE_GELU_BWD_T || g.N > kColsumMax))
         return fail(SG_EUNSUPPORTED, "fused column sums need the GELU backward and N <= 1024");
     const bool resident = g.N <= 256 && g.KC <= 4;
-    const size_t smem = resident ? (size_t)g.NBw * g.KC * kTileBytes + 2 * wl_block_bytes(g.K)
-                                 : (size_t)kTStages * 3 * kTileBytes;
+    const size_t smem0 = resident ? (size_t)g.NBw * g.KC * kTileBytes + 2 * wl_block_bytes(g.K)
+                                  : (size_t)kTStages * 3 * kTileBytes;
     const int64_t units = resident ? g.RB : g.RB * ((g.N + 255) / 256);
     const unsigned grid = (unsigned)std::min<int64_t>(units, sms);
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     auto go = [&](auto kern) -> sg_status {
+        RowGemm h = g;
+        size_t smem = smem0;
+        // row-major outputs through a shared-memory tile where it fits
+        const bool row_major = epi == TE_STORE_F32 || epi == TE_RESID_F32 || epi == TE_STORE_BF16;
+        const size_t tile = (size_t)128 * (g.N + 4) * sizeof(float);
+        cudaFuncAttributes fa{};
+        SG_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+        h.staged = 0;
+        if (resident && row_major && g.ld_out == g.N && (epi != TE_RESID_F32 || g.ld_resid == g.N) &&
+            smem0 + tile + fa.sharedSizeBytes <= (size_t)optin) {
+            h.staged = 1;
+            smem = smem0 + tile;
+        }
         SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<grid, 64 + 32 * kEpiWarps, smem, ::sg::counted(st)>>>(g);
+        kern<<<grid, 64 + 32 * kEpiWarps, smem, ::sg::counted(st)>>>(h);
         return check_launch(resident ? "row_gemm_kernel" : "tile_gemm_kernel");
     };
     if (resident) {

@@ -81,6 +81,7 @@ struct RowGemm {
     unsigned char *out_t2;    // W(R, N)
     const unsigned char *aux_t;  // W(R, N)
     float *colsum;            // TE_GELU_BWD_T: colsum[j] += sum_r out(r, j) (N <= 1024), or nullptr
+    int staged;               // set by the launcher: row-major outputs through shared memory
     int *err;
 };
 
