@@ -193,6 +193,98 @@ __device__ __forceinline__ void staged_store(const RowGemm &g, const float *sOut
     }
 }
 
+// The LayerNorm backward over a staged tile of dY rows (TE_LN_BWD): LPR =
+// N / 8 lanes per row, each lane 8 consecutive columns; per-lane sums of
+// dY xhat, dY and dX accumulate in pg, pb, pc across row blocks.
+template <int N>
+__device__ __forceinline__ void ln_bwd_tile(const RowGemm &g, const float *sOut, int64_t rb,
+                                            const float (&gl)[8], float (&pg)[8], float (&pb)[8],
+                                            float (&pc)[8])
+{
+    constexpr int LPR = N / 8, RPP = 32 / LPR, P = N + 4;
+    const int lane = threadIdx.x & 31, ew = (threadIdx.x - 64) >> 5;  // epilogue warp 0..15
+    const int sub = lane / LPR, c0 = 8 * (lane % LPR);
+    const int64_t R_end = g.ln_dxt ? tl_blocks(g.R) * 128 : g.R;
+    for (int row = ew * RPP + sub; row < 128; row += kEpiWarps * RPP) {  // same trip count for the warp
+        const int64_t r = rb * 128 + row;
+        const bool in = r < g.R;
+        const int64_t rr = in ? r : g.R - 1;
+        float dy[8], x[8];
+        const float4 a = *reinterpret_cast<const float4 *>(sOut + row * P + c0);
+        const float4 b = *reinterpret_cast<const float4 *>(sOut + row * P + c0 + 4);
+        dy[0] = a.x; dy[1] = a.y; dy[2] = a.z; dy[3] = a.w;
+        dy[4] = b.x; dy[5] = b.y; dy[6] = b.z; dy[7] = b.w;
+        const float4 xa = *reinterpret_cast<const float4 *>(g.ln_x + rr * N + c0);
+        const float4 xb = *reinterpret_cast<const float4 *>(g.ln_x + rr * N + c0 + 4);
+        x[0] = xa.x; x[1] = xa.y; x[2] = xa.z; x[3] = xa.w;
+        x[4] = xb.x; x[5] = xb.y; x[6] = xb.z; x[7] = xb.w;
+        const float m = g.ln_mu[rr], s = g.ln_rs[rr];
+        float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (!in) dy[j] = 0.f;
+            x[j] = (x[j] - m) * s;  // xhat
+            const float dxh = dy[j] * gl[j];
+            s1 += dxh;
+            s2 += dxh * x[j];
+        }
+#pragma unroll
+        for (int o = LPR / 2; o; o >>= 1) {
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        }
+        const float m1 = s1 * (1.0f / N), m2 = s2 * (1.0f / N);
+        float out[8];
+        if (g.ln_dres && in) {
+            const float4 da = *reinterpret_cast<const float4 *>(g.ln_dres + r * N + c0);
+            const float4 db = *reinterpret_cast<const float4 *>(g.ln_dres + r * N + c0 + 4);
+            out[0] = da.x; out[1] = da.y; out[2] = da.z; out[3] = da.w;
+            out[4] = db.x; out[5] = db.y; out[6] = db.z; out[7] = db.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) out[j] = 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (in) out[j] += s * (dy[j] * gl[j] - m1 - x[j] * m2);
+            pg[j] += dy[j] * x[j];
+            pb[j] += dy[j];
+            pc[j] += out[j];
+        }
+        if (in) {
+            float4 *dst = reinterpret_cast<float4 *>(g.out_f32 + r * N + c0);
+            dst[0] = make_float4(out[0], out[1], out[2], out[3]);
+            dst[1] = make_float4(out[4], out[5], out[6], out[7]);
+        }
+        if (g.ln_dxt && r < R_end) st8(g.ln_dxt, wl_offset(r, c0, N), out);
+    }
+}
+
+// Per-lane LayerNorm-backward sums (lanes of one column group added by
+// shuffles) into shared memory, then one atomic per column and CTA.
+template <int N>
+__device__ __forceinline__ void ln_bwd_flush(const RowGemm &g, float *red, float (&pg)[8],
+                                             float (&pb)[8], float (&pc)[8])
+{
+    constexpr int LPR = N / 8;
+    const int lane = threadIdx.x & 31, c0 = 8 * (lane % LPR);
+#pragma unroll
+    for (int o = LPR; o < 32; o <<= 1)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            pg[j] += __shfl_xor_sync(0xffffffffu, pg[j], o);
+            pb[j] += __shfl_xor_sync(0xffffffffu, pb[j], o);
+            pc[j] += __shfl_xor_sync(0xffffffffu, pc[j], o);
+        }
+    if (lane < LPR)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            atomicAdd(red + c0 + j, pg[j]);
+            atomicAdd(red + N + c0 + j, pb[j]);
+            atomicAdd(red + 2 * N + c0 + j, pc[j]);
+        }
+}
+
 template <int EPI>
 __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) row_gemm_kernel(const __grid_constant__ RowGemm g)
 {
@@ -202,10 +294,12 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) row_gemm_kernel(const 
     unsigned char *As = smem + (size_t)g.NBw * g.KC * kTileBytes;
     __shared__ uint64_t full[2], empty[2], tfull[2], tempty[2], wfull;
     __shared__ uint32_t tslot;
-    __shared__ float s_colbuf[EPI == TE_GELU_BWD_T ? kColsumMax : 1];
+    __shared__ float s_colbuf[EPI == TE_GELU_BWD_T ? kColsumMax : EPI == TE_LN_BWD ? 3 * 256 : 1];
     float *s_col = EPI == TE_GELU_BWD_T && g.colsum ? s_colbuf : nullptr;
     if (s_col)
         for (int j = threadIdx.x; j < g.N; j += blockDim.x) s_col[j] = 0.f;
+    if (EPI == TE_LN_BWD)
+        for (int j = threadIdx.x; j < 3 * g.N; j += blockDim.x) s_colbuf[j] = 0.f;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < 2; ++s) {
@@ -267,10 +361,18 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) row_gemm_kernel(const 
         const int q = warp & 3;             // TMEM lane quadrant of this warp
         const int part = (warp - 2) >> 2;   // which interleaved 32-column chunks
         const int row = 32 * q + lane;
-        constexpr bool kRowMajor = EPI == TE_STORE_F32 || EPI == TE_RESID_F32 || EPI == TE_STORE_BF16;
-        const bool staged = kRowMajor && g.staged;
+        constexpr bool kRowMajor = EPI == TE_STORE_F32 || EPI == TE_RESID_F32 || EPI == TE_STORE_BF16 ||
+                                   EPI == TE_LN_BWD;
+        const bool staged = kRowMajor && (g.staged || EPI == TE_LN_BWD);
         float *sOut = reinterpret_cast<float *>(As + 2 * (size_t)stage_bytes);
         bool ok = true;
+        // TE_LN_BWD: this lane's 8 columns of the LayerNorm gain and its sums
+        float gl[8], pg[8], pb[8], pc[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            gl[j] = EPI == TE_LN_BWD ? __ldg(g.ln_g + (8 * (lane % (g.N / 8)) + j)) : 0.f;
+            pg[j] = pb[j] = pc[j] = 0.f;
+        }
         for (int64_t i = 0; i < my_n; ++i) {
             const int acc = (int)(i & 1);
             const int64_t rb = blockIdx.x + i * gridDim.x;
@@ -307,9 +409,24 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) row_gemm_kernel(const 
             if (ok && lane == 0) tc::mbar_arrive(&tempty[acc]);
             if (staged) {
                 epi_sync();  // the tile is complete
-                if (ok) staged_store<EPI>(g, sOut, rb);
+                if (EPI == TE_LN_BWD) {
+                    if (ok) {
+                        if (g.N == 32) ln_bwd_tile<32>(g, sOut, rb, gl, pg, pb, pc);
+                        else if (g.N == 64) ln_bwd_tile<64>(g, sOut, rb, gl, pg, pb, pc);
+                        else if (g.N == 128) ln_bwd_tile<128>(g, sOut, rb, gl, pg, pb, pc);
+                        else ln_bwd_tile<256>(g, sOut, rb, gl, pg, pb, pc);
+                    }
+                } else if (ok) {
+                    staged_store<EPI>(g, sOut, rb);
+                }
                 epi_sync();  // the tile is free for the next row block
             }
+        }
+        if (EPI == TE_LN_BWD) {
+            if (g.N == 32) ln_bwd_flush<32>(g, s_colbuf, pg, pb, pc);
+            else if (g.N == 64) ln_bwd_flush<64>(g, s_colbuf, pg, pb, pc);
+            else if (g.N == 128) ln_bwd_flush<128>(g, s_colbuf, pg, pb, pc);
+            else ln_bwd_flush<256>(g, s_colbuf, pg, pb, pc);
         }
     }
     tc::tc_fence_before();
@@ -317,6 +434,12 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) row_gemm_kernel(const 
     if (warp == 1) tc::tmem_dealloc(tmem, 512);
     if (s_col)
         for (int j = threadIdx.x; j < g.N; j += blockDim.x) atomicAdd(g.colsum + j, s_col[j]);
+    if (EPI == TE_LN_BWD)
+        for (int j = threadIdx.x; j < g.N; j += blockDim.x) {
+            atomicAdd(g.ln_dg + j, s_colbuf[j]);
+            atomicAdd(g.ln_db + j, s_colbuf[g.N + j]);
+            if (g.ln_dcol) atomicAdd(g.ln_dcol + j, s_colbuf[2 * g.N + j]);
+        }
 }
 
 // tile_gemm_kernel: the same product and epilogues for any N (a multiple of
@@ -772,6 +895,20 @@ sg_status launch_pack_tiled(const float *W, int rows, int K, unsigned char *dst,
     return launch_to_tiled(W, rows, K, K, dst, transpose, st);
 }
 
+bool ln_bwd_fusable(const RowGemm &g)
+{
+    if (!(g.N == 32 || g.N == 64 || g.N == 128 || g.N == 256) || g.KC > 4 || g.N > g.NBw * 128)
+        return false;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, row_gemm_kernel<TE_LN_BWD>) != cudaSuccess) return false;
+    const size_t smem = (size_t)g.NBw * g.KC * kTileBytes + 2 * wl_block_bytes(g.K) +
+                        (size_t)128 * (g.N + 4) * sizeof(float) + fa.sharedSizeBytes;
+    return smem <= (size_t)optin;
+}
+
 sg_status launch_row_gemm(const RowGemm &g, int epi, cudaStream_t st)
 {
     if (g.N % 32 || g.N < 32 || g.N > g.NBw * 128 || g.KC < 1)
@@ -785,6 +922,9 @@ sg_status launch_row_gemm(const RowGemm &g, int epi, cudaStream_t st)
         return fail(SG_EUNSUPPORTED, "tensor-core GEMM needs K a multiple of 16");
     if (g.colsum && (epi != TE_GELU_BWD_T || g.N > kColsumMax))
         return fail(SG_EUNSUPPORTED, "fused column sums need the GELU backward and N <= 1024");
+    if (epi == TE_LN_BWD && !ln_bwd_fusable(g))
+        return fail(SG_EUNSUPPORTED, "the fused LayerNorm backward needs N in {32, 64, 128, 256} "
+                                     "and its output tile in shared memory");
     const bool resident = g.N <= 256 && g.KC <= 4;
     const size_t smem0 = resident ? (size_t)g.NBw * g.KC * kTileBytes + 2 * wl_block_bytes(g.K)
                                   : (size_t)kTStages * 3 * kTileBytes;
@@ -796,7 +936,8 @@ sg_status launch_row_gemm(const RowGemm &g, int epi, cudaStream_t st)
         RowGemm h = g;
         size_t smem = smem0;
         // row-major outputs through a shared-memory tile where it fits
-        const bool row_major = epi == TE_STORE_F32 || epi == TE_RESID_F32 || epi == TE_STORE_BF16;
+        const bool row_major = epi == TE_STORE_F32 || epi == TE_RESID_F32 || epi == TE_STORE_BF16 ||
+                               epi == TE_LN_BWD;
         const size_t tile = (size_t)128 * (g.N + 4) * sizeof(float);
         cudaFuncAttributes fa{};
         SG_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
@@ -806,6 +947,8 @@ sg_status launch_row_gemm(const RowGemm &g, int epi, cudaStream_t st)
             h.staged = 1;
             smem = smem0 + tile;
         }
+        if (epi == TE_LN_BWD && !h.staged)
+            return fail(SG_EUNSUPPORTED, "the fused LayerNorm backward needs its tile in shared memory");
         SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kern<<<grid, 64 + 32 * kEpiWarps, smem, ::sg::counted(st)>>>(h);
         return check_launch(resident ? "row_gemm_kernel" : "tile_gemm_kernel");
@@ -817,6 +960,7 @@ sg_status launch_row_gemm(const RowGemm &g, int epi, cudaStream_t st)
         case TE_GELU_T: return go(row_gemm_kernel<TE_GELU_T>);
         case TE_GELU_BWD_T: return go(row_gemm_kernel<TE_GELU_BWD_T>);
         case TE_STORE_BF16: return go(row_gemm_kernel<TE_STORE_BF16>);
+        case TE_LN_BWD: return go(row_gemm_kernel<TE_LN_BWD>);
         default: return go(row_gemm_kernel<TE_STORE_F32_T>);
         }
     }

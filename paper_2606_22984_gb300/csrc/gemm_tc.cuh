@@ -60,6 +60,8 @@ enum TcEpilogue {
     TE_GELU_BWD_T = 3,  // out_t = acc * aux_t, aux_t = gelu'(v) from the forward (wide BF16)
     TE_STORE_F32_T = 4, // out_f32 = acc + bias and out_t = same (tiled BF16)
     TE_STORE_BF16 = 5,  // out_h = acc + bias, row-major BF16 (ld_out elements per row)
+    TE_LN_BWD = 6,      // acc = dY of a LayerNorm: out_f32 = dX (+ ln_dres), its wide copy
+                        // ln_dxt, dg/db/dcol column sums (N in {32, 64, 128, 256})
 };
 
 struct RowGemm {
@@ -82,6 +84,12 @@ struct RowGemm {
     const unsigned char *aux_t;  // W(R, N)
     float *colsum;            // TE_GELU_BWD_T: colsum[j] += sum_r out(r, j) (N <= 1024), or nullptr
     int staged;               // set by the launcher: row-major outputs through shared memory
+    // TE_LN_BWD: the LayerNorm y = (x - mu) rs g + b whose input gradient this
+    // product's output dY feeds: dX = ln_dres + rs (dY g - mean(dY g) - xhat
+    // mean(dY g xhat)); ln_dg += sum dY xhat, ln_db += sum dY, ln_dcol += sum dX
+    const float *ln_x, *ln_mu, *ln_rs, *ln_g, *ln_dres;
+    float *ln_dg, *ln_db, *ln_dcol;
+    unsigned char *ln_dxt;    // W(R, N) copy of dX (rows past R zero), or nullptr
     int *err;
 };
 
@@ -101,6 +109,8 @@ struct WgradGemm {
 };
 
 sg_status launch_row_gemm(const RowGemm &g, int epi, cudaStream_t st);
+// Whether launch_row_gemm(g, TE_LN_BWD) can run for g's shape.
+bool ln_bwd_fusable(const RowGemm &g);
 sg_status launch_wgrad_gemm(const WgradGemm &g, cudaStream_t st);
 
 // FP32 row-major [R][F] -> T(R, F) or the transpose T(F, R) (zero padding).

@@ -2381,11 +2381,20 @@ sg_status launch_grad_f32(sg_model *m, const int8_t *spins, const float *coeff, 
                 dim3 grid((F + 31) / 32, (unsigned)((R + rpb - 1) / rpb)), block(32, 8);
                 colsum_tiled_kernel<<<grid, block, 0, ::sg::counted(st)>>>(w.dF1t, R, F, grad + o.b1, rpb);
             }
+            // dHmid = dH + LN2'(dF1 W1): the LayerNorm backward in the GEMM epilogue where it fits
             g.A = w.dF1t; g.K = F; g.KC = (F + 63) / 64; g.Bw = bt + m->bt_off[l][4];
-            g.NBw = (int)tl_blocks(D); g.N = D; g.out_f32 = w.dA; g.ld_out = D;
-            launch_row_gemm(g, TE_STORE_F32, st);
-            ln_bwd_res(w.dA, L.Hmid, L.mu2, L.rs2, W + o.ln2g, w.dH, w.dHmid, grad + o.ln2g,
-                       grad + o.ln2b, R, D, st);
+            g.NBw = (int)tl_blocks(D); g.N = D; g.ld_out = D;
+            if (ln_bwd_fusable(g)) {
+                g.out_f32 = w.dHmid;
+                g.ln_x = L.Hmid; g.ln_mu = L.mu2; g.ln_rs = L.rs2; g.ln_g = W + o.ln2g; g.ln_dres = w.dH;
+                g.ln_dg = grad + o.ln2g; g.ln_db = grad + o.ln2b; g.ln_dcol = nullptr; g.ln_dxt = nullptr;
+                launch_row_gemm(g, TE_LN_BWD, st);
+            } else {
+                g.out_f32 = w.dA;
+                launch_row_gemm(g, TE_STORE_F32, st);
+                ln_bwd_res(w.dA, L.Hmid, L.mu2, L.rs2, W + o.ln2g, w.dH, w.dHmid, grad + o.ln2g,
+                           grad + o.ln2b, R, D, st);
+            }
             // attention: Hmid = Hin + O(QKV)
             if (attn_bwd_dispatch(dh, L.QKV, L.O, w.dHmid, L.LSE, w.dQKV, w.Dt, Bc, c, st,
                                   (int *)m->err, w.dQKVt, w.bsum,
@@ -2397,13 +2406,25 @@ sg_status launch_grad_f32(sg_model *m, const int8_t *spins, const float *coeff, 
                 colsum(w.dQKV, 3 * D, R, 3 * D, grad + o.bqkv, st);
             }
             wgrad(w.dQKVt, 3 * D, L.A1t, D, grad + o.Wqkv, D, false);  // dWqkv[j][d] = sum dQKV[j] A1[d]
+            // dH of layer l - 1 = dHmid + LN1'(dQKV Wqkv), with its wide copy and b2's
+            // gradient, the LayerNorm backward in the GEMM epilogue where it fits
             g.A = w.dQKVt; g.K = 3 * D; g.KC = (3 * D + 63) / 64; g.Bw = bt + m->bt_off[l][5];
-            g.NBw = (int)tl_blocks(D); g.N = D; g.out_f32 = w.dA; g.ld_out = D;
-            launch_row_gemm(g, TE_STORE_F32, st);
-            // dH of layer l - 1: with its wide copy and b2's gradient where fused
-            dH_fused = ln_bwd_res(w.dA, L.Hin, L.mu1, L.rs1, W + o.ln1g, w.dHmid, w.dH, grad + o.ln1g,
-                                  grad + o.ln1b, R, D, st, l > 0 ? w.dHt : nullptr,
-                                  l > 0 ? grad + O.L[l - 1].b2 : nullptr);
+            g.NBw = (int)tl_blocks(D); g.N = D; g.ld_out = D;
+            if (ln_bwd_fusable(g)) {
+                g.out_f32 = w.dH;
+                g.ln_x = L.Hin; g.ln_mu = L.mu1; g.ln_rs = L.rs1; g.ln_g = W + o.ln1g; g.ln_dres = w.dHmid;
+                g.ln_dg = grad + o.ln1g; g.ln_db = grad + o.ln1b;
+                g.ln_dcol = l > 0 ? grad + O.L[l - 1].b2 : nullptr;
+                g.ln_dxt = l > 0 ? w.dHt : nullptr;
+                launch_row_gemm(g, TE_LN_BWD, st);
+                dH_fused = true;
+            } else {
+                g.out_f32 = w.dA;
+                launch_row_gemm(g, TE_STORE_F32, st);
+                dH_fused = ln_bwd_res(w.dA, L.Hin, L.mu1, L.rs1, W + o.ln1g, w.dHmid, w.dH, grad + o.ln1g,
+                                      grad + o.ln1b, R, D, st, l > 0 ? w.dHt : nullptr,
+                                      l > 0 ? grad + O.L[l - 1].b2 : nullptr);
+            }
         }
         for (int l = c.n_layers - 1; l >= 0 && !use_tc(c); --l) {
             LayerBufs &L = w.layers[l];
