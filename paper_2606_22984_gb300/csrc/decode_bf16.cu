@@ -96,6 +96,10 @@ struct DecodeArgs {
     size_t stride_bf;             // bytes between consecutive models' packed chunks
     int max_keys;                 // capacity of the per-step key-offset table
     int kv_stages;                // d = 64: keys in flight per thread (2 or 3)
+    // d = 256 with grouped models: ctas_per_model > 0 splits each model's rows
+    // over that many CTAs (row counts differing by at most one); 0: CTA c
+    // serves rows c rows_per_cta ..
+    int ctas_per_model;
     int P, K, Nspins, latD, latL; // patching (d = 64 decode): spins per token, classes
 };
 
@@ -1313,8 +1317,8 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d128_kernel(const __grid_c
 //   4 x [MMA FFN1 slice -> GELU -> A2 -> MMA FFN2 K-slice accumulated straight
 //   into the residual columns] -> h += b2.
 // Weights stream as 44 chunks of 32 KB per layer ([256 out rows x 64 K]) through
-// a two-stage ring.  Grouped models: CTA c serves rows of model
-// (c * rows_per_cta) / rows_per_model and reads that model's weights.
+// a two-stage ring.  Grouped models: each model's rows are split over
+// ctas_per_model consecutive CTAs, which read that model's weights.
 // ---------------------------------------------------------------------------
 constexpr int kChunk256 = 256 * 64 * 2;
 constexpr int kChunks256 = 44;
@@ -1364,12 +1368,25 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d256_kernel(const __grid_c
     // 64..127); a row and its mirror (thread tid ^ 64) split the attention's
     // keys and merge their partial softmax states, doubling the KV loads in
     // flight.  Only the row itself writes the KV cache, spins and log q.
-    const bool mirror_mode = a.rows_per_cta <= 64;
+    int64_t row0, mdl;
+    int rows;  // rows of this CTA
+    if (a.ctas_per_model > 0) {
+        mdl = blockIdx.x / a.ctas_per_model;
+        const int64_t j = blockIdx.x % a.ctas_per_model;
+        const int64_t lo = j * a.rows_per_model / a.ctas_per_model;
+        const int64_t hi = (j + 1) * a.rows_per_model / a.ctas_per_model;
+        row0 = mdl * a.rows_per_model + lo;
+        rows = (int)(hi - lo);
+    } else {
+        row0 = (int64_t)blockIdx.x * a.rows_per_cta;
+        mdl = row0 / a.rows_per_model;
+        rows = a.rows_per_cta;
+    }
+    const bool mirror_mode = rows <= 64;
     const int rr = mirror_mode ? (r & 63) : r;     // the sample row this thread serves
     const bool is_mirror = mirror_mode && r >= 64;
-    const int64_t b = (int64_t)blockIdx.x * a.rows_per_cta + rr;
-    const bool active = rr < a.rows_per_cta && b < a.B;
-    const int64_t mdl = ((int64_t)blockIdx.x * a.rows_per_cta) / a.rows_per_model;
+    const int64_t b = row0 + rr;
+    const bool active = rr < rows && b < a.B;
     const float *w = a.w + mdl * a.stride_w;
     const float *wt = a.wt + mdl * a.stride_wt;
     const unsigned char *bf = a.bf + mdl * a.stride_bf;
@@ -1901,21 +1918,17 @@ sg_status launch_decode_bf16(sg_model *m, int64_t B, uint64_t seed, uint32_t sid
     // CTA divide the rows per model
     int rows = (int)std::min<int64_t>(kRows, (B + sms - 1) / sms);
     rows = std::max(rows, 1);
+    // grouped models: a CTA must not straddle two models; each model's rows go
+    // to ctas_per_model CTAs (counts differing by at most one), as many as
+    // keep all models within one wave over the SMs, at most 128 rows each
+    int cpm = 0;
     if (m->n_models > 1) {
-        // the fewest waves over the SMs, then the most CTAs within them
-        int best = 1;
-        int64_t best_waves = INT64_MAX;
-        for (int r = 1; r <= kRows && r <= rows_per_model; ++r) {
-            if (rows_per_model % r) continue;
-            const int64_t waves = ((B / r) + sms - 1) / sms;
-            if (waves < best_waves) {
-                best_waves = waves;
-                best = r;
-            }
-        }
-        rows = best;
+        cpm = (int)std::max<int64_t>((rows_per_model + kRows - 1) / kRows,
+                                     std::max<int64_t>(1, sms / m->n_models));
+        cpm = (int)std::min<int64_t>(cpm, rows_per_model);
+        rows = (int)((rows_per_model + cpm - 1) / cpm);
     }
-    const int64_t tiles = (B + rows - 1) / rows;
+    const int64_t tiles = cpm > 0 ? (int64_t)cpm * m->n_models : (B + rows - 1) / rows;
     const Bf16Geom g = bgeom(c.mask_kind, c.N, c.W, c.S);
     const size_t kv_bytes = (size_t)tiles * c.n_layers * g.nslots * 2 * c.d * kRows * 2;
     SG_TRY(ensure_buffer(&m->kv, &m->kv_bytes, kv_bytes));
@@ -1949,6 +1962,7 @@ sg_status launch_decode_bf16(sg_model *m, int64_t B, uint64_t seed, uint32_t sid
     a.kv = (unsigned char *)m->kv;
     a.err = (int *)m->err;
     a.rows_per_model = rows_per_model;
+    a.ctas_per_model = cpm;
     a.stride_w = m->P1;
     a.stride_wt = m->pack.total;
     a.stride_bf = (size_t)kChunks256 * kChunk256 * c.n_layers;
