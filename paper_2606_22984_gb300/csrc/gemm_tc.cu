@@ -294,12 +294,13 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) row_gemm_kernel(const 
     unsigned char *As = smem + (size_t)g.NBw * g.KC * kTileBytes;
     __shared__ uint64_t full[2], empty[2], tfull[2], tempty[2], wfull;
     __shared__ uint32_t tslot;
-    __shared__ float s_colbuf[EPI == TE_GELU_BWD_T ? kColsumMax : EPI == TE_LN_BWD ? 3 * 256 : 1];
+    __shared__ float s_colbuf[EPI == TE_GELU_BWD_T ? kColsumMax : 1];
     float *s_col = EPI == TE_GELU_BWD_T && g.colsum ? s_colbuf : nullptr;
     if (s_col)
         for (int j = threadIdx.x; j < g.N; j += blockDim.x) s_col[j] = 0.f;
-    if (EPI == TE_LN_BWD)
-        for (int j = threadIdx.x; j < 3 * g.N; j += blockDim.x) s_colbuf[j] = 0.f;
+    // staged output tile (row-major epilogues); TE_LN_BWD reuses its first 3 N
+    // floats for the column sums once the last row block is done
+    float *sTile = reinterpret_cast<float *>(As + 2 * (size_t)stage_bytes);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < 2; ++s) {
@@ -364,7 +365,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) row_gemm_kernel(const 
         constexpr bool kRowMajor = EPI == TE_STORE_F32 || EPI == TE_RESID_F32 || EPI == TE_STORE_BF16 ||
                                    EPI == TE_LN_BWD;
         const bool staged = kRowMajor && (g.staged || EPI == TE_LN_BWD);
-        float *sOut = reinterpret_cast<float *>(As + 2 * (size_t)stage_bytes);
+        float *sOut = sTile;
         bool ok = true;
         // TE_LN_BWD: this lane's 8 columns of the LayerNorm gain and its sums
         float gl[8], pg[8], pb[8], pc[8];
@@ -423,10 +424,13 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) row_gemm_kernel(const 
             }
         }
         if (EPI == TE_LN_BWD) {
-            if (g.N == 32) ln_bwd_flush<32>(g, s_colbuf, pg, pb, pc);
-            else if (g.N == 64) ln_bwd_flush<64>(g, s_colbuf, pg, pb, pc);
-            else if (g.N == 128) ln_bwd_flush<128>(g, s_colbuf, pg, pb, pc);
-            else ln_bwd_flush<256>(g, s_colbuf, pg, pb, pc);
+            // the tile is free (the loop ended on a barrier): zero 3 N sums
+            for (int j = threadIdx.x - 64; j < 3 * g.N; j += 32 * kEpiWarps) sOut[j] = 0.f;
+            epi_sync();
+            if (g.N == 32) ln_bwd_flush<32>(g, sOut, pg, pb, pc);
+            else if (g.N == 64) ln_bwd_flush<64>(g, sOut, pg, pb, pc);
+            else if (g.N == 128) ln_bwd_flush<128>(g, sOut, pg, pb, pc);
+            else ln_bwd_flush<256>(g, sOut, pg, pb, pc);
         }
     }
     tc::tc_fence_before();
@@ -436,9 +440,9 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) row_gemm_kernel(const 
         for (int j = threadIdx.x; j < g.N; j += blockDim.x) atomicAdd(g.colsum + j, s_col[j]);
     if (EPI == TE_LN_BWD)
         for (int j = threadIdx.x; j < g.N; j += blockDim.x) {
-            atomicAdd(g.ln_dg + j, s_colbuf[j]);
-            atomicAdd(g.ln_db + j, s_colbuf[g.N + j]);
-            if (g.ln_dcol) atomicAdd(g.ln_dcol + j, s_colbuf[2 * g.N + j]);
+            atomicAdd(g.ln_dg + j, sTile[j]);
+            atomicAdd(g.ln_db + j, sTile[g.N + j]);
+            if (g.ln_dcol) atomicAdd(g.ln_dcol + j, sTile[2 * g.N + j]);
         }
 }
 
