@@ -90,6 +90,10 @@ __device__ __forceinline__ uint32_t sw_off(int r, int c)
     return (uint32_t)(r * DH * 2 + 16 * sc);
 }
 
+// The helpers below take row bases that are multiples of 8, so the swizzle
+// (bits 1..2 of the row) depends on the lane's row within its 8-row group
+// only: address = base + row0 * DH * 2 + a per-lane constant.
+
 // A fragments (16 rows from row0, all DH columns) of a staged array.
 template <int DH>
 __device__ __forceinline__ void load_a(uint32_t base, int row0, uint32_t (&a)[DH / 16][4])
@@ -97,7 +101,7 @@ __device__ __forceinline__ void load_a(uint32_t base, int row0, uint32_t (&a)[DH
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int ks = 0; ks < DH / 16; ++ks)
-        ldsm_x4(base + sw_off<DH>(row0 + (lane & 15), 2 * ks + (lane >> 4)), a[ks]);
+        ldsm_x4(base + (uint32_t)(row0 * DH * 2) + sw_off<DH>(lane & 15, 2 * ks + (lane >> 4)), a[ks]);
 }
 
 // B fragments for X Y^T with Y's rows y0 .. y0 + 15 (two n-blocks of 8) and
@@ -108,7 +112,8 @@ __device__ __forceinline__ void load_b_rows(uint32_t base, int y0, uint32_t (&b)
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int ks = 0; ks < DH / 16; ++ks)
-        ldsm_x4(base + sw_off<DH>(y0 + (lane & 7) + ((lane >> 4) << 3), 2 * ks + ((lane >> 3) & 1)),
+        ldsm_x4(base + (uint32_t)(y0 * DH * 2) +
+                    sw_off<DH>((lane & 7) + ((lane >> 4) << 3), 2 * ks + ((lane >> 3) & 1)),
                 b[ks]);
 }
 
@@ -122,7 +127,8 @@ __device__ __forceinline__ void mma_a_rows(float (&acc)[DH / 8][4], const uint32
 #pragma unroll
     for (int nb = 0; nb < DH / 8; nb += 2) {
         uint32_t t[4];
-        ldsm_x4_t(base + sw_off<DH>(y0 + (lane & 7) + (((lane >> 3) & 1) << 3), nb + (lane >> 4)), t);
+        ldsm_x4_t(base + (uint32_t)(y0 * DH * 2) +
+                      sw_off<DH>((lane & 7) + (((lane >> 3) & 1) << 3), nb + (lane >> 4)), t);
         mma_bf16_16816(acc[nb], a, t[0], t[1]);
         mma_bf16_16816(acc[nb + 1], a, t[2], t[3]);
     }
@@ -206,7 +212,7 @@ __device__ __forceinline__ void stage_qkv(unsigned char *sq, const __nv_bfloat16
 template <int DH>
 __global__ void __launch_bounds__(kThreads)
 attn_fwd_mma_kernel(const __nv_bfloat16 *__restrict__ QKVh, const float *__restrict__ Hin,
-                    float *__restrict__ O, float *__restrict__ Hmid, float *__restrict__ LSE,
+                    __nv_bfloat16 *__restrict__ O, float *__restrict__ Hmid, float *__restrict__ LSE,
                     int N, int Npad, int D, int NH, int mask, int W, int S)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -291,18 +297,19 @@ attn_fwd_mma_kernel(const __nv_bfloat16 *__restrict__ QKVh, const float *__restr
 #pragma unroll
         for (int nb = 0; nb < DH / 8; ++nb) {
             const int col = hh * DH + 8 * nb + 2 * q;
+            // O (BF16, kept only for the backward's D_t) and Hmid = Hin + O (FP32)
             if (r_lo < N) {
                 const size_t idx = ((size_t)b * N + r_lo) * D + col;
                 const float2 ov = make_float2(o[nb][0] * i_lo, o[nb][1] * i_lo);
                 const float2 hv = *reinterpret_cast<const float2 *>(Hin + idx);
-                *reinterpret_cast<float2 *>(O + idx) = ov;
+                if (O) *reinterpret_cast<uint32_t *>(O + idx) = pack_bf2(ov.x, ov.y);
                 *reinterpret_cast<float2 *>(Hmid + idx) = make_float2(hv.x + ov.x, hv.y + ov.y);
             }
             if (r_hi < N) {
                 const size_t idx = ((size_t)b * N + r_hi) * D + col;
                 const float2 ov = make_float2(o[nb][2] * i_hi, o[nb][3] * i_hi);
                 const float2 hv = *reinterpret_cast<const float2 *>(Hin + idx);
-                *reinterpret_cast<float2 *>(O + idx) = ov;
+                if (O) *reinterpret_cast<uint32_t *>(O + idx) = pack_bf2(ov.x, ov.y);
                 *reinterpret_cast<float2 *>(Hmid + idx) = make_float2(hv.x + ov.x, hv.y + ov.y);
             }
         }
@@ -357,7 +364,7 @@ __device__ __forceinline__ void put_tile(const float (&acc)[DH / 8][4], int b, i
 
 template <int DH>
 __global__ void __launch_bounds__(kThreads)
-attn_bwd_mma_kernel(const __nv_bfloat16 *__restrict__ QKVh, const float *__restrict__ O,
+attn_bwd_mma_kernel(const __nv_bfloat16 *__restrict__ QKVh, const __nv_bfloat16 *__restrict__ O,
                     const float *__restrict__ dO, const float *__restrict__ LSE,
                     unsigned char *__restrict__ dQKVt, float *__restrict__ bsum, int N, int Npad,
                     int D, int NH, int mask, int W, int S)
@@ -380,12 +387,20 @@ attn_bwd_mma_kernel(const __nv_bfloat16 *__restrict__ QKVh, const float *__restr
         if (t < N) {
             const size_t r = (size_t)b * N + t;
             const float4 *gp = reinterpret_cast<const float4 *>(dO + r * D + hh * DH);
-            const float4 *op = reinterpret_cast<const float4 *>(O + r * D + hh * DH);
+            const uint4 *op = reinterpret_cast<const uint4 *>(O + r * D + hh * DH);
 #pragma unroll
             for (int c = 0; c < DH / 8; ++c) {
-                const float4 g0 = gp[2 * c], g1 = gp[2 * c + 1], o0 = op[2 * c], o1 = op[2 * c + 1];
-                dd += g0.x * o0.x + g0.y * o0.y + g0.z * o0.z + g0.w * o0.w;
-                dd += g1.x * o1.x + g1.y * o1.y + g1.z * o1.z + g1.w * o1.w;
+                const float4 g0 = gp[2 * c], g1 = gp[2 * c + 1];
+                const uint4 ow = op[c];
+                const uint32_t w[4] = {ow.x, ow.y, ow.z, ow.w};
+                float ov[8];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    ov[2 * j] = __uint_as_float(w[j] << 16);
+                    ov[2 * j + 1] = __uint_as_float(w[j] & 0xffff0000u);
+                }
+                dd += g0.x * ov[0] + g0.y * ov[1] + g0.z * ov[2] + g0.w * ov[3];
+                dd += g1.x * ov[4] + g1.y * ov[5] + g1.z * ov[6] + g1.w * ov[7];
                 *reinterpret_cast<uint4 *>(sG + sw_off<DH>(t, c)) =
                     make_uint4(pack_bf2(g0.x, g0.y), pack_bf2(g0.z, g0.w), pack_bf2(g1.x, g1.y),
                                pack_bf2(g1.z, g1.w));
@@ -521,7 +536,7 @@ bool attn_mma_supported(const sg_config &c)
 }
 
 sg_status launch_attn_fwd_mma(const sg_config &c, const __nv_bfloat16 *QKVh, const float *Hin,
-                              float *O, float *Hmid, float *LSE, int Bc, cudaStream_t st)
+                              __nv_bfloat16 *O, float *Hmid, float *LSE, int Bc, cudaStream_t st)
 {
     const int dh = c.d / c.n_heads, Npad = (c.N + 15) & ~15;
     const size_t smem = mma_smem_bytes(dh, c.N, false);
@@ -534,7 +549,7 @@ sg_status launch_attn_fwd_mma(const sg_config &c, const __nv_bfloat16 *QKVh, con
     return dh == 16 ? go(attn_fwd_mma_kernel<16>) : go(attn_fwd_mma_kernel<32>);
 }
 
-sg_status launch_attn_bwd_mma(const sg_config &c, const __nv_bfloat16 *QKVh, const float *O,
+sg_status launch_attn_bwd_mma(const sg_config &c, const __nv_bfloat16 *QKVh, const __nv_bfloat16 *O,
                               const float *dO, const float *LSE, unsigned char *dQKVt, float *bsum,
                               int Bc, cudaStream_t st)
 {

@@ -1907,12 +1907,15 @@ bool qkv_bf16(const sg_config &c)
     return need <= kAttnSmemMax;
 }
 
+// keep_o: O is read back by the backward (the MMA path keeps it in BF16 in
+// O's buffer, and skips it for a forward-only pass).
 void attn_fwd_dispatch(int dh, const float *QKV, const float *Hin, float *O, float *Hmid,
                        float *LSE, int Bc, const sg_config &c, cudaStream_t st, int *err,
-                       const __nv_bfloat16 *QKVh = nullptr)
+                       const __nv_bfloat16 *QKVh = nullptr, bool keep_o = true)
 {
     if (QKVh && attn_mma_supported(c)) {  // BF16 QKV: warp-level tensor-core MMAs
-        launch_attn_fwd_mma(c, QKVh, Hin, O, Hmid, LSE, Bc, st);
+        launch_attn_fwd_mma(c, QKVh, Hin, keep_o ? reinterpret_cast<__nv_bfloat16 *>(O) : nullptr, Hmid,
+                            LSE, Bc, st);
         return;
     }
     if (attn_tc_supported(c)) {  // BF16 model: tcgen05 attention
@@ -1932,7 +1935,7 @@ bool attn_bwd_dispatch(int dh, const float *QKV, const float *O, const float *dO
                        float *bsum = nullptr, const __nv_bfloat16 *QKVh = nullptr)
 {
     if (QKVh && dQKVt && attn_mma_supported(c)) {
-        launch_attn_bwd_mma(c, QKVh, O, dO, LSE, dQKVt, bsum, Bc, st);
+        launch_attn_bwd_mma(c, QKVh, reinterpret_cast<const __nv_bfloat16 *>(O), dO, LSE, dQKVt, bsum, Bc, st);
         return true;
     }
     if (attn_tc_supported(c)) {
@@ -2180,7 +2183,7 @@ void forward_chunk(sg_model *m, const int8_t *spins, int Bc, Work &w, bool keep,
             __nv_bfloat16 *QKVh = hq ? reinterpret_cast<__nv_bfloat16 *>(L.QKV) : nullptr;
             g.out_f32 = L.QKV; g.out_h = QKVh;
             launch_row_gemm(g, hq ? TE_STORE_BF16 : TE_STORE_F32, st);
-            attn_fwd_dispatch(dh, L.QKV, Hin, L.O, L.Hmid, L.LSE, Bc, c, st, (int *)m->err, QKVh);
+            attn_fwd_dispatch(dh, L.QKV, Hin, L.O, L.Hmid, L.LSE, Bc, c, st, (int *)m->err, QKVh, keep);
             ln_fwd(L.Hmid, W + o.ln2g, W + o.ln2b, nullptr, L.mu2, L.rs2, R, D, L.A2t, st);
             g.A = L.A2t; g.Bw = bt + m->bt_off[l][1]; g.NBw = (int)tl_blocks(F); g.N = F;
             // G = gelu(F1) for FFN2, and gelu'(F1) kept for the backward

@@ -293,12 +293,13 @@ sg_status launch_attn_bwd_tc(const sg_config &c, const float *QKV, const float *
                              const float *LSE, float *dQKV, float *Dt, int Bc, int *err,
                              cudaStream_t st);
 // Attention of the BF16 teacher-forced pass on warp-level tensor-core MMAs
-// (head dims 16 and 32), QKV rows in BF16; the backward writes dQKV as wide
+// (head dims 16 and 32), QKV rows in BF16; O is kept in BF16 for the
+// backward (or not written when O is null); the backward writes dQKV as wide
 // BF16 and per-sample bias sums bsum [Bc][3 d].
 bool attn_mma_supported(const sg_config &c);
 sg_status launch_attn_fwd_mma(const sg_config &c, const __nv_bfloat16 *QKVh, const float *Hin,
-                              float *O, float *Hmid, float *LSE, int Bc, cudaStream_t st);
-sg_status launch_attn_bwd_mma(const sg_config &c, const __nv_bfloat16 *QKVh, const float *O,
+                              __nv_bfloat16 *O, float *Hmid, float *LSE, int Bc, cudaStream_t st);
+sg_status launch_attn_bwd_mma(const sg_config &c, const __nv_bfloat16 *QKVh, const __nv_bfloat16 *O,
                               const float *dO, const float *LSE, unsigned char *dQKVt, float *bsum,
                               int Bc, cudaStream_t st);
 sg_status launch_adam(float *w, const float *g, float *m, float *v, int64_t n, float lr,
