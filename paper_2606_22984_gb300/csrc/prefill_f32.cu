@@ -2080,14 +2080,14 @@ Work carve(const sg_config &c, float *base, int64_t R, bool bwd)
         L.Hin = take(R * D);
         L.mu1 = take(R);
         L.rs1 = take(R);
-        L.A1 = take(R * D);
+        if (!tc) L.A1 = take(R * D);  // FP32 LayerNorm outputs: the FP32 model's GEMMs
         L.QKV = take(R * 3 * D);
         L.O = take(R * D);
         L.LSE = take(R * NH);
         L.Hmid = take(R * D);
         L.mu2 = take(R);
         L.rs2 = take(R);
-        L.A2 = take(R * D);
+        if (!tc) L.A2 = take(R * D);
         if (tc) {
             L.A1t = take_t(R, D);
             L.A2t = take_t(R, D);
@@ -2117,8 +2117,10 @@ Work carve(const sg_config &c, float *base, int64_t R, bool bwd)
         w.dH = take(R * D);
         w.dHmid = take(R * D);
         w.dA = take(R * D);
-        w.dQKV = take(R * 3 * D);
-        w.dF1 = take(R * F);
+        // FP32 dQKV only where the attention backward does not write the wide
+        // BF16 copy itself (the FP32 model, the tcgen05 flash attention)
+        if (!tc || !qkv_bf16(c)) w.dQKV = take(R * 3 * D);
+        if (!tc) w.dF1 = take(R * F);
         w.Dt = take(R * NH);
     }
     w.total_floats = off;
@@ -2132,7 +2134,7 @@ sg_status plan_chunks(sg_model *m, int64_t B, bool bwd, Plan &p, size_t &bytes)
     const size_t per_sample = (size_t)carve(c, nullptr, c.N, bwd).total_floats * sizeof(float);
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
-    const size_t budget = std::min<size_t>((size_t)16 << 30, free_b / 3 + m->ws_bytes);
+    const size_t budget = std::min<size_t>((size_t)64 << 30, free_b / 3 + m->ws_bytes);
     int64_t Bc = std::max<int64_t>(1, (int64_t)(budget / per_sample));
     Bc = std::min<int64_t>(Bc, B);
     // keep the warp count of the attention kernels within a 32-bit grid
