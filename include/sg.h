@@ -49,7 +49,7 @@ typedef enum {
     SG_ENOMEM = 2,       /* device or host allocation failed                */
     SG_ECUDA = 3,        /* a CUDA runtime call or kernel launch failed     */
     SG_ENUMERIC = 4,     /* NaN / Inf seen where a finite value is required */
-    SG_EUNSUPPORTED = 5  /* valid configuration this build does not serve   */
+    SG_EUNSUPPORTED = 5  /* valid configuration the library does not serve  */
 } sg_status;
 
 typedef enum { SG_MASK_DENSE = 0, SG_MASK_BAND_SINK = 1 } sg_mask_kind;
