@@ -22,6 +22,8 @@
 // rows with its accumulator in TMEM; here the fragments stay in registers.
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include "gemm_tc.cuh"
 #include "sg_internal.cuh"
 
@@ -74,6 +76,13 @@ __device__ __forceinline__ uint32_t key_lim(int mask, int W, int S, int k)
 {
     return (mask == SG_MASK_DENSE || k < S) ? 0x7fffffffu : (uint32_t)W;
 }
+
+// Element masks of a 16 x 16 block: every entry visible (kFull); band keys
+// only (k0 >= S) and every row inside the sequence, so that one unsigned
+// compare of the offset against W decides (kBand); anything else (kAny).
+constexpr int kFull = 0, kBand = 1, kAny = 2;
+template <int K>
+using kind_t = std::integral_constant<int, K>;
 
 // Every (query, key) of the 16 x 16 block at (t0, k0) is visible.
 __device__ __forceinline__ bool block_full(int mask, int W, int S, int N, int t0, int k0)
@@ -243,21 +252,32 @@ attn_fwd_mma_kernel(const __nv_bfloat16 *__restrict__ QKVh, const float *__restr
                 float s[2][4];
                 scores<DH>(s, qa, sK, k0);
                 // scores in base 2: x = log2(e) scale s, masked to -inf
-                const bool full = block_full(mask, W, S, N, t0, k0);
                 float mx_lo = -INFINITY, mx_hi = -INFINITY;
+                auto mask_scores = [&](auto kind) {
+                    constexpr int KIND = decltype(kind)::value;
 #pragma unroll
-                for (int nb = 0; nb < 2; ++nb)
+                    for (int nb = 0; nb < 2; ++nb)
 #pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        const int key = k0 + 8 * nb + 2 * q + e;
-                        const uint32_t lim = key_lim(mask, W, S, key);
-                        const bool ok_lo = full || ((uint32_t)(r_lo - key) <= lim && r_lo < N);
-                        const bool ok_hi = full || ((uint32_t)(r_hi - key) <= lim && r_hi < N);
-                        s[nb][e] = ok_lo ? s[nb][e] * sc2 : -INFINITY;
-                        s[nb][2 + e] = ok_hi ? s[nb][2 + e] * sc2 : -INFINITY;
-                        mx_lo = fmaxf(mx_lo, s[nb][e]);
-                        mx_hi = fmaxf(mx_hi, s[nb][2 + e]);
-                    }
+                        for (int e = 0; e < 2; ++e) {
+                            const int key = k0 + 8 * nb + 2 * q + e;
+                            bool ok_lo = true, ok_hi = true;
+                            if constexpr (KIND == kBand) {
+                                ok_lo = (uint32_t)(r_lo - key) <= (uint32_t)W;
+                                ok_hi = (uint32_t)(r_hi - key) <= (uint32_t)W;
+                            } else if constexpr (KIND == kAny) {
+                                const uint32_t lim = key_lim(mask, W, S, key);
+                                ok_lo = (uint32_t)(r_lo - key) <= lim && r_lo < N;
+                                ok_hi = (uint32_t)(r_hi - key) <= lim && r_hi < N;
+                            }
+                            s[nb][e] = ok_lo ? s[nb][e] * sc2 : -INFINITY;
+                            s[nb][2 + e] = ok_hi ? s[nb][2 + e] * sc2 : -INFINITY;
+                            mx_lo = fmaxf(mx_lo, s[nb][e]);
+                            mx_hi = fmaxf(mx_hi, s[nb][2 + e]);
+                        }
+                };
+                if (block_full(mask, W, S, N, t0, k0)) mask_scores(kind_t<kFull>{});
+                else if (mask != SG_MASK_DENSE && k0 >= S && t0 + 16 <= N) mask_scores(kind_t<kBand>{});
+                else mask_scores(kind_t<kAny>{});
 #pragma unroll
                 for (int x = 1; x < 4; x <<= 1) {
                     mx_lo = fmaxf(mx_lo, __shfl_xor_sync(0xffffffffu, mx_lo, x));
@@ -442,23 +462,31 @@ attn_bwd_mma_kernel(const __nv_bfloat16 *__restrict__ QKVh, const __nv_bfloat16 
                 float s[2][4], dp[2][4];
                 scores<DH>(s, ka, sQ, t0);   // S^T: keys x queries
                 scores<DH>(dp, va, sGu, t0); // dP^T = V dO^T
-                const bool full = block_full(mask, W, S, N, t0, k0);
                 float p[2][4], ds[2][4];
+                auto grads = [&](auto kind) {
+                    constexpr int KIND = decltype(kind)::value;
 #pragma unroll
-                for (int nb = 0; nb < 2; ++nb) {
-                    const int tc0 = t0 + 8 * nb + 2 * q;  // this thread's two query columns
-                    const float2 l2 = *reinterpret_cast<const float2 *>(Ls + tc0);
-                    const float2 d2 = *reinterpret_cast<const float2 *>(Ds + tc0);
+                    for (int nb = 0; nb < 2; ++nb) {
+                        const int tc0 = t0 + 8 * nb + 2 * q;  // this thread's two query columns
+                        const float2 l2 = *reinterpret_cast<const float2 *>(Ls + tc0);
+                        const float2 d2 = *reinterpret_cast<const float2 *>(Ds + tc0);
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int t = tc0 + (j & 1);
-                        const int key = j < 2 ? key_lo : key_hi;
-                        const bool ok = full || ((uint32_t)(t - key) <= (j < 2 ? lim_lo : lim_hi) && t < N);
-                        const float pv = ok ? ex2(fmaf(s[nb][j], sc2, -((j & 1) ? l2.y : l2.x))) : 0.f;
-                        p[nb][j] = pv;
-                        ds[nb][j] = pv * fmaf(dp[nb][j], scale, -((j & 1) ? d2.y : d2.x));
+                        for (int j = 0; j < 4; ++j) {
+                            const int t = tc0 + (j & 1);
+                            const int key = j < 2 ? key_lo : key_hi;
+                            bool ok = true;
+                            if constexpr (KIND == kBand) ok = (uint32_t)(t - key) <= (uint32_t)W;
+                            else if constexpr (KIND == kAny)
+                                ok = (uint32_t)(t - key) <= (j < 2 ? lim_lo : lim_hi) && t < N;
+                            const float pv = ok ? ex2(fmaf(s[nb][j], sc2, -((j & 1) ? l2.y : l2.x))) : 0.f;
+                            p[nb][j] = pv;
+                            ds[nb][j] = pv * fmaf(dp[nb][j], scale, -((j & 1) ? d2.y : d2.x));
+                        }
                     }
-                }
+                };
+                if (block_full(mask, W, S, N, t0, k0)) grads(kind_t<kFull>{});
+                else if (mask != SG_MASK_DENSE && k0 >= S && t0 + 16 <= N) grads(kind_t<kBand>{});
+                else grads(kind_t<kAny>{});
                 uint32_t pa[4], dsa[4];
                 frag_a(p, pa);
                 frag_a(ds, dsa);
@@ -488,21 +516,32 @@ attn_bwd_mma_kernel(const __nv_bfloat16 *__restrict__ QKVh, const __nv_bfloat16 
                     float s[2][4], dp[2][4];
                     scores<DH>(s, qa, sK, k0);
                     scores<DH>(dp, ga, sV, k0);
-                    const bool full = block_full(mask, W, S, N, t0, k0);
                     float ds[2][4];
+                    auto grads = [&](auto kind) {
+                        constexpr int KIND = decltype(kind)::value;
 #pragma unroll
-                    for (int nb = 0; nb < 2; ++nb)
+                        for (int nb = 0; nb < 2; ++nb)
 #pragma unroll
-                        for (int e = 0; e < 2; ++e) {
-                            const int key = k0 + 8 * nb + 2 * q + e;
-                            const uint32_t lim = key_lim(mask, W, S, key);
-                            const bool ok_lo = full || ((uint32_t)(r_lo - key) <= lim && in_lo);
-                            const bool ok_hi = full || ((uint32_t)(r_hi - key) <= lim && in_hi);
-                            const float p_lo = ok_lo ? ex2(fmaf(s[nb][e], sc2, -lse_lo)) : 0.f;
-                            const float p_hi = ok_hi ? ex2(fmaf(s[nb][2 + e], sc2, -lse_hi)) : 0.f;
-                            ds[nb][e] = p_lo * fmaf(dp[nb][e], scale, -d_lo);
-                            ds[nb][2 + e] = p_hi * fmaf(dp[nb][2 + e], scale, -d_hi);
-                        }
+                            for (int e = 0; e < 2; ++e) {
+                                const int key = k0 + 8 * nb + 2 * q + e;
+                                bool ok_lo = true, ok_hi = true;
+                                if constexpr (KIND == kBand) {
+                                    ok_lo = (uint32_t)(r_lo - key) <= (uint32_t)W;
+                                    ok_hi = (uint32_t)(r_hi - key) <= (uint32_t)W;
+                                } else if constexpr (KIND == kAny) {
+                                    const uint32_t lim = key_lim(mask, W, S, key);
+                                    ok_lo = (uint32_t)(r_lo - key) <= lim && in_lo;
+                                    ok_hi = (uint32_t)(r_hi - key) <= lim && in_hi;
+                                }
+                                const float p_lo = ok_lo ? ex2(fmaf(s[nb][e], sc2, -lse_lo)) : 0.f;
+                                const float p_hi = ok_hi ? ex2(fmaf(s[nb][2 + e], sc2, -lse_hi)) : 0.f;
+                                ds[nb][e] = p_lo * fmaf(dp[nb][e], scale, -d_lo);
+                                ds[nb][2 + e] = p_hi * fmaf(dp[nb][2 + e], scale, -d_hi);
+                            }
+                    };
+                    if (block_full(mask, W, S, N, t0, k0)) grads(kind_t<kFull>{});
+                    else if (mask != SG_MASK_DENSE && k0 >= S && t0 + 16 <= N) grads(kind_t<kBand>{});
+                    else grads(kind_t<kAny>{});
                     uint32_t dsa[4];
                     frag_a(ds, dsa);
                     mma_a_rows<DH>(dq, dsa, sK, k0);  // dQ += dS K
