@@ -2134,6 +2134,10 @@ sg_status plan_chunks(sg_model *m, int64_t B, bool bwd, Plan &p, size_t &bytes)
     const size_t per_sample = (size_t)carve(c, nullptr, c.N, bwd).total_floats * sizeof(float);
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
+    // at most a third of the free memory and 64 GB: large enough that a batch of
+    // 16384 short sequences is one chunk (launch count and tail effects then
+    // stay per layer, not per chunk and layer), small enough that a BF16 and an
+    // FP32 model can hold their workspaces side by side on one GPU
     const size_t budget = std::min<size_t>((size_t)64 << 30, free_b / 3 + m->ws_bytes);
     int64_t Bc = std::max<int64_t>(1, (int64_t)(budget / per_sample));
     Bc = std::min<int64_t>(Bc, B);
