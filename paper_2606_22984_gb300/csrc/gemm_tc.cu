@@ -160,19 +160,15 @@ __device__ __forceinline__ void staged_store(const RowGemm &g, const float *sOut
     const int et = threadIdx.x - 64;  // epilogue thread 0 .. 511
     const int P = g.N + 4;
     if (EPI == TE_STORE_BF16) {
-        const int per_row = g.N / 8;
+        // the tile holds BF16 rows (pitch N + 8 elements, see the TMEM drain)
+        const unsigned char *sB = reinterpret_cast<const unsigned char *>(sOut);
+        const int per_row = g.N / 8, PB = 2 * (g.N + 8);
         for (int e = et; e < 128 * per_row; e += 32 * kEpiWarps) {
             const int row = e / per_row, c8 = e % per_row;
             const int64_t r = rb * 128 + row;
             if (r >= g.R) continue;
-            const float4 a = *reinterpret_cast<const float4 *>(sOut + row * P + 8 * c8);
-            const float4 b = *reinterpret_cast<const float4 *>(sOut + row * P + 8 * c8 + 4);
-            uint4 q;
-            q.x = pk2(a.x, a.y);
-            q.y = pk2(a.z, a.w);
-            q.z = pk2(b.x, b.y);
-            q.w = pk2(b.z, b.w);
-            *reinterpret_cast<uint4 *>(g.out_h + r * g.ld_out + 8 * c8) = q;
+            *reinterpret_cast<uint4 *>(g.out_h + r * g.ld_out + 8 * c8) =
+                *reinterpret_cast<const uint4 *>(sB + row * PB + 16 * c8);
         }
     } else {
         const int per_row = g.N / 4;
@@ -391,7 +387,24 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) row_gemm_kernel(const 
                 float v[32];
                 tc::tmem_ld32(tmem + acc * 256 + ((uint32_t)(32 * q) << 16) + 32 * c, v);
                 tc::tmem_wait_ld();
-                if (staged) {
+                if (staged && EPI == TE_STORE_BF16) {
+                    // BF16 rows, pitch N + 8 elements (an odd number of 16-byte
+                    // pieces: 16-byte writes of 8 consecutive rows hit distinct banks)
+                    uint4 *d = reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(sOut) +
+                                                         row * 2 * (g.N + 8) + 64 * c);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        float o[8];
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) o[k] = v[8 * j + k] + (g.bias ? __ldg(g.bias + 32 * c + 8 * j + k) : 0.f);
+                        uint4 qv;
+                        qv.x = pk2(o[0], o[1]);
+                        qv.y = pk2(o[2], o[3]);
+                        qv.z = pk2(o[4], o[5]);
+                        qv.w = pk2(o[6], o[7]);
+                        d[j] = qv;
+                    }
+                } else if (staged) {
                     float4 *d = reinterpret_cast<float4 *>(sOut + row * (g.N + 4) + 32 * c);
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
