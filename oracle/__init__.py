@@ -9,9 +9,10 @@ The arithmetic lives in ``sg_oracle.c`` (plain C, double precision, one
 function per paper passage).  This module only compiles it with gcc and
 marshals numpy arrays through ctypes.
 
-Parity unpinned: Philox4x32-10 (no published known-answer vectors are
-available here; pinned statistically and by agreement with the independent
-CUDA implementation).
+Every function is pinned by tests/test_oracle_pins.py against something other
+than itself: closed forms, enumeration, an independent composition from
+PyTorch routines, finite differences, exact Boltzmann laws and, for
+Philox4x32-10, PyTorch's independent header-only engine word for word.
 """
 from __future__ import annotations
 
@@ -84,9 +85,12 @@ _I = ctypes.c_int
 
 
 def lib():
+    """The compiled oracle.  ``SG_ORACLE_LIB`` names another build of the same
+    source to load instead; the mutation tests use it to run the pins against
+    copies of the oracle with a planted mistake."""
     global _lib
     if _lib is None:
-        L = ctypes.CDLL(build())
+        L = ctypes.CDLL(os.environ.get("SG_ORACLE_LIB") or build())
         L.or_param_count.argtypes = [ctypes.POINTER(OrCfg)]
         L.or_param_count.restype = _I64
         L.or_philox.argtypes = [_P, _P, _P]

@@ -14,10 +14,9 @@
  * code.  All floating point is double; no blocking, fusion or reordering
  * beyond the definitions.
  *
- * Parity unpinned: Philox4x32-10 has no published known-answer vectors in
- * this repository, so the generator is pinned only statistically (uniformity
- * and independence tests) and by bit-for-bit agreement with the CUDA side's
- * independent implementation.
+ * Philox4x32-10 is pinned word for word against PyTorch's independent
+ * header-only engine (at::philox_engine) by the CPU tests, besides its
+ * statistical checks.
  */
 #include <math.h>
 #include <stdint.h>

@@ -34,8 +34,74 @@ def all_states(N):
 
 
 # --------------------------------------------------------------------------
-# Philox4x32-10 (parity unpinned: statistical pins only)
+# Philox4x32-10: word for word against PyTorch's independent header-only
+# engine, plus the uniform's definition and its statistics
 # --------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def torch_philox():
+    """PyTorch's at::philox_engine (ATen/core/PhiloxRNGEngine.h, source only)
+    compiled into a small helper library with g++."""
+    import ctypes
+    import os
+    import shutil
+    import subprocess
+    import tempfile
+
+    import torch
+
+    inc = os.path.join(os.path.dirname(torch.__file__), "include")
+    hdr = os.path.join(inc, "ATen", "core", "PhiloxRNGEngine.h")
+    gxx = shutil.which("g++")
+    if gxx is None or not os.path.exists(hdr):
+        pytest.skip("g++ or PyTorch's PhiloxRNGEngine.h not available")
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "philox_torch_ref.cpp")
+    out = os.path.join(tempfile.mkdtemp(prefix="philox_ref_"), "libphilox_ref.so")
+    subprocess.run([gxx, "-O1", "-std=c++17", "-shared", "-fPIC", "-I", inc, src, "-o", out],
+                   check=True, capture_output=True)
+    lib = ctypes.CDLL(out)
+    lib.torch_philox_blocks.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int64]
+
+    def blocks(ctr, key):
+        ctr = np.ascontiguousarray(ctr, dtype=np.uint32)
+        key = np.ascontiguousarray(key, dtype=np.uint32)
+        res = np.zeros((ctr.shape[0], 4), np.uint32)
+        lib.torch_philox_blocks(ctr.ctypes.data, key.ctypes.data, res.ctypes.data, ctr.shape[0])
+        return res
+
+    return blocks
+
+
+def test_philox_matches_pytorch_engine_word_for_word(torch_philox):
+    """The oracle's Philox4x32-10 against PyTorch's engine on 4096 random
+    (counter, key) pairs and on the edge words (all zeros, all ones, single
+    high bits): every one of the four output words equal."""
+    rng = np.random.default_rng(20260604)
+    ctr = rng.integers(0, 2 ** 32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2 ** 32, size=(4096, 2), dtype=np.uint64).astype(np.uint32)
+    edge = [0, 1, 0x7FFFFFFF, 0x80000000, 0xFFFFFFFE, 0xFFFFFFFF]
+    ec = np.array([[a, b, c, d] for a in edge for b in (0, 0xFFFFFFFF) for c in edge
+                   for d in (0, 0xFFFFFFFF)], np.uint32)
+    ek = np.array([[a, b] for a in (0, 0xFFFFFFFF) for b in (0, 0xFFFFFFFF)], np.uint32)
+    ctr = np.concatenate([ctr, np.repeat(ec, len(ek), 0)])
+    key = np.concatenate([key, np.tile(ek, (len(ec), 1))])
+    ref = torch_philox(ctr, key)
+    ours = np.array([oracle.philox(c, k) for c, k in zip(ctr, key)], np.uint32)
+    assert np.array_equal(ours, ref)
+
+
+def test_philox_uniform_counter_layout_matches_pytorch_engine(torch_philox):
+    """u(seed, a, b, stream, e) reads word 0 of the block with counter
+    (a, b, stream, e) and key (seed lo, seed hi), for 64-bit seeds."""
+    rng = np.random.default_rng(7)
+    for seed in (0, 1, 12345, 2 ** 32 + 17, 2 ** 64 - 1):
+        abse = rng.integers(0, 2 ** 32, size=(200, 4), dtype=np.uint64).astype(np.uint32)
+        abse[:, 2] %= 4   # stream ids in use
+        key = np.tile(np.array([seed & 0xFFFFFFFF, seed >> 32], np.uint32), (200, 1))
+        x0 = torch_philox(abse, key)[:, 0]
+        u = np.array([oracle.uniform(seed, *map(int, r)) for r in abse])
+        assert np.array_equal(u, ((x0 >> 8).astype(np.float64) + 0.5) / 2 ** 24)
+
 
 def test_philox_uniform_definition_and_statistics():
     seed = 12345
