@@ -77,9 +77,11 @@ typedef enum { SG_SK_DENSE = 0, SG_EA_LATTICE = 1 } sg_instance_kind;
  *              stream and the draw stay FP32.
  *   n_models   0 or 1: one model.  n > 1: a group of n models of this shape
  *              (e.g. one per temperature), weight blobs concatenated; in
- *              sg_sample, sample b of B uses model b / (B / n).  Grouped
- *              models are served by the BF16 decode for d = 256; other calls
- *              return SG_EUNSUPPORTED for n > 1.
+ *              sg_sample, sg_logprob and sg_grad, sample b of B (B a multiple
+ *              of n) belongs to model b / (B / n).  Grouped sampling is served
+ *              by the BF16 decode for d = 256 (other shapes return
+ *              SG_EUNSUPPORTED); sg_logprob and sg_grad serve groups of any
+ *              shape they serve singly; sg_muon_step does not.
  *   patch      spins per token P (patching, Methods: the EA lattice cut into
  *              cells of 2^D spins, one token per cell).  0 or 1: one spin per
  *              token.  P > 1: the head is a softmax over K = 2^P classes and
@@ -149,6 +151,29 @@ sg_status sg_model_refresh(sg_model *m, sg_stream stream);
 sg_status sg_model_check(sg_model *m, sg_stream stream);
 
 /*
+ * Cap the samples per chunk of the teacher-forced pass and its backward
+ * (sg_logprob, sg_grad).  Those calls keep every layer's activations of a
+ * chunk of samples on the device, which is how batches whose activations
+ * outgrow device memory are trained (the paper recomputes activations for
+ * its large systems); by default (max_samples = 0) a chunk is sized
+ * to a third of the free device memory, at most 64 GB.  A cap bounds the
+ * workspace further; results do not depend on the chunking beyond FP32
+ * summation order.  Errors: SG_EINVAL (NULL model, max_samples < 0).
+ */
+sg_status sg_model_set_max_chunk(sg_model *m, int64_t max_samples);
+
+/*
+ * Size the model's KV-cache workspace for sampling B configurations now, so
+ * that the next sg_sample calls of at most B samples allocate nothing (the
+ * workspace of Algorithm 2's KV cache; sg_sample otherwise grows it on
+ * demand).  Synchronous; may free and re-allocate the workspace, so no
+ * sampling call of this model may be in flight.
+ * Errors: SG_EINVAL (NULL model, B outside [1, 2^32), B not a multiple of
+ * n_models), SG_ENOMEM.
+ */
+sg_status sg_model_reserve(sg_model *m, int64_t B);
+
+/*
  * Batched ancestral sampling (Algorithm 2, KV-cache decode) of B
  * configurations in one persistent kernel launch.
  *   spins  dev int8 [B][N]   out: sampled spins.
@@ -169,12 +194,12 @@ sg_status sg_sample(sg_model *m, int64_t B, double beta, uint64_t seed, uint32_t
 
 /*
  * Allocation-free variant of sg_sample (FP32 path).  The paper has no
- * counterpart: this entry point exists for callers that must not allocate
- * device memory -- code that runs while a CUDA graph is being captured, code
- * embedded in a host framework that owns every device allocation through its
- * own memory pool, or latency-critical loops where cudaMalloc's implicit
- * synchronisation is not acceptable.  It calls no cudaMalloc, cudaFree or
- * allocating library routine.  Its scratch (packed weight copies followed by
+ * counterpart: this entry point exists for callers that must not let a
+ * library allocate device memory -- code embedded in a host framework that
+ * owns every device allocation through its own memory pool (memory the pool
+ * did not hand out is memory it cannot budget), or latency-sensitive loops in
+ * which cudaMalloc / cudaFree would synchronise the device and stall its other
+ * streams.  It calls no cudaMalloc, cudaFree or allocating library routine.  Its scratch (packed weight copies followed by
  * the KV cache) is one statically sized device array of
  * SG_NOALLOC_SCRATCH_BYTES inside libsg, which every GPU that loads the
  * library holds until the process exits.
@@ -190,6 +215,9 @@ sg_status sg_sample(sg_model *m, int64_t B, double beta, uint64_t seed, uint32_t
  * last call's contents; nothing in it needs to start at zero, because each
  * call writes every byte it reads.  Calls whose work overlaps on the GPU
  * (other streams, other host threads) race on the scratch: serialise them.
+ * The looked-up address belongs to the device's current context: after
+ * cudaDeviceReset (or any teardown of the primary context) the cached address
+ * is stale, so do not call this entry point again in that process.
  */
 #define SG_NOALLOC_SCRATCH_BYTES (64ull << 20)
 sg_status sg_sample_noalloc(const sg_config *cfg, const float *weights, int64_t B, double beta,
@@ -200,7 +228,8 @@ sg_status sg_sample_noalloc(const sg_config *cfg, const float *weights, int64_t 
  * Teacher-forced log q (Algorithm 1) of B given configurations, computed over
  * the whole sequence at once (prefill).
  *   spins  dev int8 [B][N] in;  logq dev float [B] out.
- * Errors: SG_EINVAL, SG_ENOMEM, SG_ECUDA.
+ * Grouped models: sample b is scored by model b / (B / n_models).
+ * Errors: SG_EINVAL (also B not a multiple of n_models), SG_ENOMEM, SG_ECUDA.
  */
 sg_status sg_logprob(sg_model *m, const int8_t *spins, int64_t B, float *logq, sg_stream stream);
 
@@ -212,7 +241,10 @@ sg_status sg_logprob(sg_model *m, const int8_t *spins, int64_t B, float *logq, s
  *   spins  dev int8 [B][N];  coeff dev float [B];
  *   grad   dev float [sg_param_count] out (overwritten, blob layout);
  *   logq   dev float [B] or NULL: out, the teacher-forced log q.
- * Errors: SG_EINVAL, SG_ENOMEM, SG_ECUDA.
+ * Grouped models: samples [i B/n, (i+1) B/n) belong to model i and their
+ * gradient fills model i's block of grad (blobs concatenated like the
+ * weights); the models run one after another on the stream.
+ * Errors: SG_EINVAL (also B not a multiple of n_models), SG_ENOMEM, SG_ECUDA.
  */
 sg_status sg_grad(sg_model *m, const int8_t *spins, const float *coeff, int64_t B, float *grad,
                   float *logq, sg_stream stream);

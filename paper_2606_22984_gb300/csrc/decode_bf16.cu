@@ -1419,7 +1419,10 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d256_kernel(const __grid_c
 
     // chunk stream (thread 0): chunk c sits in stage c % 2; chunk c >= 2 is
     // loaded once the MMAs of chunk c - 2 have completed (commit on empty[]).
-    int64_t next_load = 0, next_use = 0;
+    // Loads stop short of load_limit: after a layer's q product the ring stays
+    // empty so that the attention can stage keys in it, and its two loads go
+    // out once the key loop is done.
+    int64_t next_load = 0, next_use = 0, load_limit = INT64_MAX;
     uint32_t fphase[kStages256] = {0, 0}, ephase[kStages256] = {0, 0}, mphase = 0;
     auto load_chunk = [&]() {
         const int s = (int)(next_load % kStages256);
@@ -1456,7 +1459,7 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d256_kernel(const __grid_c
                 ok = tc::mbar_wait(&empty[s], ephase[s]);
                 if (!ok) break;
                 ephase[s] ^= 1u;
-                if (next_load < total_chunks) load_chunk();
+                if (next_load < total_chunks && next_load < load_limit) load_chunk();
             }
             if (!ok) {
                 atomicExch(a.err, 1);
@@ -1582,7 +1585,9 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d256_kernel(const __grid_c
             append(slot, 1, bq + 2 * D);
             tc::tc_fence_before();
             __syncthreads();
+            if (tid == 0) load_limit = ((int64_t)t * a.L + l) * kChunks256 + 12;
             run(Abuf, 4, ACC, false);  // q_t stays in TMEM
+            if (tid == 0) load_limit = INT64_MAX;
             if (s_err) break;
             // attention: heads 2 qr and 2 qr + 1, keys 0..t from the ring
             // (key t of row rr was written before the barriers of the q run)
@@ -1599,10 +1604,11 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d256_kernel(const __grid_c
                     acc[j] = 0.f;
                 }
                 float m0 = -INFINITY, l0 = 0.f;
-                // keys 0..t staged through shared memory by cp.async, two keys
-                // in flight per thread: the stages are the A and A2 tiles (idle
-                // during attention); per thread, K pieces at +0..+24 KB and V
-                // pieces at +32..+56 KB of a stage, 8 KB apart (conflict-free).
+                // keys 0..t staged through shared memory by cp.async, three keys
+                // in flight per thread: the stages are the A and A2 tiles and the
+                // weight ring (all idle during attention); per thread, K pieces
+                // at +0..+24 KB and V pieces at +32..+56 KB of a stage, 8 KB
+                // apart (conflict-free).
                 const uint4 *kb = reinterpret_cast<const uint4 *>(kvl) + (4 * hh) * kRows + rr;
                 // Every row reduces its keys as two halves, [0, half) and
                 // [half, nk), each an online softmax from the empty state,
@@ -1628,9 +1634,10 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d256_kernel(const __grid_c
                     m0 = -INFINITY;
                     l0 = 0.f;
                 };
+                auto stage = [&](int s) { return s == 0 ? Abuf : (s == 1 ? A2buf : ring); };
                 auto fetch = [&](int i, int s) {
                     const uint4 *pp = kb + koff[i];
-                    unsigned char *dst = (s == 0 ? Abuf : A2buf) + tid * 16;
+                    unsigned char *dst = stage(s) + tid * 16;
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
                         tc::cp_async16(dst + c * 8192, pp + c * kRows);
@@ -1638,12 +1645,13 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d256_kernel(const __grid_c
                     }
                     tc::cp_async_commit();
                 };
-                for (int i = i0; i < i1 && i < i0 + 2; ++i) fetch(i, i - i0);
+                for (int i = i0; i < i1 && i < i0 + 3; ++i) fetch(i, i - i0);
                 for (int i = i0; i < i1; ++i) {
                     if (!mirror_mode && i == half) park();
-                    if (i + 1 < i1) tc::cp_async_wait<1>();
+                    if (i + 2 < i1) tc::cp_async_wait<2>();
+                    else if (i + 1 < i1) tc::cp_async_wait<1>();
                     else tc::cp_async_wait<0>();
-                    const unsigned char *src = (((i - i0) & 1) ? A2buf : Abuf) + tid * 16;
+                    const unsigned char *src = stage((i - i0) % 3) + tid * 16;
                     float s = 0.f;
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
@@ -1668,7 +1676,7 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d256_kernel(const __grid_c
                         }
                     }
                     // the stage is refilled only after its data has been consumed
-                    if (i + 2 < i1) fetch(i + 2, (i - i0) & 1);
+                    if (i + 3 < i1) fetch(i + 3, (i - i0) % 3);
                 }
                 if (!mirror_mode && half >= nk) park();  // nk <= 1: the second half is empty
                 if (mirror_mode) {
@@ -1725,9 +1733,14 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d256_kernel(const __grid_c
                 tc::tmem_st32(tmem + tq + HCOL + DH * hh, hv);
                 tc::tmem_wait_st();
             }
+            // the ring's key pieces are consumed: order these generic-proxy
+            // accesses before the bulk copies that refill it with weights
+            tc::fence_async_smem();
             tc::tc_fence_before();
             __syncthreads();
             tc::tc_fence_after();
+            if (tid == 0)
+                while (next_load < total_chunks && next_load < next_use + kStages256) load_chunk();
             layernorm_to(w + o.ln2g, w + o.ln2b);
             const float *b1 = wt + a.p.b1[l];
             for (int j = 0; j < 4 && !s_err; ++j) {
@@ -1893,6 +1906,37 @@ sg_status launch_pack_bf16(sg_model *m, cudaStream_t st)
     return check_launch("pack bf16 operands");
 }
 
+// Launch geometry of the BF16 decode for B samples: rows per CTA, CTAs per
+// model (grouped models) and CTAs; returns the bytes of KV cache it needs.
+size_t decode_bf16_layout(const sg_model *m, int64_t B, int *rows_out, int *cpm_out,
+                          int64_t *tiles_out)
+{
+    const sg_config &c = m->seq;  // N = tokens
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t rows_per_model = B / m->n_models;
+    // spread the batch over every SM: rows per CTA = ceil(B / SMs), at most 128
+    int rows = (int)std::min<int64_t>(kRows, (B + sms - 1) / sms);
+    rows = std::max(rows, 1);
+    // grouped models: a CTA must not straddle two models; each model's rows go
+    // to ctas_per_model CTAs (counts differing by at most one), as many as
+    // keep all models within one wave over the SMs, at most 128 rows each
+    int cpm = 0;
+    if (m->n_models > 1) {
+        cpm = (int)std::max<int64_t>((rows_per_model + kRows - 1) / kRows,
+                                     std::max<int64_t>(1, sms / m->n_models));
+        cpm = (int)std::min<int64_t>(cpm, rows_per_model);
+        rows = (int)((rows_per_model + cpm - 1) / cpm);
+    }
+    const int64_t tiles = cpm > 0 ? (int64_t)cpm * m->n_models : (B + rows - 1) / rows;
+    const Bf16Geom g = bgeom(c.mask_kind, c.N, c.W, c.S);
+    if (rows_out) *rows_out = rows;
+    if (cpm_out) *cpm_out = cpm;
+    if (tiles_out) *tiles_out = tiles;
+    return (size_t)tiles * c.n_layers * g.nslots * 2 * c.d * kRows * 2;
+}
+
 sg_status launch_decode_bf16(sg_model *m, int64_t B, uint64_t seed, uint32_t sid, float band,
                              int8_t *spins, float *logq, uint32_t *flags, cudaStream_t st)
 {
@@ -1909,28 +1953,11 @@ sg_status launch_decode_bf16(sg_model *m, int64_t B, uint64_t seed, uint32_t sid
     if (P > 1 && !(d64 && c.d_token <= 16 && (1 << P) <= 32))
         return fail(SG_EUNSUPPORTED, "patched BF16 decode is built for d = 64 with at most 32 "
                                      "classes (2D cells); use SG_FP32");
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t rows_per_model = B / m->n_models;
-    // spread the batch over every SM: rows per CTA = ceil(B / SMs), at most 128;
-    // with grouped models a CTA must not straddle two models, so the rows per
-    // CTA divide the rows per model
-    int rows = (int)std::min<int64_t>(kRows, (B + sms - 1) / sms);
-    rows = std::max(rows, 1);
-    // grouped models: a CTA must not straddle two models; each model's rows go
-    // to ctas_per_model CTAs (counts differing by at most one), as many as
-    // keep all models within one wave over the SMs, at most 128 rows each
-    int cpm = 0;
-    if (m->n_models > 1) {
-        cpm = (int)std::max<int64_t>((rows_per_model + kRows - 1) / kRows,
-                                     std::max<int64_t>(1, sms / m->n_models));
-        cpm = (int)std::min<int64_t>(cpm, rows_per_model);
-        rows = (int)((rows_per_model + cpm - 1) / cpm);
-    }
-    const int64_t tiles = cpm > 0 ? (int64_t)cpm * m->n_models : (B + rows - 1) / rows;
+    int rows = 0, cpm = 0;
+    int64_t tiles = 0;
+    const size_t kv_bytes = decode_bf16_layout(m, B, &rows, &cpm, &tiles);
     const Bf16Geom g = bgeom(c.mask_kind, c.N, c.W, c.S);
-    const size_t kv_bytes = (size_t)tiles * c.n_layers * g.nslots * 2 * c.d * kRows * 2;
     SG_TRY(ensure_buffer(&m->kv, &m->kv_bytes, kv_bytes));
     SG_TRY(ensure_buffer(&m->err, &m->err_bytes, sizeof(int)));
     const size_t smem = (size_t)kRows * c.d * 2 + (size_t)kRows * c.d_ff * 2 +

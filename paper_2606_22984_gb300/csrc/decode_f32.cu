@@ -392,6 +392,16 @@ decode_f32_kernel(const __grid_constant__ DevModel m, int64_t B, uint64_t seed, 
         if (b0 + s < B) logq[b0 + s] = lq[s];
 }
 
+// KV-cache bytes of the FP32 decode for B samples (tiles of 256 / n_heads
+// samples, every slot of the ring for every layer).
+size_t decode_f32_kv_bytes(const sg_model *m, int64_t B)
+{
+    const sg_config &c = m->seq;  // N = tokens
+    const int64_t MS = 256 / c.n_heads;
+    const RingGeom g = ring_geom(c.mask_kind, c.N, c.W, c.S);
+    return (size_t)((B + MS - 1) / MS) * c.n_layers * g.nslots * 2 * c.d * MS * sizeof(float);
+}
+
 template <int D, int DH>
 static sg_status run_decode(sg_model *m, int64_t B, uint64_t seed, uint32_t sid, float band,
                             int8_t *spins, float *logq, uint32_t *flags, cudaStream_t st)
@@ -400,10 +410,8 @@ static sg_status run_decode(sg_model *m, int64_t B, uint64_t seed, uint32_t sid,
     constexpr int MS = 256 / NH;
     const sg_config &c = m->seq;  // N = tokens
     const int P = spins_per_token(c), K = 1 << P;
-    const RingGeom g = ring_geom(c.mask_kind, c.N, c.W, c.S);
     const int64_t tiles = (B + MS - 1) / MS;
-    const size_t kv_bytes = (size_t)tiles * c.n_layers * g.nslots * 2 * D * MS * sizeof(float);
-    SG_TRY(ensure_buffer(&m->kv, &m->kv_bytes, kv_bytes));
+    SG_TRY(ensure_buffer(&m->kv, &m->kv_bytes, decode_f32_kv_bytes(m, B)));
     int US = (3 * D > c.d_ff ? 3 * D : c.d_ff) + 4;
     if (US < K + 4) US = K + 4;  // the head's K logits per sample reuse u
     const size_t smem = ((size_t)MS * (2 * (D + 4) + US) + 2 * MS) * sizeof(float);

@@ -2141,6 +2141,7 @@ sg_status plan_chunks(sg_model *m, int64_t B, bool bwd, Plan &p, size_t &bytes)
     const size_t budget = std::min<size_t>((size_t)64 << 30, free_b / 3 + m->ws_bytes);
     int64_t Bc = std::max<int64_t>(1, (int64_t)(budget / per_sample));
     Bc = std::min<int64_t>(Bc, B);
+    if (m->max_chunk > 0) Bc = std::min<int64_t>(Bc, m->max_chunk);
     // keep the warp count of the attention kernels within a 32-bit grid
     Bc = std::min<int64_t>(Bc, (int64_t)((1ll << 30) / ((int64_t)c.N * c.n_heads)));
     p.Bc = Bc;

@@ -139,6 +139,38 @@ static sg_status validate(const sg_config *c)
 
 static int models_of(const sg_config &c) { return c.n_models > 1 ? c.n_models : 1; }
 
+// Grouped models in the teacher-forced calls: model mi scores samples
+// [mi B/n, (mi+1) B/n).  Each model runs on a view of the group -- its own
+// blob and packed FP32 copies, its tiled BF16 weights repacked into the
+// group's one buffer -- one after another on the stream, so the repack of
+// model mi + 1 is ordered after model mi's kernels.  Buffers a view grows
+// belong to the group.
+template <class F>
+static sg_status for_each_model(sg_model *m, int64_t B, cudaStream_t st, F &&f)
+{
+    if (m->n_models == 1) return f(m, (int64_t)0, B);
+    if (B % m->n_models) return fail(SG_EINVAL, "B must be a multiple of n_models");
+    const int64_t Bm = B / m->n_models;
+    for (int mi = 0; mi < m->n_models; ++mi) {
+        sg_model v = *m;
+        v.n_models = 1;
+        v.cfg.n_models = 1;
+        v.seq.n_models = 1;
+        v.P = m->P1;
+        v.w = m->w + (size_t)mi * m->P1;
+        v.wt = m->wt + (size_t)mi * m->pack.total;
+        sg_status s = launch_pack_tiled_weights(&v, st);
+        if (s == SG_OK) s = f(&v, mi * Bm, Bm);
+        m->ws = v.ws;
+        m->ws_bytes = v.ws_bytes;
+        m->bt = v.bt;
+        m->bt_bytes = v.bt_bytes;
+        std::memcpy(m->bt_off, v.bt_off, sizeof(m->bt_off));
+        if (s != SG_OK) return s;
+    }
+    return SG_OK;
+}
+
 }  // namespace sg
 
 using namespace sg;
@@ -241,6 +273,25 @@ sg_status sg_model_check(sg_model *m, sg_stream stream)
                               "); its outputs are not valid");
 }
 
+sg_status sg_model_set_max_chunk(sg_model *m, int64_t max_samples)
+{
+    if (!m) return fail(SG_EINVAL, "NULL model");
+    if (max_samples < 0) return fail(SG_EINVAL, "max_samples must be >= 0");
+    m->max_chunk = max_samples;
+    return SG_OK;
+}
+
+sg_status sg_model_reserve(sg_model *m, int64_t B)
+{
+    if (!m) return fail(SG_EINVAL, "NULL model");
+    if (B < 1 || B >= (int64_t)1 << 32) return fail(SG_EINVAL, "B must be in [1, 2^32)");
+    if (m->n_models > 1 && B % m->n_models)
+        return fail(SG_EINVAL, "B must be a multiple of n_models");
+    const size_t need = m->cfg.precision == SG_BF16 ? decode_bf16_layout(m, B, nullptr, nullptr, nullptr)
+                                                    : decode_f32_kv_bytes(m, B);
+    return ensure_buffer(&m->kv, &m->kv_bytes, need);
+}
+
 sg_status sg_sample(sg_model *m, int64_t B, double beta, uint64_t seed, uint32_t stream_id,
                     float flag_band, int8_t *spins, float *logq, uint32_t *flags, sg_stream stream)
 {
@@ -265,8 +316,11 @@ sg_status sg_logprob(sg_model *m, const int8_t *spins, int64_t B, float *logq, s
 {
     if (!m || !spins || !logq) return fail(SG_EINVAL, "NULL model or pointer");
     if (B < 1) return fail(SG_EINVAL, "B must be >= 1");
-    if (m->n_models > 1) return fail(SG_EUNSUPPORTED, "sg_logprob serves single models");
-    return launch_logprob_f32(m, spins, B, logq, (cudaStream_t)stream);
+    const cudaStream_t st = (cudaStream_t)stream;
+    const int64_t N = m->cfg.N;
+    return for_each_model(m, B, st, [&](sg_model *v, int64_t b0, int64_t Bm) {
+        return launch_logprob_f32(v, spins + b0 * N, Bm, logq + b0, st);
+    });
 }
 
 sg_status sg_grad(sg_model *m, const int8_t *spins, const float *coeff, int64_t B, float *grad,
@@ -274,8 +328,12 @@ sg_status sg_grad(sg_model *m, const int8_t *spins, const float *coeff, int64_t 
 {
     if (!m || !spins || !coeff || !grad) return fail(SG_EINVAL, "NULL model or pointer");
     if (B < 1) return fail(SG_EINVAL, "B must be >= 1");
-    if (m->n_models > 1) return fail(SG_EUNSUPPORTED, "sg_grad serves single models");
-    return launch_grad_f32(m, spins, coeff, B, grad, logq, (cudaStream_t)stream);
+    const cudaStream_t st = (cudaStream_t)stream;
+    const int64_t N = m->cfg.N;
+    return for_each_model(m, B, st, [&](sg_model *v, int64_t b0, int64_t Bm) {
+        return launch_grad_f32(v, spins + b0 * N, coeff + b0, Bm, grad + (b0 / Bm) * m->P1,
+                               logq ? logq + b0 : nullptr, st);
+    });
 }
 
 sg_status sg_instance_create(int32_t kind, int32_t N, int32_t D, int32_t L, int32_t periodic,

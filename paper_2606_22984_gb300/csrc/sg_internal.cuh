@@ -232,6 +232,7 @@ struct sg_model {
     size_t kv_bytes = 0;
     void *ws = nullptr;       // prefill / backward workspace
     size_t ws_bytes = 0;
+    int64_t max_chunk = 0;    // cap on samples per prefill / backward chunk (0: by free memory)
     void *err = nullptr;      // device error word written by kernels (bounded waits, NaN)
     size_t err_bytes = 0;
     // tiled BF16 weights for the tensor-core teacher-forced pass and backward
@@ -269,6 +270,10 @@ sg_status launch_decode_bf16(sg_model *m, int64_t B, uint64_t seed, uint32_t sid
                              int8_t *spins, float *logq, uint32_t *flags, cudaStream_t st);
 sg_status launch_decode_f32(sg_model *m, int64_t B, uint64_t seed, uint32_t sid, float band,
                             int8_t *spins, float *logq, uint32_t *flags, cudaStream_t st);
+// KV-cache bytes the decodes need for B samples (sg_model_reserve sizes the
+// workspace with these before a launch).
+size_t decode_bf16_layout(const sg_model *m, int64_t B, int *rows, int *cpm, int64_t *tiles);
+size_t decode_f32_kv_bytes(const sg_model *m, int64_t B);
 sg_status launch_logprob_f32(sg_model *m, const int8_t *spins, int64_t B, float *logq,
                              cudaStream_t st);
 sg_status launch_grad_f32(sg_model *m, const int8_t *spins, const float *coeff, int64_t B,

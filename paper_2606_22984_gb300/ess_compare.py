@@ -1,9 +1,10 @@
 """Neural independence MH versus single-spin-flip Metropolis: ESS per second.
 
-The transformer (optionally trained first with the REINFORCE loop: sg_sample,
-sg_energy, sg_free_energy, sg_grad, sg_adam_step) proposes whole
-configurations; sg_mh_step accepts them against the exact energies, chain by
-chain.  sg_metropolis runs the classical sweeps on the same instance.  Both
+The transformer (optionally trained first by train.Trainer: variational
+annealing from T0 down to the target temperature, local Monte Carlo
+refinement of the samples with the self-distillation term of Eq. loss2, Adam
+or Muon) proposes whole configurations; sg_mh_step accepts them against the
+exact energies, chain by chain.  sg_metropolis runs the classical sweeps on the same instance.  Both
 chains' energy traces give tau_int and the ESS (analysis.py); ESS/sec divides by
 the GPU time of the calls that produced them (for MH: sampling + energies +
 MH; for Metropolis: the sweeps).  Prints one JSON line.
@@ -27,19 +28,27 @@ def _events():
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
-def train(model, inst, B, beta, steps, lr, seed0=10_000):
-    w = model.weights()
-    m, v, g = torch.zeros_like(w), torch.zeros_like(w), torch.empty_like(w)
-    out = None
-    for i in range(steps):
-        s, lq = model.sample(B, seed=seed0 + i)
-        E = inst.energy(s)
-        out, coeff = sg.free_energy(E, lq, beta, want_coeff=True)
-        model.grad(s, coeff, grad=g)
-        sg.adam_step(w, g, m, v, lr, i + 1)
-        model.refresh()
-    model.check()
-    return None if out is None else out.cpu().numpy()
+def train(model, inst, a, beta):
+    """Variational annealing toward T = 1 / beta (Methods "Variational
+    annealing"): T held at T0 for the warm-up, then lowered in n_anneal
+    equal decrements every n_eq steps, clamped at 1 / beta; returns the
+    trainer's log and the batch free energies of the trained model."""
+    from .train import TrainConfig, Trainer, anneal_temperature
+
+    T_target = 1.0 / beta
+    T0 = max(a.anneal_T0, T_target)
+
+    def sched(i):
+        return max(T_target, anneal_temperature(i, T0, a.anneal_warmup, a.anneal_steps,
+                                                 a.anneal_eq))
+
+    cfg = TrainConfig(B=a.train_batch, steps=a.train_steps, lr=a.lr, schedule=sched,
+                      lmc_sweeps=a.lmc_sweeps, w=a.w, optimizer=a.optimizer, seed=a.seed,
+                      log_every=max(1, a.train_steps // 10))
+    log = Trainer(model, inst, cfg).run()
+    s, lq = model.sample(a.train_batch, seed=987654)
+    out = sg.free_energy(inst.energy(s), lq, beta).cpu().numpy()
+    return log, out
 
 
 def main():
@@ -54,6 +63,13 @@ def main():
     p.add_argument("--train-steps", type=int, default=0)
     p.add_argument("--train-batch", type=int, default=1024)
     p.add_argument("--lr", type=float, default=1e-3)
+    p.add_argument("--optimizer", default="muon", choices=["adam", "muon"])
+    p.add_argument("--lmc-sweeps", type=int, default=2, help="local MC sweeps per step (Eq. loss2)")
+    p.add_argument("--w", type=float, default=0.05, help="self-distillation weight of Eq. loss2")
+    p.add_argument("--anneal-T0", type=float, default=3.0)
+    p.add_argument("--anneal-warmup", type=int, default=50)
+    p.add_argument("--anneal-steps", type=int, default=20)
+    p.add_argument("--anneal-eq", type=int, default=10)
     p.add_argument("--proposals", type=int, default=0, help="proposals per MH step (default: B)")
     p.add_argument("--chains", type=int, default=1024)
     p.add_argument("--mh-steps", type=int, default=4)
@@ -86,7 +102,7 @@ def main():
     model = sg.Model(shape, weights, prec)
     inst = sg.Instance(inst_src)
     stream = torch.cuda.current_stream()
-    F_train = train(model, inst, a.train_batch, beta, a.train_steps, a.lr) if a.train_steps else None
+    log, F_train = train(model, inst, a, beta) if a.train_steps else (None, None)
 
     # ---- neural MH
     cs, clq = model.sample(C, seed=1)
@@ -140,6 +156,10 @@ def main():
            "mean_E_gap_per_spin_mh_minus_metropolis": gap,
            "mh_equilibrated": abs(gap) < 0.01,
            "train_steps": a.train_steps, "train_batch": a.train_batch,
+           "training": None if log is None else {
+               "optimizer": a.optimizer, "lmc_sweeps": a.lmc_sweeps, "w": a.w,
+               "anneal": [a.anneal_T0, a.anneal_warmup, a.anneal_steps, a.anneal_eq],
+               "T": log.T, "mean_E_per_spin": [e / Ns for e in log.mean_E]},
            "F_q_per_spin_after_training": None if F_train is None else float(F_train[0] / Ns),
            "F_IS_per_spin_after_training": None if F_train is None else float(F_train[1] / Ns),
            "mh": mh, "metropolis": met,

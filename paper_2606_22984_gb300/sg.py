@@ -48,6 +48,8 @@ _SIGS = {
     "sg_model_weights": ([_P], _P),
     "sg_model_refresh": ([_P, _P], _I32),
     "sg_model_check": ([_P, _P], _I32),
+    "sg_model_reserve": ([_P, _I64], _I32),
+    "sg_model_set_max_chunk": ([_P, _I64], _I32),
     "sg_sample": ([_P, _I64, _D, _U64, _U32, _F, _P, _P, _P, _P], _I32),
     "sg_logprob": ([_P, _P, _I64, _P, _P], _I32),
     "sg_grad": ([_P, _P, _P, _I64, _P, _P, _P], _I32),
@@ -162,6 +164,14 @@ class Model:
 
     def refresh(self, stream=None):
         _check("sg_model_refresh", lib().sg_model_refresh(self.handle, _stream(stream)))
+
+    def reserve(self, B):
+        """Size the sampling workspace for B configurations (sg_model_reserve)."""
+        _check("sg_model_reserve", lib().sg_model_reserve(self.handle, B))
+
+    def set_max_chunk(self, max_samples):
+        """Cap the samples per chunk of sg_logprob / sg_grad (0: automatic)."""
+        _check("sg_model_set_max_chunk", lib().sg_model_set_max_chunk(self.handle, max_samples))
 
     def check(self, stream=None):
         """Synchronise and raise if a kernel recorded a bounded-wait timeout or NaN."""

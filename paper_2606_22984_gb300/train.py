@@ -10,16 +10,18 @@ One step (Methods "Training strategy", "Variational annealing"; Eq. loss2):
   3. energies (sg_energy);
   4. REINFORCE weights of L = E + T ln q (or beta E + ln q at a fixed beta),
      with the likelihood term w of Eq. loss2 (sg_loss_coeff);
-  5. gradient (sg_grad) and optimiser step (sg_adam_step, or sg_muon_step:
-     Muon on the weight matrices, AdamW on the rest), weights repacked
-     (sg_model_refresh).
+  5. gradient through torch.autograd: the surrogate sum_b c_b ln q_b of
+     autograd.reinforce_loss, whose forward and backward are one sg_grad
+     call, and loss.backward() fills the weight blob's .grad; optimiser step
+     on that gradient (sg_adam_step, or sg_muon_step: Muon on the weight
+     matrices, AdamW on the rest), weights repacked (sg_model_refresh).
 """
 from dataclasses import dataclass, field
 from typing import Callable, List, Optional
 
 import torch
 
-from . import sg
+from . import autograd, sg
 
 
 def anneal_temperature(i: int, T0: float, n_warmup: int, n_anneal: int, n_eq: int) -> float:
@@ -70,11 +72,11 @@ class Trainer:
         if cfg.optimizer not in ("adam", "muon"):
             raise ValueError("optimizer must be 'adam' or 'muon'")
         self.model, self.inst, self.cfg = model, inst, cfg
-        w = model.weights()
-        self.m = torch.zeros_like(w)
-        self.v = torch.zeros_like(w)
-        self.mom = torch.zeros_like(w) if cfg.optimizer == "muon" else None
-        self.grad = torch.empty_like(w)
+        # the master blob as an autograd leaf: backward() writes its .grad
+        self.w = model.weights().requires_grad_(True)
+        self.m = torch.zeros_like(self.w, requires_grad=False)
+        self.v = torch.zeros_like(self.m)
+        self.mom = torch.zeros_like(self.m) if cfg.optimizer == "muon" else None
         self.log = TrainLog()
 
     def temperature(self, i: int) -> float:
@@ -95,11 +97,13 @@ class Trainer:
         else:                    # ground-state form: L = E + T ln q
             a, cc = 1.0, T
         coeff, mean = sg.loss_coeff(E, logq, a, cc, c.w)
-        model.grad(spins, coeff, grad=self.grad)
+        self.w.grad = None
+        autograd.reinforce_loss(model, spins, coeff, weights=self.w).backward()
+        grad = self.w.grad
         if self.mom is None:
-            sg.adam_step(model.weights(), self.grad, self.m, self.v, c.lr, i + 1)
+            sg.adam_step(self.w.detach(), grad, self.m, self.v, c.lr, i + 1)
         else:
-            model.muon_step(self.grad, self.mom, self.m, self.v, c.lr, i + 1, mu=c.momentum,
+            model.muon_step(grad, self.mom, self.m, self.v, c.lr, i + 1, mu=c.momentum,
                             weight_decay=c.weight_decay)
         model.refresh()
         if i % c.log_every == 0 or i == c.steps - 1:

@@ -13,12 +13,19 @@ import torch
 import oracle
 from paper_2606_22984_gb300 import inputs, sg
 
-from helpers import ocfg, oracle_replay, unpack_flags
+from helpers import assert_grad_blocks, grad_block_errors, ocfg, oracle_replay, unpack_flags
 
 pytestmark = pytest.mark.gpu
 
 FP32_LOGQ_TOL = 1e-4     # per spin, FP32 path (per-sample bound 1e-4 * N)
 BF16_LOGQ_TOL = 2e-2     # per spin, BF16 path
+BF16_GRAD_BLOCK_TOL = 5e-2  # per weight tensor, BF16 gradient (relative, see assert_grad_blocks)
+FP32_BAND = 1e-5         # flag bands the library uses by default
+BF16_BAND = 1e-2
+
+
+def _band(precision):
+    return BF16_BAND if precision == sg.SG_BF16 else FP32_BAND
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -49,7 +56,7 @@ def _sample_and_check(m, w, B, seed, precision, tol):
     spins, logq, flags = model.sample(B, seed=seed, with_flags=True)
     torch.cuda.synchronize()
     s, lq, fl = _np(spins), _np(logq), _np(flags)
-    so, lqo, ppo, flo = oracle_replay(m, w, seed, s, fl)
+    so, lqo, ppo, flo = oracle_replay(m, w, seed, s, fl, _band(precision))
     assert np.array_equal(so, s), "spins differ from the oracle outside flagged draws"
     assert np.all(np.isin(s, (-1, 1)))
     dl = np.abs(lqo - lq)
@@ -104,7 +111,7 @@ def test_full_size_d128_sampled_rows(name, precision, rows):
     gi = sg.Instance(inst)
     s, lq, fl = _np(spins), _np(logq), _np(flags)
     rows = np.array(rows)
-    so, lqo, _, _ = oracle_replay(m, w, 2025, s, fl, rows=rows)
+    so, lqo, _, _ = oracle_replay(m, w, 2025, s, fl, _band(prec), rows=rows)
     assert np.array_equal(so, s[rows])
     assert np.abs(lqo - lq[rows]).max() <= tol * m.N
     assert unpack_flags(fl, m.N).mean() < (0.05 if precision == "bf16" else 0.01)
@@ -160,7 +167,7 @@ def test_bf16_grouped_models_match_oracle(n_models, per_model):
     for i in range(n_models):
         rows = np.arange(i * per_model, (i + 1) * per_model)
         rows = rows if per_model <= 100 else rows[[0, 1, per_model // 2, per_model - 1]]
-        so, lqo, _, _ = oracle_replay(m, w[i * P1:(i + 1) * P1], 99, s, fl, rows=rows)
+        so, lqo, _, _ = oracle_replay(m, w[i * P1:(i + 1) * P1], 99, s, fl, BF16_BAND, rows=rows)
         assert np.array_equal(so, s[rows]), f"model {i}: spins differ"
         assert np.abs(lqo - lq[rows]).max() <= BF16_LOGQ_TOL * m.N
     # rows of model 0 are bit-identical to a single-model launch of model 0
@@ -187,7 +194,7 @@ def test_d256_rows_do_not_depend_on_rows_per_cta():
     assert np.array_equal(_np(l_big[:100]), _np(l_small))
     s, lq, fl = _np(s_big), _np(l_big), _np(f_big)
     rows = [0, 64, B - 1]
-    so, lqo, _, _ = oracle_replay(m, w, 4, s, fl, rows=rows)
+    so, lqo, _, _ = oracle_replay(m, w, 4, s, fl, BF16_BAND, rows=rows)
     assert np.array_equal(so, s[rows])
     assert np.abs(lqo - lq[rows]).max() <= BF16_LOGQ_TOL * m.N
 
@@ -202,7 +209,7 @@ def test_bf16_grouped_models_at_the_group_limit():
     model.check()
     s, lq, fl = _np(spins), _np(logq), _np(flags)
     for i in (0, 31, 63):
-        so, lqo, _, _ = oracle_replay(m, w[i * P1:(i + 1) * P1], 5, s, fl, rows=[i])
+        so, lqo, _, _ = oracle_replay(m, w[i * P1:(i + 1) * P1], 5, s, fl, BF16_BAND, rows=[i])
         assert np.array_equal(so, s[[i]])
         assert abs(lqo[0] - lq[i]) <= BF16_LOGQ_TOL * m.N
     with pytest.raises(sg.SgError):
@@ -234,7 +241,7 @@ def test_patched_sampling_and_scoring_match_oracle(name):
     model.check()
     s, lq, fl = _np(spins), _np(logq), _np(flags)
     assert np.all(np.isin(s, (-1, 1)))
-    so, lqo, _, _ = oracle_replay(m, w, 31, s, fl)
+    so, lqo, _, _ = oracle_replay(m, w, 31, s, fl, _band(prec))
     assert np.array_equal(so, s), "spins differ from the oracle outside flagged draws"
     assert np.abs(lqo - lq).max() <= tol * m.N
     tf = _np(model.logprob(spins))
@@ -264,7 +271,104 @@ def test_grouped_models_rejected_outside_d256():
     with pytest.raises(sg.SgError):
         g.sample(7, seed=1)  # B not a multiple of n_models
     with pytest.raises(sg.SgError):
-        g.logprob(torch.ones(2, 8, dtype=torch.int8, device="cuda"))
+        g.logprob(torch.ones(3, 8, dtype=torch.int8, device="cuda"))
+    with pytest.raises(sg.SgError):
+        g.grad(torch.ones(3, 8, dtype=torch.int8, device="cuda"),
+               torch.zeros(3, dtype=torch.float32, device="cuda"))
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_grouped_logprob_and_grad_equal_per_model_calls(precision):
+    """A group of 3 models in one sg_logprob / sg_grad call: model i scores
+    samples [i B/3, (i+1) B/3) and fills its own gradient block, equal to a
+    single-model call on the same samples (up to FP32 summation order), and
+    to the oracle."""
+    m = inputs.ModelShape(30, 2, 64, 4, mask_kind=1, W=4, S=5)
+    prec = sg.SG_BF16 if precision == "bf16" else sg.SG_FP32
+    n, per = 3, 40
+    w = inputs.make_group_weights(m, 11, n)
+    P1 = w.size // n
+    B = n * per
+    s = inputs.random_spins(B, m.N, 6)
+    c = np.random.default_rng(8).normal(0, 1, B).astype(np.float32)
+    group = sg.Model(m, w, prec, n_models=n)
+    ts, tc = torch.tensor(s, device="cuda"), torch.tensor(c, device="cuda")
+    lq = torch.empty(B, dtype=torch.float32, device="cuda")
+    g = _np(group.grad(ts, tc, logq=lq))
+    lp = _np(group.logprob(ts))
+    group.check()
+    assert np.array_equal(lp, _np(lq))
+    for i in range(n):
+        one = sg.Model(m, w[i * P1:(i + 1) * P1], prec)
+        sl = slice(i * per, (i + 1) * per)
+        gi = _np(one.grad(ts[sl].contiguous(), tc[sl].contiguous()))
+        assert np.abs(g[i * P1:(i + 1) * P1] - gi).max() <= 1e-5 * np.abs(gi).max()
+        assert np.array_equal(_np(one.logprob(ts[sl].contiguous())), lp[sl])
+    go, lqo = oracle.grad(ocfg(m), w[:P1], s[:per], c[:per].astype(np.float64))
+    tol = BF16_LOGQ_TOL if prec == sg.SG_BF16 else FP32_LOGQ_TOL
+    assert np.abs(lp[:per] - lqo).max() <= tol * m.N
+    rel = np.linalg.norm(g[:P1] - go) / np.linalg.norm(go)
+    assert rel < (2e-2 if prec == sg.SG_BF16 else 1e-4), rel
+
+
+def test_full_size_ea2d64_grouped_training_step():
+    """One REINFORCE step of the 2D EA L=64 workload at full size (N = 4096,
+    8 layers d = 256, 8 models = 8 betas x 1024 samples, BF16): grouped
+    sampling, Gaussian energies, per-beta loss weights (Eq. loss1), one
+    grouped sg_grad (chunked by free memory), Adam.  Checks: weight blocks of
+    models whose coefficients are all zero get exactly zero gradient; models 0
+    and 7 equal single-model gradients of their samples under a different
+    chunking; log q of the teacher-forced pass agrees with the sampler's.
+    Prints the time and the device memory the step needed."""
+    import time
+    wl = inputs.workloads()["ea2d64"]
+    m, betas = wl.model, [float(b) for b in wl.betas]
+    nb, per = len(betas), wl.B
+    B = nb * per
+    w = wl.group_weights()
+    P1 = w.size // nb
+    free0 = torch.cuda.mem_get_info()[0]
+    group = sg.Model(m, w, sg.SG_BF16, n_models=nb)
+    inst = sg.Instance(wl.instance())
+    t0 = time.perf_counter()
+    spins, logq = group.sample(B, seed=31)
+    E = inst.energy(spins)
+    coeff = torch.empty(B, dtype=torch.float32, device="cuda")
+    for i, beta in enumerate(betas):
+        sl = slice(i * per, (i + 1) * per)
+        cf, _ = sg.loss_coeff(E[sl].contiguous(), logq[sl].contiguous(), beta, 1.0)
+        coeff[sl] = cf
+    # zero every model's weights except those of models 0 and 7
+    keep = torch.zeros(B, dtype=torch.bool, device="cuda")
+    keep[:per] = True
+    keep[(nb - 1) * per:] = True
+    coeff = torch.where(keep, coeff, torch.zeros_like(coeff))
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    tf = torch.empty(B, dtype=torch.float32, device="cuda")
+    g = group.grad(spins, coeff, logq=tf)
+    group.check()
+    t2 = time.perf_counter()
+    free1 = torch.cuda.mem_get_info()[0]
+    mv, vv = torch.zeros_like(g), torch.zeros_like(g)
+    sg.adam_step(group.weights(), g, mv, vv, 1e-3, 1)
+    group.refresh()
+    group.check()
+    gn = _np(g)
+    print(f"ea2d64 grouped step: sample + energy {t1 - t0:.2f} s, grouped grad (B={B}) "
+          f"{t2 - t1:.2f} s, device memory in use by the step {(free0 - free1) / 2**30:.1f} GiB")
+    assert np.all(np.isfinite(gn))
+    for i in range(1, nb - 1):
+        assert not gn[i * P1:(i + 1) * P1].any(), f"model {i} has no weight but got a gradient"
+    assert np.abs(_np(tf) - _np(logq)).max() <= BF16_LOGQ_TOL * m.N
+    for i in (0, nb - 1):
+        one = sg.Model(m, w[i * P1:(i + 1) * P1], sg.SG_BF16)
+        one.set_max_chunk(96)
+        sl = slice(i * per, (i + 1) * per)
+        gi = _np(one.grad(spins[sl].contiguous(), coeff[sl].contiguous()))
+        one.check()
+        assert np.abs(gn[i * P1:(i + 1) * P1] - gi).max() <= 1e-4 * np.abs(gi).max()
+        del one
 
 
 def test_full_size_ea2d64_grouped_bf16_sampled_rows():
@@ -290,7 +394,7 @@ def test_full_size_ea2d64_grouped_bf16_sampled_rows():
     assert np.all(np.isin(s, (-1, 1)))
     assert unpack_flags(fl, m.N).mean() < 0.05
     for i, rows in ((0, [0, 1023]), (3, [3 * 1024 + 17]), (7, [B - 1])):
-        so, lqo, _, _ = oracle_replay(m, w[i * P1:(i + 1) * P1], 2026, s, fl, rows=rows)
+        so, lqo, _, _ = oracle_replay(m, w[i * P1:(i + 1) * P1], 2026, s, fl, BF16_BAND, rows=rows)
         assert np.array_equal(so, s[rows]), f"model {i}: spins differ"
         assert np.abs(lqo - lq[rows]).max() <= BF16_LOGQ_TOL * m.N
     inst = wl.instance()
@@ -307,7 +411,7 @@ def test_full_size_ea2d16_bf16_sampled_rows():
     model.check()
     s, lq, fl = _np(spins), _np(logq), _np(flags)
     rows = np.array([0, 107, 108, 5000, 9999, wl.B - 1])
-    so, lqo, _, _ = oracle_replay(m, w, 77, s, fl, rows=rows)
+    so, lqo, _, _ = oracle_replay(m, w, 77, s, fl, BF16_BAND, rows=rows)
     assert np.array_equal(so, s[rows])
     assert np.abs(lqo - lq[rows]).max() <= BF16_LOGQ_TOL * m.N
     assert unpack_flags(fl, m.N).mean() < 0.05
@@ -482,9 +586,76 @@ def test_bf16_teacher_forced_logq_and_grad(m):
     model.check()
     go, _ = oracle.grad(ocfg(m), w, s, c.astype(np.float64))
     rel = np.linalg.norm(g - go) / np.linalg.norm(go)
-    print(f"N={m.N} d={m.d}: max|dlogq|/N {np.abs(lq - lqo).max() / m.N:.2e}, grad rel err {rel:.2e}")
+    worst = max(grad_block_errors(m, g, go), key=lambda x: x[1] / max(x[2], 0.1 * x[3]))
+    print(f"N={m.N} d={m.d}: max|dlogq|/N {np.abs(lq - lqo).max() / m.N:.2e}, grad rel err "
+          f"{rel:.2e}, worst block {worst[0]} {worst[1] / max(worst[2], 0.1 * worst[3]):.2e}")
     assert rel < 2e-2
+    assert_grad_blocks(m, g, go, BF16_GRAD_BLOCK_TOL)
     assert np.abs(_np(logq) - lqo).max() <= BF16_LOGQ_TOL * m.N
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_grad_chunking_matches_one_chunk_and_oracle(precision):
+    """sg_grad over several chunks of samples (a chunk cap of 64 samples on
+    B = 300: five chunks, the last ragged) equals one chunk up to FP32
+    summation order, and the oracle within the precision's bound."""
+    m = inputs.ModelShape(40, 2, 64, 4, mask_kind=1, W=8, S=9)
+    prec = sg.SG_BF16 if precision == "bf16" else sg.SG_FP32
+    w = inputs.make_weights(m, 5)
+    B = 300
+    s = inputs.random_spins(B, m.N, 19)
+    c = np.random.default_rng(4).normal(0, 1, B).astype(np.float32)
+    model = sg.Model(m, w, prec)
+    ts, tc = torch.tensor(s, device="cuda"), torch.tensor(c, device="cuda")
+    lq1 = torch.empty(B, dtype=torch.float32, device="cuda")
+    g1 = _np(model.grad(ts, tc, logq=lq1))
+    model.set_max_chunk(64)
+    lq5 = torch.empty(B, dtype=torch.float32, device="cuda")
+    g5 = _np(model.grad(ts, tc, logq=lq5))
+    lp5 = _np(model.logprob(ts))
+    model.set_max_chunk(0)
+    model.check()
+    assert np.array_equal(_np(lq1), _np(lq5))  # log q is per sample: chunking cannot change it
+    assert np.array_equal(lp5, _np(lq1))
+    assert np.abs(g5 - g1).max() <= 1e-5 * np.abs(g1).max()
+    go, lqo = oracle.grad(ocfg(m), w, s, c.astype(np.float64))
+    rel = np.linalg.norm(g5 - go) / np.linalg.norm(go)
+    assert rel < (2e-2 if prec == sg.SG_BF16 else 1e-4), rel
+    if prec == sg.SG_BF16:
+        assert_grad_blocks(m, g5, go, BF16_GRAD_BLOCK_TOL)
+
+
+@pytest.mark.parametrize("precision,cap", [("bf16", 0), ("bf16", 4096), ("fp32", 0)])
+def test_full_size_ea2d16_grad_on_isolated_samples(precision, cap):
+    """The bench's gradient call at full size (2D EA L=16, B = 16384, one
+    chunk of 16384 for BF16 or several under a chunk cap): coefficients zero
+    except on four samples spread over the batch, so the oracle's gradient of
+    those four is the whole expected gradient.  Log q of those samples against
+    the oracle too."""
+    wl = inputs.workloads()["ea2d16"]
+    m = wl.model
+    w = wl.weights()
+    prec = sg.SG_BF16 if precision == "bf16" else sg.SG_FP32
+    model = sg.Model(m, w, prec)
+    if cap:
+        model.set_max_chunk(cap)
+    B = wl.B
+    spins, _ = model.sample(B, seed=404)
+    rows = np.array([0, 5000, 12345, B - 1])
+    c = np.zeros(B, np.float32)
+    c[rows] = [0.7, -1.1, 0.4, 0.9]
+    lq = torch.empty(B, dtype=torch.float32, device="cuda")
+    g = _np(model.grad(spins, torch.tensor(c, device="cuda"), logq=lq))
+    model.check()
+    s = _np(spins)
+    go, lqo = oracle.grad(ocfg(m), w, s[rows], c[rows].astype(np.float64))
+    tol = BF16_LOGQ_TOL if prec == sg.SG_BF16 else FP32_LOGQ_TOL
+    assert np.abs(_np(lq)[rows] - lqo).max() <= tol * m.N
+    rel = np.linalg.norm(g - go) / np.linalg.norm(go)
+    print(f"{precision} cap {cap}: full-size grad rel err {rel:.2e}")
+    assert rel < (2e-2 if prec == sg.SG_BF16 else 1e-4), rel
+    if prec == sg.SG_BF16:
+        assert_grad_blocks(m, g, go, BF16_GRAD_BLOCK_TOL)
 
 
 # --------------------------------------------------------------------------
@@ -581,7 +752,7 @@ def test_full_size_ea2d16_fp32_sampled_rows():
     torch.cuda.synchronize()
     s, lq, fl = _np(spins), _np(logq), _np(flags)
     rows = np.array([0, 1, 4095, 8191, 12345, wl.B - 1])
-    so, lqo, _, _ = oracle_replay(m, w, 31, s, fl, rows=rows)
+    so, lqo, _, _ = oracle_replay(m, w, 31, s, fl, FP32_BAND, rows=rows)
     assert np.array_equal(so, s[rows])
     assert np.abs(lqo - lq[rows]).max() <= FP32_LOGQ_TOL * m.N
     assert np.array_equal(_np(Ei).astype(np.float64), oracle.energy(inst, s))
