@@ -488,10 +488,17 @@ def run_ours(args):
         # is quoted at (BF16 and FP32 both within 1e-3 of the exact F/N)
         line["decode_by_workload"] = decode_by_workload(sg, inputs, peak)
         line["fixed_FN_check"] = fixed_fn_check(sg, inputs, train)
+        # an independence sampler's ESS/sec is at most its proposal rate, which
+        # the decode's HBM roofline bounds; the measured ESS/sec of both chains
+        # come from a separate run that trains the proposal first
+        d3 = line["decode_by_workload"]["ea3d10"]
         line["ess_per_sec"] = {
             "workload": "3D EA L=10 +-J, beta=0.9",
-            "source": "paper_2606_22984_gb300/ess_compare.py (a separate run: it trains the "
-                      "proposal first); its summary is profiles/ess_mh_vs_metropolis.md"}
+            "neural_mh_upper_bound": d3["B"] / (d3["algorithmic_bytes"] / (peak * 1e9)),
+            "proposal_rate_measured": d3["configs_per_s"],
+            "source": "paper_2606_22984_gb300/ess_compare.py (trains the proposal, then "
+                      "times neural MH and single-spin-flip Metropolis on the same instance); "
+                      "summary in profiles/ess_mh_vs_metropolis.md"}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, beta, args.cpu_seconds)
     if rank == 0:
