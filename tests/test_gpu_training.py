@@ -12,6 +12,12 @@ from helpers import ocfg
 
 pytestmark = pytest.mark.gpu
 
+# Muon on a BF16 model: the Newton-Schulz iterate and its products' operands
+# are BF16 (unit roundoff 2^-8); five steps of rounding X, A and Bm give update
+# errors of 1.0e-2 to 1.9e-2 relative on GB300 (d = 64, 96, 128); the bound
+# leaves a factor of about 2.5
+MUON_BF16_TOL = 5e-2
+
 
 def _train(model, inst, B, beta, steps, lr, seed0=100):
     w = model.weights()
@@ -172,3 +178,52 @@ def test_sk20_training_with_muon_reaches_exact_free_energy():
           f"  exact (F_q - F)/N {(ex['Fq'] - ex['F']) / m.N:.2e}")
     assert abs(out[1] - ex["F"]) / m.N <= 1e-3
     assert 0 <= (ex["Fq"] - ex["F"]) / m.N < 2e-3  # the variational gap (KL / beta N)
+
+
+@pytest.mark.parametrize("shape", [inputs.ModelShape(20, 1, 64, 4), inputs.ModelShape(8, 1, 128, 8),
+                                   inputs.ModelShape(12, 1, 96, 6)])
+def test_muon_step_tensor_cores_matches_oracle(shape):
+    """BF16 models run Muon's Newton-Schulz iteration on tcgen05 (one launch
+    for every matrix; the iterate X in BF16, FP32 accumulators).  Three steps
+    against the FP64 oracle: the matrices' update within the BF16 bound, the
+    momentum and the AdamW parameters as for the FP32 path."""
+    import time
+    m = shape
+    w0 = inputs.make_weights(m, 8)
+    model = sg.Model(m, w0, sg.SG_BF16)
+    n = model.n_params
+    dev = torch.device("cuda")
+    mom, am, av = (torch.zeros(n, device=dev) for _ in range(3))
+    w, mo, amo, avo = (w0.astype(np.float64).copy(), np.zeros(n), np.zeros(n), np.zeros(n))
+    rng = np.random.default_rng(9)
+    for step in range(1, 4):
+        g = rng.normal(0, 1e-2, n).astype(np.float32)
+        model.muon_step(torch.tensor(g, device=dev), mom, am, av, 2e-3, step, mu=0.95,
+                        weight_decay=0.1)
+        oracle.muon_step(ocfg(m), w, g, mo, amo, avo, 2e-3, 0.95, 0.1, 5, step)
+    model.check()
+    wg = model.weights().cpu().numpy().astype(np.float64)
+    dg, do = wg - w0, w - w0
+    mat = np.zeros(n, bool)
+    for name, (off, shp) in inputs.offsets(m).items():
+        if name.split(".")[-1] in ("Wqkv", "W1", "W2"):
+            mat[off:off + int(np.prod(shp))] = True
+    rel_mat = np.linalg.norm(dg[mat] - do[mat]) / np.linalg.norm(do[mat])
+    rel_rest = np.linalg.norm(dg[~mat] - do[~mat]) / np.linalg.norm(do[~mat])
+    # time one step against the FP32 path on the same shape
+    m32 = sg.Model(m, w0, sg.SG_FP32)
+    gt = torch.tensor(rng.normal(0, 1e-2, n).astype(np.float32), device=dev)
+    ts = {}
+    for name, mdl in (("bf16 tensor cores", model), ("fp32", m32)):
+        mdl.muon_step(gt, mom.clone(), am.clone(), av.clone(), 2e-3, 4)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(5):
+            mdl.muon_step(gt, mom.clone(), am.clone(), av.clone(), 2e-3, 4)
+        torch.cuda.synchronize()
+        ts[name] = (time.perf_counter() - t0) / 5 * 1e3
+    print(f"d={m.d}: Muon update rel err matrices {rel_mat:.2e}, other parameters {rel_rest:.2e}; "
+          f"step time " + ", ".join(f"{k} {v:.2f} ms" for k, v in ts.items()))
+    assert rel_mat < MUON_BF16_TOL
+    assert rel_rest < 1e-5
+    assert np.allclose(mom.cpu().numpy(), mo, rtol=1e-5, atol=1e-7)
