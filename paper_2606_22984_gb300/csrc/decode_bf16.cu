@@ -908,6 +908,65 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d64_kernel(const __grid_co
 // through a 3-stage ring of bulk copies.  TMEM: QKV at columns [0, 384), the
 // FFN1 slice at [0, 128), the FFN2 accumulator at [384, 512).
 // ---------------------------------------------------------------------------
+// Patched head (K = 2^P <= 32 classes) of the d = 128 and d = 256 decodes, for
+// a row whose four quarter threads hold its final-LayerNorm output y at dims
+// [Q qr, Q qr + Q) (w: this row's model's weight blob): each quarter's partial
+// logits over its dims go through zp ([4][128][K] floats of a tile idle at
+// the head), the row's quarter-0 thread adds them, draws the class whose
+// cumulative probability (classes in index order) first exceeds u, adds its
+// log-probability to lq and returns the class as the next token.  A draw
+// within the flag band of any cumulative boundary is flagged.  Only `writer`
+// threads store spins, flags and the error word.
+template <int Q>
+__device__ __forceinline__ void patched_head(const DecodeArgs &a, const float *w, const float (&y)[Q],
+                                             int D, int r, int qr, float *zp, int64_t b, int t,
+                                             bool writer, int nfw, float &lq, int &tok)
+{
+    for (int k = 0; k < a.K; ++k) {
+        const float *wh = w + a.o.Wh + (size_t)k * D + Q * qr;
+        float zk = 0.f;
+#pragma unroll
+        for (int j = 0; j < Q; ++j) zk += y[j] * __ldg(wh + j);
+        zp[((size_t)qr * kRows + r) * a.K + k] = zk;
+    }
+    __syncthreads();
+    if (qr == 0) {
+        auto logit = [&](int k) {
+            float zk = __ldg(w + a.o.bh + k);
+#pragma unroll
+            for (int q4 = 0; q4 < 4; ++q4) zk += zp[((size_t)q4 * kRows + r) * a.K + k];
+            return zk;
+        };
+        float mx = -INFINITY;
+        for (int k = 0; k < a.K; ++k) mx = fmaxf(mx, logit(k));
+        float se = 0.f;
+        for (int k = 0; k < a.K; ++k) se += expf(logit(k) - mx);
+        const float lse = mx + logf(se);
+        const float u = philox_uniform(a.seed, (uint32_t)b, (uint32_t)t, a.sid, 0u);
+        float cdf = 0.f, near = INFINITY;
+        int cls = a.K - 1;
+        bool found = false;
+        for (int k = 0; k < a.K - 1; ++k) {
+            cdf += expf(logit(k) - lse);
+            near = fminf(near, fabsf(u - cdf));
+            if (!found && u < cdf) {
+                cls = k;
+                found = true;
+            }
+        }
+        const float zc = logit(cls);
+        lq += zc - lse;
+        tok = cls;
+        if (writer) {
+            for (int j = 0; j < a.P; ++j)
+                a.spins[(size_t)b * a.Nspins + patch_site(t, j, a.P, a.latD, a.latL)] =
+                    (int8_t)(((cls >> j) & 1) ? 1 : -1);
+            if (a.flags && near < a.band) a.flags[(size_t)b * nfw + (t >> 5)] |= 1u << (t & 31);
+            if (!isfinite(zc - lse)) atomicOr(a.err, 4);
+        }
+    }
+}
+
 constexpr int kChunkBytes = 128 * 128 * 2;
 constexpr int kChunksPerLayer = 11;
 constexpr int kStages = 3;
@@ -1256,6 +1315,19 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d128_kernel(const __grid_c
             const float mean = t1 * (1.0f / D);
             const float var = fmaxf(t2 * (1.0f / D) - mean * mean, 0.f);
             const float rs = 1.0f / sqrtf(var + 1e-5f);
+            if (a.P > 1) {
+                // the A and A2 tiles (64 KB, contiguous) are idle from the last
+                // FFN2 of a step to the next step's first LayerNorm
+                float y[Q32];
+#pragma unroll
+                for (int j = 0; j < Q32; ++j) {
+                    const int d = Q32 * qr + j;
+                    y[j] = (h[j] - mean) * rs * __ldg(a.w + a.o.lnfg + d) + __ldg(a.w + a.o.lnfb + d);
+                }
+                patched_head<Q32>(a, a.w, y, D, r, qr, reinterpret_cast<float *>(Abuf), b, t, active,
+                                  nfw, lq, tok);
+                continue;
+            }
             float z0 = 0.f, z1 = 0.f;
 #pragma unroll
             for (int j = 0; j < Q32; ++j) {
@@ -1805,6 +1877,23 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d256_kernel(const __grid_c
             const float mean = t1 * (1.0f / D);
             const float var = fmaxf(t2 * (1.0f / D) - mean * mean, 0.f);
             const float rs = 1.0f / sqrtf(var + 1e-5f);
+            if (a.P > 1) {
+                // the A and A2 tiles are idle from the last FFN2 of a step to
+                // the next step's first LayerNorm
+                float y[64];
+#pragma unroll
+                for (int j = 0; j < 64; ++j) {
+                    const int d = 64 * qr + j;
+                    const float x = j < 32 ? v0[j] : v1[j - 32];
+                    y[j] = (x - mean) * rs * __ldg(w + a.o.lnfg + d) + __ldg(w + a.o.lnfb + d);
+                }
+                int tk = 0;
+                patched_head<64>(a, w, y, D, r, qr, reinterpret_cast<float *>(Abuf), b, t,
+                                 active && !is_mirror, nfw, lq, tk);
+                if (qr == 0) stok[r] = tk;
+                __syncthreads();  // stok is read by every thread of the row
+                continue;
+            }
             float z0 = 0.f, z1 = 0.f;
 #pragma unroll
             for (int j = 0; j < 64; ++j) {
@@ -1950,9 +2039,9 @@ sg_status launch_decode_bf16(sg_model *m, int64_t B, uint64_t seed, uint32_t sid
                                      "(128, 8, 512) and (256, 8, 1024)");
     if (m->n_models > 1 && !d256)
         return fail(SG_EUNSUPPORTED, "grouped models are served by the d = 256 decode");
-    if (P > 1 && !(d64 && c.d_token <= 16 && (1 << P) <= 32))
-        return fail(SG_EUNSUPPORTED, "patched BF16 decode is built for d = 64 with at most 32 "
-                                     "classes (2D cells); use SG_FP32");
+    if (P > 1 && !((1 << P) <= 32 && ((d64 && c.d_token <= 16) || d128 || d256)))
+        return fail(SG_EUNSUPPORTED, "patched BF16 decode is built for at most 32 classes "
+                                     "(2D cells); use SG_FP32");
     const int64_t rows_per_model = B / m->n_models;
     int rows = 0, cpm = 0;
     int64_t tiles = 0;

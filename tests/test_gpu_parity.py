@@ -225,6 +225,11 @@ PATCHED_CASES = {
                       sg.SG_FP32),
     "lat2d_p4_bf16": (inputs.ModelShape(256, 2, 64, 4, d_token=16, mask_kind=1, W=8, S=9,
                                         patch=4, lat_D=2, lat_L=16), 300, sg.SG_BF16),
+    "lat2d_p4_bf16_d128": (inputs.ModelShape(256, 2, 128, 8, d_token=16, mask_kind=1, W=8, S=9,
+                                             patch=4, lat_D=2, lat_L=16), 300, sg.SG_BF16),
+    "lat2d_p4_bf16_d256": (inputs.ModelShape(144, 2, 256, 8, d_token=16, mask_kind=1, W=6, S=7,
+                                             patch=4, lat_D=2, lat_L=12), 200, sg.SG_BF16),
+    "chain_p2_bf16_d128": (inputs.ModelShape(60, 1, 128, 8, d_token=8, patch=2), 130, sg.SG_BF16),
 }
 
 
@@ -255,10 +260,31 @@ def test_patched_sampling_and_scoring_match_oracle(name):
 
 
 def test_patched_bf16_rejected_where_not_built():
-    m = inputs.ModelShape(64, 1, 128, 8, d_token=16, patch=4, lat_D=2, lat_L=8)
+    """3D cells of (2, 2, 2) spins (256 classes) are beyond the BF16 decodes'
+    K <= 32 head; the FP32 decode serves them."""
+    m = inputs.ModelShape(64, 1, 128, 8, d_token=16, patch=8, lat_D=3, lat_L=4)
     model = sg.Model(m, inputs.make_weights(m, 1), sg.SG_BF16)
     with pytest.raises(sg.SgError):
         model.sample(8, seed=1)
+
+
+def test_patched_bf16_d256_grouped_models_match_oracle():
+    """Two patched d = 256 models in one grouped launch: each model's rows
+    against the oracle with that model's weights."""
+    m = inputs.ModelShape(144, 1, 256, 8, d_token=16, mask_kind=1, W=6, S=7, patch=4, lat_D=2,
+                          lat_L=12)
+    n, per = 2, 100
+    w = inputs.make_group_weights(m, 23, n)
+    P1 = w.size // n
+    model = sg.Model(m, w, sg.SG_BF16, n_models=n)
+    spins, logq, flags = model.sample(n * per, seed=41, with_flags=True)
+    model.check()
+    s, lq, fl = _np(spins), _np(logq), _np(flags)
+    for i in range(n):
+        rows = np.arange(i * per, (i + 1) * per)
+        so, lqo, _, _ = oracle_replay(m, w[i * P1:(i + 1) * P1], 41, s, fl, BF16_BAND, rows=rows)
+        assert np.array_equal(so, s[rows]), f"model {i}: spins differ outside flagged draws"
+        assert np.abs(lqo - lq[rows]).max() <= BF16_LOGQ_TOL * m.N
 
 
 def test_grouped_models_rejected_outside_d256():
