@@ -22,6 +22,8 @@
 // rows with its accumulator in TMEM; here the fragments stay in registers.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include <type_traits>
 
 #include "gemm_tc.cuh"
@@ -62,6 +64,12 @@ __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a
         "{%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
         : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Bulk prefetch of [p, p + bytes) into L2 (one thread; bytes a multiple of 16).
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
 // The softmax runs in base 2 (ex2_approx) with log2(e) folded into its scale
@@ -222,12 +230,18 @@ template <int DH>
 __global__ void __launch_bounds__(kThreads)
 attn_fwd_mma_kernel(const __nv_bfloat16 *__restrict__ QKVh, const float *__restrict__ Hin,
                     __nv_bfloat16 *__restrict__ O, float *__restrict__ Hmid, float *__restrict__ LSE,
-                    int N, int Npad, int D, int NH, int mask, int W, int S)
+                    int N, int Npad, int D, int NH, int mask, int W, int S, int Bc, int ahead)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     const int b = blockIdx.x / NH, hh = blockIdx.x % NH;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, q = lane & 3;
     const size_t part_bytes = (size_t)Npad * DH * 2;
+    // the rows of the sample whose CTAs start about one wave later, into L2
+    if (hh == 0 && threadIdx.x == 0 && b + ahead < Bc) {
+        const size_t nb = (size_t)b + ahead;
+        prefetch_l2(QKVh + nb * N * 3 * D, (uint32_t)((size_t)N * 3 * D * 2));
+        prefetch_l2(Hin + nb * N * D, (uint32_t)((size_t)N * D * 4));
+    }
     stage_qkv<DH>(smem, QKVh, b, hh, N, Npad, D, 3);
     tc::cp_async_wait<0>();
     __syncthreads();
@@ -387,12 +401,20 @@ __global__ void __launch_bounds__(kThreads)
 attn_bwd_mma_kernel(const __nv_bfloat16 *__restrict__ QKVh, const __nv_bfloat16 *__restrict__ O,
                     const float *__restrict__ dO, const float *__restrict__ LSE,
                     unsigned char *__restrict__ dQKVt, float *__restrict__ bsum, int N, int Npad,
-                    int D, int NH, int mask, int W, int S)
+                    int D, int NH, int mask, int W, int S, int Bc, int ahead)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ float csum[3 * DH];
     __shared__ int next_task;
     const int b = blockIdx.x / NH, hh = blockIdx.x % NH;
+    // the rows of the sample whose CTAs start about one wave later, into L2
+    if (hh == 0 && threadIdx.x == 0 && b + ahead < Bc) {
+        const size_t nb = (size_t)b + ahead;
+        prefetch_l2(QKVh + nb * N * 3 * D, (uint32_t)((size_t)N * 3 * D * 2));
+        prefetch_l2(O + nb * N * D, (uint32_t)((size_t)N * D * 2));
+        prefetch_l2(dO + nb * N * D, (uint32_t)((size_t)N * D * 4));
+        if ((N * NH) % 4 == 0) prefetch_l2(LSE + nb * N * NH, (uint32_t)((size_t)N * NH * 4));
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, q = lane & 3;
     const size_t part_bytes = (size_t)Npad * DH * 2;
     unsigned char *sG = smem + 3 * part_bytes;  // dO rows (BF16)
@@ -559,6 +581,18 @@ attn_bwd_mma_kernel(const __nv_bfloat16 *__restrict__ QKVh, const __nv_bfloat16 
     }
 }
 
+// Samples whose CTAs are resident at once (one CTA per sample and head): the
+// distance at which a CTA prefetches a later sample's rows.
+template <class K>
+int samples_per_wave(K kern, size_t smem, int NH)
+{
+    int dev = 0, sms = 148, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+    return std::max(1, sms * std::max(per_sm, 1) / NH);
+}
+
 size_t mma_smem_bytes(int DH, int N, bool bwd)
 {
     const size_t Npad = (size_t)(N + 15) & ~(size_t)15;
@@ -582,7 +616,8 @@ sg_status launch_attn_fwd_mma(const sg_config &c, const __nv_bfloat16 *QKVh, con
     auto go = [&](auto kern) -> sg_status {
         SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kern<<<(unsigned)(Bc * c.n_heads), kThreads, smem, ::sg::counted(st)>>>(
-            QKVh, Hin, O, Hmid, LSE, c.N, Npad, c.d, c.n_heads, c.mask_kind, c.W, c.S);
+            QKVh, Hin, O, Hmid, LSE, c.N, Npad, c.d, c.n_heads, c.mask_kind, c.W, c.S, Bc,
+            samples_per_wave(kern, smem, c.n_heads));
         return check_launch("attn_fwd_mma_kernel");
     };
     return dh == 16 ? go(attn_fwd_mma_kernel<16>) : go(attn_fwd_mma_kernel<32>);
@@ -597,7 +632,8 @@ sg_status launch_attn_bwd_mma(const sg_config &c, const __nv_bfloat16 *QKVh, con
     auto go = [&](auto kern) -> sg_status {
         SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kern<<<(unsigned)(Bc * c.n_heads), kThreads, smem, ::sg::counted(st)>>>(
-            QKVh, O, dO, LSE, dQKVt, bsum, c.N, Npad, c.d, c.n_heads, c.mask_kind, c.W, c.S);
+            QKVh, O, dO, LSE, dQKVt, bsum, c.N, Npad, c.d, c.n_heads, c.mask_kind, c.W, c.S, Bc,
+            samples_per_wave(kern, smem, c.n_heads));
         return check_launch("attn_bwd_mma_kernel");
     };
     return dh == 16 ? go(attn_bwd_mma_kernel<16>) : go(attn_bwd_mma_kernel<32>);

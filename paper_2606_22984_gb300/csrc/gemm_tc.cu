@@ -71,6 +71,36 @@ __device__ __forceinline__ float warp_colsum32(float (&y)[32])
 
 constexpr int kColsumMax = 1024;
 
+// Bulk prefetch of [p, p + bytes) into L2 (one thread; bytes a multiple of 16).
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// The epilogue inputs of row block rb that are read from global memory (each
+// one contiguous range), prefetched into L2 while an earlier block is drained.
+template <int EPI>
+__device__ __forceinline__ void prefetch_epilogue(const RowGemm &g, int64_t rb)
+{
+    if (rb >= g.RB) return;
+    const int64_t r0 = rb * 128, rows = min((int64_t)128, g.R - r0);
+    if (rows <= 0) return;
+    if (EPI == TE_LN_BWD) {
+        prefetch_l2(g.ln_x + r0 * g.N, (uint32_t)(rows * g.N * 4));
+        if (g.ln_dres) prefetch_l2(g.ln_dres + r0 * g.N, (uint32_t)(rows * g.N * 4));
+        // whole 16-byte pieces only: the statistics end with the rows
+        const uint32_t sb = (uint32_t)((rows * 4) & ~int64_t(15));
+        if (sb) {
+            prefetch_l2(g.ln_mu + r0, sb);
+            prefetch_l2(g.ln_rs + r0, sb);
+        }
+    } else if (EPI == TE_RESID_F32) {
+        if (g.ld_resid == g.N) prefetch_l2(g.resid + r0 * g.N, (uint32_t)(rows * g.N * 4));
+    } else if (EPI == TE_GELU_BWD_T) {
+        prefetch_l2(g.aux_t + (size_t)rb * wl_block_bytes(g.N), (uint32_t)wl_block_bytes(g.N));
+    }
+}
+
 template <int EPI>
 __device__ __forceinline__ void row_epilogue(const RowGemm &g, const float (&v)[32], int64_t r,
                                              int col0, bool valid, float *s_col)
@@ -172,19 +202,32 @@ __device__ __forceinline__ void staged_store(const RowGemm &g, const float *sOut
         }
     } else {
         const int per_row = g.N / 4;
-        for (int e = et; e < 128 * per_row; e += 32 * kEpiWarps) {
-            const int row = e / per_row, c4 = e % per_row;
-            const int64_t r = rb * 128 + row;
-            if (r >= g.R) continue;
-            float4 v = *reinterpret_cast<const float4 *>(sOut + row * P + 4 * c4);
-            if (EPI == TE_RESID_F32) {
-                const float4 h = *reinterpret_cast<const float4 *>(g.resid + r * g.ld_resid + 4 * c4);
-                v.x += h.x;
-                v.y += h.y;
-                v.z += h.z;
-                v.w += h.w;
+        constexpr int U = EPI == TE_RESID_F32 ? 4 : 1;  // residual loads in flight per thread
+        const int step = 32 * kEpiWarps;
+        for (int e0 = et; e0 < 128 * per_row; e0 += U * step) {
+            float4 h[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * step;
+                const int row = e / per_row, c4 = e % per_row;
+                const int64_t r = rb * 128 + row;
+                h[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (EPI == TE_RESID_F32 && e < 128 * per_row && r < g.R)
+                    h[u] = *reinterpret_cast<const float4 *>(g.resid + r * g.ld_resid + 4 * c4);
             }
-            *reinterpret_cast<float4 *>(g.out_f32 + r * g.ld_out + 4 * c4) = v;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * step;
+                const int row = e / per_row, c4 = e % per_row;
+                const int64_t r = rb * 128 + row;
+                if (e >= 128 * per_row || r >= g.R) continue;
+                float4 v = *reinterpret_cast<const float4 *>(sOut + row * P + 4 * c4);
+                v.x += h[u].x;
+                v.y += h[u].y;
+                v.z += h[u].z;
+                v.w += h[u].w;
+                *reinterpret_cast<float4 *>(g.out_f32 + r * g.ld_out + 4 * c4) = v;
+            }
         }
     }
 }
@@ -381,6 +424,8 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1) row_gemm_kernel(const 
             }
             if (!ok && !staged) break;
             tc::tc_fence_after();
+            // the next row block's epilogue inputs into L2 while this one drains
+            if (warp == 2 && lane == 0) prefetch_epilogue<EPI>(g, rb + gridDim.x);
             const int64_t r = rb * 128 + row;
             const bool valid = r < g.R;
             for (int c = part; ok && c < g.N / 32; c += kEpiPerQuad) {
