@@ -1489,34 +1489,51 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d256_kernel(const __grid_c
     tc::tc_fence_after();
     const uint32_t tmem = tslot;
 
-    // chunk stream (thread 0): chunk c sits in stage c % 2; chunk c >= 2 is
-    // loaded once the MMAs of chunk c - 2 have completed (commit on empty[]).
+    // Chunk stream.  Chunk c (the global count over steps and layers) sits in
+    // stage c % kStages256; its full[] and empty[] phases have parity
+    // (c / kStages256) & 1.  Two threads share the stream inside a product:
+    // thread 0 issues the MMAs of each chunk as soon as it has landed and
+    // commits them on empty[] without waiting; thread 32 (otherwise idle
+    // there) refills a stage once the MMAs of its previous chunk completed.
     // Loads stop short of load_limit: after a layer's q product the ring stays
-    // empty so that the attention can stage keys in it, and its two loads go
-    // out once the key loop is done.
-    int64_t next_load = 0, next_use = 0, load_limit = INT64_MAX;
-    uint32_t fphase[kStages256] = {0, 0}, ephase[kStages256] = {0, 0}, mphase = 0;
-    auto load_chunk = [&]() {
-        const int s = (int)(next_load % kStages256);
-        const int64_t lc = next_load % ((int64_t)a.L * kChunks256);
-        tc::mbar_arrive_expect_tx(&full[s], kChunk256);
-        tc::bulk_g2s(ring + (size_t)s * kChunk256, bf + (size_t)lc * kChunk256, kChunk256, &full[s]);
-        ++next_load;
+    // empty so that the attention can stage keys in it, and its loads go out
+    // once the key loop is done.
+    constexpr int kProducer = 32;
+    int64_t use_ctr = 0;                       // chunks consumed by the products so far (every thread)
+    int64_t next_load = 0, load_limit = INT64_MAX;  // thread kProducer
+    uint32_t mphase = 0;
+    auto parity = [](int64_t c) { return (uint32_t)((c / kStages256) & 1); };
+    // thread kProducer: load chunks while they are below `upto`; false when a
+    // bounded wait gave up (the error word is set)
+    auto produce = [&](int64_t upto) {
+        while (next_load < total_chunks && next_load < load_limit && next_load < upto) {
+            const int s = (int)(next_load % kStages256);
+            if (next_load >= kStages256 && !tc::mbar_wait(&empty[s], parity(next_load - kStages256))) {
+                atomicExch(a.err, 4);
+                s_err = 1;
+                return;
+            }
+            const int64_t lc = next_load % ((int64_t)a.L * kChunks256);
+            tc::mbar_arrive_expect_tx(&full[s], kChunk256);
+            tc::bulk_g2s(ring + (size_t)s * kChunk256, bf + (size_t)lc * kChunk256, kChunk256, &full[s]);
+            ++next_load;
+        }
     };
-    if (tid == 0)
-        while (next_load < total_chunks && next_load < kStages256) load_chunk();
+    if (tid == kProducer) produce(kStages256);
 
     // MMAs of `nchunks` consecutive K chunks (64 wide) of A x chunk^T into TMEM
     // column col; accumulate onto existing contents when `onto` is set.
     auto run = [&](const unsigned char *A, int nchunks, uint32_t col, bool onto) {
+        const int64_t first = use_ctr;
+        use_ctr += nchunks;
         if (tid == 0) {
             bool ok = s_err == 0;
             const uint32_t idesc = tc::idesc_bf16(kRows, 256);
             for (int i = 0; i < nchunks && ok; ++i) {
-                const int s = (int)(next_use % kStages256);
-                ok = tc::mbar_wait(&full[s], fphase[s]);
+                const int64_t c = first + i;
+                const int s = (int)(c % kStages256);
+                ok = tc::mbar_wait(&full[s], parity(c));
                 if (!ok) break;
-                fphase[s] ^= 1u;
                 tc::tc_fence_after();
                 const uint32_t sa = tc::smem_u32(A) + (uint32_t)(8 * i) * 128;
                 const uint32_t sb = tc::smem_u32(ring + (size_t)s * kChunk256);
@@ -1526,18 +1543,15 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d256_kernel(const __grid_c
                                  tc::smem_desc(sb + 256 * k, 128, 8 * 128), idesc,
                                  (onto || i > 0 || k > 0) ? 1u : 0u);
                 tc::mma_commit(&empty[s]);
-                ++next_use;
-                // refill this stage with chunk next_use + 1 once its MMAs are done
-                ok = tc::mbar_wait(&empty[s], ephase[s]);
-                if (!ok) break;
-                ephase[s] ^= 1u;
-                if (next_load < total_chunks && next_load < load_limit) load_chunk();
             }
             if (!ok) {
                 atomicExch(a.err, 1);
                 s_err = 1;
             }
             tc::mma_commit(&mbar);
+        } else if (tid == kProducer) {
+            // keep the ring full through this product and into the next one
+            produce(use_ctr + kStages256);
         }
         __syncwarp();
         if (!tc::mbar_wait(&mbar, mphase)) {
@@ -1657,9 +1671,9 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d256_kernel(const __grid_c
             append(slot, 1, bq + 2 * D);
             tc::tc_fence_before();
             __syncthreads();
-            if (tid == 0) load_limit = ((int64_t)t * a.L + l) * kChunks256 + 12;
+            if (tid == kProducer) load_limit = ((int64_t)t * a.L + l) * kChunks256 + 12;
             run(Abuf, 4, ACC, false);  // q_t stays in TMEM
-            if (tid == 0) load_limit = INT64_MAX;
+            if (tid == kProducer) load_limit = INT64_MAX;
             if (s_err) break;
             // attention: heads 2 qr and 2 qr + 1, keys 0..t from the ring
             // (key t of row rr was written before the barriers of the q run)
@@ -1811,8 +1825,7 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d256_kernel(const __grid_c
             tc::tc_fence_before();
             __syncthreads();
             tc::tc_fence_after();
-            if (tid == 0)
-                while (next_load < total_chunks && next_load < next_use + kStages256) load_chunk();
+            if (tid == kProducer) produce(use_ctr + kStages256);
             layernorm_to(w + o.ln2g, w + o.ln2b);
             const float *b1 = wt + a.p.b1[l];
             for (int j = 0; j < 4 && !s_err; ++j) {
@@ -1931,16 +1944,14 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d256_kernel(const __grid_c
         }
     }
     if (qr == 0 && active && !is_mirror) a.logq[b] = lq;
-    if (tid == 0)
-        while (next_use < next_load) {
-            const int s = (int)(next_use % kStages256);
-            if (!tc::mbar_wait(&full[s], fphase[s])) {
+    // no bulk copy may be in flight when the CTA exits: wait for the chunks
+    // loaded ahead of the products that did not run
+    if (tid == kProducer)
+        for (int64_t c = use_ctr; c < next_load; ++c)
+            if (!tc::mbar_wait(&full[c % kStages256], parity(c))) {
                 atomicExch(a.err, 3);
                 break;
             }
-            fphase[s] ^= 1u;
-            ++next_use;
-        }
     tc::tc_fence_before();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, 512);
