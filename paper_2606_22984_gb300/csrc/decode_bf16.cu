@@ -1006,8 +1006,16 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d128_kernel(const __grid_c
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int r = 32 * (warp & 3) + lane, qr = warp >> 2;
-    const int64_t b = (int64_t)blockIdx.x * a.rows_per_cta + r;
-    const bool active = r < a.rows_per_cta && b < a.B;
+    // With at most 64 rows per CTA, rows 64..127 mirror rows 0..63 (same
+    // inputs, so every phase computes identical copies); a row and its mirror
+    // (thread tid ^ 64) split the attention's keys and merge their partial
+    // softmax states, doubling the KV loads in flight.  Only the row itself
+    // writes the KV cache, spins and log q.
+    const bool mirror_mode = a.rows_per_cta <= 64;
+    const int rr = mirror_mode ? (r & 63) : r;  // the sample row this thread serves
+    const bool is_mirror = mirror_mode && r >= 64;
+    const int64_t b = (int64_t)blockIdx.x * a.rows_per_cta + rr;
+    const bool active = rr < a.rows_per_cta && b < a.B;
     const Bf16Geom g = bgeom(a.mask, a.N, a.W, a.S);
     const size_t slot_bytes = (size_t)2 * D * kRows * 2;
     const size_t layer_bytes = slot_bytes * g.nslots;
@@ -1156,7 +1164,7 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d128_kernel(const __grid_c
 #pragma unroll
                 for (int j = 0; j < Q32; ++j) kk[j] = round_bf(kk[j] + __ldg(bq + D + Q32 * qr + j));
                 uint4 *dk = reinterpret_cast<uint4 *>(kvl + (size_t)slot_t * slot_bytes);
-                if (active)
+                if (active && !is_mirror)
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
                         uint4 x;
@@ -1171,7 +1179,7 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d128_kernel(const __grid_c
 #pragma unroll
                 for (int j = 0; j < Q32; ++j) kk[j] = round_bf(kk[j] + __ldg(bq + 2 * D + Q32 * qr + j));
                 uint4 *dv = dk + (D / 8) * kRows;
-                if (active)
+                if (active && !is_mirror)
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
                         uint4 x;
@@ -1204,11 +1212,40 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d128_kernel(const __grid_c
 #pragma unroll
                     for (int j = 0; j < DH; ++j)
                         acc[j] = round_bf(kk[DH * p + j] + __ldg(bq + 2 * D + DH * hh + j));
+                    // The row's keys reduce as two halves, the current key (held
+                    // above) with keys [0, half) and keys [half, nk) from the empty
+                    // state, merged as (first, second).  In mirror mode the row's
+                    // thread takes the first half and its mirror the second;
+                    // otherwise one thread runs both and parks the first half's
+                    // state.  The arithmetic is the same either way.
+                    const int half = (nk + 1) >> 1;
+                    const int i0 = mirror_mode && is_mirror ? half : 0;
+                    const int i1 = mirror_mode && !is_mirror ? half : nk;
+                    float sm = -INFINITY, sl = 0.f, sacc[DH];  // the parked first half
+#pragma unroll
+                    for (int j = 0; j < DH; ++j) sacc[j] = 0.f;
+                    auto park = [&]() {
+                        sm = m0;
+                        sl = l0;
+#pragma unroll
+                        for (int j = 0; j < DH; ++j) {
+                            sacc[j] = acc[j];
+                            acc[j] = 0.f;
+                        }
+                        m0 = -INFINITY;
+                        l0 = 0.f;
+                    };
+                    if (is_mirror) {  // the second half starts from the empty state
+                        m0 = -INFINITY;
+                        l0 = 0.f;
+#pragma unroll
+                        for (int j = 0; j < DH; ++j) acc[j] = 0.f;
+                    }
                     // keys < t staged through shared memory by cp.async, three keys
                     // in flight per thread: stages are the A and A2 tiles (idle
                     // during attention) and the spare tile; per thread, K pieces at
                     // +0, +8 KB and V pieces at +16 KB, +24 KB of a stage.
-                    const uint4 *kb = reinterpret_cast<const uint4 *>(kvl) + (2 * hh) * kRows + r;
+                    const uint4 *kb = reinterpret_cast<const uint4 *>(kvl) + (2 * hh) * kRows + rr;
                     auto stage = [&](int s) {
                         return (s == 0 ? Abuf : (s == 1 ? A2buf : kvspare)) + tid * 16;
                     };
@@ -1221,12 +1258,13 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d128_kernel(const __grid_c
                         tc::cp_async16(dst + 24576, pp + (D / 8) * kRows + kRows);
                         tc::cp_async_commit();
                     };
-                    for (int i = 0; i < nk && i < 3; ++i) fetch(i, i);
-                    for (int i = 0; i < nk; ++i) {
-                        if (i + 2 < nk) tc::cp_async_wait<2>();
-                        else if (i + 1 < nk) tc::cp_async_wait<1>();
+                    for (int i = i0; i < i1 && i < i0 + 3; ++i) fetch(i, i - i0);
+                    for (int i = i0; i < i1; ++i) {
+                        if (!mirror_mode && i == half) park();
+                        if (i + 2 < i1) tc::cp_async_wait<2>();
+                        else if (i + 1 < i1) tc::cp_async_wait<1>();
                         else tc::cp_async_wait<0>();
-                        const int si = i % 3;
+                        const int si = (i - i0) % 3;
                         const unsigned char *src = stage(si);
                         uint4 ck[2], cv[2];
                         ck[0] = *reinterpret_cast<const uint4 *>(src);
@@ -1255,7 +1293,51 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d128_kernel(const __grid_c
                             }
                         }
                         // the stage is refilled only after its data has been consumed
-                        if (i + 3 < nk) fetch(i + 3, si);
+                        if (i + 3 < i1) fetch(i + 3, si);
+                    }
+                    if (!mirror_mode && half >= nk) park();  // nk <= 1: the second half is empty
+                    if (mirror_mode) {
+                        // exchange partial states through this thread's own stage
+                        // slots (its copies are complete): the row's thread parks
+                        // its half and takes the mirror's as the second; the
+                        // mirror parks the row's half and keeps its own
+                        float *mine = reinterpret_cast<float *>(Abuf + tid * 16);
+#pragma unroll
+                        for (int c = 0; c < DH / 4; ++c)
+                            *reinterpret_cast<float4 *>(mine + c * 2048) =
+                                make_float4(acc[4 * c], acc[4 * c + 1], acc[4 * c + 2], acc[4 * c + 3]);
+                        *reinterpret_cast<float4 *>(A2buf + tid * 16) = make_float4(m0, l0, 0.f, 0.f);
+                        __syncthreads();
+                        const int ptid = tid ^ 64;
+                        const float *other = reinterpret_cast<const float *>(Abuf + ptid * 16);
+                        const float4 ox = *reinterpret_cast<const float4 *>(A2buf + ptid * 16);
+                        if (!is_mirror) park();
+#pragma unroll
+                        for (int c = 0; c < DH / 4; ++c) {
+                            const float4 v = *reinterpret_cast<const float4 *>(other + c * 2048);
+                            const float ov[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                            for (int kq = 0; kq < 4; ++kq) {
+                                if (is_mirror) sacc[4 * c + kq] = ov[kq];
+                                else acc[4 * c + kq] = ov[kq];
+                            }
+                        }
+                        if (is_mirror) {
+                            sm = ox.x;
+                            sl = ox.y;
+                        } else {
+                            m0 = ox.x;
+                            l0 = ox.y;
+                        }
+                        __syncthreads();  // the slots are free again for the next head
+                    }
+                    {   // merge: parked = first half, current = second half
+                        const float mm = fmaxf(sm, m0);
+                        const float ca = sm == -INFINITY ? 0.f : __expf(sm - mm);
+                        const float cb = m0 == -INFINITY ? 0.f : __expf(m0 - mm);
+#pragma unroll
+                        for (int j = 0; j < DH; ++j) acc[j] = __fmaf_rn(sacc[j], ca, __fmul_rn(acc[j], cb));
+                        l0 = __fmaf_rn(sl, ca, __fmul_rn(l0, cb));
                     }
                     const float inv = 1.0f / l0;
 #pragma unroll
@@ -1324,8 +1406,8 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d128_kernel(const __grid_c
                     const int d = Q32 * qr + j;
                     y[j] = (h[j] - mean) * rs * __ldg(a.w + a.o.lnfg + d) + __ldg(a.w + a.o.lnfb + d);
                 }
-                patched_head<Q32>(a, a.w, y, D, r, qr, reinterpret_cast<float *>(Abuf), b, t, active,
-                                  nfw, lq, tok);
+                patched_head<Q32>(a, a.w, y, D, r, qr, reinterpret_cast<float *>(Abuf), b, t,
+                                  active && !is_mirror, nfw, lq, tok);
                 continue;
             }
             float z0 = 0.f, z1 = 0.f;
@@ -1353,7 +1435,7 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d128_kernel(const __grid_c
                 const int sp = u < p ? 1 : -1;
                 lq += log_sigmoid_f((float)sp * ell);
                 tok = (sp + 1) >> 1;
-                if (active) {
+                if (active && !is_mirror) {
                     a.spins[(size_t)b * a.N + t] = (int8_t)sp;
                     if (a.flags && fabsf(p - u) < a.band)
                         a.flags[(size_t)b * nfw + (t >> 5)] |= 1u << (t & 31);
@@ -1362,7 +1444,7 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d128_kernel(const __grid_c
             }
         }
     }
-    if (qr == 0 && active) a.logq[b] = lq;
+    if (qr == 0 && active && !is_mirror) a.logq[b] = lq;
     // drain the bulk copies still in flight before the CTA exits
     if (tid == 0)
         while (next_use < next_load) {
