@@ -1936,6 +1936,11 @@ void attn_fwd_dispatch(int dh, const float *QKV, const float *Hin, float *O, flo
                        float *LSE, int Bc, const sg_config &c, cudaStream_t st, int *err,
                        const __nv_bfloat16 *QKVh = nullptr, bool keep_o = true)
 {
+    if (QKVh && attn_mma_supported(c) && attn_tmem_supported(c)) {  // many keys per query: tcgen05
+        launch_attn_fwd_tmem(c, QKVh, Hin, keep_o ? reinterpret_cast<__nv_bfloat16 *>(O) : nullptr, Hmid,
+                             LSE, Bc, err, st);
+        return;
+    }
     if (QKVh && attn_mma_supported(c)) {  // BF16 QKV: warp-level tensor-core MMAs
         launch_attn_fwd_mma(c, QKVh, Hin, keep_o ? reinterpret_cast<__nv_bfloat16 *>(O) : nullptr, Hmid,
                             LSE, Bc, st);
@@ -1957,6 +1962,11 @@ bool attn_bwd_dispatch(int dh, const float *QKV, const float *O, const float *dO
                        cudaStream_t st, int *err, unsigned char *dQKVt = nullptr,
                        float *bsum = nullptr, const __nv_bfloat16 *QKVh = nullptr)
 {
+    if (QKVh && dQKVt && attn_mma_supported(c) && attn_tmem_supported(c)) {
+        launch_attn_bwd_tmem(c, QKVh, reinterpret_cast<const __nv_bfloat16 *>(O), dO, LSE, dQKVt, bsum, Bc,
+                             err, st);
+        return true;
+    }
     if (QKVh && dQKVt && attn_mma_supported(c)) {
         launch_attn_bwd_mma(c, QKVh, reinterpret_cast<const __nv_bfloat16 *>(O), dO, LSE, dQKVt, bsum, Bc, st);
         return true;

@@ -307,6 +307,14 @@ sg_status launch_attn_fwd_mma(const sg_config &c, const __nv_bfloat16 *QKVh, con
 sg_status launch_attn_bwd_mma(const sg_config &c, const __nv_bfloat16 *QKVh, const __nv_bfloat16 *O,
                               const float *dO, const float *LSE, unsigned char *dQKVt, float *bsum,
                               int Bc, cudaStream_t st);
+// The same contract on tcgen05 (TMEM scores, thread-per-row softmax) for
+// d_h = 16 shapes whose queries see many keys; err receives a time-out code.
+bool attn_tmem_supported(const sg_config &c);
+sg_status launch_attn_fwd_tmem(const sg_config &c, const __nv_bfloat16 *QKVh, const float *Hin,
+                               __nv_bfloat16 *O, float *Hmid, float *LSE, int Bc, int *err, cudaStream_t st);
+sg_status launch_attn_bwd_tmem(const sg_config &c, const __nv_bfloat16 *QKVh, const __nv_bfloat16 *O,
+                               const float *dO, const float *LSE, unsigned char *dQKVt, float *bsum, int Bc,
+                               int *err, cudaStream_t st);
 sg_status launch_adam(float *w, const float *g, float *m, float *v, int64_t n, float lr,
                       float b1, float b2, float eps, int64_t step, cudaStream_t st);
 }  // namespace sg

@@ -582,11 +582,17 @@ BF16_TF_MODELS = [inputs.ModelShape(20, 2, 32, 4), inputs.ModelShape(40, 2, 64, 
                   inputs.ModelShape(24, 2, 128, 8),
                   inputs.ModelShape(30, 1, 96, 6, mask_kind=1, W=5, S=4),
                   inputs.ModelShape(20, 1, 256, 8, mask_kind=1, W=6, S=3),
-                  # warp-level MMA attention with many keys per query: dense
-                  # over several tiles with a ragged tail, a band crossing
-                  # tile edges with its sink, d_h = 32
+                  # dense causal at d_h = 16 from 128 positions (the tcgen05
+                  # attention): several 128-row tiles with a ragged tail, one
+                  # row past a tile, the SK widths (d 128, 8 heads)
                   inputs.ModelShape(160, 2, 64, 4),
+                  inputs.ModelShape(129, 1, 64, 4),
+                  inputs.ModelShape(300, 2, 128, 8),
+                  # warp-level MMA attention with many keys per query: a band
+                  # crossing tile edges with its sink, the 3D EA widths with a
+                  # sink that ends inside a 16-key block, d_h = 32
                   inputs.ModelShape(300, 1, 64, 4, mask_kind=1, W=70, S=9),
+                  inputs.ModelShape(333, 1, 128, 8, mask_kind=1, W=100, S=37),
                   inputs.ModelShape(140, 1, 256, 8),
                   # a sequence beyond the MMA kernels' shared memory (d_h = 32):
                   # the tcgen05 flash attention
@@ -651,14 +657,17 @@ def test_grad_chunking_matches_one_chunk_and_oracle(precision):
         assert_grad_blocks(m, g5, go, BF16_GRAD_BLOCK_TOL)
 
 
-@pytest.mark.parametrize("precision,cap", [("bf16", 0), ("bf16", 4096), ("fp32", 0)])
-def test_full_size_ea2d16_grad_on_isolated_samples(precision, cap):
-    """The bench's gradient call at full size (2D EA L=16, B = 16384, one
-    chunk of 16384 for BF16 or several under a chunk cap): coefficients zero
-    except on four samples spread over the batch, so the oracle's gradient of
-    those four is the whole expected gradient.  Log q of those samples against
+@pytest.mark.parametrize("name,precision,cap", [("ea2d16", "bf16", 0), ("ea2d16", "bf16", 4096),
+                                                ("ea2d16", "fp32", 0), ("sk1024", "bf16", 0),
+                                                ("ea3d10", "bf16", 0)])
+def test_full_size_grad_on_isolated_samples(name, precision, cap):
+    """The gradient call at full size (2D EA L=16, B = 16384, one chunk of
+    16384 for BF16 or several under a chunk cap; SK N=1024, B = 8192, on the
+    tcgen05 attention; 3D EA L=10, B = 32768): coefficients zero except on
+    a few samples spread over the batch, so the oracle's gradient of those
+    samples is the whole expected gradient.  Log q of those samples against
     the oracle too."""
-    wl = inputs.workloads()["ea2d16"]
+    wl = inputs.workloads()[name]
     m = wl.model
     w = wl.weights()
     prec = sg.SG_BF16 if precision == "bf16" else sg.SG_FP32
@@ -667,9 +676,9 @@ def test_full_size_ea2d16_grad_on_isolated_samples(precision, cap):
         model.set_max_chunk(cap)
     B = wl.B
     spins, _ = model.sample(B, seed=404)
-    rows = np.array([0, 5000, 12345, B - 1])
+    rows = np.array([0, 5000, 12345, B - 1]) if m.N <= 256 else np.array([0, B // 2 + 77, B - 1])
     c = np.zeros(B, np.float32)
-    c[rows] = [0.7, -1.1, 0.4, 0.9]
+    c[rows] = [0.7, -1.1, 0.4, 0.9][: len(rows)]
     lq = torch.empty(B, dtype=torch.float32, device="cuda")
     g = _np(model.grad(spins, torch.tensor(c, device="cuda"), logq=lq))
     model.check()
@@ -678,7 +687,7 @@ def test_full_size_ea2d16_grad_on_isolated_samples(precision, cap):
     tol = BF16_LOGQ_TOL if prec == sg.SG_BF16 else FP32_LOGQ_TOL
     assert np.abs(_np(lq)[rows] - lqo).max() <= tol * m.N
     rel = np.linalg.norm(g - go) / np.linalg.norm(go)
-    print(f"{precision} cap {cap}: full-size grad rel err {rel:.2e}")
+    print(f"{name} {precision} cap {cap}: full-size grad rel err {rel:.2e}")
     assert rel < (2e-2 if prec == sg.SG_BF16 else 1e-4), rel
     if prec == sg.SG_BF16:
         assert_grad_blocks(m, g, go, BF16_GRAD_BLOCK_TOL)
