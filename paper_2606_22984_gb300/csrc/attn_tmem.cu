@@ -168,10 +168,29 @@ __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// Bounded wait on an mbarrier phase that suspends the thread (up to about a
+// microsecond per probe) instead of spinning, so that waiting warps leave
+// their issue slots to the warps that compute; false after about 4 s.
+__device__ __forceinline__ bool mwait(uint64_t *bar, uint32_t parity)
+{
+    for (uint32_t i = 0; i < (1u << 22); ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(tc::smem_u32(bar)), "r"(parity), "r"(1000u)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
 // Bounded wait of the whole warpgroup on its MMA barrier.
 __device__ __forceinline__ bool wg_wait(uint64_t *bar, uint32_t &phase, int *err, int code)
 {
-    const bool ok = tc::mbar_wait(bar, phase);
+    const bool ok = mwait(bar, phase);
     phase ^= 1u;
     if (!ok && (threadIdx.x & 127) == 0) atomicExch(err, code);
     tc::tc_fence_after();
@@ -250,21 +269,60 @@ __device__ __forceinline__ void chunk_exp(const float (&s)[32], int t, int k0, i
 
 // ---------------------------------------------------------------------------
 // Forward: O = softmax(scale Q K^T + mask) V, Hmid = Hin + O, LSE per row.
-// TMEM per warpgroup (128 columns): S at [0, 128); P (BF16) over [0, 64);
-// the block's P V at [64, 64 + DH).
+//
+// A query tile runs as a pipeline of 32-key steps over its visible keys.
+// TMEM per warpgroup: a ring of three score buffers at columns 0, 32, 64
+// (S of a step, then its P in BF16 over the first 16 columns) and the output
+// accumulator O at column 96.  Each warpgroup (4 softmax warps, one row per
+// thread) has its own MMA warp.  Per step the softmax warps wait for the
+// step's scores, store P and arrive on the step's "P ready" barrier; the MMA
+// warp waits for it, adds P V into O and issues the scores of step i + 2 into
+// the buffer step i - 1 used (after the commit that covers step i - 1's P V),
+// so the scores of the next two steps are in flight during a softmax.  A row
+// keeps its reference maximum m until the running maximum exceeds it by more
+// than 8 (base 2): P stays below 2^8, and O (in TMEM) and the row sum are
+// rescaled only then, after the pending products have landed.  Query tiles go
+// to the two warpgroups in a fixed order (most keys first), which both the
+// softmax warps and the MMA warp follow.
 // ---------------------------------------------------------------------------
+constexpr int kRing = 3;
+constexpr uint32_t kOcol = 96;
+
+// The visible 32-key chunks of query tile qt: the sink's [0, ns) and the
+// band's [bstart, cend) (all chunks up to the diagonal under the dense mask).
+struct TileSteps {
+    int n, ns, bstart;
+    __device__ __forceinline__ TileSteps(int mask, int W, int S, int N, int qt)
+    {
+        const int tile0 = qt * kT, tile1 = min(tile0 + kT, N) - 1;
+        const int cend = min(4 * (qt + 1), (N + 31) / 32);
+        ns = 0;
+        bstart = 0;
+        if (mask != SG_MASK_DENSE) {
+            ns = (min(S, tile1 + 1) + 31) / 32;
+            bstart = max(ns, max(0, tile0 - W) / 32);
+        }
+        n = ns + max(0, cend - bstart);
+    }
+    __device__ __forceinline__ int key0(int i) const { return 32 * (i < ns ? i : bstart + (i - ns)); }
+};
+
 template <int DH>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(320, 2)
 attn_fwd_tmem_kernel(const __nv_bfloat16 *__restrict__ QKVh, const float *__restrict__ Hin,
                      __nv_bfloat16 *__restrict__ O, float *__restrict__ Hmid, float *__restrict__ LSE,
                      int N, int Npad, int D, int NH, int mask, int W, int S, int Bc, int ahead, int *err)
 {
+    static_assert(DH == 16, "the TMEM layout holds a 16-column O");
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint64_t bar[2];
+    __shared__ uint64_t sbar[2][kRing], pbar[2][kRing], obar[2], dbar[2];
     __shared__ uint32_t tslot;
-    __shared__ int next_task, wg_task[2], s_err[2];
+    __shared__ int s_err;
     const int b = blockIdx.x / NH, hh = blockIdx.x % NH;
-    const int tid = threadIdx.x, wg = tid >> 7, r = tid & 127, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // warps 0-3 and 4-7: softmax warpgroups 0 and 1; warps 8 and 9: their MMA warps
+    const bool mma_warp = warp >= 8;
+    const int wg = mma_warp ? warp - 8 : warp >> 2, r = tid & 127;
     // the rows of the sample whose CTAs start about one wave later, into L2
     if (hh == 0 && tid == 0 && b + ahead < Bc) {
         const size_t nb = (size_t)b + ahead;
@@ -272,11 +330,16 @@ attn_fwd_tmem_kernel(const __nv_bfloat16 *__restrict__ QKVh, const float *__rest
         prefetch_l2(Hin + nb * N * D, (uint32_t)((size_t)N * D * 4));
     }
     if (tid == 0) {
-        tc::mbar_init(&bar[0], 1);
-        tc::mbar_init(&bar[1], 1);
+        for (int g = 0; g < 2; ++g) {
+            for (int i = 0; i < kRing; ++i) {
+                tc::mbar_init(&sbar[g][i], 1);
+                tc::mbar_init(&pbar[g][i], 4);
+            }
+            tc::mbar_init(&obar[g], 4);
+            tc::mbar_init(&dbar[g], 1);
+        }
         tc::fence_mbar_init();
-        next_task = 2;
-        s_err[0] = s_err[1] = 0;
+        s_err = 0;
     }
     if (warp == 0) {
         tc::tmem_alloc(&tslot, 256);
@@ -290,122 +353,161 @@ attn_fwd_tmem_kernel(const __nv_bfloat16 *__restrict__ QKVh, const float *__rest
     tc::tc_fence_after();
     const uint32_t part_bytes = (uint32_t)Npad * DH * 2;
     const uint32_t sQ = tc::smem_u32(smem), sK = sQ + part_bytes, sV = sK + part_bytes;
-    const uint32_t tm = tslot + 128u * (uint32_t)wg;                 // this warpgroup's columns
-    const uint32_t tl = tm + ((uint32_t)(32 * (warp & 3)) << 16);    // this warp's lanes
-    const float sc2 = rsqrtf((float)DH) * kLog2e;  // softmax scale in base 2
+    const uint32_t tm = tslot + 128u * (uint32_t)wg;  // this warpgroup's columns
     const int nq = Npad / kT;
-    const uint32_t idesc_s = tc::idesc_bf16(kT, kT);
-    const uint32_t idesc_o = tc::idesc_bf16(kT, DH) | (1u << 16);  // V read MN-major
-    uint32_t phase = 0;
-    for (int task = wg; task < nq;) {
-        const int qt = nq - 1 - task;  // the later tiles see more keys: they go first
-        const int t = qt * kT + r, t0w = qt * kT + 32 * (warp & 3);
-        float m = -INFINITY, l = 0.f, o[DH];
+    uint64_t *sb = sbar[wg], *pb = pbar[wg];
+    // completed phases of each ring barrier before the current tile, as parity bits
+    uint32_t sbits = 0, pbits = 0;
+    auto spar = [&](int j) { return ((sbits >> (j % kRing)) + (uint32_t)(j / kRing)) & 1u; };
+    auto ppar = [&](int j) { return ((pbits >> (j % kRing)) + (uint32_t)(j / kRing)) & 1u; };
+    auto advance = [&](int n) {  // commits j = 0 .. n + 1, P phases i = 0 .. n - 1
 #pragma unroll
-        for (int j = 0; j < DH; ++j) o[j] = 0.f;
-        for (int kb = 0; kb <= qt; ++kb) {
-            if (!range_visible(mask, W, S, N, qt * kT, kT, kb * kT, kT)) continue;
-            if (r == 0) {
+        for (int bb = 0; bb < kRing; ++bb) {
+            sbits ^= (uint32_t)(((n + 4 - bb) / kRing) & 1) << bb;
+            pbits ^= (uint32_t)(((n + 2 - bb) / kRing) & 1) << bb;
+        }
+    };
+    auto fail = [&](int code) {
+        atomicExch(err, code);
+        s_err = 1;
+    };
+
+    if (mma_warp) {
+        if (lane == 0) {
+            const uint32_t idesc_s = tc::idesc_bf16(kT, 32);
+            const uint32_t idesc_o = tc::idesc_bf16(kT, DH) | (1u << 16);  // V read MN-major
+            int tile_no = 0;
+            for (int task = wg; task < nq && !s_err; task += 2, ++tile_no) {
+                const int qt = nq - 1 - task;  // the later tiles see more keys: they go first
+                const TileSteps st(mask, W, S, N, qt);
+                const uint64_t dq = desc_k<DH>(sQ, qt * kT, 0);
+                auto issue_s = [&](int j) {  // scores of step j into ring buffer j % 3
+                    tc::mma_bf16(tm + 32u * (uint32_t)(j % kRing), dq, desc_k<DH>(sK, st.key0(j), 0), idesc_s, 0u);
+                };
+                tc::tc_fence_after();
+                issue_s(0);
+                tc::mma_commit(&sb[0]);
+                if (st.n > 1) issue_s(1);
+                tc::mma_commit(&sb[1]);
+                for (int i = 0; i < st.n && !s_err; ++i) {
+                    const int bi = i % kRing;
+                    if (!mwait(&pb[bi], ppar(i))) fail(43);
+                    // step i + 2 reuses step i - 1's buffer: its P V must have landed
+                    if (i >= 1 && i + 2 < st.n && !mwait(&sb[(i + 1) % kRing], spar(i + 1))) fail(44);
+                    // the first P V of a tile overwrites O: the previous tile's O must have been read
+                    if (i == 0 && tile_no > 0 && !mwait(&obar[wg], (uint32_t)(tile_no - 1) & 1u)) fail(46);
+                    tc::tc_fence_after();
+                    if (s_err) break;
+                    const int k0 = st.key0(i);
 #pragma unroll
-                for (int ks = 0; ks < DH / 16; ++ks)
-                    tc::mma_bf16(tm, desc_k<DH>(sQ, qt * kT, ks), desc_k<DH>(sK, kb * kT, ks), idesc_s,
-                                 ks > 0 ? 1u : 0u);
-                tc::mma_commit(&bar[wg]);
+                    for (int ks = 0; ks < 2; ++ks)
+                        mma_bf16_ta(tm + kOcol, tm + 32u * (uint32_t)bi + 8u * (uint32_t)ks, desc_mn<DH>(sV, k0, ks),
+                                    idesc_o, (i > 0 || ks > 0) ? 1u : 0u);
+                    if (i + 2 < st.n) issue_s(i + 2);
+                    tc::mma_commit(&sb[(i + 2) % kRing]);  // also marks step i's P V
+                }
+                // the next tile's scores overwrite buffers that this tile's last
+                // P V products read: wait for the commit after the last one
+                if (!s_err && !mwait(&sb[(st.n + 1) % kRing], spar(st.n + 1))) fail(47);
+                advance(st.n);
             }
-            __syncwarp();
-            if (!wg_wait(&bar[wg], phase, err, 41)) s_err[wg] = 1;
-            // the row's maximum over its visible keys of the block
-            float mx = -INFINITY;
-#pragma unroll 1
-            for (int c = 0; c < 4; ++c) {
-                const int k0 = kb * kT + 32 * c;
+            // let this thread's MMAs land before TMEM is freed
+            tc::mma_commit(&dbar[wg]);
+            tc::mbar_wait(&dbar[wg], 0, 1u << 22);
+        }
+    } else {
+        const uint32_t tl = tm + ((uint32_t)(32 * (warp & 3)) << 16);  // this warp's lanes
+        const float sc2 = rsqrtf((float)DH) * kLog2e;                  // softmax scale in base 2
+        for (int task = wg; task < nq && !s_err; task += 2) {
+            const int qt = nq - 1 - task;
+            const TileSteps st(mask, W, S, N, qt);
+            const int t = qt * kT + r, t0w = qt * kT + 32 * (warp & 3);
+            float mref = -INFINITY, l = 0.f;
+            for (int i = 0; i < st.n; ++i) {
+                const int bi = i % kRing;
+                const int k0 = st.key0(i);
+                if (!mwait(&sb[bi], spar(i))) fail(41);
+                tc::tc_fence_after();
+                if (s_err) break;
                 const int kind = chunk_kind(mask, W, S, N, t0w, k0);
-                if (kind == kNone) continue;
-                float s[32];
-                tc::tmem_ld32(tl + 32 * c, s);
-                tc::tmem_wait_ld();
-                mx = fmaxf(mx, kind == kAll ? chunk_max<kAll>(s, t, k0, mask, W, S, N)
-                                            : chunk_max<kSome>(s, t, k0, mask, W, S, N));
-            }
-            const float mn = fmaxf(m, mx * sc2);
-            // rows with nothing visible yet keep scale 1 and add nothing
-            const float corr = mn == -INFINITY ? 1.f : ex2_approx(m - mn);
-            const float z = mn == -INFINITY ? 0.f : mn;
-            float2 ps2 = make_float2(0.f, 0.f);
-            // P = 2^(scale s - m) in BF16, over the scores already read
-#pragma unroll 1
-            for (int c = 0; c < 4; ++c) {
                 uint32_t pk[16];
-                const int k0 = kb * kT + 32 * c;
-                const int kind = chunk_kind(mask, W, S, N, t0w, k0);
                 if (kind == kNone) {
 #pragma unroll
                     for (int j = 0; j < 16; ++j) pk[j] = 0u;
                 } else {
                     float s[32];
-                    tc::tmem_ld32(tl + 32 * c, s);
+                    tc::tmem_ld32(tl + 32u * (uint32_t)bi, s);
                     tc::tmem_wait_ld();
+                    const float mx = kind == kAll ? chunk_max<kAll>(s, t, k0, mask, W, S, N)
+                                                  : chunk_max<kSome>(s, t, k0, mask, W, S, N);
+                    const float mn = fmaxf(mref, mx * sc2);
+                    const bool grow = mn > mref + 8.f;  // also the first visible key (mref = -inf)
+                    const bool rescale = grow && mref != -INFINITY;
+                    if (__any_sync(0xffffffffu, rescale)) {
+                        // O of this warp's rows, once every P V issued so far has
+                        // landed (the commit of step i + 1 follows step i - 1's)
+                        if (!mwait(&sb[(i + 1) % kRing], spar(i + 1))) fail(42);
+                        tc::tc_fence_after();
+                        float o[16];
+                        tc::tmem_ld16(tl + kOcol, o);
+                        tc::tmem_wait_ld();
+                        const float f = rescale ? ex2_approx(mref - mn) : 1.f;
+                        uint32_t ou[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) ou[j] = __float_as_uint(o[j] * f);
+                        tmem_st16(tl + kOcol, ou);
+                    }
+                    if (grow) {
+                        if (rescale) l *= ex2_approx(mref - mn);
+                        mref = mn;
+                    }
+                    const float z = mref == -INFINITY ? 0.f : mref;
+                    float2 ps2 = make_float2(0.f, 0.f);
                     if (kind == kAll) chunk_exp<kAll>(s, t, k0, mask, W, S, N, sc2, z, ps2, pk);
                     else chunk_exp<kSome>(s, t, k0, mask, W, S, N, sc2, z, ps2, pk);
+                    l += ps2.x + ps2.y;
                 }
-                tmem_st16(tl + 16 * c, pk);
+                tmem_st16(tl + 32u * (uint32_t)bi, pk);  // P over the scores already read
+                tc::tmem_wait_st();
+                tc::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&pb[bi]);
             }
-            const float ps = ps2.x + ps2.y;
-            l = l * corr + ps;
-            m = mn;
-            tc::tmem_wait_st();
+            if (s_err) break;
+            // O is complete once the commit of step n + 1 (after the last P V) lands
+            if (!mwait(&sb[(st.n + 1) % kRing], spar(st.n + 1))) fail(45);
+            tc::tc_fence_after();
+            float o[16];
+            tc::tmem_ld16(tl + kOcol, o);
+            tc::tmem_wait_ld();
             tc::tc_fence_before();
-            wg_sync(wg);
-            if (s_err[wg]) break;
-            if (r == 0) {
-                tc::tc_fence_after();
-#pragma unroll
-                for (int ks = 0; ks < kT / 16; ++ks)
-                    mma_bf16_ta(tm + 64, tm + 8 * ks, desc_mn<DH>(sV, kb * kT, ks), idesc_o, ks > 0 ? 1u : 0u);
-                tc::mma_commit(&bar[wg]);
-            }
             __syncwarp();
-            if (!wg_wait(&bar[wg], phase, err, 42)) s_err[wg] = 1;
-            {
-                float ob[DH];
-                tmem_ld_dh<DH>(tl + 64, ob);
-                tc::tmem_wait_ld();
+            if (lane == 0) tc::mbar_arrive(&obar[wg]);  // O read: the next tile may overwrite it
+            if (t < N) {
+                const float inv = 1.0f / l;
+                const size_t idx = ((size_t)b * N + t) * D + hh * DH;
 #pragma unroll
-                for (int j = 0; j < DH; ++j) o[j] = fmaf(o[j], corr, ob[j]);
+                for (int c = 0; c < DH / 8; ++c) {
+                    float ov[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) ov[j] = o[8 * c + j] * inv;
+                    const float4 h0 = __ldg(reinterpret_cast<const float4 *>(Hin + idx) + 2 * c);
+                    const float4 h1 = __ldg(reinterpret_cast<const float4 *>(Hin + idx) + 2 * c + 1);
+                    reinterpret_cast<float4 *>(Hmid + idx)[2 * c] =
+                        make_float4(h0.x + ov[0], h0.y + ov[1], h0.z + ov[2], h0.w + ov[3]);
+                    reinterpret_cast<float4 *>(Hmid + idx)[2 * c + 1] =
+                        make_float4(h1.x + ov[4], h1.y + ov[5], h1.z + ov[6], h1.w + ov[7]);
+                    if (O)  // O in BF16, kept only for the backward's D_t
+                        *reinterpret_cast<uint4 *>(O + idx + 8 * c) =
+                            make_uint4(pack_bf2(ov[0], ov[1]), pack_bf2(ov[2], ov[3]), pack_bf2(ov[4], ov[5]),
+                                       pack_bf2(ov[6], ov[7]));
+                }
+                // natural log-sum-exp: (m + log2 l) ln 2
+                LSE[((size_t)b * N + t) * NH + hh] = (mref + log2f(l)) * 0.69314718055994531f;
             }
-            tc::tc_fence_before();
-            wg_sync(wg);  // the next block's S overwrites these columns
-            if (s_err[wg]) break;
+            advance(st.n);
         }
-        if (s_err[wg]) break;
-        if (t < N) {
-            const float inv = 1.0f / l;
-            const size_t idx = ((size_t)b * N + t) * D + hh * DH;
-#pragma unroll
-            for (int c = 0; c < DH / 8; ++c) {
-                float ov[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) ov[j] = o[8 * c + j] * inv;
-                const float4 h0 = __ldg(reinterpret_cast<const float4 *>(Hin + idx) + 2 * c);
-                const float4 h1 = __ldg(reinterpret_cast<const float4 *>(Hin + idx) + 2 * c + 1);
-                reinterpret_cast<float4 *>(Hmid + idx)[2 * c] =
-                    make_float4(h0.x + ov[0], h0.y + ov[1], h0.z + ov[2], h0.w + ov[3]);
-                reinterpret_cast<float4 *>(Hmid + idx)[2 * c + 1] =
-                    make_float4(h1.x + ov[4], h1.y + ov[5], h1.z + ov[6], h1.w + ov[7]);
-                if (O)  // O in BF16, kept only for the backward's D_t
-                    *reinterpret_cast<uint4 *>(O + idx + 8 * c) =
-                        make_uint4(pack_bf2(ov[0], ov[1]), pack_bf2(ov[2], ov[3]), pack_bf2(ov[4], ov[5]),
-                                   pack_bf2(ov[6], ov[7]));
-            }
-            // natural log-sum-exp: (m + log2 l) ln 2
-            LSE[((size_t)b * N + t) * NH + hh] = (m + log2f(l)) * 0.69314718055994531f;
-        }
-        if (r == 0) wg_task[wg] = atomicAdd(&next_task, 1);
-        wg_sync(wg);
-        task = wg_task[wg];
-        wg_sync(wg);
     }
-    drain_on_error(&bar[wg], phase, s_err[wg] != 0);
     tc::tc_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -794,9 +896,9 @@ sg_status launch_attn_fwd_tmem(const sg_config &c, const __nv_bfloat16 *QKVh, co
     const size_t smem = tmem_smem_bytes(dh, c.N, false);
     auto kern = attn_fwd_tmem_kernel<16>;
     SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<(unsigned)(Bc * c.n_heads), 256, smem, ::sg::counted(st)>>>(
+    kern<<<(unsigned)(Bc * c.n_heads), 320, smem, ::sg::counted(st)>>>(
         QKVh, Hin, O, Hmid, LSE, c.N, Npad, c.d, c.n_heads, c.mask_kind, c.W, c.S, Bc,
-        tmem_samples_per_wave(kern, 256, smem, c.n_heads), err);
+        tmem_samples_per_wave(kern, 320, smem, c.n_heads), err);
     return check_launch("attn_fwd_tmem_kernel");
 }
 
