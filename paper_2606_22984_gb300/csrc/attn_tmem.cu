@@ -359,7 +359,6 @@ attn_fwd_tmem_kernel(const __nv_bfloat16 *__restrict__ QKVh, const float *__rest
     // completed phases of each ring barrier before the current tile, as parity bits
     uint32_t sbits = 0, pbits = 0;
     auto spar = [&](int j) { return ((sbits >> (j % kRing)) + (uint32_t)(j / kRing)) & 1u; };
-    auto ppar = [&](int j) { return ((pbits >> (j % kRing)) + (uint32_t)(j / kRing)) & 1u; };
     auto advance = [&](int n) {  // commits j = 0 .. n + 1, P phases i = 0 .. n - 1
 #pragma unroll
         for (int bb = 0; bb < kRing; ++bb) {
@@ -376,35 +375,41 @@ attn_fwd_tmem_kernel(const __nv_bfloat16 *__restrict__ QKVh, const float *__rest
         if (lane == 0) {
             const uint32_t idesc_s = tc::idesc_bf16(kT, 32);
             const uint32_t idesc_o = tc::idesc_bf16(kT, DH) | (1u << 16);  // V read MN-major
+            // descriptors of row 0; a step adds its rows' byte offset (in 16-byte
+            // units) to the start-address field, which cannot carry below 256 KB
+            const uint64_t dK0 = desc_k<DH>(sK, 0, 0), dV0 = desc_mn<DH>(sV, 0, 0), dV1 = desc_mn<DH>(sV, 0, 1);
+            auto rows = [](int row0) { return (uint64_t)((uint32_t)(row0 * DH * 2) >> 4); };
             int tile_no = 0;
             for (int task = wg; task < nq && !s_err; task += 2, ++tile_no) {
                 const int qt = nq - 1 - task;  // the later tiles see more keys: they go first
                 const TileSteps st(mask, W, S, N, qt);
                 const uint64_t dq = desc_k<DH>(sQ, qt * kT, 0);
-                auto issue_s = [&](int j) {  // scores of step j into ring buffer j % 3
-                    tc::mma_bf16(tm + 32u * (uint32_t)(j % kRing), dq, desc_k<DH>(sK, st.key0(j), 0), idesc_s, 0u);
+                auto issue_s = [&](int j, int bj) {  // scores of step j into ring buffer bj = j % 3
+                    tc::mma_bf16(tm + 32u * (uint32_t)bj, dq, dK0 + rows(st.key0(j)), idesc_s, 0u);
                 };
                 tc::tc_fence_after();
-                issue_s(0);
+                issue_s(0, 0);
                 tc::mma_commit(&sb[0]);
-                if (st.n > 1) issue_s(1);
+                if (st.n > 1) issue_s(1, 1);
                 tc::mma_commit(&sb[1]);
+                int bi = 0, q = 0;  // i % 3 and i / 3
                 for (int i = 0; i < st.n && !s_err; ++i) {
-                    const int bi = i % kRing;
-                    if (!mwait(&pb[bi], ppar(i))) fail(43);
+                    const int b1 = bi == 2 ? 0 : bi + 1, b2 = bi == 0 ? 2 : bi - 1;  // (i + 1) % 3, (i + 2) % 3
+                    const int q1 = q + (bi == 2);                                    // (i + 1) / 3
+                    if (!mwait(&pb[bi], ((pbits >> bi) + (uint32_t)q) & 1u)) fail(43);
                     // step i + 2 reuses step i - 1's buffer: its P V must have landed
-                    if (i >= 1 && i + 2 < st.n && !mwait(&sb[(i + 1) % kRing], spar(i + 1))) fail(44);
+                    if (i >= 1 && i + 2 < st.n && !mwait(&sb[b1], ((sbits >> b1) + (uint32_t)q1) & 1u)) fail(44);
                     // the first P V of a tile overwrites O: the previous tile's O must have been read
                     if (i == 0 && tile_no > 0 && !mwait(&obar[wg], (uint32_t)(tile_no - 1) & 1u)) fail(46);
                     tc::tc_fence_after();
                     if (s_err) break;
-                    const int k0 = st.key0(i);
-#pragma unroll
-                    for (int ks = 0; ks < 2; ++ks)
-                        mma_bf16_ta(tm + kOcol, tm + 32u * (uint32_t)bi + 8u * (uint32_t)ks, desc_mn<DH>(sV, k0, ks),
-                                    idesc_o, (i > 0 || ks > 0) ? 1u : 0u);
-                    if (i + 2 < st.n) issue_s(i + 2);
-                    tc::mma_commit(&sb[(i + 2) % kRing]);  // also marks step i's P V
+                    const uint64_t kr = rows(st.key0(i));
+                    mma_bf16_ta(tm + kOcol, tm + 32u * (uint32_t)bi, dV0 + kr, idesc_o, i > 0 ? 1u : 0u);
+                    mma_bf16_ta(tm + kOcol, tm + 32u * (uint32_t)bi + 8u, dV1 + kr, idesc_o, 1u);
+                    if (i + 2 < st.n) issue_s(i + 2, b2);
+                    tc::mma_commit(&sb[b2]);  // also marks step i's P V
+                    bi = b1;
+                    q = q1;
                 }
                 // the next tile's scores overwrite buffers that this tile's last
                 // P V products read: wait for the commit after the last one
@@ -423,10 +428,11 @@ attn_fwd_tmem_kernel(const __nv_bfloat16 *__restrict__ QKVh, const float *__rest
             const TileSteps st(mask, W, S, N, qt);
             const int t = qt * kT + r, t0w = qt * kT + 32 * (warp & 3);
             float mref = -INFINITY, l = 0.f;
+            int bi = 0, q = 0;  // i % 3 and i / 3
             for (int i = 0; i < st.n; ++i) {
-                const int bi = i % kRing;
+                const int b1 = bi == 2 ? 0 : bi + 1, q1 = q + (bi == 2);  // (i + 1) % 3, (i + 1) / 3
                 const int k0 = st.key0(i);
-                if (!mwait(&sb[bi], spar(i))) fail(41);
+                if (!mwait(&sb[bi], ((sbits >> bi) + (uint32_t)q) & 1u)) fail(41);
                 tc::tc_fence_after();
                 if (s_err) break;
                 const int kind = chunk_kind(mask, W, S, N, t0w, k0);
@@ -446,7 +452,7 @@ attn_fwd_tmem_kernel(const __nv_bfloat16 *__restrict__ QKVh, const float *__rest
                     if (__any_sync(0xffffffffu, rescale)) {
                         // O of this warp's rows, once every P V issued so far has
                         // landed (the commit of step i + 1 follows step i - 1's)
-                        if (!mwait(&sb[(i + 1) % kRing], spar(i + 1))) fail(42);
+                        if (!mwait(&sb[b1], ((sbits >> b1) + (uint32_t)q1) & 1u)) fail(42);
                         tc::tc_fence_after();
                         float o[16];
                         tc::tmem_ld16(tl + kOcol, o);
@@ -472,6 +478,8 @@ attn_fwd_tmem_kernel(const __nv_bfloat16 *__restrict__ QKVh, const float *__rest
                 tc::tc_fence_before();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&pb[bi]);
+                bi = b1;
+                q = q1;
             }
             if (s_err) break;
             // O is complete once the commit of step n + 1 (after the last P V) lands
