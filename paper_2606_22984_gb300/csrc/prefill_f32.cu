@@ -893,8 +893,11 @@ gemm_nn_kernel(const float *__restrict__ A, int lda, const float *__restrict__ B
     __shared__ float As[16][64 + 4];
     __shared__ float Bs[16][64 + 4];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int64_t m0 = (int64_t)blockIdx.y * 64;
-    const int n0 = blockIdx.x * 64;
+    // one-dimensional grid, column tile fastest: consecutive blocks share a
+    // row tile of A, and M / 64 may exceed the 65535 limit of grid.y
+    const int nt = (N + 63) / 64;
+    const int64_t m0 = (int64_t)(blockIdx.x / nt) * 64;
+    const int n0 = (int)(blockIdx.x % nt) * 64;
     float acc[4][4] = {};
     for (int k0 = 0; k0 < K; k0 += 16) {
         {   // A tile: 64 rows x 16 k, stored transposed
@@ -1985,8 +1988,8 @@ void gemm(const float *A, int lda, const float *Bm, int ldb, const float *bias, 
           int64_t M, int N, int K, cudaStream_t st, const float *aux = nullptr, int ldaux = 0,
           float *aux_out = nullptr)
 {
-    dim3 grid((N + 63) / 64, (unsigned)((M + 63) / 64));
-    gemm_nn_kernel<EPI><<<grid, 256, 0, ::sg::counted(st)>>>(A, lda, Bm, ldb, bias, C, ldc, aux, ldaux, aux_out,
+    const int64_t blocks = (int64_t)((N + 63) / 64) * ((M + 63) / 64);
+    gemm_nn_kernel<EPI><<<(unsigned)blocks, 256, 0, ::sg::counted(st)>>>(A, lda, Bm, ldb, bias, C, ldc, aux, ldaux, aux_out,
                                              M, N, K);
 }
 

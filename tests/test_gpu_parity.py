@@ -461,6 +461,23 @@ def test_fp32_teacher_forced_logq_matches_oracle_and_sampler(name):
     assert (tf - logq).abs().max().item() <= FP32_LOGQ_TOL * m.N
 
 
+def test_fp32_logprob_beyond_65535_row_tiles():
+    """FP32 teacher-forced pass over 70000 samples of N = 64 in one call:
+    4.48 million rows, so a row-tiled launch needs more than 65535 tiles of
+    64 rows (past the limit of a grid's y dimension).  Sampled rows against
+    the oracle."""
+    m = inputs.ModelShape(64, 2, 32, 4)
+    w = inputs.make_weights(m, 4)
+    B = 70000
+    model = sg.Model(m, w, sg.SG_FP32)
+    rs = inputs.random_spins(B, m.N, 21)
+    lq = _np(model.logprob(torch.tensor(rs, device="cuda")))
+    model.check()
+    rows = np.array([0, 33333, 65536, B - 1])
+    lqo = oracle.logprob(ocfg(m), w, rs[rows])
+    assert np.abs(lq[rows] - lqo).max() <= FP32_LOGQ_TOL * m.N
+
+
 def test_sampling_is_deterministic_and_seeded():
     m, B, _ = SAMPLE_CASES["ea6_ring"]
     model = sg.Model(m, inputs.make_weights(m, 1), sg.SG_FP32)
