@@ -210,15 +210,13 @@ sg_status sg_sample(sg_model *m, int64_t B, double beta, uint64_t seed, uint32_t
  * Errors: SG_EINVAL when cfg is invalid or when the packed weights plus the
  * KV cache of B samples exceed SG_NOALLOC_SCRATCH_BYTES (reduce B, or use
  * sg_sample); SG_EUNSUPPORTED for shapes the FP32 decode is not built for.
- * The first call on a device looks up the scratch's device address (once per
- * device, with that device current); make that first call before any stream
- * capture begins.  Every call shares the one scratch array and it keeps the
- * last call's contents; nothing in it needs to start at zero, because each
- * call writes every byte it reads.  Calls whose work overlaps on the GPU
- * (other streams, other host threads) race on the scratch: serialise them.
- * The looked-up address belongs to the device's current context: after
- * cudaDeviceReset (or any teardown of the primary context) the cached address
- * is stale, so do not call this entry point again in that process.
+ * Every call looks up the scratch's address in the current device context
+ * (cudaGetSymbolAddress, a host-side lookup), so the entry point stays valid
+ * across a cudaDeviceReset.  Every call shares the one scratch array and it
+ * keeps the last call's contents; nothing in it needs to start at zero,
+ * because each call writes every byte it reads.  Calls whose work overlaps on
+ * the GPU (other streams, other host threads) race on the scratch: serialise
+ * them.
  */
 #define SG_NOALLOC_SCRATCH_BYTES (64ull << 20)
 sg_status sg_sample_noalloc(const sg_config *cfg, const float *weights, int64_t B, double beta,

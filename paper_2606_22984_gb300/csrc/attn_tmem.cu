@@ -7,23 +7,20 @@
 // The same bytes serve as a K-major operand (rows = M or N, d_h = K) and as
 // an MN-major operand (d_h = N, rows = K), so no transposed copy is made.
 //
-// Each warpgroup takes 128-row tiles (one row per thread, its warp's TMEM
-// lane quarter) and owns 128 TMEM columns.  Per step: one elected thread
-// issues the score products into TMEM; the 128 threads read their row of
-// scores (tcgen05.ld), run the softmax (or its gradient) in registers and
-// store the BF16 probabilities back over the scores they have read; the
-// elected thread then issues the products that take those probabilities as
-// the A operand straight from TMEM, and the threads fold the FP32 results
-// into registers.  Row maxima and sums are per thread: no shuffles, and the
-// online-softmax rescale happens once per 128 keys.  Each warp skips the
-// 32-key chunks that none of its rows can see (it stores zeros there), so a
-// band costs about the keys it holds.  With several warpgroups per SM, one
-// warpgroup's MMA round trip hides behind another's exponentials.
+// Rows of a 128-row tile map one to one onto TMEM lanes and threads (a warp
+// reads its lane quarter), so row maxima and sums are per thread: no
+// shuffles.  Scores land in TMEM; the threads read their row (tcgen05.ld),
+// run the softmax (or its gradient) in registers and store the BF16
+// probabilities back over the scores they have read, where the next product
+// takes them as its A operand straight from TMEM.  A warp skips the 32-key
+// chunks that none of its rows can see (it stores zeros there).
 //
-// Forward  (2 warpgroups, 2 CTAs per SM): per query tile and visible 128-key
-//          block, S = Q K^T -> P (BF16, TMEM cols [0, 64)) -> O_blk = P V
-//          (TMEM cols [64, 64 + d_h)) -> o = o corr + O_blk.
-// Backward (4 warpgroups, 1 CTA per SM), in 64-wide steps:
+// Forward  (2 CTAs per SM; per CTA two softmax warpgroups and one MMA warp
+//          each): a query tile is a pipeline of 32-key steps -- S = Q K^T
+//          into a ring of three TMEM buffers, P over S, O += P V accumulated
+//          in TMEM -- with the MMA warp issuing the scores two steps ahead.
+// Backward (1 CTA per SM, 4 warpgroups, each issuing its own products), in
+//          64-wide steps:
 //          key tile (thread = key):   S^T = K Q^T, dP^T = V dO^T ->
 //                                     P^T, dS^T -> dV += P^T dO, dK += dS^T Q
 //          query tile (thread = query): S = Q K^T, dP = dO V^T -> dS ->
@@ -525,7 +522,8 @@ attn_fwd_tmem_kernel(const __nv_bfloat16 *__restrict__ QKVh, const float *__rest
 }
 
 // ---------------------------------------------------------------------------
-// Backward.  TMEM per warpgroup (128 columns), per 64-wide step:
+// Backward.  TMEM per warpgroup (128 columns), per 64-wide step (one elected
+// thread of the warpgroup issues; two MMA round trips per step):
 //   [0, 64)   scores (S or S^T); then P^T (key tiles) or dS (query tiles) in
 //             BF16 over [0, 32); the step's dV (key) or dQ (query) at [32, 32 + DH)
 //   [64, 128) dP or dP^T; then dS^T in BF16 over [64, 96) and the step's dK

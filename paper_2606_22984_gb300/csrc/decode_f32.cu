@@ -14,7 +14,6 @@
 // (32 consecutive samples, one head) reads 512 contiguous bytes per float4.
 // Slot of key k: dense or short sequence -> k; band + sink ring -> k for
 // k < S, else S + (k - S) mod (W + 1).
-#include <mutex>
 #include <string>
 
 #include "sg_internal.cuh"
@@ -445,30 +444,20 @@ sg_status launch_decode_f32(sg_model *m, int64_t B, uint64_t seed, uint32_t sid,
 // Allocation-free sampling (sg_sample_noalloc).  Its scratch -- the packed
 // weight copies followed by the KV cache -- lives in one file-scope device
 // array instead of memory from cudaMalloc.  Host code cannot use the array's
-// name as a device address, so the address is looked up once per device with
-// cudaGetSymbolAddress and cached.
+// name as a device address, so every call looks it up with
+// cudaGetSymbolAddress in the current context (a host-side table lookup).  No
+// address is cached, so a device reset or a new primary context cannot leave
+// a stale pointer behind.
 // ---------------------------------------------------------------------------
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SG_NOALLOC_SCRATCH_BYTES];
 
-static constexpr int kMaxDevices = 64;
-static std::mutex g_noalloc_mu;
-static void *g_noalloc_addr[kMaxDevices];
-
 static sg_status noalloc_scratch(void **out)
 {
-    int dev = 0;
-    SG_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return fail(SG_EUNSUPPORTED, "device index out of range");
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return fail(SG_ECUDA, std::string("cudaGetSymbolAddress(scratch): ") +
-                                      cudaGetErrorString(e));
-        g_noalloc_addr[dev] = p;
-    }
-    *out = g_noalloc_addr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+        return fail(SG_ECUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+    *out = p;
     return SG_OK;
 }
 
