@@ -43,6 +43,9 @@ namespace sg {
 namespace {
 
 constexpr int kT = 128;             // rows per tile = TMEM lanes
+// Error-word values of the bounded waits: kWaitCode + 8 * site (bit 2, the
+// non-finite-logit flag of the error word, stays clear).
+constexpr int kWaitCode = 0x1000;
 constexpr float kLog2e = 1.4426950408889634f;
 
 __device__ __forceinline__ uint32_t pack_bf2(float lo, float hi)
@@ -167,10 +170,11 @@ __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
 
 // Bounded wait on an mbarrier phase that suspends the thread (up to about a
 // microsecond per probe) instead of spinning, so that waiting warps leave
-// their issue slots to the warps that compute; false after about 4 s.
+// their issue slots to the warps that compute; false after about 0.26 s
+// (every wait here covers microseconds of work).
 __device__ __forceinline__ bool mwait(uint64_t *bar, uint32_t parity)
 {
-    for (uint32_t i = 0; i < (1u << 22); ++i) {
+    for (uint32_t i = 0; i < (1u << 18); ++i) {
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -304,13 +308,197 @@ struct TileSteps {
     __device__ __forceinline__ int key0(int i) const { return 32 * (i < ns ? i : bstart + (i - ns)); }
 };
 
+// Ring-barrier phases: bit b of the parity words holds the parity of buffer
+// b's next phase at the start of a tile; a tile commits j = 0 .. n + 1 (one
+// per step and two more) and completes P phases i = 0 .. n - 1.
+__device__ __forceinline__ uint32_t ring_parity(uint32_t bits, int j)
+{
+    return ((bits >> (j % kRing)) + (uint32_t)(j / kRing)) & 1u;
+}
+
+__device__ __forceinline__ void ring_advance(uint32_t &sbits, uint32_t &pbits, int n)
+{
+#pragma unroll
+    for (int bb = 0; bb < kRing; ++bb) {
+        sbits ^= (uint32_t)(((n + 4 - bb) / kRing) & 1) << bb;
+        pbits ^= (uint32_t)(((n + 2 - bb) / kRing) & 1) << bb;
+    }
+}
+
+// The MMA warp's part of one query tile (lane 0 only).  dq: the Q tile's
+// descriptor; dK0, dV0: descriptors of row 0 of the staged K and V arrays;
+// krow(i): the row in them of step i's 32 keys.  tile_no > 0 makes the tile
+// wait until the previous tile's O has been read (obar).  Returns false
+// after a time-out (the error word is set).
+template <int DH, class KRow>
+__device__ __forceinline__ bool fwd_tile_mma(uint32_t tm, uint64_t dq, uint64_t dK0, uint64_t dV0, int n, KRow krow,
+                                             uint64_t *sb, uint64_t *pb, uint64_t *obar, int tile_no, uint32_t sbits,
+                                             uint32_t pbits, int *err, volatile int *s_err)
+{
+    const uint32_t idesc_s = tc::idesc_bf16(kT, 32);
+    const uint32_t idesc_o = tc::idesc_bf16(kT, DH) | (1u << 16);  // V read MN-major
+    // a step adds its rows' byte offset (in 16-byte units) to the start-address
+    // field of the row-0 descriptors, which cannot carry below 256 KB
+    auto rows = [](int row0) { return (uint64_t)((uint32_t)(row0 * DH * 2) >> 4); };
+    auto issue_s = [&](int j, int bj) {  // scores of step j into ring buffer bj = j % 3
+        const uint64_t kr = rows(krow(j));
+#pragma unroll
+        for (int ks = 0; ks < DH / 16; ++ks)  // K-step: 2 core matrices = 256 bytes
+            tc::mma_bf16(tm + 32u * (uint32_t)bj, dq + 16u * ks, dK0 + kr + 16u * ks, idesc_s, ks > 0 ? 1u : 0u);
+    };
+    auto fail = [&](int code) {
+        atomicExch(err, code);
+        *s_err = 1;
+        return false;
+    };
+    // A new tile's commits reuse the ring barriers.  Every softmax warp has
+    // observed the previous tile's last commit (and read its O) before it
+    // arrives on obar, so no warp can still be polling a phase that this
+    // tile's commits would complete twice over; and the first P V overwrites O.
+    if (tile_no > 0 && !mwait(obar, (uint32_t)(tile_no - 1) & 1u)) return fail(kWaitCode + 8 * 46);
+    tc::tc_fence_after();
+    issue_s(0, 0);
+    tc::mma_commit(&sb[0]);
+    if (n > 1) issue_s(1, 1);
+    tc::mma_commit(&sb[1]);
+    int bi = 0, q = 0;  // i % 3 and i / 3
+    for (int i = 0; i < n; ++i) {
+        const int b1 = bi == 2 ? 0 : bi + 1, b2 = bi == 0 ? 2 : bi - 1;  // (i + 1) % 3, (i + 2) % 3
+        const int q1 = q + (bi == 2);                                    // (i + 1) / 3
+        if (!mwait(&pb[bi], ((pbits >> bi) + (uint32_t)q) & 1u)) return fail(kWaitCode + 8 * 43);
+        // step i + 2 reuses step i - 1's buffer: its P V must have landed
+        if (i >= 1 && i + 2 < n && !mwait(&sb[b1], ((sbits >> b1) + (uint32_t)q1) & 1u)) return fail(kWaitCode + 8 * 44);
+        tc::tc_fence_after();
+        if (*s_err) return false;
+        const uint64_t kr = rows(krow(i));
+        // P V: K = 32 keys in two 16-key steps of 2 core-matrix rows (2 * 16 * DH bytes)
+        mma_bf16_ta(tm + kOcol, tm + 32u * (uint32_t)bi, dV0 + kr, idesc_o, i > 0 ? 1u : 0u);
+        mma_bf16_ta(tm + kOcol, tm + 32u * (uint32_t)bi + 8u, dV0 + kr + (uint64_t)(2 * DH), idesc_o, 1u);
+        if (i + 2 < n) issue_s(i + 2, b2);
+        tc::mma_commit(&sb[b2]);  // also marks step i's P V
+        bi = b1;
+        q = q1;
+    }
+    // the next tile's scores overwrite buffers that this tile's last P V
+    // products read: wait for the commit after the last one
+    if (!mwait(&sb[(n + 1) % kRing], ring_parity(sbits, n + 1))) return fail(kWaitCode + 8 * 47);
+    return true;
+}
+
+// The softmax warps' part of one query tile: steps over the n visible chunks
+// (keys key0(i) .. + 31) for row t of the warp's rows t0w .. t0w + 31; on
+// return o holds the row's unnormalised output, mref its reference maximum
+// (base 2) and l its sum.  Returns false after a time-out.
+template <int DH, class Key0>
+__device__ __forceinline__ bool fwd_tile_softmax(uint32_t tl, int n, Key0 key0, int t, int t0w, int mask, int W, int S,
+                                                 int N, uint64_t *sb, uint64_t *pb, uint32_t sbits, int *err,
+                                                 volatile int *s_err, float &mref, float &l, float (&o)[DH])
+{
+    const int lane = threadIdx.x & 31;
+    const float sc2 = rsqrtf((float)DH) * kLog2e;  // softmax scale in base 2
+    auto fail = [&](int code) {
+        atomicExch(err, code);
+        *s_err = 1;
+        return false;
+    };
+    mref = -INFINITY;
+    l = 0.f;
+    int bi = 0, q = 0;  // i % 3 and i / 3
+    for (int i = 0; i < n; ++i) {
+        const int b1 = bi == 2 ? 0 : bi + 1, q1 = q + (bi == 2);  // (i + 1) % 3, (i + 1) / 3
+        const int k0 = key0(i);
+        if (!mwait(&sb[bi], ((sbits >> bi) + (uint32_t)q) & 1u)) return fail(kWaitCode + 8 * 41);
+        tc::tc_fence_after();
+        if (*s_err) return false;
+        const int kind = chunk_kind(mask, W, S, N, t0w, k0);
+        uint32_t pk[16];
+        if (kind == kNone) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) pk[j] = 0u;
+        } else {
+            float s[32];
+            tc::tmem_ld32(tl + 32u * (uint32_t)bi, s);
+            tc::tmem_wait_ld();
+            const float mx = kind == kAll ? chunk_max<kAll>(s, t, k0, mask, W, S, N)
+                                          : chunk_max<kSome>(s, t, k0, mask, W, S, N);
+            const float mn = fmaxf(mref, mx * sc2);
+            const bool grow = mn > mref + 8.f;  // also the first visible key (mref = -inf)
+            const bool rescale = grow && mref != -INFINITY;
+            if (__any_sync(0xffffffffu, rescale)) {
+                // O of this warp's rows, once every P V issued so far has
+                // landed (the commit of step i + 1 follows step i - 1's)
+                if (!mwait(&sb[b1], ((sbits >> b1) + (uint32_t)q1) & 1u)) return fail(kWaitCode + 8 * 42);
+                tc::tc_fence_after();
+                float ov[DH];
+                tmem_ld_dh<DH>(tl + kOcol, ov);
+                tc::tmem_wait_ld();
+                const float f = rescale ? ex2_approx(mref - mn) : 1.f;
+#pragma unroll
+                for (int c = 0; c < DH / 16; ++c) {
+                    uint32_t ou[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) ou[j] = __float_as_uint(ov[16 * c + j] * f);
+                    tmem_st16(tl + kOcol + 16u * c, ou);
+                }
+            }
+            if (grow) {
+                if (rescale) l *= ex2_approx(mref - mn);
+                mref = mn;
+            }
+            const float z = mref == -INFINITY ? 0.f : mref;
+            float2 ps2 = make_float2(0.f, 0.f);
+            if (kind == kAll) chunk_exp<kAll>(s, t, k0, mask, W, S, N, sc2, z, ps2, pk);
+            else chunk_exp<kSome>(s, t, k0, mask, W, S, N, sc2, z, ps2, pk);
+            l += ps2.x + ps2.y;
+        }
+        tmem_st16(tl + 32u * (uint32_t)bi, pk);  // P over the scores already read
+        tc::tmem_wait_st();
+        tc::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&pb[bi]);
+        bi = b1;
+        q = q1;
+    }
+    // O is complete once the commit of step n + 1 (after the last P V) lands
+    if (!mwait(&sb[(n + 1) % kRing], ring_parity(sbits, n + 1))) return fail(kWaitCode + 8 * 45);
+    tc::tc_fence_after();
+    tmem_ld_dh<DH>(tl + kOcol, o);
+    tc::tmem_wait_ld();
+    return true;
+}
+
+// Row t's outputs: O (BF16, optional) and Hmid = Hin + O / l (FP32), LSE.
+template <int DH>
+__device__ __forceinline__ void fwd_row_out(const float (&o)[DH], float mref, float l, int64_t b, int t, int hh, int N,
+                                            int D, int NH, const float *__restrict__ Hin, __nv_bfloat16 *__restrict__ O,
+                                            float *__restrict__ Hmid, float *__restrict__ LSE)
+{
+    const float inv = 1.0f / l;
+    const size_t idx = ((size_t)b * N + t) * D + hh * DH;
+#pragma unroll
+    for (int c = 0; c < DH / 8; ++c) {
+        float ov[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) ov[j] = o[8 * c + j] * inv;
+        const float4 h0 = __ldg(reinterpret_cast<const float4 *>(Hin + idx) + 2 * c);
+        const float4 h1 = __ldg(reinterpret_cast<const float4 *>(Hin + idx) + 2 * c + 1);
+        reinterpret_cast<float4 *>(Hmid + idx)[2 * c] = make_float4(h0.x + ov[0], h0.y + ov[1], h0.z + ov[2], h0.w + ov[3]);
+        reinterpret_cast<float4 *>(Hmid + idx)[2 * c + 1] =
+            make_float4(h1.x + ov[4], h1.y + ov[5], h1.z + ov[6], h1.w + ov[7]);
+        if (O)  // O in BF16, kept only for the backward's D_t
+            *reinterpret_cast<uint4 *>(O + idx + 8 * c) = make_uint4(
+                pack_bf2(ov[0], ov[1]), pack_bf2(ov[2], ov[3]), pack_bf2(ov[4], ov[5]), pack_bf2(ov[6], ov[7]));
+    }
+    // natural log-sum-exp: (m + log2 l) ln 2
+    LSE[((size_t)b * N + t) * NH + hh] = (mref + log2f(l)) * 0.69314718055994531f;
+}
+
 template <int DH>
 __global__ void __launch_bounds__(320, 2)
 attn_fwd_tmem_kernel(const __nv_bfloat16 *__restrict__ QKVh, const float *__restrict__ Hin,
                      __nv_bfloat16 *__restrict__ O, float *__restrict__ Hmid, float *__restrict__ LSE,
                      int N, int Npad, int D, int NH, int mask, int W, int S, int Bc, int ahead, int *err)
 {
-    static_assert(DH == 16, "the TMEM layout holds a 16-column O");
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t sbar[2][kRing], pbar[2][kRing], obar[2], dbar[2];
     __shared__ uint32_t tslot;
@@ -352,66 +540,19 @@ attn_fwd_tmem_kernel(const __nv_bfloat16 *__restrict__ QKVh, const float *__rest
     const uint32_t sQ = tc::smem_u32(smem), sK = sQ + part_bytes, sV = sK + part_bytes;
     const uint32_t tm = tslot + 128u * (uint32_t)wg;  // this warpgroup's columns
     const int nq = Npad / kT;
-    uint64_t *sb = sbar[wg], *pb = pbar[wg];
-    // completed phases of each ring barrier before the current tile, as parity bits
     uint32_t sbits = 0, pbits = 0;
-    auto spar = [&](int j) { return ((sbits >> (j % kRing)) + (uint32_t)(j / kRing)) & 1u; };
-    auto advance = [&](int n) {  // commits j = 0 .. n + 1, P phases i = 0 .. n - 1
-#pragma unroll
-        for (int bb = 0; bb < kRing; ++bb) {
-            sbits ^= (uint32_t)(((n + 4 - bb) / kRing) & 1) << bb;
-            pbits ^= (uint32_t)(((n + 2 - bb) / kRing) & 1) << bb;
-        }
-    };
-    auto fail = [&](int code) {
-        atomicExch(err, code);
-        s_err = 1;
-    };
-
     if (mma_warp) {
         if (lane == 0) {
-            const uint32_t idesc_s = tc::idesc_bf16(kT, 32);
-            const uint32_t idesc_o = tc::idesc_bf16(kT, DH) | (1u << 16);  // V read MN-major
-            // descriptors of row 0; a step adds its rows' byte offset (in 16-byte
-            // units) to the start-address field, which cannot carry below 256 KB
-            const uint64_t dK0 = desc_k<DH>(sK, 0, 0), dV0 = desc_mn<DH>(sV, 0, 0), dV1 = desc_mn<DH>(sV, 0, 1);
-            auto rows = [](int row0) { return (uint64_t)((uint32_t)(row0 * DH * 2) >> 4); };
+            const uint64_t dK0 = desc_k<DH>(sK, 0, 0), dV0 = desc_mn<DH>(sV, 0, 0);
             int tile_no = 0;
             for (int task = wg; task < nq && !s_err; task += 2, ++tile_no) {
                 const int qt = nq - 1 - task;  // the later tiles see more keys: they go first
                 const TileSteps st(mask, W, S, N, qt);
-                const uint64_t dq = desc_k<DH>(sQ, qt * kT, 0);
-                auto issue_s = [&](int j, int bj) {  // scores of step j into ring buffer bj = j % 3
-                    tc::mma_bf16(tm + 32u * (uint32_t)bj, dq, dK0 + rows(st.key0(j)), idesc_s, 0u);
-                };
-                tc::tc_fence_after();
-                issue_s(0, 0);
-                tc::mma_commit(&sb[0]);
-                if (st.n > 1) issue_s(1, 1);
-                tc::mma_commit(&sb[1]);
-                int bi = 0, q = 0;  // i % 3 and i / 3
-                for (int i = 0; i < st.n && !s_err; ++i) {
-                    const int b1 = bi == 2 ? 0 : bi + 1, b2 = bi == 0 ? 2 : bi - 1;  // (i + 1) % 3, (i + 2) % 3
-                    const int q1 = q + (bi == 2);                                    // (i + 1) / 3
-                    if (!mwait(&pb[bi], ((pbits >> bi) + (uint32_t)q) & 1u)) fail(43);
-                    // step i + 2 reuses step i - 1's buffer: its P V must have landed
-                    if (i >= 1 && i + 2 < st.n && !mwait(&sb[b1], ((sbits >> b1) + (uint32_t)q1) & 1u)) fail(44);
-                    // the first P V of a tile overwrites O: the previous tile's O must have been read
-                    if (i == 0 && tile_no > 0 && !mwait(&obar[wg], (uint32_t)(tile_no - 1) & 1u)) fail(46);
-                    tc::tc_fence_after();
-                    if (s_err) break;
-                    const uint64_t kr = rows(st.key0(i));
-                    mma_bf16_ta(tm + kOcol, tm + 32u * (uint32_t)bi, dV0 + kr, idesc_o, i > 0 ? 1u : 0u);
-                    mma_bf16_ta(tm + kOcol, tm + 32u * (uint32_t)bi + 8u, dV1 + kr, idesc_o, 1u);
-                    if (i + 2 < st.n) issue_s(i + 2, b2);
-                    tc::mma_commit(&sb[b2]);  // also marks step i's P V
-                    bi = b1;
-                    q = q1;
-                }
-                // the next tile's scores overwrite buffers that this tile's last
-                // P V products read: wait for the commit after the last one
-                if (!s_err && !mwait(&sb[(st.n + 1) % kRing], spar(st.n + 1))) fail(47);
-                advance(st.n);
+                if (!fwd_tile_mma<DH>(tm, desc_k<DH>(sQ, qt * kT, 0), dK0, dV0, st.n,
+                                      [&](int i) { return st.key0(i); }, sbar[wg], pbar[wg], &obar[wg], tile_no,
+                                      sbits, pbits, err, &s_err))
+                    break;
+                ring_advance(sbits, pbits, st.n);
             }
             // let this thread's MMAs land before TMEM is freed
             tc::mma_commit(&dbar[wg]);
@@ -419,98 +560,19 @@ attn_fwd_tmem_kernel(const __nv_bfloat16 *__restrict__ QKVh, const float *__rest
         }
     } else {
         const uint32_t tl = tm + ((uint32_t)(32 * (warp & 3)) << 16);  // this warp's lanes
-        const float sc2 = rsqrtf((float)DH) * kLog2e;                  // softmax scale in base 2
         for (int task = wg; task < nq && !s_err; task += 2) {
             const int qt = nq - 1 - task;
             const TileSteps st(mask, W, S, N, qt);
             const int t = qt * kT + r, t0w = qt * kT + 32 * (warp & 3);
-            float mref = -INFINITY, l = 0.f;
-            int bi = 0, q = 0;  // i % 3 and i / 3
-            for (int i = 0; i < st.n; ++i) {
-                const int b1 = bi == 2 ? 0 : bi + 1, q1 = q + (bi == 2);  // (i + 1) % 3, (i + 1) / 3
-                const int k0 = st.key0(i);
-                if (!mwait(&sb[bi], ((sbits >> bi) + (uint32_t)q) & 1u)) fail(41);
-                tc::tc_fence_after();
-                if (s_err) break;
-                const int kind = chunk_kind(mask, W, S, N, t0w, k0);
-                uint32_t pk[16];
-                if (kind == kNone) {
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) pk[j] = 0u;
-                } else {
-                    float s[32];
-                    tc::tmem_ld32(tl + 32u * (uint32_t)bi, s);
-                    tc::tmem_wait_ld();
-                    const float mx = kind == kAll ? chunk_max<kAll>(s, t, k0, mask, W, S, N)
-                                                  : chunk_max<kSome>(s, t, k0, mask, W, S, N);
-                    const float mn = fmaxf(mref, mx * sc2);
-                    const bool grow = mn > mref + 8.f;  // also the first visible key (mref = -inf)
-                    const bool rescale = grow && mref != -INFINITY;
-                    if (__any_sync(0xffffffffu, rescale)) {
-                        // O of this warp's rows, once every P V issued so far has
-                        // landed (the commit of step i + 1 follows step i - 1's)
-                        if (!mwait(&sb[b1], ((sbits >> b1) + (uint32_t)q1) & 1u)) fail(42);
-                        tc::tc_fence_after();
-                        float o[16];
-                        tc::tmem_ld16(tl + kOcol, o);
-                        tc::tmem_wait_ld();
-                        const float f = rescale ? ex2_approx(mref - mn) : 1.f;
-                        uint32_t ou[16];
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) ou[j] = __float_as_uint(o[j] * f);
-                        tmem_st16(tl + kOcol, ou);
-                    }
-                    if (grow) {
-                        if (rescale) l *= ex2_approx(mref - mn);
-                        mref = mn;
-                    }
-                    const float z = mref == -INFINITY ? 0.f : mref;
-                    float2 ps2 = make_float2(0.f, 0.f);
-                    if (kind == kAll) chunk_exp<kAll>(s, t, k0, mask, W, S, N, sc2, z, ps2, pk);
-                    else chunk_exp<kSome>(s, t, k0, mask, W, S, N, sc2, z, ps2, pk);
-                    l += ps2.x + ps2.y;
-                }
-                tmem_st16(tl + 32u * (uint32_t)bi, pk);  // P over the scores already read
-                tc::tmem_wait_st();
-                tc::tc_fence_before();
-                __syncwarp();
-                if (lane == 0) tc::mbar_arrive(&pb[bi]);
-                bi = b1;
-                q = q1;
-            }
-            if (s_err) break;
-            // O is complete once the commit of step n + 1 (after the last P V) lands
-            if (!mwait(&sb[(st.n + 1) % kRing], spar(st.n + 1))) fail(45);
-            tc::tc_fence_after();
-            float o[16];
-            tc::tmem_ld16(tl + kOcol, o);
-            tc::tmem_wait_ld();
+            float mref, l, o[DH];
+            if (!fwd_tile_softmax<DH>(tl, st.n, [&](int i) { return st.key0(i); }, t, t0w, mask, W, S, N, sbar[wg],
+                                      pbar[wg], sbits, err, &s_err, mref, l, o))
+                break;
             tc::tc_fence_before();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&obar[wg]);  // O read: the next tile may overwrite it
-            if (t < N) {
-                const float inv = 1.0f / l;
-                const size_t idx = ((size_t)b * N + t) * D + hh * DH;
-#pragma unroll
-                for (int c = 0; c < DH / 8; ++c) {
-                    float ov[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) ov[j] = o[8 * c + j] * inv;
-                    const float4 h0 = __ldg(reinterpret_cast<const float4 *>(Hin + idx) + 2 * c);
-                    const float4 h1 = __ldg(reinterpret_cast<const float4 *>(Hin + idx) + 2 * c + 1);
-                    reinterpret_cast<float4 *>(Hmid + idx)[2 * c] =
-                        make_float4(h0.x + ov[0], h0.y + ov[1], h0.z + ov[2], h0.w + ov[3]);
-                    reinterpret_cast<float4 *>(Hmid + idx)[2 * c + 1] =
-                        make_float4(h1.x + ov[4], h1.y + ov[5], h1.z + ov[6], h1.w + ov[7]);
-                    if (O)  // O in BF16, kept only for the backward's D_t
-                        *reinterpret_cast<uint4 *>(O + idx + 8 * c) =
-                            make_uint4(pack_bf2(ov[0], ov[1]), pack_bf2(ov[2], ov[3]), pack_bf2(ov[4], ov[5]),
-                                       pack_bf2(ov[6], ov[7]));
-                }
-                // natural log-sum-exp: (m + log2 l) ln 2
-                LSE[((size_t)b * N + t) * NH + hh] = (mref + log2f(l)) * 0.69314718055994531f;
-            }
-            advance(st.n);
+            if (t < N) fwd_row_out<DH>(o, mref, l, b, t, hh, N, D, NH, Hin, O, Hmid, LSE);
+            ring_advance(sbits, pbits, st.n);
         }
     }
     tc::tc_fence_before();
@@ -518,6 +580,100 @@ attn_fwd_tmem_kernel(const __nv_bfloat16 *__restrict__ QKVh, const float *__rest
     if (warp == 0) {
         tc::tc_fence_after();
         tc::tmem_dealloc(tslot, 256);
+    }
+}
+
+// Stage the CTA's query tile (rows qt * 128 .. + 127 of part 0, zero beyond N)
+// at sq and the K and V rows of its n visible 32-key chunks compactly (chunk
+// i at rows 32 i .. 32 i + 31 of sk, sv; zero beyond N).
+template <int DH, class Key0>
+__device__ __forceinline__ void stage_tile(unsigned char *sq, unsigned char *sk, unsigned char *sv,
+                                           const __nv_bfloat16 *__restrict__ QKVh, int64_t b, int hh, int N, int D,
+                                           int qt, int n, Key0 key0)
+{
+    constexpr int CH = DH / 8;
+    for (int e = threadIdx.x; e < kT * CH; e += blockDim.x) {
+        const int row = e / CH, c = e % CH, t = qt * kT + row;
+        unsigned char *dst = sq + tc::cm_offset(row, 8 * c, CH);
+        if (t < N) tc::cp_async16(dst, QKVh + ((size_t)b * N + t) * 3 * D + hh * DH + 8 * c);
+        else *reinterpret_cast<uint4 *>(dst) = make_uint4(0, 0, 0, 0);
+    }
+    const int per_part = n * 32 * CH;
+    for (int e = threadIdx.x; e < 2 * per_part; e += blockDim.x) {
+        const int part = e / per_part, rem = e % per_part, row = rem / CH, c = rem % CH;
+        const int k = key0(row >> 5) + (row & 31);
+        unsigned char *dst = (part ? sv : sk) + tc::cm_offset(row, 8 * c, CH);
+        if (k < N) tc::cp_async16(dst, QKVh + ((size_t)b * N + k) * 3 * D + (1 + part) * D + hh * DH + 8 * c);
+        else *reinterpret_cast<uint4 *>(dst) = make_uint4(0, 0, 0, 0);
+    }
+    tc::cp_async_commit();
+}
+
+// Forward for sequences longer than a CTA can stage whole, under the band +
+// sink mask: one CTA per (sample, head, query tile) with one softmax
+// warpgroup and one MMA warp (the pipeline above), staging only the tile's
+// queries and the keys and values of its visible chunks.
+template <int DH>
+__global__ void __launch_bounds__(160, 3)
+attn_fwd_band_kernel(const __nv_bfloat16 *__restrict__ QKVh, const float *__restrict__ Hin,
+                     __nv_bfloat16 *__restrict__ O, float *__restrict__ Hmid, float *__restrict__ LSE, int N, int D,
+                     int NH, int mask, int W, int S, int *err)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint64_t sbar[kRing], pbar[kRing], obar, dbar;
+    __shared__ uint32_t tslot;
+    __shared__ int s_err;
+    const int nq = (N + kT - 1) / kT;
+    const int qt = (int)(blockIdx.x % nq);
+    const int64_t bh = blockIdx.x / nq;
+    const int64_t b = bh / NH;
+    const int hh = (int)(bh % NH);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, r = tid & 127;
+    const TileSteps st(mask, W, S, N, qt);
+    if (tid == 0) {
+        for (int i = 0; i < kRing; ++i) {
+            tc::mbar_init(&sbar[i], 1);
+            tc::mbar_init(&pbar[i], 4);
+        }
+        tc::mbar_init(&obar, 4);
+        tc::mbar_init(&dbar, 1);
+        tc::fence_mbar_init();
+        s_err = 0;
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(&tslot, 128);
+        tc::tmem_relinquish();
+    }
+    unsigned char *sq = smem, *sk = sq + kT * DH * 2, *sv = sk + st.n * 32 * DH * 2;
+    stage_tile<DH>(sq, sk, sv, QKVh, b, hh, N, D, qt, st.n, [&](int i) { return st.key0(i); });
+    tc::cp_async_wait<0>();
+    tc::fence_async_smem();
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tm = tslot;
+    if (warp == 4) {
+        if (lane == 0) {
+            fwd_tile_mma<DH>(tm, desc_k<DH>(tc::smem_u32(sq), 0, 0), desc_k<DH>(tc::smem_u32(sk), 0, 0),
+                             desc_mn<DH>(tc::smem_u32(sv), 0, 0), st.n, [](int i) { return 32 * i; }, sbar, pbar, &obar,
+                             0, 0u, 0u, err, &s_err);
+            tc::mma_commit(&dbar);
+            tc::mbar_wait(&dbar, 0, 1u << 22);
+        }
+    } else {
+        const uint32_t tl = tm + ((uint32_t)(32 * warp) << 16);
+        const int t = qt * kT + r, t0w = qt * kT + 32 * warp;
+        float mref, l, o[DH];
+        if (fwd_tile_softmax<DH>(tl, st.n, [&](int i) { return st.key0(i); }, t, t0w, mask, W, S, N, sbar, pbar, 0u,
+                                 err, &s_err, mref, l, o) &&
+            t < N)
+            fwd_row_out<DH>(o, mref, l, b, t, hh, N, D, NH, Hin, O, Hmid, LSE);
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tslot, 128);
     }
 }
 
@@ -718,7 +874,7 @@ attn_bwd_tmem_kernel(const __nv_bfloat16 *__restrict__ QKVh, const __nv_bfloat16
                     tc::mma_commit(&bar[wg]);
                 }
                 __syncwarp();
-                if (!wg_wait(&bar[wg], phase, err, 43)) s_err[wg] = 1;
+                if (!wg_wait(&bar[wg], phase, err, kWaitCode + 8 * 61)) s_err[wg] = 1;
 #pragma unroll 1
                 for (int c = 0; c < 2; ++c) {
                     const int tq = q0 + 32 * c;  // this chunk's first query
@@ -757,7 +913,7 @@ attn_bwd_tmem_kernel(const __nv_bfloat16 *__restrict__ QKVh, const __nv_bfloat16
                     tc::mma_commit(&bar[wg]);
                 }
                 __syncwarp();
-                if (!wg_wait(&bar[wg], phase, err, 44)) s_err[wg] = 1;
+                if (!wg_wait(&bar[wg], phase, err, kWaitCode + 8 * 62)) s_err[wg] = 1;
                 {
                     float x[DH];
                     tmem_ld_dh<DH>(tl + 32, x);
@@ -797,7 +953,7 @@ attn_bwd_tmem_kernel(const __nv_bfloat16 *__restrict__ QKVh, const __nv_bfloat16
                     tc::mma_commit(&bar[wg]);
                 }
                 __syncwarp();
-                if (!wg_wait(&bar[wg], phase, err, 45)) s_err[wg] = 1;
+                if (!wg_wait(&bar[wg], phase, err, kWaitCode + 8 * 63)) s_err[wg] = 1;
 #pragma unroll 1
                 for (int c = 0; c < 2; ++c) {
                     const int kc = k0 + 32 * c;  // this chunk's first key
@@ -829,7 +985,7 @@ attn_bwd_tmem_kernel(const __nv_bfloat16 *__restrict__ QKVh, const __nv_bfloat16
                     tc::mma_commit(&bar[wg]);
                 }
                 __syncwarp();
-                if (!wg_wait(&bar[wg], phase, err, 46)) s_err[wg] = 1;
+                if (!wg_wait(&bar[wg], phase, err, kWaitCode + 8 * 64)) s_err[wg] = 1;
                 {
                     float x[DH];
                     tmem_ld_dh<DH>(tl + 32, x);
@@ -862,6 +1018,371 @@ attn_bwd_tmem_kernel(const __nv_bfloat16 *__restrict__ QKVh, const __nv_bfloat16
     }
 }
 
+// ---------------------------------------------------------------------------
+// Backward for long band sequences (the gradient of attn_fwd_band_kernel).
+// One CTA (one warpgroup, 128 TMEM columns) per task; the tasks of a
+// (sample, head):
+//   query tile qt      dQ of queries qt * 128 + r over the tile's visible
+//                      32-key chunks (those of the forward)
+//   key tile kt        dK, dV of the band keys kt * 128 + r (S <= k < N)
+//                      over the queries that see them (k .. k + W)
+//   sink (qt, st)      query tile qt's part of dK, dV of the sink keys
+//                      st * 128 + r (k < S), added into an FP32 buffer that a
+//                      final pass turns into the sink keys' rows
+// Steps are 32 keys (query tiles) or 32 queries wide.  TMEM: scores at
+// [0, 32), dP at [32, 64); P^T in BF16 over [0, 16) and dS over [32, 48);
+// accumulators at 64 (dQ or dV) and 96 (dK).  Rows whose gradient a task does
+// not own (sink keys in a key tile, keys at or past N) compute unused values:
+// a row of dK or dV depends only on its own row of P^T and dS^T.
+// ---------------------------------------------------------------------------
+
+// Queries t0 .. t0 + cnt - 1 (zero beyond N) at rows 0 .. cnt - 1: Q (by
+// cp.async) into sq, dO in BF16 into sg, Ln = -log2(e) LSE and
+// Dn = -(dO . O) / sqrt(d_h) into Ln, Dn.
+template <int DH>
+__device__ __forceinline__ void stage_queries(unsigned char *sq, unsigned char *sg, float *Ln, float *Dn,
+                                              const __nv_bfloat16 *__restrict__ QKVh, const __nv_bfloat16 *__restrict__ O,
+                                              const float *__restrict__ dO, const float *__restrict__ LSE, int64_t b,
+                                              int hh, int N, int D, int NH, int t0, int cnt)
+{
+    constexpr int CH = DH / 8;
+    for (int e = threadIdx.x; e < cnt * CH; e += blockDim.x) {
+        const int row = e / CH, c = e % CH, t = t0 + row;
+        unsigned char *dst = sq + tc::cm_offset(row, 8 * c, CH);
+        if (t < N) tc::cp_async16(dst, QKVh + ((size_t)b * N + t) * 3 * D + hh * DH + 8 * c);
+        else *reinterpret_cast<uint4 *>(dst) = make_uint4(0, 0, 0, 0);
+    }
+    tc::cp_async_commit();
+    for (int row = threadIdx.x; row < cnt; row += blockDim.x) {
+        const int t = t0 + row;
+        float dd = 0.f, lse = 0.f;
+        if (t < N) {
+            const size_t rr = (size_t)b * N + t;
+            const float4 *gp = reinterpret_cast<const float4 *>(dO + rr * D + hh * DH);
+            const uint4 *op = reinterpret_cast<const uint4 *>(O + rr * D + hh * DH);
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const float4 g0 = gp[2 * c], g1 = gp[2 * c + 1];
+                const uint4 ow = op[c];
+                const uint32_t w[4] = {ow.x, ow.y, ow.z, ow.w};
+                float ov[8];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    ov[2 * j] = __uint_as_float(w[j] << 16);
+                    ov[2 * j + 1] = __uint_as_float(w[j] & 0xffff0000u);
+                }
+                dd += g0.x * ov[0] + g0.y * ov[1] + g0.z * ov[2] + g0.w * ov[3];
+                dd += g1.x * ov[4] + g1.y * ov[5] + g1.z * ov[6] + g1.w * ov[7];
+                *reinterpret_cast<uint4 *>(sg + tc::cm_offset(row, 8 * c, CH)) = make_uint4(
+                    pack_bf2(g0.x, g0.y), pack_bf2(g0.z, g0.w), pack_bf2(g1.x, g1.y), pack_bf2(g1.z, g1.w));
+            }
+            lse = LSE[rr * NH + hh];
+        } else {
+#pragma unroll
+            for (int c = 0; c < CH; ++c)
+                *reinterpret_cast<uint4 *>(sg + tc::cm_offset(row, 8 * c, CH)) = make_uint4(0, 0, 0, 0);
+        }
+        Ln[row] = -lse * kLog2e;
+        Dn[row] = -dd * rsqrtf((float)DH);
+    }
+}
+
+// Keys key0(i) + j, i < nchunks, j < 32 (zero at or beyond klim) at rows
+// 32 i + j of sk (part 1) and sv (part 2).
+template <int DH, class Key0>
+__device__ __forceinline__ void stage_keys(unsigned char *sk, unsigned char *sv, const __nv_bfloat16 *__restrict__ QKVh,
+                                           int64_t b, int hh, int N, int D, int nchunks, Key0 key0, int klim)
+{
+    constexpr int CH = DH / 8;
+    const int per_part = nchunks * 32 * CH;
+    for (int e = threadIdx.x; e < 2 * per_part; e += blockDim.x) {
+        const int part = e / per_part, rem = e % per_part, row = rem / CH, c = rem % CH;
+        const int k = key0(row >> 5) + (row & 31);
+        unsigned char *dst = (part ? sv : sk) + tc::cm_offset(row, 8 * c, CH);
+        if (k < klim) tc::cp_async16(dst, QKVh + ((size_t)b * N + k) * 3 * D + (1 + part) * D + hh * DH + 8 * c);
+        else *reinterpret_cast<uint4 *>(dst) = make_uint4(0, 0, 0, 0);
+    }
+    tc::cp_async_commit();
+}
+
+// Key rows: P^T and dS^T of 32 queries (compact rows q0 .. q0 + 31 of Ln, Dn;
+// query indices tq .. tq + 31) for this thread's key k; kSome chunks mask
+// query t by vis(t).
+template <int KIND, class Vis>
+__device__ __forceinline__ void key_grads32(const float (&s)[32], const float (&dp)[32], const float *Ln,
+                                            const float *Dn, int q0, int tq, Vis vis, float sc2, float scale,
+                                            uint32_t (&pp)[16], uint32_t (&dd)[16])
+{
+    const float2 a2 = make_float2(sc2, sc2), c2 = make_float2(scale, scale);
+#pragma unroll
+    for (int j4 = 0; j4 < 8; ++j4) {
+        const float4 l4 = *reinterpret_cast<const float4 *>(Ln + q0 + 4 * j4);
+        const float4 d4 = *reinterpret_cast<const float4 *>(Dn + q0 + 4 * j4);
+#pragma unroll
+        for (int e2 = 0; e2 < 2; ++e2) {
+            const int j = 4 * j4 + 2 * e2;
+            float2 x = __ffma2_rn(make_float2(s[j], s[j + 1]), a2,
+                                  e2 ? make_float2(l4.z, l4.w) : make_float2(l4.x, l4.y));
+            if constexpr (KIND == kSome) {
+                if (!vis(tq + j)) x.x = -INFINITY;
+                if (!vis(tq + j + 1)) x.y = -INFINITY;
+            }
+            const float2 p = make_float2(ex2_approx(x.x), ex2_approx(x.y));
+            const float2 g = __ffma2_rn(make_float2(dp[j], dp[j + 1]), c2,
+                                        e2 ? make_float2(d4.z, d4.w) : make_float2(d4.x, d4.y));
+            const float2 ds = __fmul2_rn(p, g);
+            pp[j / 2] = pack_bf2(p.x, p.y);
+            dd[j / 2] = pack_bf2(ds.x, ds.y);
+        }
+    }
+}
+
+// Largest number of visible 32-key chunks of a query tile (query tasks) and
+// of 32-query chunks that see a key tile (key tasks) under the band mask.
+__host__ __device__ __forceinline__ int band_query_chunks(int W, int S, int N, int kt)
+{
+    const int qc0 = 4 * kt, qc1 = min((N + 31) / 32, (kt * kT + kT - 1 + W) / 32 + 1);
+    return max(0, qc1 - qc0);
+}
+
+template <int DH>
+__global__ void __launch_bounds__(128, 3)
+attn_bwd_band_kernel(const __nv_bfloat16 *__restrict__ QKVh, const __nv_bfloat16 *__restrict__ O,
+                     const float *__restrict__ dO, const float *__restrict__ LSE, unsigned char *__restrict__ dQKVt,
+                     float *__restrict__ bsum, float *__restrict__ sinkacc, int N, int D, int NH, int mask, int W, int S,
+                     int nq, int nst, int *err)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ float csum[3 * DH];
+    __shared__ uint64_t bar, dbar;
+    __shared__ uint32_t tslot;
+    __shared__ int s_err;
+    const int tasks = 2 * nq + nq * nst;
+    const int task = (int)(blockIdx.x % tasks);
+    const int64_t bh = blockIdx.x / tasks;
+    const int64_t b = bh / NH;
+    const int hh = (int)(bh % NH);
+    const int tid = threadIdx.x, warp = tid >> 5, r = tid;
+    // 0: query tile, 1: key tile, 2: sink keys x query tile
+    const int kind_of_task = task < nq ? 0 : (task < 2 * nq ? 1 : 2);
+    const int tile = kind_of_task == 0 ? task : (kind_of_task == 1 ? task - nq : (task - 2 * nq) % nq);
+    const int stile = kind_of_task == 2 ? (task - 2 * nq) / nq : 0;
+    if (kind_of_task == 1 && min(N, tile * kT + kT) <= max(S, tile * kT)) return;  // no band key in the tile
+    if (kind_of_task == 2 && tile * kT + kT - 1 < stile * kT) return;              // queries all before the keys
+    if (tid == 0) {
+        tc::mbar_init(&bar, 1);
+        tc::mbar_init(&dbar, 1);
+        tc::fence_mbar_init();
+        s_err = 0;
+    }
+    for (int j = tid; j < 3 * DH; j += blockDim.x) csum[j] = 0.f;
+    if (warp == 0) {
+        tc::tmem_alloc(&tslot, 128);
+        tc::tmem_relinquish();
+    }
+    // shared memory: the 128-row operand tile(s) first, then the chunked rows
+    const TileSteps st(mask, W, S, N, tile);
+    int nsteps = 0;
+    unsigned char *sA = smem, *sB = sA + kT * DH * 2;  // query task: Q, dO tile; key tasks: K, V tile
+    unsigned char *sC = sB + kT * DH * 2;                 // query task: K chunks; key tasks: Q chunks
+    unsigned char *sD;                                    // V chunks / dO chunks
+    float *Ln, *Dn;
+    int q0row = 0;  // first query of the staged query rows (key tasks)
+    if (kind_of_task == 0) {
+        nsteps = st.n;
+        sD = sC + nsteps * 32 * DH * 2;
+        Ln = reinterpret_cast<float *>(sD + nsteps * 32 * DH * 2);
+        Dn = Ln + kT;
+        stage_queries<DH>(sA, sB, Ln, Dn, QKVh, O, dO, LSE, b, hh, N, D, NH, tile * kT, kT);
+        stage_keys<DH>(sC, sD, QKVh, b, hh, N, D, nsteps, [&](int i) { return st.key0(i); }, N);
+    } else {
+        const int k0 = kind_of_task == 1 ? tile * kT : stile * kT;
+        stage_keys<DH>(sA, sB, QKVh, b, hh, N, D, 4, [&](int i) { return k0 + 32 * i; },
+                       kind_of_task == 1 ? N : min(S, N));
+        q0row = tile * kT;  // key tile: its first key; sink task: the query tile
+        nsteps = kind_of_task == 1 ? band_query_chunks(W, S, N, tile) : min(4, (N - tile * kT + 31) / 32);
+        sD = sC + nsteps * 32 * DH * 2;
+        Ln = reinterpret_cast<float *>(sD + nsteps * 32 * DH * 2);
+        Dn = Ln + nsteps * 32;
+        stage_queries<DH>(sC, sD, Ln, Dn, QKVh, O, dO, LSE, b, hh, N, D, NH, q0row, nsteps * 32);
+    }
+    tc::cp_async_wait<0>();
+    tc::fence_async_smem();
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tm = tslot, tl = tm + ((uint32_t)(32 * warp) << 16);
+    const float scale = rsqrtf((float)DH), sc2 = scale * kLog2e;
+    const uint32_t idesc_s = tc::idesc_bf16(kT, 32);
+    const uint32_t idesc_p = tc::idesc_bf16(kT, DH) | (1u << 16);  // B read MN-major
+    const uint32_t uA = tc::smem_u32(sA), uB = tc::smem_u32(sB), uC = tc::smem_u32(sC), uD = tc::smem_u32(sD);
+    uint32_t phase = 0;
+    auto wait_mma = [&](int code) {
+        if (!mwait(&bar, phase)) {
+            if ((tid & 31) == 0) atomicExch(err, code + (kind_of_task << 16));
+            s_err = 1;
+        }
+        phase ^= 1u;
+        tc::tc_fence_after();
+    };
+    for (int i = 0; i < nsteps; ++i) {
+        // scores: query task S = Q K_c^T, dP = dO V_c^T; key tasks S^T = K Q_c^T, dP^T = V dO_c^T
+        if (tid == 0) {
+#pragma unroll
+            for (int ks = 0; ks < DH / 16; ++ks) {
+                tc::mma_bf16(tm, desc_k<DH>(uA, 0, ks), desc_k<DH>(uC, 32 * i, ks), idesc_s, ks > 0 ? 1u : 0u);
+                tc::mma_bf16(tm + 32, desc_k<DH>(uB, 0, ks), desc_k<DH>(uD, 32 * i, ks), idesc_s, ks > 0 ? 1u : 0u);
+            }
+            tc::mma_commit(&bar);
+        }
+        __syncwarp();
+        wait_mma(kWaitCode + 8 * 51);
+        float sv[32], dp[32];
+        uint32_t pp[16], dd[16];
+        bool any;
+        if (kind_of_task == 0) {
+            const int t = tile * kT + r, t0w = tile * kT + 32 * warp, k0 = st.key0(i);
+            const int kind = chunk_kind(mask, W, S, N, t0w, k0);
+            any = kind != kNone;
+            if (any) {
+                tc::tmem_ld32(tl, sv);
+                tc::tmem_ld32(tl + 32, dp);
+                tc::tmem_wait_ld();
+                if (kind == kAll) query_grads32<kAll>(sv, dp, t, k0, mask, W, S, N, sc2, scale, Ln[r], Dn[r], dd);
+                else query_grads32<kSome>(sv, dp, t, k0, mask, W, S, N, sc2, scale, Ln[r], Dn[r], dd);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) dd[j] = 0u;
+            }
+            tmem_st16(tl + 32, dd);  // dS over dP already read
+        } else {
+            const int k = (kind_of_task == 1 ? tile : stile) * kT + r;
+            const int k0w = (kind_of_task == 1 ? tile : stile) * kT + 32 * warp, tq = q0row + 32 * i;
+            // key tiles: band keys (query t sees key k iff 0 <= t - k <= W);
+            // sink tiles: sink keys (t >= k); other rows are not this task's
+            const int kind = kind_of_task == 1 ? chunk_kind(mask, W, 0, N, tq, k0w)
+                                               : chunk_kind(SG_MASK_DENSE, W, 0, N, tq, k0w);
+            any = kind != kNone;
+            if (any) {
+                tc::tmem_ld32(tl, sv);
+                tc::tmem_ld32(tl + 32, dp);
+                tc::tmem_wait_ld();
+                const uint32_t lim = kind_of_task == 1 ? (uint32_t)W : 0x7fffffffu;
+                auto vis = [&](int t) { return (uint32_t)(t - k) <= lim && t < N; };
+                if (kind == kAll) key_grads32<kAll>(sv, dp, Ln, Dn, 32 * i, tq, vis, sc2, scale, pp, dd);
+                else key_grads32<kSome>(sv, dp, Ln, Dn, 32 * i, tq, vis, sc2, scale, pp, dd);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) pp[j] = dd[j] = 0u;
+            }
+            tmem_st16(tl, pp);       // P^T over S^T already read
+            tmem_st16(tl + 32, dd);  // dS^T over dP^T already read
+        }
+        tc::tmem_wait_st();
+        tc::tc_fence_before();
+        wg_sync(0);
+        if (s_err) break;
+        // products, accumulated in TMEM over the steps (K = 32 in two 16-row steps)
+        if (tid == 0) {
+            tc::tc_fence_after();
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+                const uint32_t acc = (i > 0 || ks > 0) ? 1u : 0u;
+                if (kind_of_task == 0) {
+                    mma_bf16_ta(tm + 64, tm + 32 + 8 * ks, desc_mn<DH>(uC, 32 * i, ks), idesc_p, acc);  // dQ += dS K
+                } else {
+                    mma_bf16_ta(tm + 64, tm + 8 * ks, desc_mn<DH>(uD, 32 * i, ks), idesc_p, acc);       // dV += P^T dO
+                    mma_bf16_ta(tm + 96, tm + 32 + 8 * ks, desc_mn<DH>(uC, 32 * i, ks), idesc_p, acc);  // dK += dS^T Q
+                }
+            }
+            tc::mma_commit(&bar);
+        }
+        // The next step's scores overwrite what these products read.  Thread 0
+        // waits for them and issues those scores after the barrier, so no
+        // thread can still be polling this phase when the next one completes
+        // (a parity wait cannot tell a phase from the one two later).
+        if (tid == 0) wait_mma(kWaitCode + 8 * 52);
+        else phase ^= 1u;
+        tc::tc_fence_before();
+        wg_sync(0);
+        tc::tc_fence_after();
+        if (s_err) break;
+    }
+    if (!s_err) {
+        if (kind_of_task == 0) {
+            float x[DH];
+            tmem_ld_dh<DH>(tl + 64, x);
+            tc::tmem_wait_ld();
+            const int t = tile * kT + r;
+            if (nsteps == 0 || t >= N) {
+#pragma unroll
+                for (int j = 0; j < DH; ++j) x[j] = 0.f;
+            }
+            put_rows<DH>(x, b, hh, N, D, t < N ? t : N, 0, dQKVt, csum);
+        } else {
+            float xv[DH], xk[DH];
+            tmem_ld_dh<DH>(tl + 64, xv);
+            tmem_ld_dh<DH>(tl + 96, xk);
+            tc::tmem_wait_ld();
+            const int k = (kind_of_task == 1 ? tile : stile) * kT + r;
+            const bool own = kind_of_task == 1 ? (k >= S && k < N) : (k < S && k < N);
+            if (!own || nsteps == 0) {
+#pragma unroll
+                for (int j = 0; j < DH; ++j) xv[j] = xk[j] = 0.f;
+            }
+            if (kind_of_task == 1) {
+                put_rows<DH>(xk, b, hh, N, D, own ? k : N, 1, dQKVt, csum);
+                put_rows<DH>(xv, b, hh, N, D, own ? k : N, 2, dQKVt, csum);
+            } else if (own) {
+                float *dst = sinkacc + ((size_t)bh * S + k) * 2 * DH;
+#pragma unroll
+                for (int j = 0; j < DH; ++j) {
+                    atomicAdd(dst + j, xk[j]);
+                    atomicAdd(dst + DH + j, xv[j]);
+                }
+            }
+        }
+    }
+    if (s_err && tid == 0) {  // let this thread's MMAs land before TMEM is freed
+        tc::mma_commit(&dbar);
+        tc::mbar_wait(&dbar, 0, 1u << 20);
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (kind_of_task != 2)
+        for (int j = tid; j < 3 * DH; j += blockDim.x)
+            if (csum[j] != 0.f) atomicAdd(bsum + (size_t)b * 3 * D + (j / DH) * D + hh * DH + j % DH, csum[j]);
+    if (warp == 0) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tslot, 128);
+    }
+}
+
+// The sink keys' rows: dK, dV (parts 1, 2) of keys k < S from the FP32 buffer
+// into the wide BF16 dQKVt, and their column sums into bsum.  One CTA per
+// (sample, head).
+template <int DH>
+__global__ void __launch_bounds__(128)
+attn_band_sink_rows_kernel(const float *__restrict__ sinkacc, unsigned char *__restrict__ dQKVt,
+                           float *__restrict__ bsum, int N, int D, int NH, int S)
+{
+    const int64_t bh = blockIdx.x, b = bh / NH;
+    const int hh = (int)(bh % NH), ns = min(S, N);
+    const float *src = sinkacc + (size_t)bh * S * 2 * DH;
+    for (int e = threadIdx.x; e < ns * 2 * (DH / 8); e += blockDim.x) {
+        const int k = e / (2 * (DH / 8)), c8 = e % (2 * (DH / 8));  // c8 < DH / 8: dK, else dV
+        const float *v = src + (size_t)k * 2 * DH + 8 * c8;
+        const int part = 1 + c8 / (DH / 8), col = part * D + hh * DH + 8 * (c8 % (DH / 8));
+        *reinterpret_cast<uint4 *>(dQKVt + wl_offset(b * N + k, col, 3 * D)) =
+            make_uint4(pack_bf2(v[0], v[1]), pack_bf2(v[2], v[3]), pack_bf2(v[4], v[5]), pack_bf2(v[6], v[7]));
+    }
+    for (int j = threadIdx.x; j < 2 * DH; j += blockDim.x) {
+        float sum = 0.f;
+        for (int k = 0; k < ns; ++k) sum += src[(size_t)k * 2 * DH + j];
+        atomicAdd(bsum + (size_t)b * 3 * D + (1 + j / DH) * D + hh * DH + j % DH, sum);
+    }
+}
+
 size_t tmem_smem_bytes(int DH, int N, bool bwd)
 {
     const size_t Npad = (size_t)(N + kT - 1) / kT * kT;
@@ -881,6 +1402,39 @@ int tmem_samples_per_wave(K kern, int threads, size_t smem, int NH)
 
 }  // namespace
 
+// Largest number of visible 32-key chunks of a query tile (TileSteps).
+static int band_max_tile_chunks(const sg_config &c)
+{
+    const int nq = (c.N + kT - 1) / kT;
+    int best = 0;
+    for (int qt = 0; qt < nq; ++qt) {
+        const int tile0 = qt * kT, tile1 = std::min(tile0 + kT, c.N) - 1;
+        const int cend = std::min(4 * (qt + 1), (c.N + 31) / 32);
+        const int ns = (std::min(c.S, tile1 + 1) + 31) / 32;
+        const int bstart = std::max(ns, std::max(0, tile0 - c.W) / 32);
+        best = std::max(best, ns + std::max(0, cend - bstart));
+    }
+    return best;
+}
+
+static size_t band_fwd_smem(const sg_config &c)
+{
+    const int dh = c.d / c.n_heads;
+    return (size_t)kT * dh * 2 + (size_t)2 * band_max_tile_chunks(c) * 32 * dh * 2;
+}
+
+static size_t band_bwd_smem(const sg_config &c)
+{
+    const int dh = c.d / c.n_heads, nq = (c.N + kT - 1) / kT;
+    int nqc = 0;
+    for (int kt = 0; kt < nq; ++kt) nqc = std::max(nqc, band_query_chunks(c.W, c.S, c.N, kt));
+    const size_t tile = (size_t)2 * kT * dh * 2;
+    const size_t q = tile + (size_t)2 * band_max_tile_chunks(c) * 32 * dh * 2 + 2 * kT * sizeof(float);
+    const size_t k = tile + (size_t)2 * nqc * 32 * dh * 2 + (size_t)2 * nqc * 32 * sizeof(float);
+    const size_t sk = tile + (size_t)2 * 4 * 32 * dh * 2 + 2 * kT * sizeof(float);
+    return std::max(q, std::max(k, sk));
+}
+
 // The tcgen05 attention serves BF16 models with d_h = 16 under the dense
 // causal mask from 128 positions on (a query sees on average N / 2 keys).
 // Band masks stay on the warp-level MMA kernels: their 16-key blocks follow
@@ -893,6 +1447,54 @@ bool attn_tmem_supported(const sg_config &c)
     const int dh = c.d / c.n_heads;
     return c.precision == SG_BF16 && dh == 16 && c.d % 8 == 0 && c.mask_kind == SG_MASK_DENSE &&
            c.N >= kT && tmem_smem_bytes(dh, c.N, true) <= 200 * 1024;
+}
+
+// Band masks on sequences beyond the staged kernels' shared memory: the
+// per-tile tcgen05 kernels, where a tile's keys (and a key tile's queries)
+// fit in 72 KB.
+bool attn_band_supported(const sg_config &c)
+{
+    const int dh = c.d / c.n_heads;
+    return c.precision == SG_BF16 && (dh == 16 || dh == 32) && c.d % 8 == 0 && c.mask_kind != SG_MASK_DENSE &&
+           c.N >= 1 && !attn_mma_supported(c) && band_bwd_smem(c) <= 72 * 1024;
+}
+
+sg_status launch_attn_fwd_band(const sg_config &c, const __nv_bfloat16 *QKVh, const float *Hin, __nv_bfloat16 *O,
+                               float *Hmid, float *LSE, int Bc, int *err, cudaStream_t st)
+{
+    const int dh = c.d / c.n_heads, nq = (c.N + kT - 1) / kT;
+    const size_t smem = band_fwd_smem(c);
+    auto go = [&](auto kern) -> sg_status {
+        SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<(unsigned)((int64_t)Bc * c.n_heads * nq), 160, smem, ::sg::counted(st)>>>(
+            QKVh, Hin, O, Hmid, LSE, c.N, c.d, c.n_heads, c.mask_kind, c.W, c.S, err);
+        return check_launch("attn_fwd_band_kernel");
+    };
+    return dh == 16 ? go(attn_fwd_band_kernel<16>) : go(attn_fwd_band_kernel<32>);
+}
+
+sg_status launch_attn_bwd_band(const sg_config &c, const __nv_bfloat16 *QKVh, const __nv_bfloat16 *O,
+                               const float *dO, const float *LSE, unsigned char *dQKVt, float *bsum,
+                               float *sinkacc, int Bc, int *err, cudaStream_t st)
+{
+    const int dh = c.d / c.n_heads, nq = (c.N + kT - 1) / kT, nst = (c.S + kT - 1) / kT;
+    const size_t smem = band_bwd_smem(c);
+    SG_CUDA_TRY(cudaMemsetAsync(bsum, 0, (size_t)Bc * 3 * c.d * sizeof(float), st));
+    if (nst > 0) SG_CUDA_TRY(cudaMemsetAsync(sinkacc, 0, (size_t)Bc * c.S * 2 * c.d * sizeof(float), st));
+    auto go = [&](auto kern, auto fin) -> sg_status {
+        SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<(unsigned)((int64_t)Bc * c.n_heads * (2 * nq + nq * nst)), 128, smem, ::sg::counted(st)>>>(
+            QKVh, O, dO, LSE, dQKVt, bsum, sinkacc, c.N, c.d, c.n_heads, c.mask_kind, c.W, c.S, nq, nst, err);
+        SG_TRY(check_launch("attn_bwd_band_kernel"));
+        if (nst > 0) {
+            fin<<<(unsigned)((int64_t)Bc * c.n_heads), 128, 0, ::sg::counted(st)>>>(sinkacc, dQKVt, bsum, c.N, c.d,
+                                                                                   c.n_heads, c.S);
+            SG_TRY(check_launch("attn_band_sink_rows_kernel"));
+        }
+        return SG_OK;
+    };
+    return dh == 16 ? go(attn_bwd_band_kernel<16>, attn_band_sink_rows_kernel<16>)
+                    : go(attn_bwd_band_kernel<32>, attn_band_sink_rows_kernel<32>);
 }
 
 sg_status launch_attn_fwd_tmem(const sg_config &c, const __nv_bfloat16 *QKVh, const float *Hin,

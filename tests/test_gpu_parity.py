@@ -611,9 +611,11 @@ BF16_TF_MODELS = [inputs.ModelShape(20, 2, 32, 4), inputs.ModelShape(40, 2, 64, 
                   inputs.ModelShape(300, 1, 64, 4, mask_kind=1, W=70, S=9),
                   inputs.ModelShape(333, 1, 128, 8, mask_kind=1, W=100, S=37),
                   inputs.ModelShape(140, 1, 256, 8),
-                  # a sequence beyond the MMA kernels' shared memory (d_h = 32):
-                  # the tcgen05 flash attention
-                  inputs.ModelShape(650, 1, 64, 2, mask_kind=1, W=70, S=9)]
+                  # sequences beyond the MMA kernels' shared memory (d_h = 32): a
+                  # band (the per-tile tcgen05 kernels) and a dense one (the
+                  # tcgen05 flash attention)
+                  inputs.ModelShape(650, 1, 64, 2, mask_kind=1, W=70, S=9),
+                  inputs.ModelShape(650, 1, 64, 2)]
 
 
 @pytest.mark.parametrize("m", BF16_TF_MODELS)
@@ -641,6 +643,45 @@ def test_bf16_teacher_forced_logq_and_grad(m):
     assert rel < 2e-2
     assert_grad_blocks(m, g, go, BF16_GRAD_BLOCK_TOL)
     assert np.abs(_np(logq) - lqo).max() <= BF16_LOGQ_TOL * m.N
+
+
+LONG_BAND_MODELS = [
+    # d_h = 16 past the MMA kernels' 1200 positions, a ragged last tile
+    inputs.ModelShape(1300, 1, 64, 4, mask_kind=1, W=60, S=33),
+    # d_h = 32: two sink tiles (S = 150), two layers
+    inputs.ModelShape(700, 2, 64, 2, mask_kind=1, W=60, S=150),
+    # no sink
+    inputs.ModelShape(640, 1, 64, 2, mask_kind=1, W=50, S=0),
+    # the 2D EA L=64 widths and mask (d 256 is d_h 32 as here), 900 positions
+    inputs.ModelShape(900, 1, 128, 4, mask_kind=1, W=64, S=65),
+]
+
+
+@pytest.mark.parametrize("m", LONG_BAND_MODELS)
+def test_bf16_long_band_attention_logq_and_grad(m):
+    """Band sequences too long to stage whole run on the per-tile tcgen05
+    kernels (a CTA per sample, head and 128-query tile; sink keys' gradients
+    gathered over the query tiles): log q and the REINFORCE gradient against
+    the oracle within the BF16 bounds, the gradient also per weight tensor."""
+    w = inputs.make_weights(m, 6)
+    B = 40
+    s = inputs.random_spins(B, m.N, 13)
+    c = np.random.default_rng(5).normal(0, 1, B).astype(np.float32)
+    model = sg.Model(m, w, sg.SG_BF16)
+    ts = torch.tensor(s, device="cuda")
+    lq = _np(model.logprob(ts))
+    lqo = oracle.logprob(ocfg(m), w, s)
+    assert np.abs(lq - lqo).max() <= BF16_LOGQ_TOL * m.N
+    logq = torch.empty(B, dtype=torch.float32, device="cuda")
+    g = _np(model.grad(ts, torch.tensor(c, device="cuda"), logq=logq))
+    model.check()
+    go, _ = oracle.grad(ocfg(m), w, s, c.astype(np.float64))
+    rel = np.linalg.norm(g - go) / np.linalg.norm(go)
+    print(f"N={m.N} d={m.d} h={m.n_heads} W={m.W} S={m.S}: max|dlogq|/N "
+          f"{np.abs(lq - lqo).max() / m.N:.2e}, grad rel err {rel:.2e}")
+    assert rel < 2e-2
+    assert_grad_blocks(m, g, go, BF16_GRAD_BLOCK_TOL)
+    assert np.array_equal(_np(logq), lq)
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
