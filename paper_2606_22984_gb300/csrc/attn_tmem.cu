@@ -1026,9 +1026,12 @@ attn_bwd_tmem_kernel(const __nv_bfloat16 *__restrict__ QKVh, const __nv_bfloat16
 //                      32-key chunks (those of the forward)
 //   key tile kt        dK, dV of the band keys kt * 128 + r (S <= k < N)
 //                      over the queries that see them (k .. k + W)
-//   sink (qt, st)      query tile qt's part of dK, dV of the sink keys
-//                      st * 128 + r (k < S), added into an FP32 buffer that a
-//                      final pass turns into the sink keys' rows
+//   sink tile st       dK, dV of the sink keys st * 128 + r (k < S) over
+//                      every query tile from st on (128 queries staged per
+//                      tile); these tasks run longest and come first in the
+//                      grid.  Every row is summed in one fixed order, so the
+//                      gradient does not depend on scheduling (only the bias
+//                      column sums are gathered by FP32 atomics).
 // Steps are 32 keys (query tiles) or 32 queries wide.  TMEM: scores at
 // [0, 32), dP at [32, 64); P^T in BF16 over [0, 16) and dS over [32, 48);
 // accumulators at 64 (dQ or dV) and 96 (dK).  Rows whose gradient a task does
@@ -1149,26 +1152,36 @@ template <int DH>
 __global__ void __launch_bounds__(128, 3)
 attn_bwd_band_kernel(const __nv_bfloat16 *__restrict__ QKVh, const __nv_bfloat16 *__restrict__ O,
                      const float *__restrict__ dO, const float *__restrict__ LSE, unsigned char *__restrict__ dQKVt,
-                     float *__restrict__ bsum, float *__restrict__ sinkacc, int N, int D, int NH, int mask, int W, int S,
-                     int nq, int nst, int *err)
+                     float *__restrict__ bsum, int N, int D, int NH, int mask, int W, int S, int nq, int nst,
+                     int64_t nbh, int *err)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ float csum[3 * DH];
     __shared__ uint64_t bar, dbar;
     __shared__ uint32_t tslot;
     __shared__ int s_err;
-    const int tasks = 2 * nq + nq * nst;
-    const int task = (int)(blockIdx.x % tasks);
-    const int64_t bh = blockIdx.x / tasks;
+    // the sink tasks (one per sample, head and sink tile, each over every
+    // query tile from its own on) come first in the grid: they run longest
+    const int64_t nsink = nbh * nst;
+    int kind_of_task, tile, stile = 0;
+    int64_t bh;
+    if ((int64_t)blockIdx.x < nsink) {
+        kind_of_task = 2;  // sink keys stile * 128 + r
+        bh = blockIdx.x / nst;
+        stile = (int)(blockIdx.x % nst);
+        tile = stile;
+    } else {
+        const int64_t rr = blockIdx.x - nsink;
+        bh = rr / (2 * nq);
+        const int task = (int)(rr % (2 * nq));
+        kind_of_task = task < nq ? 0 : 1;  // query tile / key tile
+        tile = task % nq;
+    }
     const int64_t b = bh / NH;
     const int hh = (int)(bh % NH);
     const int tid = threadIdx.x, warp = tid >> 5, r = tid;
-    // 0: query tile, 1: key tile, 2: sink keys x query tile
-    const int kind_of_task = task < nq ? 0 : (task < 2 * nq ? 1 : 2);
-    const int tile = kind_of_task == 0 ? task : (kind_of_task == 1 ? task - nq : (task - 2 * nq) % nq);
-    const int stile = kind_of_task == 2 ? (task - 2 * nq) / nq : 0;
     if (kind_of_task == 1 && min(N, tile * kT + kT) <= max(S, tile * kT)) return;  // no band key in the tile
-    if (kind_of_task == 2 && tile * kT + kT - 1 < stile * kT) return;              // queries all before the keys
+    if (kind_of_task == 2 && stile * kT >= min(S, N)) return;                      // no sink key in the tile
     if (tid == 0) {
         tc::mbar_init(&bar, 1);
         tc::mbar_init(&dbar, 1);
@@ -1187,7 +1200,6 @@ attn_bwd_band_kernel(const __nv_bfloat16 *__restrict__ QKVh, const __nv_bfloat16
     unsigned char *sC = sB + kT * DH * 2;                 // query task: K chunks; key tasks: Q chunks
     unsigned char *sD;                                    // V chunks / dO chunks
     float *Ln, *Dn;
-    int q0row = 0;  // first query of the staged query rows (key tasks)
     if (kind_of_task == 0) {
         nsteps = st.n;
         sD = sC + nsteps * 32 * DH * 2;
@@ -1196,15 +1208,17 @@ attn_bwd_band_kernel(const __nv_bfloat16 *__restrict__ QKVh, const __nv_bfloat16
         stage_queries<DH>(sA, sB, Ln, Dn, QKVh, O, dO, LSE, b, hh, N, D, NH, tile * kT, kT);
         stage_keys<DH>(sC, sD, QKVh, b, hh, N, D, nsteps, [&](int i) { return st.key0(i); }, N);
     } else {
-        const int k0 = kind_of_task == 1 ? tile * kT : stile * kT;
+        const int k0 = tile * kT;
         stage_keys<DH>(sA, sB, QKVh, b, hh, N, D, 4, [&](int i) { return k0 + 32 * i; },
                        kind_of_task == 1 ? N : min(S, N));
-        q0row = tile * kT;  // key tile: its first key; sink task: the query tile
-        nsteps = kind_of_task == 1 ? band_query_chunks(W, S, N, tile) : min(4, (N - tile * kT + 31) / 32);
-        sD = sC + nsteps * 32 * DH * 2;
-        Ln = reinterpret_cast<float *>(sD + nsteps * 32 * DH * 2);
-        Dn = Ln + nsteps * 32;
-        stage_queries<DH>(sC, sD, Ln, Dn, QKVh, O, dO, LSE, b, hh, N, D, NH, q0row, nsteps * 32);
+        // key tile: the queries k0 .. k0 + 127 + W in one stage; sink tile:
+        // the query tiles from its own on, 128 queries (4 steps) per stage
+        const int staged = kind_of_task == 1 ? band_query_chunks(W, S, N, tile) : 4;
+        nsteps = kind_of_task == 1 ? staged : 4 * (nq - tile);
+        sD = sC + staged * 32 * DH * 2;
+        Ln = reinterpret_cast<float *>(sD + staged * 32 * DH * 2);
+        Dn = Ln + staged * 32;
+        stage_queries<DH>(sC, sD, Ln, Dn, QKVh, O, dO, LSE, b, hh, N, D, NH, k0, staged * 32);
     }
     tc::cp_async_wait<0>();
     tc::fence_async_smem();
@@ -1226,12 +1240,23 @@ attn_bwd_band_kernel(const __nv_bfloat16 *__restrict__ QKVh, const __nv_bfloat16
         tc::tc_fence_after();
     };
     for (int i = 0; i < nsteps; ++i) {
+        // a sink task restages the next query tile once the previous step's
+        // products (which read the staged rows) have landed (checked below)
+        if (kind_of_task == 2 && i > 0 && (i & 3) == 0) {
+            stage_queries<DH>(sC, sD, Ln, Dn, QKVh, O, dO, LSE, b, hh, N, D, NH, (tile + (i >> 2)) * kT, kT);
+            tc::cp_async_wait<0>();
+            tc::fence_async_smem();
+            tc::tc_fence_before();
+            __syncthreads();
+            tc::tc_fence_after();
+        }
+        const int crow = kind_of_task == 2 ? 32 * (i & 3) : 32 * i;  // the step's staged rows
         // scores: query task S = Q K_c^T, dP = dO V_c^T; key tasks S^T = K Q_c^T, dP^T = V dO_c^T
         if (tid == 0) {
 #pragma unroll
             for (int ks = 0; ks < DH / 16; ++ks) {
-                tc::mma_bf16(tm, desc_k<DH>(uA, 0, ks), desc_k<DH>(uC, 32 * i, ks), idesc_s, ks > 0 ? 1u : 0u);
-                tc::mma_bf16(tm + 32, desc_k<DH>(uB, 0, ks), desc_k<DH>(uD, 32 * i, ks), idesc_s, ks > 0 ? 1u : 0u);
+                tc::mma_bf16(tm, desc_k<DH>(uA, 0, ks), desc_k<DH>(uC, crow, ks), idesc_s, ks > 0 ? 1u : 0u);
+                tc::mma_bf16(tm + 32, desc_k<DH>(uB, 0, ks), desc_k<DH>(uD, crow, ks), idesc_s, ks > 0 ? 1u : 0u);
             }
             tc::mma_commit(&bar);
         }
@@ -1256,8 +1281,9 @@ attn_bwd_band_kernel(const __nv_bfloat16 *__restrict__ QKVh, const __nv_bfloat16
             }
             tmem_st16(tl + 32, dd);  // dS over dP already read
         } else {
-            const int k = (kind_of_task == 1 ? tile : stile) * kT + r;
-            const int k0w = (kind_of_task == 1 ? tile : stile) * kT + 32 * warp, tq = q0row + 32 * i;
+            const int k = tile * kT + r;
+            const int k0w = tile * kT + 32 * warp;
+            const int tq = kind_of_task == 1 ? tile * kT + 32 * i : (tile + (i >> 2)) * kT + crow;
             // key tiles: band keys (query t sees key k iff 0 <= t - k <= W);
             // sink tiles: sink keys (t >= k); other rows are not this task's
             const int kind = kind_of_task == 1 ? chunk_kind(mask, W, 0, N, tq, k0w)
@@ -1269,8 +1295,8 @@ attn_bwd_band_kernel(const __nv_bfloat16 *__restrict__ QKVh, const __nv_bfloat16
                 tc::tmem_wait_ld();
                 const uint32_t lim = kind_of_task == 1 ? (uint32_t)W : 0x7fffffffu;
                 auto vis = [&](int t) { return (uint32_t)(t - k) <= lim && t < N; };
-                if (kind == kAll) key_grads32<kAll>(sv, dp, Ln, Dn, 32 * i, tq, vis, sc2, scale, pp, dd);
-                else key_grads32<kSome>(sv, dp, Ln, Dn, 32 * i, tq, vis, sc2, scale, pp, dd);
+                if (kind == kAll) key_grads32<kAll>(sv, dp, Ln, Dn, crow, tq, vis, sc2, scale, pp, dd);
+                else key_grads32<kSome>(sv, dp, Ln, Dn, crow, tq, vis, sc2, scale, pp, dd);
             } else {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) pp[j] = dd[j] = 0u;
@@ -1289,10 +1315,10 @@ attn_bwd_band_kernel(const __nv_bfloat16 *__restrict__ QKVh, const __nv_bfloat16
             for (int ks = 0; ks < 2; ++ks) {
                 const uint32_t acc = (i > 0 || ks > 0) ? 1u : 0u;
                 if (kind_of_task == 0) {
-                    mma_bf16_ta(tm + 64, tm + 32 + 8 * ks, desc_mn<DH>(uC, 32 * i, ks), idesc_p, acc);  // dQ += dS K
+                    mma_bf16_ta(tm + 64, tm + 32 + 8 * ks, desc_mn<DH>(uC, crow, ks), idesc_p, acc);  // dQ += dS K
                 } else {
-                    mma_bf16_ta(tm + 64, tm + 8 * ks, desc_mn<DH>(uD, 32 * i, ks), idesc_p, acc);       // dV += P^T dO
-                    mma_bf16_ta(tm + 96, tm + 32 + 8 * ks, desc_mn<DH>(uC, 32 * i, ks), idesc_p, acc);  // dK += dS^T Q
+                    mma_bf16_ta(tm + 64, tm + 8 * ks, desc_mn<DH>(uD, crow, ks), idesc_p, acc);       // dV += P^T dO
+                    mma_bf16_ta(tm + 96, tm + 32 + 8 * ks, desc_mn<DH>(uC, crow, ks), idesc_p, acc);  // dK += dS^T Q
                 }
             }
             tc::mma_commit(&bar);
@@ -1324,23 +1350,14 @@ attn_bwd_band_kernel(const __nv_bfloat16 *__restrict__ QKVh, const __nv_bfloat16
             tmem_ld_dh<DH>(tl + 64, xv);
             tmem_ld_dh<DH>(tl + 96, xk);
             tc::tmem_wait_ld();
-            const int k = (kind_of_task == 1 ? tile : stile) * kT + r;
+            const int k = tile * kT + r;
             const bool own = kind_of_task == 1 ? (k >= S && k < N) : (k < S && k < N);
             if (!own || nsteps == 0) {
 #pragma unroll
                 for (int j = 0; j < DH; ++j) xv[j] = xk[j] = 0.f;
             }
-            if (kind_of_task == 1) {
-                put_rows<DH>(xk, b, hh, N, D, own ? k : N, 1, dQKVt, csum);
-                put_rows<DH>(xv, b, hh, N, D, own ? k : N, 2, dQKVt, csum);
-            } else if (own) {
-                float *dst = sinkacc + ((size_t)bh * S + k) * 2 * DH;
-#pragma unroll
-                for (int j = 0; j < DH; ++j) {
-                    atomicAdd(dst + j, xk[j]);
-                    atomicAdd(dst + DH + j, xv[j]);
-                }
-            }
+            put_rows<DH>(xk, b, hh, N, D, own ? k : N, 1, dQKVt, csum);
+            put_rows<DH>(xv, b, hh, N, D, own ? k : N, 2, dQKVt, csum);
         }
     }
     if (s_err && tid == 0) {  // let this thread's MMAs land before TMEM is freed
@@ -1349,8 +1366,7 @@ attn_bwd_band_kernel(const __nv_bfloat16 *__restrict__ QKVh, const __nv_bfloat16
     }
     tc::tc_fence_before();
     __syncthreads();
-    if (kind_of_task != 2)
-        for (int j = tid; j < 3 * DH; j += blockDim.x)
+    for (int j = tid; j < 3 * DH; j += blockDim.x)
             if (csum[j] != 0.f) atomicAdd(bsum + (size_t)b * 3 * D + (j / DH) * D + hh * DH + j % DH, csum[j]);
     if (warp == 0) {
         tc::tc_fence_after();
@@ -1358,30 +1374,6 @@ attn_bwd_band_kernel(const __nv_bfloat16 *__restrict__ QKVh, const __nv_bfloat16
     }
 }
 
-// The sink keys' rows: dK, dV (parts 1, 2) of keys k < S from the FP32 buffer
-// into the wide BF16 dQKVt, and their column sums into bsum.  One CTA per
-// (sample, head).
-template <int DH>
-__global__ void __launch_bounds__(128)
-attn_band_sink_rows_kernel(const float *__restrict__ sinkacc, unsigned char *__restrict__ dQKVt,
-                           float *__restrict__ bsum, int N, int D, int NH, int S)
-{
-    const int64_t bh = blockIdx.x, b = bh / NH;
-    const int hh = (int)(bh % NH), ns = min(S, N);
-    const float *src = sinkacc + (size_t)bh * S * 2 * DH;
-    for (int e = threadIdx.x; e < ns * 2 * (DH / 8); e += blockDim.x) {
-        const int k = e / (2 * (DH / 8)), c8 = e % (2 * (DH / 8));  // c8 < DH / 8: dK, else dV
-        const float *v = src + (size_t)k * 2 * DH + 8 * c8;
-        const int part = 1 + c8 / (DH / 8), col = part * D + hh * DH + 8 * (c8 % (DH / 8));
-        *reinterpret_cast<uint4 *>(dQKVt + wl_offset(b * N + k, col, 3 * D)) =
-            make_uint4(pack_bf2(v[0], v[1]), pack_bf2(v[2], v[3]), pack_bf2(v[4], v[5]), pack_bf2(v[6], v[7]));
-    }
-    for (int j = threadIdx.x; j < 2 * DH; j += blockDim.x) {
-        float sum = 0.f;
-        for (int k = 0; k < ns; ++k) sum += src[(size_t)k * 2 * DH + j];
-        atomicAdd(bsum + (size_t)b * 3 * D + (1 + j / DH) * D + hh * DH + j % DH, sum);
-    }
-}
 
 size_t tmem_smem_bytes(int DH, int N, bool bwd)
 {
@@ -1474,27 +1466,20 @@ sg_status launch_attn_fwd_band(const sg_config &c, const __nv_bfloat16 *QKVh, co
 }
 
 sg_status launch_attn_bwd_band(const sg_config &c, const __nv_bfloat16 *QKVh, const __nv_bfloat16 *O,
-                               const float *dO, const float *LSE, unsigned char *dQKVt, float *bsum,
-                               float *sinkacc, int Bc, int *err, cudaStream_t st)
+                               const float *dO, const float *LSE, unsigned char *dQKVt, float *bsum, int Bc,
+                               int *err, cudaStream_t st)
 {
     const int dh = c.d / c.n_heads, nq = (c.N + kT - 1) / kT, nst = (c.S + kT - 1) / kT;
     const size_t smem = band_bwd_smem(c);
-    SG_CUDA_TRY(cudaMemsetAsync(bsum, 0, (size_t)Bc * 3 * c.d * sizeof(float), st));
-    if (nst > 0) SG_CUDA_TRY(cudaMemsetAsync(sinkacc, 0, (size_t)Bc * c.S * 2 * c.d * sizeof(float), st));
-    auto go = [&](auto kern, auto fin) -> sg_status {
+    SG_CUDA_TRY(cudaMemsetAsync(bsum, 0, (size_t)Bc * 3 * c.d * sizeof(float), st));  // gathered by atomics
+    const int64_t nbh = (int64_t)Bc * c.n_heads;
+    auto go = [&](auto kern) -> sg_status {
         SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<(unsigned)((int64_t)Bc * c.n_heads * (2 * nq + nq * nst)), 128, smem, ::sg::counted(st)>>>(
-            QKVh, O, dO, LSE, dQKVt, bsum, sinkacc, c.N, c.d, c.n_heads, c.mask_kind, c.W, c.S, nq, nst, err);
-        SG_TRY(check_launch("attn_bwd_band_kernel"));
-        if (nst > 0) {
-            fin<<<(unsigned)((int64_t)Bc * c.n_heads), 128, 0, ::sg::counted(st)>>>(sinkacc, dQKVt, bsum, c.N, c.d,
-                                                                                   c.n_heads, c.S);
-            SG_TRY(check_launch("attn_band_sink_rows_kernel"));
-        }
-        return SG_OK;
+        kern<<<(unsigned)(nbh * (2 * nq + nst)), 128, smem, ::sg::counted(st)>>>(
+            QKVh, O, dO, LSE, dQKVt, bsum, c.N, c.d, c.n_heads, c.mask_kind, c.W, c.S, nq, nst, nbh, err);
+        return check_launch("attn_bwd_band_kernel");
     };
-    return dh == 16 ? go(attn_bwd_band_kernel<16>, attn_band_sink_rows_kernel<16>)
-                    : go(attn_bwd_band_kernel<32>, attn_band_sink_rows_kernel<32>);
+    return dh == 16 ? go(attn_bwd_band_kernel<16>) : go(attn_bwd_band_kernel<32>);
 }
 
 sg_status launch_attn_fwd_tmem(const sg_config &c, const __nv_bfloat16 *QKVh, const float *Hin,

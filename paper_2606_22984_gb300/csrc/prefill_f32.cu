@@ -1968,11 +1968,10 @@ void attn_fwd_dispatch(int dh, const float *QKV, const float *Hin, float *O, flo
 bool attn_bwd_dispatch(int dh, const float *QKV, const float *O, const float *dO,
                        const float *LSE, float *dQKV, float *Dt, int Bc, const sg_config &c,
                        cudaStream_t st, int *err, unsigned char *dQKVt = nullptr,
-                       float *bsum = nullptr, const __nv_bfloat16 *QKVh = nullptr, float *sinkacc = nullptr)
+                       float *bsum = nullptr, const __nv_bfloat16 *QKVh = nullptr)
 {
-    if (QKVh && dQKVt && (sinkacc || c.S == 0) && attn_band_supported(c)) {
-        launch_attn_bwd_band(c, QKVh, reinterpret_cast<const __nv_bfloat16 *>(O), dO, LSE, dQKVt, bsum, sinkacc, Bc,
-                             err, st);
+    if (QKVh && dQKVt && attn_band_supported(c)) {
+        launch_attn_bwd_band(c, QKVh, reinterpret_cast<const __nv_bfloat16 *>(O), dO, LSE, dQKVt, bsum, Bc, err, st);
         return true;
     }
     if (QKVh && dQKVt && attn_mma_supported(c) && attn_tmem_supported(c)) {
@@ -2102,7 +2101,6 @@ struct Work {
     // tensor-core backward scratch (wide BF16)
     unsigned char *dHt, *dF1t, *dQKVt;
     float *bsum;    // per-sample bias sums of dQKV [R / N][3 D]
-    float *sinkacc = nullptr;  // sink keys' dK, dV of the long band attention [R / N][S][2 D]
     uint8_t *tok8;  // patched models: the token class of every row
     int64_t total_floats;
 };
@@ -2151,7 +2149,6 @@ Work carve(const sg_config &c, float *base, int64_t R, bool bwd)
         w.dF1t = take_t(R, F);
         w.dQKVt = take_t(R, 3 * D);
         w.bsum = take((R / c.N + 1) * 3 * D);
-        if (attn_band_supported(c) && c.S > 0) w.sinkacc = take((R / c.N) * c.S * 2 * D);
     }
     w.Hfin = take(R * D);
     w.Hping = take(R * D);
@@ -2460,8 +2457,7 @@ sg_status launch_grad_f32(sg_model *m, const int8_t *spins, const float *coeff, 
             // attention: Hmid = Hin + O(QKV)
             if (attn_bwd_dispatch(dh, L.QKV, L.O, w.dHmid, L.LSE, w.dQKV, w.Dt, Bc, c, st,
                                   (int *)m->err, w.dQKVt, w.bsum,
-                                  qkv_bf16(c) ? reinterpret_cast<const __nv_bfloat16 *>(L.QKV) : nullptr,
-                                  w.sinkacc)) {
+                                  qkv_bf16(c) ? reinterpret_cast<const __nv_bfloat16 *>(L.QKV) : nullptr)) {
                 if (l == c.n_layers - 1) launch_zero_wide_tail(R, 3 * D, w.dQKVt, st);
                 colsum(w.bsum, 3 * D, Bc, 3 * D, grad + o.bqkv, st);
             } else {

@@ -316,14 +316,13 @@ sg_status launch_attn_bwd_tmem(const sg_config &c, const __nv_bfloat16 *QKVh, co
                                const float *dO, const float *LSE, unsigned char *dQKVt, float *bsum, int Bc,
                                int *err, cudaStream_t st);
 // Band masks on sequences too long to stage whole: per-tile tcgen05 kernels
-// (d_h 16 or 32) with the same contract; the backward also takes an FP32
-// buffer sinkacc of Bc * S * 2 d floats for the sink keys' gradients.
+// (d_h 16 or 32) with the same contract.
 bool attn_band_supported(const sg_config &c);
 sg_status launch_attn_fwd_band(const sg_config &c, const __nv_bfloat16 *QKVh, const float *Hin, __nv_bfloat16 *O,
                                float *Hmid, float *LSE, int Bc, int *err, cudaStream_t st);
 sg_status launch_attn_bwd_band(const sg_config &c, const __nv_bfloat16 *QKVh, const __nv_bfloat16 *O,
-                               const float *dO, const float *LSE, unsigned char *dQKVt, float *bsum,
-                               float *sinkacc, int Bc, int *err, cudaStream_t st);
+                               const float *dO, const float *LSE, unsigned char *dQKVt, float *bsum, int Bc,
+                               int *err, cudaStream_t st);
 sg_status launch_adam(float *w, const float *g, float *m, float *v, int64_t n, float lr,
                       float b1, float b2, float eps, int64_t step, cudaStream_t st);
 }  // namespace sg
