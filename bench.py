@@ -31,6 +31,7 @@ import numpy as np  # noqa: E402
 METRIC = "spin configs/sec sampled+scored, BF16 vs FP32 at fixed F/N error; ESS/sec"
 UNIT = "configs/s"
 FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS = 1900.0
 
 
 def parse():
@@ -99,6 +100,15 @@ def measured_peaks():
             d = json.load(f)
         return float(d["hbm_gbs"]), "measured"
     return FALLBACK_HBM_GBS, "fallback"
+
+
+def measured_bf16_peak():
+    """Dense BF16 tensor peak (TFLOP/s) for a kernel timed alone: the burst figure."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    return FALLBACK_BF16_TFLOPS, "fallback"
 
 
 class ClockSampler:
@@ -276,6 +286,41 @@ def decode_by_workload(sg, inputs, peak, names=("sk1024", "ea3d10", "ea2d64")):
         del spins, logq
         torch.cuda.empty_cache()
     return out
+
+
+def sk_energy_tensor(sg, inputs, iters=20):
+    """The dense s.J.s energy of the SK N=1024 workload (B = 8192, BF16 hi/lo
+    split of J on tcgen05) through the public sg_energy call: CUDA events
+    around `iters` calls, each the spin conversion and the tensor-core
+    product.  The product runs 4 B N^2 flops on the tensor cores (J_hi and
+    J_lo); the energy itself needs 2 B N^2."""
+    import torch
+
+    wl = inputs.workloads()["sk1024"]
+    N, B = wl.model.N, wl.B
+    gi = sg.Instance(wl.instance())
+    gen = torch.Generator(device="cpu").manual_seed(7)
+    spins = (2 * torch.randint(0, 2, (B, N), generator=gen, dtype=torch.int8) - 1).cuda()
+    E = torch.empty(B, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        gi.energy(spins, E=E, precision=sg.SG_BF16, stream=stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(iters):
+        gi.energy(spins, E=E, precision=sg.SG_BF16, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / iters
+    peak, kind = measured_bf16_peak()
+    mma = 4.0 * B * N * N
+    return {"workload": wl.name, "B": B, "N": N, "us_per_call": us,
+            "configs_per_s": B / (us / 1e6), "mma_flops": mma,
+            "achieved_tflops": mma / (us / 1e6) / 1e12, "peak_tflops": peak, "peak_kind": kind,
+            "frac": mma / (us / 1e6) / 1e12 / peak, "frac_one_product": 0.5 * mma / (us / 1e6) / 1e12 / peak,
+            "timed": "sg_energy calls (spin conversion + tensor-core product), CUDA events"}
 
 
 def fixed_fn_check(sg, inputs, train):
@@ -487,6 +532,7 @@ def run_ours(args):
         # the other full-size workloads' decodes, and the accuracy the metric
         # is quoted at (BF16 and FP32 both within 1e-3 of the exact F/N)
         line["decode_by_workload"] = decode_by_workload(sg, inputs, peak)
+        line["sk_energy_tensor"] = sk_energy_tensor(sg, inputs)
         line["fixed_FN_check"] = fixed_fn_check(sg, inputs, train)
         # an independence sampler's ESS/sec is at most its proposal rate, which
         # the decode's HBM roofline bounds; the measured ESS/sec of both chains

@@ -7,9 +7,15 @@
 // TMEM accumulator, so the product carries about 16 mantissa bits of J.  The
 // epilogue forms the row dot with the spins and adds -1/2 of it to E_b.
 //
-// One CTA per (128-sample block, 256-column block of Y): warp 0 streams the S
-// tile and the J_hi / J_lo tiles of each 64-wide K chunk through two
-// shared-memory stages, warp 1 issues the MMAs, warps 2-5 run the epilogue.
+// Persistent over the SMs.  A work unit is one 64-wide K chunk of one tile
+// (128 samples x 256 columns of Y): unit u = tile * KC + kc with tile =
+// rb * CB + cb.  CTA i of G takes the units [U i / G, U (i + 1) / G), so every
+// SM does the same number of MMAs whatever the tile count; a tile split
+// between two CTAs is summed by both into E_b (the energy is linear in Y).
+// Warp 0 streams the S tile and the J_hi / J_lo tiles of each unit through two
+// shared-memory stages, warp 1 issues the MMAs into one of two TMEM
+// accumulators (alternating per tile segment), and warps 2-5 run the
+// epilogue of one segment while the MMAs of the next run.
 #include <cuda_bf16.h>
 
 #include "gemm_tc.cuh"
@@ -25,7 +31,9 @@ struct SkArgs {
     const unsigned char *Jlo;  // T(N, N)
     int NRB;                   // row blocks of J
     int KC;                    // K chunks (N / 64)
+    int CB;                    // column blocks of Y (N / 256)
     int N;
+    int64_t U;                 // work units: RB * CB * KC
     const int8_t *spins;
     int64_t B;
     float *E;
@@ -35,24 +43,30 @@ struct SkArgs {
 constexpr int kSkStages = 2;
 constexpr uint32_t kSkStage = 5 * 16384;  // S tile + 2 J_hi tiles + 2 J_lo tiles
 
+// VEC: the spin rows are 16-byte aligned (spins pointer aligned, N a multiple
+// of 256), so the epilogue fetches a row's 256 spins as 16 vector loads.
+template <bool VEC>
 __global__ void __launch_bounds__(192, 1) sk_energy_tc_kernel(const __grid_constant__ SkArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint64_t full[kSkStages], empty[kSkStages], tfull;
+    __shared__ uint64_t full[kSkStages], empty[kSkStages], acc_full[2], acc_empty[2], done;
     __shared__ uint32_t tslot;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t rb = blockIdx.x / (a.N / 256);
-    const int cb = (int)(blockIdx.x % (a.N / 256));
+    const int64_t u0 = a.U * blockIdx.x / gridDim.x, u1 = a.U * (blockIdx.x + 1) / gridDim.x;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kSkStages; ++s) {
             tc::mbar_init(&full[s], 1);
             tc::mbar_init(&empty[s], 1);
         }
-        tc::mbar_init(&tfull, 1);
+        for (int x = 0; x < 2; ++x) {
+            tc::mbar_init(&acc_full[x], 1);
+            tc::mbar_init(&acc_empty[x], 128);
+        }
+        tc::mbar_init(&done, 1);
         tc::fence_mbar_init();
     }
     if (warp == 1) {
-        tc::tmem_alloc(&tslot, 256);
+        tc::tmem_alloc(&tslot, 512);
         tc::tmem_relinquish();
     }
     tc::tc_fence_before();
@@ -60,10 +74,17 @@ __global__ void __launch_bounds__(192, 1) sk_energy_tc_kernel(const __grid_const
     tc::tc_fence_after();
     const uint32_t tmem = tslot;
     if (warp == 0 && lane == 0) {
-        for (int kc = 0; kc < a.KC; ++kc) {
-            const int s = kc % kSkStages;
-            if (kc >= kSkStages &&
-                !tc::mbar_wait(&empty[s], (uint32_t)((kc / kSkStages - 1) & 1))) {
+        // Chunk j of this CTA uses stage j % 2; its refill waits for the MMAs
+        // of chunk j - 2 (completion (j - 2) / 2 of that stage's empty
+        // barrier).  (rb, cb, kc) of unit u are stepped without divisions: a
+        // refill is issued right after a stage frees, so its address math is
+        // on the critical path.
+        int64_t rb = (u0 / a.KC) / a.CB;
+        int cb = (int)((u0 / a.KC) % a.CB), kc = (int)(u0 % a.KC);
+        int64_t j = 0;
+        for (int64_t u = u0; u < u1; ++u, ++j) {
+            const int s = (int)(j & 1);
+            if (j >= kSkStages && !tc::mbar_wait(&empty[s], (uint32_t)(((j >> 1) - 1) & 1))) {
                 atomicExch(a.err, 31);
                 break;
             }
@@ -73,78 +94,168 @@ __global__ void __launch_bounds__(192, 1) sk_energy_tc_kernel(const __grid_const
             const size_t jt = (size_t)(kc * a.NRB + 2 * cb) << 14;  // two adjacent row blocks
             tc::bulk_g2s(dst + 16384, a.Jhi + jt, 32768, &full[s]);
             tc::bulk_g2s(dst + 49152, a.Jlo + jt, 32768, &full[s]);
+            if (++kc == a.KC) {
+                kc = 0;
+                if (++cb == a.CB) {
+                    cb = 0;
+                    ++rb;
+                }
+            }
+        }
+        // no copy may still be landing when the CTA exits (after a time-out):
+        // wait for the last fill of each stage
+        for (int s = 0; s < kSkStages; ++s) {
+            const int64_t last = (j - 1 - s) >= 0 ? ((j - 1 - s) & ~(int64_t)1) + s : -1;
+            if (last >= 0) tc::mbar_wait(&full[s], (uint32_t)((last >> 1) & 1), 1u << 22);
         }
     } else if (warp == 1 && lane == 0) {
         const uint32_t idesc = tc::idesc_bf16(128, 256);
         bool ok = true;
-        for (int kc = 0; kc < a.KC; ++kc) {
-            const int s = kc % kSkStages;
-            if (!tc::mbar_wait(&full[s], (uint32_t)((kc / kSkStages) & 1))) {
+        int64_t j = 0;
+        int seg = 0;
+        int kc0 = (int)(u0 % a.KC);  // K chunk of the segment's first unit
+        for (int64_t u = u0; u < u1; ++seg, kc0 = 0) {
+            const int64_t uend = min(u1, u + (a.KC - kc0));  // this tile's units
+            const int acc = seg & 1;
+            // the accumulator's previous segment (seg - 2) has been read out
+            if (seg >= 2 && !tc::mbar_wait(&acc_empty[acc], (uint32_t)(((seg >> 1) + 1) & 1))) {
                 ok = false;
                 break;
             }
             tc::tc_fence_after();
-            const uint32_t sa = tc::smem_u32(smem + (size_t)s * kSkStage);
+            const uint32_t d = tmem + 256 * acc;
+            for (bool first = true; u < uend; ++u, ++j, first = false) {
+                const int s = (int)(j & 1);
+                if (!tc::mbar_wait(&full[s], (uint32_t)((j >> 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                tc::tc_fence_after();
+                const uint32_t sa = tc::smem_u32(smem + (size_t)s * kSkStage);
 #pragma unroll
-            for (int ks = 0; ks < 4; ++ks) {
-                const uint64_t ad = tc::smem_desc(sa + 256 * ks, 128, 1024);
-                tc::mma_bf16(tmem, ad, tc::smem_desc(sa + 16384 + 256 * ks, 128, 1024), idesc,
-                             (kc | ks) != 0 ? 1u : 0u);
-                tc::mma_bf16(tmem, ad, tc::smem_desc(sa + 49152 + 256 * ks, 128, 1024), idesc, 1u);
+                for (int ks = 0; ks < 4; ++ks) {
+                    const uint64_t ad = tc::smem_desc(sa + 256 * ks, 128, 1024);
+                    tc::mma_bf16(d, ad, tc::smem_desc(sa + 16384 + 256 * ks, 128, 1024), idesc,
+                                 (first && ks == 0) ? 0u : 1u);
+                    tc::mma_bf16(d, ad, tc::smem_desc(sa + 49152 + 256 * ks, 128, 1024), idesc, 1u);
+                }
+                tc::mma_commit(&empty[s]);
             }
-            tc::mma_commit(&empty[s]);
+            if (!ok) break;
+            tc::mma_commit(&acc_full[acc]);
         }
         if (!ok) atomicExch(a.err, 32);
-        tc::mma_commit(&tfull);
+        // every MMA of this thread has completed before TMEM is freed
+        tc::mma_commit(&done);
+        tc::mbar_wait(&done, 0, 1u << 22);
     } else if (warp >= 2) {
         const int q = warp & 3;
-        const int64_t b = rb * 128 + 32 * q + lane;
-        if (tc::mbar_wait(&tfull, 0)) {
+        int seg = 0;
+        int64_t tile = u0 / a.KC, rb = tile / a.CB;
+        int cb = (int)(tile % a.CB);
+        for (int64_t u = u0; u < u1; ++seg) {
+            u = min(u1, (tile + 1) * a.KC);
+            const int64_t b = rb * 128 + 32 * q + lane;
+            // The row's 256 spins of this column block, fetched while the
+            // MMAs run.  A warp's load touches 32 rows, so byte loads would
+            // cost 32 L1 wavefronts per spin; 16-byte loads cost 16 per row.
+            uint4 sv[16];
+            if constexpr (VEC) {
+                const uint4 *src =
+                    reinterpret_cast<const uint4 *>(a.spins + (b < a.B ? b : 0) * a.N + 256 * cb);
+#pragma unroll
+                for (int x = 0; x < 16; ++x) sv[x] = __ldg(src + x);
+            }
+            const int acc = seg & 1;
+            if (!tc::mbar_wait(&acc_full[acc], (uint32_t)((seg >> 1) & 1))) {
+                if (lane == 0) atomicExch(a.err, 33);
+                break;
+            }
             tc::tc_fence_after();
             float part = 0.f;
+#pragma unroll
             for (int c = 0; c < 8; ++c) {
                 float v[32];
-                tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + 32 * c, v);
+                tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + 256 * acc + 32 * c, v);
                 tc::tmem_wait_ld();
-                if (b < a.B) {
+                if constexpr (VEC) {
+                    const uint32_t w[8] = {sv[2 * c].x,     sv[2 * c].y,     sv[2 * c].z,     sv[2 * c].w,
+                                           sv[2 * c + 1].x, sv[2 * c + 1].y, sv[2 * c + 1].z, sv[2 * c + 1].w};
+#pragma unroll
+                    for (int x = 0; x < 32; ++x)
+                        part += (float)(int8_t)(w[x >> 2] >> (8 * (x & 3))) * v[x];
+                } else if (b < a.B) {
                     const int8_t *sp = a.spins + b * a.N + 256 * cb + 32 * c;
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) part += (float)sp[j] * v[j];
+                    for (int x = 0; x < 32; ++x) part += (float)sp[x] * v[x];
                 }
             }
+            tc::tc_fence_before();
+            tc::mbar_arrive(&acc_empty[acc]);
             if (b < a.B) atomicAdd(a.E + b, -0.5f * part);
-        } else if (lane == 0) {
-            atomicExch(a.err, 33);
+            ++tile;
+            if (++cb == a.CB) {
+                cb = 0;
+                ++rb;
+            }
         }
     }
     tc::tc_fence_before();
     __syncthreads();
-    if (warp == 1) tc::tmem_dealloc(tmem, 256);
+    if (warp == 1) tc::tmem_dealloc(tmem, 512);
 }
 
-// spins int8 [B][N] -> T(B, N) BF16 (+-1; zero padding)
+// spins int8 [B][N] -> T(B, N) BF16 (+-1; zero padding), and E[b] = 0 for
+// the energy kernel's sums.  Thread (r, kc) converts row r's 64 spins of K
+// chunk kc; rows run fastest, so the 8 threads of an 8-row group fill a
+// core-matrix column's 128 contiguous bytes with each store.  VEC: 16-byte
+// aligned rows (read as 4 vector loads).
+template <bool VEC>
 __global__ void spins_to_tiled_kernel(const int8_t *__restrict__ spins, int64_t B, int N,
-                                      unsigned char *__restrict__ dst)
+                                      unsigned char *__restrict__ dst, float *__restrict__ E)
 {
-    const int64_t RB = tl_blocks(B);
-    const int groups = ((N + 63) >> 6) * 8;
+    const int64_t RB = tl_blocks(B), rows = RB * 128;
+    const int KC = (N + 63) >> 6;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= RB * 128 * groups) return;
-    const int64_t r = i / groups;
-    const int kg = (int)(i % groups);
-    uint32_t w[4];
+    if (i >= rows * KC) return;
+    const int64_t r = i % rows;
+    const int kc = (int)(i / rows);
+    if (kc == 0 && r < B) E[r] = 0.f;
+    uint32_t w[16];  // the 64 spins, 4 per word
+    if (VEC && r < B && 64 * kc + 64 <= N) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(spins + r * N + 64 * kc);
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
-        float v[2];
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const int k = kg * 8 + 2 * p + e;
-            v[e] = (r < B && k < N) ? (float)spins[r * N + k] : 0.f;
+        for (int x = 0; x < 4; ++x) {
+            const uint4 v = __ldg(src + x);
+            w[4 * x] = v.x;
+            w[4 * x + 1] = v.y;
+            w[4 * x + 2] = v.z;
+            w[4 * x + 3] = v.w;
         }
-        const __nv_bfloat162 h = __floats2bfloat162_rn(v[0], v[1]);
-        w[p] = *reinterpret_cast<const uint32_t *>(&h);
+    } else {
+#pragma unroll
+        for (int x = 0; x < 16; ++x) {
+            uint32_t u = 0;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int k = 64 * kc + 4 * x + e;
+                if (r < B && k < N) u |= (uint32_t)(uint8_t)spins[r * N + k] << (8 * e);
+            }
+            w[x] = u;
+        }
     }
-    *reinterpret_cast<uint4 *>(dst + tl_offset(r, kg * 8, RB)) = make_uint4(w[0], w[1], w[2], w[3]);
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+        uint32_t h[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const uint32_t u = w[2 * g + (p >> 1)] >> (16 * (p & 1));
+            const __nv_bfloat162 v =
+                __floats2bfloat162_rn((float)(int8_t)(u & 0xff), (float)(int8_t)((u >> 8) & 0xff));
+            h[p] = *reinterpret_cast<const uint32_t *>(&v);
+        }
+        *reinterpret_cast<uint4 *>(dst + tl_offset(r, 64 * kc + 8 * g, RB)) = make_uint4(h[0], h[1], h[2], h[3]);
+    }
 }
 
 // J [N][N] fp32 -> T(N, N) of bf16(J) and of bf16(J - bf16(J))
@@ -204,9 +315,13 @@ sg_status launch_energy_sk_tc(const sg_instance *inst, const int8_t *spins, int6
     const size_t sbytes = tl_bytes(B, N);
     SG_TRY(ensure_buffer(ws, ws_bytes, sbytes));
     unsigned char *S = (unsigned char *)*ws;
-    const int64_t n = tl_blocks(B) * 128 * (((N + 63) >> 6) * 8);
-    spins_to_tiled_kernel<<<(unsigned)((n + 255) / 256), 256, 0, ::sg::counted(st)>>>(spins, B, N, S);
-    SG_CUDA_TRY(cudaMemsetAsync(E, 0, (size_t)B * sizeof(float), st));
+    const bool vec = (uintptr_t)spins % 16 == 0;  // N is a multiple of 256
+    const int64_t n = tl_blocks(B) * 128 * ((N + 63) >> 6);
+    if (vec)
+        spins_to_tiled_kernel<true><<<(unsigned)((n + 255) / 256), 256, 0, ::sg::counted(st)>>>(spins, B, N, S, E);
+    else
+        spins_to_tiled_kernel<false><<<(unsigned)((n + 255) / 256), 256, 0, ::sg::counted(st)>>>(spins, B, N, S, E);
+    SG_TRY(check_launch("spins_to_tiled_kernel"));
     SkArgs a{};
     a.S = S;
     a.RB = tl_blocks(B);
@@ -214,16 +329,25 @@ sg_status launch_energy_sk_tc(const sg_instance *inst, const int8_t *spins, int6
     a.Jlo = a.Jhi + tl_bytes(N, N);
     a.NRB = (int)tl_blocks(N);
     a.KC = N / 64;
+    a.CB = N / 256;
     a.N = N;
+    a.U = a.RB * a.CB * a.KC;
     a.spins = spins;
     a.B = B;
     a.E = E;
     a.err = err;
     const size_t smem = (size_t)kSkStages * kSkStage;
-    SG_CUDA_TRY(cudaFuncSetAttribute(sk_energy_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
-    sk_energy_tc_kernel<<<(unsigned)(a.RB * (N / 256)), 192, smem, ::sg::counted(st)>>>(a);
-    return check_launch("sk_energy_tc_kernel");
+    // one CTA per SM (the stages take 160 KB), never more CTAs than units
+    int dev = 0, sms = 0;
+    SG_CUDA_TRY(cudaGetDevice(&dev));
+    SG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const unsigned grid = (unsigned)std::min<int64_t>(sms, a.U);
+    auto go = [&](auto kern) -> sg_status {
+        SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<grid, 192, smem, ::sg::counted(st)>>>(a);
+        return check_launch("sk_energy_tc_kernel");
+    };
+    return vec ? go(sk_energy_tc_kernel<true>) : go(sk_energy_tc_kernel<false>);
 }
 
 }  // namespace sg

@@ -534,13 +534,18 @@ def test_sk_energy_fp32(N, B):
     assert np.allclose(E, Eo, rtol=1e-5, atol=1e-4)
 
 
-@pytest.mark.parametrize("N,B", [(256, 1), (256, 130), (1024, 8192)])
-def test_sk_energy_bf16_tensor_cores(N, B):
-    """s.J.s on tcgen05 with J split into two BF16 terms: FP32-level accuracy."""
+@pytest.mark.parametrize("N,B,offset", [(256, 1, 0), (256, 130, 0), (256, 130, 1), (1024, 8192, 0)])
+def test_sk_energy_bf16_tensor_cores(N, B, offset):
+    """s.J.s on tcgen05 with J split into two BF16 terms: FP32-level accuracy.
+    offset 1 places the spins one byte past an aligned address (the epilogue's
+    byte-wise spin loads instead of its 16-byte loads)."""
     inst = inputs.make_sk(N, N + 1)
     s = inputs.random_spins(B, N, 5)
     gi = sg.Instance(inst)
-    ts = torch.tensor(s, device="cuda")
+    buf = torch.empty(B * N + offset, dtype=torch.int8, device="cuda")
+    ts = buf[offset:].view(B, N)
+    ts.copy_(torch.tensor(s))
+    assert ts.data_ptr() % 16 == offset
     E = _np(gi.energy(ts, precision=sg.SG_BF16))
     E32 = _np(gi.energy(ts, precision=sg.SG_FP32))
     rows = np.arange(B) if B <= 256 else np.linspace(0, B - 1, 256).astype(int)
