@@ -97,7 +97,7 @@ def lib():
         L.or_uniform.argtypes = [_U64, _U32, _U32, _U32, _U32]
         L.or_uniform.restype = _D
         L.or_sample.argtypes = [ctypes.POINTER(OrCfg), _P, _I64, _P, _U64, _U32, _D, _P, _P, _P,
-                                _P, _P, _P, _I]
+                                _P, _P, _P, _I, _P]
         L.or_logprob.argtypes = [ctypes.POINTER(OrCfg), _P, _I64, _P, _P, _P, _I]
         L.or_grad.argtypes = [ctypes.POINTER(OrCfg), _P, _I64, _P, _P, _P, _P, _I]
         L.or_energy_sk.argtypes = [_I, _P, _I64, _P, _P]
@@ -154,10 +154,12 @@ def num_threads() -> int:
 
 
 def sample(cfg: ModelCfg, weights, B, seed, stream=0, flag_band=1e-5, override_mask=None,
-           override_spins=None, n_threads=0, rows=None):
+           override_spins=None, n_threads=0, rows=None, with_cdf=False):
     """Ancestral sampling (Algorithm 2).  Returns spins, logq, pplus, flags.
     ``rows`` (optional) lists the sample index of each output row; then B is
-    its length."""
+    its length.  ``with_cdf`` (patched models) also returns cdf_lo [B][N]: the
+    cumulative probability of the classes before each drawn class, whose
+    interval is then [cdf_lo, cdf_lo + pplus)."""
     w = _f64(weights)
     N = cfg.N
     rid = None
@@ -168,12 +170,14 @@ def sample(cfg: ModelCfg, weights, B, seed, stream=0, flag_band=1e-5, override_m
     logq = np.zeros(B, np.float64)
     pplus = np.zeros((B, N), np.float64)
     flags = np.zeros((B, N), np.uint8)
+    cdf_lo = np.zeros((B, N), np.float64) if with_cdf else None
     om = None if override_mask is None else np.ascontiguousarray(override_mask, dtype=np.uint8)
     os_ = None if override_spins is None else _i8(override_spins)
     rc = lib().or_sample(ctypes.byref(cfg.c()), _ptr(w), B, _ptr(rid), seed, stream, flag_band, _ptr(om),
-                         _ptr(os_), _ptr(spins), _ptr(logq), _ptr(pplus), _ptr(flags), n_threads)
+                         _ptr(os_), _ptr(spins), _ptr(logq), _ptr(pplus), _ptr(flags), n_threads,
+                         _ptr(cdf_lo))
     assert rc == 0
-    return spins, logq, pplus, flags
+    return (spins, logq, pplus, flags, cdf_lo) if with_cdf else (spins, logq, pplus, flags)
 
 
 def logprob(cfg: ModelCfg, weights, spins, n_threads=0, with_pplus=False):

@@ -361,10 +361,14 @@ static void log_softmax(const double *z, int K, double *lp)
 /* Outputs (any may be NULL except spins/logq): spins int8 +-1 [B][N],       */
 /* logq [B], pplus [B][N], flags uint8 [B][N].  row_ids (may be NULL) gives  */
 /* the sample index b used in the counter of output row i (default i).       */
+/* cdf_lo [B][N] (may be NULL; patched models only): the cumulative          */
+/* probability of the classes before the drawn class, so that the draw's     */
+/* class interval is [cdf_lo, cdf_lo + pplus).                               */
 /* ------------------------------------------------------------------------ */
 int or_sample(const or_cfg *c, const double *weights, int64_t B, const int64_t *row_ids,
               uint64_t seed, uint32_t stream, double flag_band, const uint8_t *override_mask, const int8_t *override_spins,
-              int8_t *spins, double *logq, double *pplus, uint8_t *flags, int n_threads)
+              int8_t *spins, double *logq, double *pplus, uint8_t *flags, int n_threads,
+              double *cdf_lo)
 {
     or_model m;
     if (model_load(c, weights, &m)) return -1;
@@ -412,6 +416,11 @@ int or_sample(const or_cfg *c, const double *weights, int64_t B, const int64_t *
                     for (int j = 0; j < P; ++j)
                         spins[(size_t)b * N + patch_site(c, t, j)] = (int8_t)(((k >> j) & 1) ? 1 : -1);
                     if (pplus) pplus[bt] = exp(lp[k]);
+                    if (cdf_lo) {
+                        double below = 0.0;
+                        for (int j = 0; j < k; ++j) below += exp(lp[j]);
+                        cdf_lo[bt] = below;
+                    }
                     if (flags) flags[bt] = (uint8_t)(near < flag_band);
                     lq += lp[k];
                     tok = k;

@@ -477,6 +477,102 @@ __global__ void __launch_bounds__(kThreads, 1) decode_bf16_kernel(const __grid_c
     if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
+// Patched head (K = 2^P classes) of the BF16 decodes, for a row whose four
+// quarter threads hold its final-LayerNorm output y at dims [Q qr, Q qr + Q)
+// (w: this row's model's weight blob).  The classes go through zp, a tile idle
+// at the head, in chunks of kHeadChunk: each quarter writes its partial logits
+// over its dims ([4][128][chunk] floats) and the row's quarter-0 thread adds
+// them.  A first pass keeps the row's running maximum and sum of
+// exponentials; a second recomputes each chunk (or, with one chunk, reuses
+// it) and walks the cumulative probabilities in class order, drawing the
+// first class whose cumulative probability exceeds u.  Its log-probability is
+// added to lq and the class is the next token.  A draw within the flag band of
+// any cumulative boundary is flagged.  Only `writer` threads store spins,
+// flags and the error word.  Every thread of the CTA must call it.
+constexpr int kHeadChunk = 32;
+
+template <int Q>
+__device__ __forceinline__ void head_partials(const DecodeArgs &a, const float *w, const float (&y)[Q],
+                                              int D, int r, int qr, float *zp, int c0, int kc)
+{
+    for (int k = 0; k < kc; ++k) {
+        const float *wh = w + a.o.Wh + (size_t)(c0 + k) * D + Q * qr;
+        float zk = 0.f;
+#pragma unroll
+        for (int j = 0; j < Q; ++j) zk += y[j] * __ldg(wh + j);
+        zp[((size_t)qr * kRows + r) * kc + k] = zk;
+    }
+}
+
+template <int Q>
+__device__ __forceinline__ void patched_head(const DecodeArgs &a, const float *w, const float (&y)[Q],
+                                             int D, int r, int qr, float *zp, int64_t b, int t,
+                                             bool writer, int nfw, float &lq, int &tok)
+{
+    const int kc = min(a.K, kHeadChunk);
+    auto logit = [&](int c0, int k) {
+        float zk = __ldg(w + a.o.bh + c0 + k);
+#pragma unroll
+        for (int q4 = 0; q4 < 4; ++q4) zk += zp[((size_t)q4 * kRows + r) * kc + k];
+        return zk;
+    };
+    // pass 1: the log-sum-exp (with one chunk: the chunk's max, then its sum)
+    float mx = -INFINITY, se = 0.f;
+    for (int c0 = 0; c0 < a.K; c0 += kc) {
+        head_partials<Q>(a, w, y, D, r, qr, zp, c0, kc);
+        __syncthreads();
+        if (qr == 0) {
+            float cm = mx;
+            for (int k = 0; k < kc; ++k) cm = fmaxf(cm, logit(c0, k));
+            float sc = 0.f;
+            for (int k = 0; k < kc; ++k) sc += expf(logit(c0, k) - cm);
+            se = se * expf(mx - cm) + sc;  // the first chunk: 0 * 0 + sc
+            mx = cm;
+        }
+        if (c0 + kc < a.K) __syncthreads();  // the next chunk overwrites zp
+    }
+    const float lse = mx + logf(se);
+    // pass 2: the draw
+    const float u = qr == 0 ? philox_uniform(a.seed, (uint32_t)b, (uint32_t)t, a.sid, 0u) : 0.f;
+    float cdf = 0.f, near = INFINITY, zc = 0.f;
+    int cls = a.K - 1;
+    bool found = false;
+    for (int c0 = 0; c0 < a.K; c0 += kc) {
+        if (kc < a.K) {
+            __syncthreads();  // quarter 0 has read the previous chunk
+            head_partials<Q>(a, w, y, D, r, qr, zp, c0, kc);
+            __syncthreads();
+        }
+        if (qr == 0) {
+            for (int k = 0; k < kc; ++k) {
+                const float z = logit(c0, k);
+                if (c0 + k < a.K - 1) {
+                    cdf += expf(z - lse);
+                    near = fminf(near, fabsf(u - cdf));
+                    if (!found && u < cdf) {
+                        cls = c0 + k;
+                        zc = z;
+                        found = true;
+                    }
+                } else if (!found) {
+                    zc = z;
+                }
+            }
+        }
+    }
+    if (qr == 0) {
+        lq += zc - lse;
+        tok = cls;
+        if (writer) {
+            for (int j = 0; j < a.P; ++j)
+                a.spins[(size_t)b * a.Nspins + patch_site(t, j, a.P, a.latD, a.latL)] =
+                    (int8_t)(((cls >> j) & 1) ? 1 : -1);
+            if (a.flags && near < a.band) a.flags[(size_t)b * nfw + (t >> 5)] |= 1u << (t & 31);
+            if (!isfinite(zc - lse)) atomicOr(a.err, 4);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // d = 64 (4 heads of 16, d_ff = 256) with four threads per sample: thread
 // (row r, quarter qr) keeps h[r][16 qr .. 16 qr + 15] and serves head qr.
@@ -801,57 +897,15 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d64_kernel(const __grid_co
             const float rs = 1.0f / sqrtf(var + 1e-5f);
             if constexpr (PATCH) {
                 // patched: K logits; this quarter's partial sums over its 16
-                // dims go to the A2 tile (idle until the next step's attention)
+                // dims go through the A2 tile (idle until the next step's attention)
                 float y[DH];
 #pragma unroll
                 for (int j = 0; j < DH; ++j) {
                     const int d = DH * qr + j;
                     y[j] = (h[j] - mean) * rs * __ldg(a.w + a.o.lnfg + d) + __ldg(a.w + a.o.lnfb + d);
                 }
-                float *zp = reinterpret_cast<float *>(A2buf);  // [4][128][K]
-                for (int k = 0; k < a.K; ++k) {
-                    float zk = 0.f;
-#pragma unroll
-                    for (int j = 0; j < DH; ++j) zk += y[j] * __ldg(a.w + a.o.Wh + (size_t)k * D + DH * qr + j);
-                    zp[((size_t)qr * kRows + r) * a.K + k] = zk;
-                }
-                __syncthreads();
-                if (qr == 0) {
-                    auto logit = [&](int k) {
-                        float zk = __ldg(a.w + a.o.bh + k);
-#pragma unroll
-                        for (int q4 = 0; q4 < 4; ++q4) zk += zp[((size_t)q4 * kRows + r) * a.K + k];
-                        return zk;
-                    };
-                    float mx = -INFINITY;
-                    for (int k = 0; k < a.K; ++k) mx = fmaxf(mx, logit(k));
-                    float se = 0.f;
-                    for (int k = 0; k < a.K; ++k) se += expf(logit(k) - mx);
-                    const float lse = mx + logf(se);
-                    const float u = philox_uniform(a.seed, (uint32_t)b, (uint32_t)t, a.sid, 0u);
-                    float cdf = 0.f, near = INFINITY;
-                    int cls = a.K - 1;
-                    bool found = false;
-                    for (int k = 0; k < a.K - 1; ++k) {
-                        cdf += expf(logit(k) - lse);
-                        near = fminf(near, fabsf(u - cdf));
-                        if (!found && u < cdf) {
-                            cls = k;
-                            found = true;
-                        }
-                    }
-                    const float zc = logit(cls);
-                    lq += zc - lse;
-                    tok = cls;
-                    if (active) {
-                        for (int j = 0; j < a.P; ++j)
-                            a.spins[(size_t)b * a.Nspins + patch_site(t, j, a.P, a.latD, a.latL)] =
-                                (int8_t)(((cls >> j) & 1) ? 1 : -1);
-                        if (a.flags && near < a.band)
-                            a.flags[(size_t)b * nfw + (t >> 5)] |= 1u << (t & 31);
-                        if (!isfinite(zc - lse)) atomicOr(a.err, 4);
-                    }
-                }
+                patched_head<DH>(a, a.w, y, D, r, qr, reinterpret_cast<float *>(A2buf), b, t, active, nfw,
+                                 lq, tok);
             } else {
             float z0 = 0.f, z1 = 0.f;
 #pragma unroll
@@ -908,65 +962,6 @@ __global__ void __launch_bounds__(512, 1) decode_bf16_d64_kernel(const __grid_co
 // through a 3-stage ring of bulk copies.  TMEM: QKV at columns [0, 384), the
 // FFN1 slice at [0, 128), the FFN2 accumulator at [384, 512).
 // ---------------------------------------------------------------------------
-// Patched head (K = 2^P <= 32 classes) of the d = 128 and d = 256 decodes, for
-// a row whose four quarter threads hold its final-LayerNorm output y at dims
-// [Q qr, Q qr + Q) (w: this row's model's weight blob): each quarter's partial
-// logits over its dims go through zp ([4][128][K] floats of a tile idle at
-// the head), the row's quarter-0 thread adds them, draws the class whose
-// cumulative probability (classes in index order) first exceeds u, adds its
-// log-probability to lq and returns the class as the next token.  A draw
-// within the flag band of any cumulative boundary is flagged.  Only `writer`
-// threads store spins, flags and the error word.
-template <int Q>
-__device__ __forceinline__ void patched_head(const DecodeArgs &a, const float *w, const float (&y)[Q],
-                                             int D, int r, int qr, float *zp, int64_t b, int t,
-                                             bool writer, int nfw, float &lq, int &tok)
-{
-    for (int k = 0; k < a.K; ++k) {
-        const float *wh = w + a.o.Wh + (size_t)k * D + Q * qr;
-        float zk = 0.f;
-#pragma unroll
-        for (int j = 0; j < Q; ++j) zk += y[j] * __ldg(wh + j);
-        zp[((size_t)qr * kRows + r) * a.K + k] = zk;
-    }
-    __syncthreads();
-    if (qr == 0) {
-        auto logit = [&](int k) {
-            float zk = __ldg(w + a.o.bh + k);
-#pragma unroll
-            for (int q4 = 0; q4 < 4; ++q4) zk += zp[((size_t)q4 * kRows + r) * a.K + k];
-            return zk;
-        };
-        float mx = -INFINITY;
-        for (int k = 0; k < a.K; ++k) mx = fmaxf(mx, logit(k));
-        float se = 0.f;
-        for (int k = 0; k < a.K; ++k) se += expf(logit(k) - mx);
-        const float lse = mx + logf(se);
-        const float u = philox_uniform(a.seed, (uint32_t)b, (uint32_t)t, a.sid, 0u);
-        float cdf = 0.f, near = INFINITY;
-        int cls = a.K - 1;
-        bool found = false;
-        for (int k = 0; k < a.K - 1; ++k) {
-            cdf += expf(logit(k) - lse);
-            near = fminf(near, fabsf(u - cdf));
-            if (!found && u < cdf) {
-                cls = k;
-                found = true;
-            }
-        }
-        const float zc = logit(cls);
-        lq += zc - lse;
-        tok = cls;
-        if (writer) {
-            for (int j = 0; j < a.P; ++j)
-                a.spins[(size_t)b * a.Nspins + patch_site(t, j, a.P, a.latD, a.latL)] =
-                    (int8_t)(((cls >> j) & 1) ? 1 : -1);
-            if (a.flags && near < a.band) a.flags[(size_t)b * nfw + (t >> 5)] |= 1u << (t & 31);
-            if (!isfinite(zc - lse)) atomicOr(a.err, 4);
-        }
-    }
-}
-
 constexpr int kChunkBytes = 128 * 128 * 2;
 constexpr int kChunksPerLayer = 11;
 constexpr int kStages = 3;
@@ -2132,9 +2127,8 @@ sg_status launch_decode_bf16(sg_model *m, int64_t B, uint64_t seed, uint32_t sid
                                      "(128, 8, 512) and (256, 8, 1024)");
     if (m->n_models > 1 && !d256)
         return fail(SG_EUNSUPPORTED, "grouped models are served by the d = 256 decode");
-    if (P > 1 && !((1 << P) <= 32 && ((d64 && c.d_token <= 16) || d128 || d256)))
-        return fail(SG_EUNSUPPORTED, "patched BF16 decode is built for at most 32 classes "
-                                     "(2D cells); use SG_FP32");
+    if (P > 1 && d64 && c.d_token > 16)
+        return fail(SG_EUNSUPPORTED, "patched BF16 decode (d = 64) needs d_token <= 16; use SG_FP32");
     const int64_t rows_per_model = B / m->n_models;
     int rows = 0, cpm = 0;
     int64_t tiles = 0;

@@ -25,22 +25,33 @@ def oracle_replay(m, w, seed, gpu_spins, gpu_flags, band, rows=None, stream=0, n
     ``band`` is the GPU's flag band.  A flag only excuses a draw the oracle
     also finds close: at every GPU-flagged draw of an unpatched model, the
     oracle's own p+ (computed from the same prefix) must lie within 2 band of
-    the draw's uniform u, so a wrong GPU logit cannot hide behind its flag."""
+    the draw's uniform u, so a wrong GPU logit cannot hide behind its flag.  For
+    a patched model, u must lie within 2 band of the oracle's cumulative
+    probability interval of the class the GPU drew."""
     rows = np.arange(gpu_spins.shape[0]) if rows is None else np.asarray(rows, np.int64)
     T = m.N // max(1, getattr(m, "patch", 1))  # flags are per token position
     fl = unpack_flags(gpu_flags[rows], T)
     if T < m.N:
         fl = np.pad(fl, ((0, 0), (0, m.N - T)))
+    patched = T < m.N
     res = oracle.sample(ocfg(m), w, len(rows), seed, stream, override_mask=fl,
-                        override_spins=gpu_spins[rows], n_threads=n_threads, rows=rows)
-    if T == m.N:
-        pp = res[2]
-        for i, t in zip(*np.nonzero(fl)):
-            u = oracle.uniform(seed, int(rows[i]), int(t), stream)
+                        override_spins=gpu_spins[rows], n_threads=n_threads, rows=rows,
+                        with_cdf=patched)
+    pp = res[2]
+    for i, t in zip(*np.nonzero(fl)):
+        u = oracle.uniform(seed, int(rows[i]), int(t), stream)
+        if not patched:
             assert abs(pp[i, t] - u) < 2 * band, (
                 f"GPU flagged draw (row {rows[i]}, t {t}) but the oracle's p+ {pp[i, t]:.6g} "
                 f"is {abs(pp[i, t] - u):.3g} from u {u:.6g} (band {band})")
-    return res
+        else:
+            # the GPU's class: u inside the oracle's interval of that class,
+            # widened by 2 band
+            lo = res[4][i, t]
+            assert lo - 2 * band < u < lo + pp[i, t] + 2 * band, (
+                f"GPU flagged draw (row {rows[i]}, token {t}) took a class whose oracle "
+                f"interval [{lo:.6g}, {lo + pp[i, t]:.6g}) is more than 2 band from u {u:.6g}")
+    return res[:4]
 
 
 def grad_block_errors(m, g, go):

@@ -230,6 +230,13 @@ PATCHED_CASES = {
     "lat2d_p4_bf16_d256": (inputs.ModelShape(144, 2, 256, 8, d_token=16, mask_kind=1, W=6, S=7,
                                              patch=4, lat_D=2, lat_L=12), 200, sg.SG_BF16),
     "chain_p2_bf16_d128": (inputs.ModelShape(60, 1, 128, 8, d_token=8, patch=2), 130, sg.SG_BF16),
+    # 3D cells of (2, 2, 2) spins: 256 classes through the decodes' chunked head
+    "lat3d_p8_bf16": (inputs.ModelShape(512, 2, 64, 4, d_token=16, mask_kind=1, W=16, S=17,
+                                        patch=8, lat_D=3, lat_L=8), 200, sg.SG_BF16),
+    "lat3d_p8_bf16_d128": (inputs.ModelShape(512, 2, 128, 8, d_token=16, mask_kind=1, W=16, S=17,
+                                             patch=8, lat_D=3, lat_L=8), 200, sg.SG_BF16),
+    "lat3d_p8_bf16_d256": (inputs.ModelShape(216, 2, 256, 8, d_token=16, mask_kind=1, W=9, S=10,
+                                             patch=8, lat_D=3, lat_L=6), 130, sg.SG_BF16),
 }
 
 
@@ -260,9 +267,9 @@ def test_patched_sampling_and_scoring_match_oracle(name):
 
 
 def test_patched_bf16_rejected_where_not_built():
-    """3D cells of (2, 2, 2) spins (256 classes) are beyond the BF16 decodes'
-    K <= 32 head; the FP32 decode serves them."""
-    m = inputs.ModelShape(64, 1, 128, 8, d_token=16, patch=8, lat_D=3, lat_L=4)
+    """The d = 64 decode keeps the token columns in one quarter of a row
+    (d_token <= 16); a wider token embedding is served by the FP32 decode."""
+    m = inputs.ModelShape(64, 1, 64, 4, d_token=32, patch=8, lat_D=3, lat_L=4)
     model = sg.Model(m, inputs.make_weights(m, 1), sg.SG_BF16)
     with pytest.raises(sg.SgError):
         model.sample(8, seed=1)

@@ -661,6 +661,41 @@ def test_patched_zero_model_is_uniform():
     assert np.allclose(lq, -m.N * math.log(2), rtol=0, atol=1e-12)
 
 
+@pytest.mark.parametrize("m", PATCHED)
+def test_patched_draw_lies_in_its_class_interval(m):
+    """The inverse-CDF draw: every token's uniform u lies in the interval
+    [cdf_lo, cdf_lo + p) of the class drawn (the oracle's cdf_lo output, used
+    to check the GPU's classes at flagged draws)."""
+    w = inputs.make_weights(m, 5, scale=1.3)
+    B, T = 30, m.N // m.patch
+    _, _, pp, _, lo = oracle.sample(ocfg(m), w, B, seed=12, with_cdf=True)
+    for b in range(B):
+        for t in range(T):
+            u = oracle.uniform(12, b, t, 0)
+            assert lo[b, t] - 1e-12 <= u < lo[b, t] + pp[b, t] + 1e-12
+
+
+def test_patched_uniform_model_class_intervals():
+    """All classes equally likely (zero weights, unit LayerNorm gains): the
+    class drawn, read back from the spins through the torch patch map, is k
+    with cdf_lo = k / K and p = 1 / K."""
+    m = PATCHED[2]
+    w = inputs.make_weights(m, 1) * 0.0
+    o = inputs.offsets(m)
+    for name in o:
+        if name.endswith("_g"):
+            off, shape = o[name]
+            w[off:off + int(np.prod(shape))] = 1.0
+    K = 1 << m.patch
+    s, _, pp, _, lo = oracle.sample(ocfg(m), w, 64, seed=3, with_cdf=True)
+    sites = _torch_ref.patch_sites(m)
+    for b in range(64):
+        for t in range(sites.shape[0]):
+            k = sum(1 << j for j in range(m.patch) if s[b, sites[t, j]] > 0)
+            assert abs(lo[b, t] - k / K) < 1e-12
+            assert abs(pp[b, t] - 1 / K) < 1e-12
+
+
 def test_patch_bits_land_on_the_patch_map():
     """A head bias that is a sum over bits, everything else zero: the classes
     factorise, bit j is +1 with probability sigmoid(a_j), and every site
