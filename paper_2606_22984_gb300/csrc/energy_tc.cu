@@ -205,6 +205,18 @@ __global__ void __launch_bounds__(192, 1) sk_energy_tc_kernel(const __grid_const
     if (warp == 1) tc::tmem_dealloc(tmem, 512);
 }
 
+// BF16 of two int8 values (given as bytes lo, hi), packed lo | hi << 16, with
+// integer and FP32-add operations only: the float with bits
+// 0x4B000000 | (b ^ 0x80) is 2^23 + 128 + int8(b), so subtracting 2^23 + 128
+// leaves int8(b) exactly; every int8 has at most 8 significant bits, so its
+// BF16 is the float's upper half.
+__device__ __forceinline__ uint32_t bf16_pair_of_bytes(uint32_t lo, uint32_t hi)
+{
+    const float fl = __uint_as_float((lo ^ 0x80u) | 0x4B000000u) - 8388736.0f;
+    const float fh = __uint_as_float((hi ^ 0x80u) | 0x4B000000u) - 8388736.0f;
+    return __byte_perm(__float_as_uint(fl), __float_as_uint(fh), 0x7632);
+}
+
 // spins int8 [B][N] -> T(B, N) BF16 (+-1; zero padding), and E[b] = 0 for
 // the energy kernel's sums.  Thread (r, kc) converts row r's 64 spins of K
 // chunk kc; rows run fastest, so the 8 threads of an 8-row group fill a
@@ -250,9 +262,7 @@ __global__ void spins_to_tiled_kernel(const int8_t *__restrict__ spins, int64_t 
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
             const uint32_t u = w[2 * g + (p >> 1)] >> (16 * (p & 1));
-            const __nv_bfloat162 v =
-                __floats2bfloat162_rn((float)(int8_t)(u & 0xff), (float)(int8_t)((u >> 8) & 0xff));
-            h[p] = *reinterpret_cast<const uint32_t *>(&v);
+            h[p] = bf16_pair_of_bytes(u & 0xff, (u >> 8) & 0xff);
         }
         *reinterpret_cast<uint4 *>(dst + tl_offset(r, 64 * kc + 8 * g, RB)) = make_uint4(h[0], h[1], h[2], h[3]);
     }

@@ -128,6 +128,29 @@ def test_full_size_d128_sampled_rows(name, precision, rows):
     del model
 
 
+def test_full_size_patched_3d_rows():
+    """The 3D EA L=10 model with (2, 2, 2) cells (125 tokens of 8 spins, 256
+    classes, 6L d128 h8, band and sink over the token lattice of side 5) at
+    the benchmark's batch, B = 32768, BF16: sampled rows against the oracle
+    (each flagged draw inside the oracle's interval for the drawn class), and
+    the teacher-forced log q of the same spins."""
+    W, S = inputs.lattice_mask(3, 5)
+    m = inputs.ModelShape(1000, 6, 128, 8, d_token=16, mask_kind=1, W=W, S=S, patch=8, lat_D=3,
+                          lat_L=10)
+    w = inputs.make_weights(m, 4)
+    model = sg.Model(m, w, sg.SG_BF16)
+    spins, logq, flags = model.sample(32768, seed=77, with_flags=True)
+    model.check()
+    s, lq, fl = _np(spins), _np(logq), _np(flags)
+    assert np.all(np.isin(s, (-1, 1)))
+    rows = np.array([0, 127, 128, 32767])
+    so, lqo, _, _ = oracle_replay(m, w, 77, s, fl, BF16_BAND, rows=rows)
+    assert np.array_equal(so, s[rows])
+    assert np.abs(lqo - lq[rows]).max() <= BF16_LOGQ_TOL * m.N
+    tf = _np(model.logprob(spins[:256]))
+    assert np.abs(tf - lq[:256]).max() <= BF16_LOGQ_TOL * m.N
+    del model
+
 def test_bf16_gelu_approximation_within_its_bound():
     """The GELU of the BF16 path (erf by Abramowitz & Stegun 7.1.26, |error|
     <= 1.5e-7) against CUDA's erff / expf over [-12, 12]: within that bound
