@@ -6,7 +6,8 @@ bias, a wrong GELU constant, a flipped head sign, a wrong attention scale, a
 wrong lattice neighbour, a double-counted SK bond, wrong LayerNorm, attention,
 GELU or head backward, a wrong Metropolis field, a flipped MH ratio, a missing
 ln B in F_IS, a shifted token or position index, swapped Philox words or key
-constants, a missing half-step in the uniform, a flipped likelihood weight),
+constants, a missing half-step in the uniform, a flipped likelihood weight, a
+patched draw one class off, a class interval that includes its own class),
 builds it, and runs the pins of tests/test_oracle_pins.py against it: at
 least one pin must fail for every mistake.  The unmodified source built the
 same way must pass them all.
@@ -64,6 +65,10 @@ MUTANTS = {
     "likelihood_weight_sign": [("coeff[b] = (a * E[b] + c * logq[b] - meanL - w) / (double)B;",
                                 "coeff[b] = (a * E[b] + c * logq[b] - meanL + w) / (double)B;")],
     "fq_without_beta": [("out[0] = (double)(sumL / B / beta);", "out[0] = (double)(sumL / B);")],
+    "patched_draw_next_class": [("if (!found && u < cdf) { k = j; found = 1; }",
+                                 "if (!found && u < cdf) { k = j + 1; found = 1; }")],
+    "cdf_lo_includes_class": [("for (int j = 0; j < k; ++j) below += exp(lp[j]);",
+                               "for (int j = 0; j <= k; ++j) below += exp(lp[j]);")],
 }
 
 
