@@ -73,6 +73,11 @@ __global__ void __launch_bounds__(192, 1) sk_energy_tc_kernel(const __grid_const
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = tslot;
+    // Launched as a programmatic dependent of the spin conversion: the setup
+    // above overlaps the conversion's tail, and nothing below (S tiles, E)
+    // is touched before the conversion has completed and its writes are
+    // visible.  Without that launch attribute the wait returns at once.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if (warp == 0 && lane == 0) {
         // Chunk j of this CTA uses stage j % 2; its refill waits for the MMAs
         // of chunk j - 2 (completion (j - 2) / 2 of that stage's empty
@@ -226,6 +231,9 @@ template <bool VEC>
 __global__ void spins_to_tiled_kernel(const int8_t *__restrict__ spins, int64_t B, int N,
                                       unsigned char *__restrict__ dst, float *__restrict__ E)
 {
+    // the energy kernel may be scheduled once every block of this grid runs;
+    // it waits for this grid's completion before reading S or E
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int64_t RB = tl_blocks(B), rows = RB * 128;
     const int KC = (N + 63) >> 6;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -354,7 +362,18 @@ sg_status launch_energy_sk_tc(const sg_instance *inst, const int8_t *spins, int6
     const unsigned grid = (unsigned)std::min<int64_t>(sms, a.U);
     auto go = [&](auto kern) -> sg_status {
         SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<grid, 192, smem, ::sg::counted(st)>>>(a);
+        // may start while the conversion still runs (it waits for it first)
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(192);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = ::sg::counted(st);
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        SG_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, a));
         return check_launch("sk_energy_tc_kernel");
     };
     return vec ? go(sk_energy_tc_kernel<true>) : go(sk_energy_tc_kernel<false>);
