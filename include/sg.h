@@ -266,9 +266,15 @@ sg_status sg_instance_destroy(sg_instance *inst);
  *   E      dev float [B] out.
  *   E_int  dev int32 [B] or NULL: exact integer energies, only for EA
  *          instances whose bonds are all integers (else SG_EINVAL).
- * precision SG_BF16 on an SK instance runs the s.J.s contraction on tcgen05
- * tensor cores (J split into two BF16 terms, FP32 accumulation); SG_FP32
- * uses CUDA cores.  EA is a coalesced neighbour gather either way.
+ *   spins  dev int8 [B][N], values +-1.
+ * precision SG_BF16 on an SK instance with N a multiple of 256 runs the
+ * s.J.s contraction on tcgen05 tensor cores (J split into two BF16 terms,
+ * FP32 accumulation; other N use CUDA cores); SG_FP32 uses CUDA cores.  The
+ * tensor-core path adds the partial sums of E_b by FP32 atomics, so E is not
+ * bit-reproducible from call to call (FP32 rounding order).  Its spins are
+ * read in 16-byte pieces when the pointer is 16-byte aligned; otherwise a
+ * BF16 copy of them (2 B N bytes, in the instance's workspace) is written
+ * first.  EA is a coalesced neighbour gather either way.
  */
 sg_status sg_energy(const sg_instance *inst, const int8_t *spins, int64_t B, int32_t precision,
                     float *E, int32_t *E_int, sg_stream stream);
