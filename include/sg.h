@@ -94,9 +94,9 @@ typedef enum { SG_SK_DENSE = 0, SG_EA_LATTICE = 1 } sg_instance_kind;
  *              j at offset (j & 1, (j >> 1) & 1, ...) from the cell's even
  *              corner (x0 fastest).  Spins stay in lattice raster order.
  *              Patched models are served by the FP32 decode, the BF16
- *              decodes for K <= 32 classes (2D cells; d = 64, 128, 256,
- *              grouped d = 256 included) and the teacher-forced pass; 3D
- *              cells (K = 256) on the BF16 decodes return SG_EUNSUPPORTED.
+ *              decodes (2D and 3D cells, K up to 256; d = 64, 128, 256,
+ *              grouped d = 256 included; at d = 64 with d_token <= 16, else
+ *              SG_EUNSUPPORTED) and the teacher-forced pass.
  * Key position k holds the token of position k-1; key 0 holds the start token 0.
  */
 typedef struct {
